@@ -330,6 +330,7 @@ def test_multigrid_matches_dst_direct_solve():
 
 def test_multigrid_matches_fft_direct_solve_periodic():
     p = W.grf(32, seed=3)
+    p.rho = p.rho + 2.0            # a positive density: the mean must be removed
     h = O.spacing(p.shape, p.lo, p.hi)
     ref = fft_solve(p.rho, h)
     opts = O.Options(rkl_order=1, s_smooth=2, tau_frac=0.75)
