@@ -1,0 +1,416 @@
+#!/usr/bin/env python3
+"""Benchmark of the RKL-multigrid Poisson solver on GB300.
+
+Workload (one "step" = one complete solve through the library's public API):
+  uniform-density sphere (R = 0.25, rho = 1) centred in [-1, 1]^3 on a 256^3
+  cell-centred grid, Dirichlet faces from the analytic sphere potential,
+  4 pi G = 1; RKL2-smoothed V-cycle (s = 3, tau = tau_max, N_pre = 2,
+  N_post = 1), five levels down to 16^3, accelerated-RKL coarsest solve;
+  FP32 V-cycle inside an FP64 residual / defect-correction loop; solved to
+  relative residual 1e-8.  Each step resets the density (device copy) and
+  solves from phi = 0.
+
+Metric: solves/s (whole job; N ranks solve independent instances: weak
+scaling, no collective).  Inputs (256^3 x 8 B = 134 MB per array, working set
+about 1 GB) are larger than the 129 MB L2, and L2 is also flushed between
+steps by writing 512 MB outside the timed brackets.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+N = 256
+LEVELS = 5
+TOL = 1e-8
+SOLVER = dict(rkl_order=2, s_smooth=3, tau_frac=1.0, n_pre=2, n_post=1, coarse_tol=1e-3, coarse_max_ss=64)
+METRIC = "Poisson solves/s to rel. residual 1e-8 at 256^3"
+FALLBACK_HBM_GBS = 6800.0
+
+
+def args_():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-profile", action="store_true")
+    ap.add_argument("--no-extra", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def config(world):
+    return {"workload": f"sphere{N}", "grid": [N, N, N], "levels": LEVELS, "tol": TOL,
+            "precision": "mixed (FP32 V-cycle, FP64 residual + defect correction)",
+            "smoother": "RKL2 s=3 tau=tau_max, N_pre=2, N_post=1",
+            "coarse": "accelerated RKL1 on 16^3, coarse_tol=1e-3",
+            "boundary": "Dirichlet from analytic sphere potential",
+            "per_gpu_instances": 1, "instances_total": world,
+            "l2": "flushed between steps (512 MB write); inputs > L2",
+            "parallelism": f"replicas x{world}"}
+
+
+# ---------------------------------------------------------------------------
+# Clock sampling during the timed region
+# ---------------------------------------------------------------------------
+class Clocks:
+    FIELDS = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid):
+        self.uuid = uuid
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.out = open(self.path, "w")
+            sel = ["-i", self.uuid] if self.uuid else []
+            self.proc = subprocess.Popen(["nvidia-smi", *sel, f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.out, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self, t0=None, t1=None):
+        """Summary of the samples taken between wall-clock times t0 and t1."""
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.out.close()
+        sm, smax, reasons, power, allsm = [], [], set(), [], []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                ts = time.mktime(time.strptime(parts[0].split(".")[0], "%Y/%m/%d %H:%M:%S"))
+                ts += float("0." + parts[0].split(".")[1]) if "." in parts[0] else 0.0
+                vals = (float(parts[1]), float(parts[2]), float(parts[3]))
+            except (ValueError, IndexError):
+                continue
+            allsm.append(vals[0])
+            if t0 is not None and not (t0 - 0.15 <= ts <= t1 + 0.15):
+                continue
+            sm.append(vals[0])
+            smax.append(vals[1])
+            power.append(vals[2])
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:          # timed region shorter than the sampling period: all samples
+            sm = allsm
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(power) if power else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def hbm_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        return float(json.load(open(path))["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2306_05332_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh")):
+            h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(cls, cells):
+    """DRAM bytes per launch of kernel class `cls` from the committed ncu
+    summary, scaled by cells; None if absent or taken on other kernel sources."""
+    path = os.path.join(ROOT, "profiles", "ncu_dram_per_cell.txt")
+    if not os.path.exists(path):
+        return None
+    text = open(path).read()
+    m = re.search(r"source_sha:\s*([0-9a-f]+)", text)
+    if not m or m.group(1) != kernel_source_hash():
+        return None
+    m = re.search(rf"^{cls}\s+([0-9.eE+-]+)\s*$", text, re.M)
+    return float(m.group(1)) * cells if m else None
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (bounded sample)
+# ---------------------------------------------------------------------------
+def oracle_vcycle_seconds(p, reps=1):
+    import numpy as np
+    import oracle as O
+    opts = O.Options(**SOLVER)
+    h = O.spacing(p.shape, p.lo, p.hi)
+    f = O.source(p.rho, 1.0, p.bc)
+    phi = np.zeros(p.shape)
+    t = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        phi = O.vcycle(phi, f, h, p.bc, p.faces, LEVELS, opts)
+        O.l2norm(O.residual(phi, f, h, p.bc, p.faces))
+        t.append(time.perf_counter() - t0)
+    return statistics.median(t)
+
+
+def cpu_baseline_obj(p, cycles):
+    t = oracle_vcycle_seconds(p, 1)
+    per_solve = cycles * t
+    return {"value": 1.0 / per_solve, "unit": "solves/s", "cores": 1, "kind": "oracle",
+            "sample": f"1 V-cycle + residual norm of the numpy FP64 oracle at {N}^3 ({t:.2f} s), "
+                      f"x {cycles} cycles per solve (the count this solve needs)"}
+
+
+# ---------------------------------------------------------------------------
+# Reference arm: the oracle, timed on the host cores
+# ---------------------------------------------------------------------------
+CYCLES_PER_SOLVE_REF = 18
+
+
+def run_reference(a, world, rank):
+    if rank != 0:
+        return
+    import workloads as W
+    p = W.sphere(N)
+    for _ in range(a.warmup):
+        oracle_vcycle_seconds(p, 1)
+    ts = [oracle_vcycle_seconds(p, 1) for _ in range(a.steps)]
+    t = statistics.mean(ts) * CYCLES_PER_SOLVE_REF
+    value = 1.0 / t
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config(world),
+            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                             "sample": f"each step: 1 V-cycle + residual of the numpy FP64 oracle at {N}^3, "
+                                       f"x {CYCLES_PER_SOLVE_REF} cycles per solve"},
+            "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# Our arm
+# ---------------------------------------------------------------------------
+def run_ours(a, world, rank, local):
+    import numpy as np
+    import torch
+
+    import paper_2306_05332_gb300 as sg
+    import workloads as W
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    def max_ranks(x):
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def sum_ranks(x):
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        return float(t.item())
+
+    p = W.sphere(N)
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
+    g = sg.Grid(p.shape, p.lo, p.hi, p.bc, precision="mixed", stream=stream.cuda_stream)
+    g.set_boundary(p.faces)
+    g.set_options(**SOLVER)
+    rho_dev = torch.tensor(p.rho, device=dev)
+    flush = torch.empty(512 * 2 ** 20 // 4, dtype=torch.float32, device=dev)
+
+    def step():
+        g.set_density(rho_dev, 1.0)
+        return g.solve(tol=TOL, levels=LEVELS)
+
+    for _ in range(max(3, a.warmup)):
+        step()
+    torch.cuda.synchronize()
+    barrier()
+    uuid = None
+    try:
+        uuid = str(torch.cuda.get_device_properties(dev).uuid)
+        uuid = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
+    except Exception:
+        pass
+    clocks = Clocks(uuid)
+    clocks.start()
+    time.sleep(0.5)                   # let nvidia-smi start sampling
+    e0 = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps)]
+    e1 = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps)]
+    infos = []
+    torch.cuda.synchronize()
+    barrier()
+    wall0 = time.perf_counter()
+    epoch0 = time.time()
+    for k in range(a.steps):
+        flush.zero_()
+        e0[k].record(stream)
+        infos.append(step())
+        e1[k].record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    wall = time.perf_counter() - wall0
+    epoch1 = time.time()
+    clk = clocks.stop(epoch0, epoch1)
+    step_ms = [e0[k].elapsed_time(e1[k]) for k in range(a.steps)]
+    total_ms = max_ranks(sum(step_ms))
+    ms_per_step = total_ms / a.steps
+    value = world * 1000.0 / ms_per_step
+    cycles = infos[-1]["cycles"]
+    su = statistics.mean(i["stage_cell_updates"] for i in infos)
+    launches = int(sum(i["kernel_launches"] for i in infos) + a.steps)   # + one source kernel per step
+    launches = int(sum_ranks(launches))
+
+    # ---- end to end: host (pinned) density in, host potential out ----
+    rho_host = torch.tensor(p.rho).pin_memory()
+    phi_host = torch.empty(p.shape, dtype=torch.float64).pin_memory()
+    e2e_ms = []
+    for _ in range(max(1, min(a.steps, 5))):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        g.set_density(rho_host, 1.0)
+        info = g.solve(tol=TOL, levels=LEVELS)
+        g.potential(phi_host)
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    e2e_step = max_ranks(statistics.mean(e2e_ms))
+    n0 = N ** 3
+    e2e = {"value": world * 1000.0 / e2e_step, "unit": "solves/s",
+           "h2d_bytes_per_step": 8 * n0, "d2h_bytes_per_step": 8 * n0 + 36 * (info["cycles"] + 1),
+           "ms_per_step": e2e_step}
+
+    # ---- roofline of the dominant kernel: per-kernel CUDA events in a profiled pass ----
+    roof = None
+    kernels = None
+    if not a.no_profile:
+        g.set_profiling(True)
+        for _ in range(max(1, min(a.steps, 5))):
+            flush.zero_()
+            step()
+        torch.cuda.synchronize()
+        kernels = g.kernel_stats()
+        g.set_profiling(False)
+        tot = sum(v["ms"] for v in kernels.values())
+        dom = max(kernels, key=lambda k: kernels[k]["ms"])
+        d = kernels[dom]
+        peak, src = hbm_peak()
+        ach = d["bytes"] / (d["ms"] * 1e-3) / 1e9 if d["ms"] > 0 else 0.0
+        per_launch = d["bytes"] / max(1, d["launches"])
+        traffic = ncu_traffic(dom, 1.0) if dom in ("rkl_stage_l0", "residual_l0", "update") else None
+        if traffic is not None:
+            cells_per_launch = n0
+            traffic = traffic * cells_per_launch
+        roof = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+                "frac": ach / peak, "peak_source": f"of {src}", "traffic": traffic,
+                "algorithmic_bytes_per_launch": per_launch, "launches": d["launches"],
+                "avg_launch_us": d["ms"] * 1e3 / max(1, d["launches"]),
+                "share_of_kernel_time": d["ms"] / tot if tot > 0 else None}
+        kernels = {k: {"launches": v["launches"], "ms_per_solve": v["ms"] / max(1, min(a.steps, 5)),
+                       "GBps": (v["bytes"] / (v["ms"] * 1e-3) / 1e9) if v["ms"] > 0 else 0.0,
+                       "share": v["ms"] / tot if tot > 0 else 0.0} for k, v in kernels.items()}
+
+    extra = {}
+    if not a.no_extra:
+        # the plain FP64 GPU solve of the same problem, and an RKL1-smoothed variant
+        g64 = sg.Grid(p.shape, p.lo, p.hi, p.bc, precision="fp64", stream=stream.cuda_stream)
+        g64.set_boundary(p.faces)
+        g64.set_options(**SOLVER)
+        g64.set_density(rho_dev, 1.0)
+        g64.solve(tol=TOL, levels=LEVELS)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        i64 = g64.solve(tol=TOL, levels=LEVELS)
+        t64 = (time.perf_counter() - t0) * 1e3
+        extra["fp64_gpu_solve"] = {"solves_per_s": 1000.0 / t64, "ms": t64, "cycles": i64["cycles"]}
+        del g64
+        g.set_options(**dict(SOLVER, rkl_order=1, s_smooth=2, tau_frac=0.75))
+        step()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        i1 = step()
+        t1 = (time.perf_counter() - t0) * 1e3
+        extra["rkl1_s2_smoother"] = {"solves_per_s": 1000.0 / t1, "ms": t1, "cycles": i1["cycles"]}
+        g.set_options(**SOLVER)
+
+    cpu = None
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        cpu = cpu_baseline_obj(p, cycles)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": a.steps,
+                "warmup": a.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+                "config": config(world),
+                "cell_updates_per_s": world * su / (ms_per_step * 1e-3),
+                "cycles_per_solve": cycles, "final_rel_residual": infos[-1]["rel_residual"],
+                "wall_s_timed_region": wall,
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+                "clocks": clk, "kernels": kernels, "extra": extra}
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    a = args_()
+    world, rank, local = dist_env()
+    if a.impl == "reference":
+        run_reference(a, world, rank)
+        return
+    run_ours(a, world, rank, local)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,250 @@
+/*
+ * sg.h -- C ABI of a single-GPU (GB300, sm_103a) RKL-multigrid Poisson solver.
+ *
+ * Solves the Poisson equation  grad^2 phi = 4 pi G rho  (Sec. 2.2.1, Eq.
+ * poisson_eqaution) on a uniform cell-centred Cartesian grid, as the steady
+ * state of d phi / dt = grad^2 phi - 4 pi G rho advanced by s-stage
+ * Runge-Kutta-Legendre super-time-steps (App. A, Eqs. RKL_intermediate_source),
+ * used both as the smoother and as the coarsest-grid solver of a
+ * correction-scheme multigrid V-cycle (Sec. 2.1).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * Layout.   Every 3D array is dense C order [nz][ny][nx] (x fastest), float64,
+ *           without ghost cells.  Cell centres are lo + (i + 1/2) h, with
+ *           h_d = (hi_d - lo_d) / n_d.
+ * Faces.    Dirichlet boundary values (Sec. 2.3, Eq. solution_ghost) come as six
+ *           arrays in the order -x, +x, -y, +y, -z, +z; the x faces are
+ *           [nz][ny], the y faces [nz][nx], the z faces [ny][nx], sampled at the
+ *           centres of the boundary faces.  Unset faces are zero.
+ * Memory.   `on_device = 1`: the pointer is CUDA device memory on the grid's
+ *           device; `on_device = 0`: host memory (pageable or pinned).  Caller
+ *           buffers are borrowed for the duration of the call only.  All work is
+ *           ordered on the CUDA stream given to sg_create_grid; calls that
+ *           return data to a host pointer synchronise that stream, calls that
+ *           return data to a device pointer do not.
+ * Ownership. The grid owns every device buffer it allocates (cudaMalloc at
+ *           creation and, for the adjoint, at the first sg_backward); they are
+ *           freed by sg_destroy.
+ * Errors.   Every call returns an sg_status.  Nothing throws or exits across
+ *           the ABI.  On an error the output buffers are left untouched unless
+ *           stated otherwise, and sg_last_error() returns a message (thread
+ *           local, valid until the next call on the same thread).
+ * Threads.  A grid may be used by one host thread at a time.
+ */
+#ifndef SG_H
+#define SG_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sg_grid sg_grid;                 /* opaque solver state */
+
+typedef enum sg_status {
+    SG_OK = 0,
+    SG_ERR_ARG = 1,              /* invalid argument (sizes, levels, options) */
+    SG_ERR_CUDA = 2,             /* a CUDA runtime call failed */
+    SG_ERR_OOM = 3,              /* device allocation failed */
+    SG_ERR_NOT_CONVERGED = 4,    /* max_cycles reached above the tolerance (result kept) */
+    SG_ERR_TIMEOUT = 5,          /* a bounded device wait ran out */
+    SG_ERR_NONFINITE = 6,        /* the residual norm became NaN or Inf */
+    SG_ERR_STATE = 7             /* call out of order (e.g. potential before solve) */
+} sg_status;
+
+typedef enum sg_bc {
+    SG_BC_DIRICHLET = 0,         /* Eq. solution_ghost on level 0, Eq. error_ghost below */
+    SG_BC_PERIODIC = 1           /* Eq. periodic on every level */
+} sg_bc;
+
+typedef enum sg_precision {
+    SG_FP64 = 0,                 /* every sweep in FP64 */
+    SG_MIXED = 1                 /* FP32 V-cycle on the error equation inside an FP64
+                                    residual / defect-correction loop */
+} sg_precision;
+
+/* Solver options.  sg_default_options fills the defaults noted here. */
+typedef struct sg_options {
+    int    rkl_order;       /* smoother order, 1 or 2                              [2]  */
+    int    s_smooth;        /* stages per smoothing super-step; RKL2 needs >= 2     [3]  */
+    double tau_frac;        /* smoother tau / tau_max, in (0, 1]                    [1.0]*/
+    int    n_pre;           /* smoothing super-steps on the way down (Sec. 4.1)     [2]  */
+    int    n_post;          /* smoothing super-steps on the way up                  [1]  */
+    double coarse_tol;      /* coarsest solve: stop at this relative residual;
+                               0 runs exactly coarse_max_ss super-steps             [1e-3]*/
+    int    coarse_max_ss;   /* coarsest solve: cap on super-steps                   [64] */
+    double coarse_tau_frac; /* coarsest solve tau / tau_max; 0 = cos^2(pi / 2N)     [0]  */
+    int    max_cycles;      /* V-cycle (or single-level super-step) cap             [100]*/
+    int    single_s;        /* levels == 1: fixed s; 0 = Legendre-zero schedule     [0]  */
+    double single_tau_frac; /* levels == 1: tau / tau_max; 0 = cos^2(pi / 2N)       [0]  */
+    int    fixed_cycles;    /* > 0: run exactly this many cycles, ignore tol        [0]  */
+    int    use_graph;       /* replay each V-cycle as a captured CUDA graph         [1]  */
+    int    fused;           /* fused multi-stage super-step kernels where possible  [1]  */
+} sg_options;
+
+#define SG_MAX_HISTORY 256
+
+/* Filled by sg_solve / sg_backward when the pointer is not NULL. */
+typedef struct sg_solve_info {
+    int    status;                      /* the sg_status of the call */
+    int    cycles;                      /* V-cycles (or super-steps when levels == 1) run */
+    int    levels;                      /* multigrid levels used */
+    int    s_smooth;                    /* smoother stages used */
+    int    rkl_order;                   /* smoother order used */
+    int    precision;                   /* sg_precision used */
+    double r0;                          /* ||L 0 - f||_2 (volume-weighted L2, Sec. 4.1) */
+    double rel_residual;                /* final ||L phi - f||_2 / r0 */
+    double max_residual;                /* final max |L phi - f| */
+    double history[SG_MAX_HISTORY];     /* rel. residual before cycle m (m = 0..cycles) */
+    int    coarse_ss[SG_MAX_HISTORY];   /* coarsest-level super-steps in cycle m */
+    double elapsed_ms;                  /* device time of the solve (CUDA events) */
+    long long stage_cell_updates;       /* sum over levels of cells x RKL stages */
+    long long kernel_launches;          /* kernels launched by the solve */
+} sg_solve_info;
+
+/* Fill *opt with the defaults listed in sg_options.  Never fails for a non-NULL opt. */
+sg_status sg_default_options(sg_options* opt);
+
+/*
+ * Create a solver grid of nx x ny x nz cells on the box [lo, hi] (lo[d] < hi[d],
+ * order x, y, z) with per-axis boundary kinds bc[3] (sg_bc values) and the
+ * given precision, on CUDA stream `cuda_stream` (a cudaStream_t) of the current
+ * device.  NULL (the legacy default stream, which cannot be captured into a CUDA
+ * graph) makes the grid create and use a private blocking stream, which the
+ * legacy default stream orders implicitly.  Sizes: 2 <= n_d <= 4096,
+ * total cells <= 2^31 - 1.  Allocates all level buffers for the deepest
+ * hierarchy the level rule allows (Sec. 4.1: N / 2^(L-1) even on every axis).
+ * Errors: SG_ERR_ARG, SG_ERR_OOM, SG_ERR_CUDA; *out is set only on SG_OK.
+ */
+sg_status sg_create_grid(int nx, int ny, int nz, const double lo[3], const double hi[3],
+                         const int bc[3], int precision, void* cuda_stream, sg_grid** out);
+
+/* Replace the grid's options (copied).  SG_ERR_ARG if a field is out of range. */
+sg_status sg_set_options(sg_grid* g, const sg_options* opt);
+
+/* Read the grid's current options into *opt. */
+sg_status sg_get_options(const sg_grid* g, sg_options* opt);
+
+/*
+ * Dirichlet boundary potential on the six faces (Sec. 2.3, Eq. solution_ghost:
+ * ghost = 2 phi_face - phi_active on the finest level).  faces[f] may be NULL
+ * (that face is zero).  Faces of periodic axes are ignored.
+ */
+sg_status sg_set_boundary(sg_grid* g, const double* const faces[6], int on_device);
+
+/*
+ * Source of the solve: f = four_pi_G * rho, with rho -> rho - mean(rho) when
+ * every axis is periodic (Sec. 2.3, Eq. source_modification).  rho is
+ * [nz][ny][nx].  Resets the initial guess to zero.
+ */
+sg_status sg_set_density(sg_grid* g, const double* rho, int on_device, double four_pi_G);
+
+/* Optional warm start: initial guess for the next sg_solve (Sec. 4.1 end). */
+sg_status sg_set_potential_guess(sg_grid* g, const double* phi, int on_device);
+
+/*
+ * Solve (Sec. 2.1): repeat V-cycles until ||L phi - f||_2 / ||L 0 - f||_2 <= tol
+ * (Sec. 4.1 norm) or max_cycles.  s > 0 overrides options.s_smooth (for
+ * levels == 1: the fixed stage count; 0 = the Legendre-zero schedule of App.
+ * A.5).  levels = 0 uses the level rule; 1 <= levels <= that maximum otherwise
+ * (SG_ERR_ARG beyond it).  tol must be >= 0.  Returns SG_ERR_NOT_CONVERGED
+ * (potential kept) when max_cycles is reached above tol, SG_ERR_NONFINITE on a
+ * NaN/Inf residual.  With periodic axes on every side the potential is
+ * returned with zero mean.
+ */
+sg_status sg_solve(sg_grid* g, double tol, int s, int levels, sg_solve_info* info);
+
+/* Copy the potential of the last solve into phi_out ([nz][ny][nx]).  SG_ERR_STATE before a solve. */
+sg_status sg_potential(sg_grid* g, double* phi_out, int on_device);
+
+/*
+ * Adjoint of the solve for a loss L(phi): given dL/dphi, return
+ * dL/drho = four_pi_G * lambda with L_h lambda = dL/dphi under homogeneous
+ * boundaries (the discrete operator is symmetric, so it is its own adjoint; the
+ * Dirichlet data do not depend on rho).  Periodic: dL/dphi and the result are
+ * projected to zero mean.  Solved to relative residual `tol` with the grid's
+ * options and level count of the last solve.  Uses its own buffers: the forward
+ * potential is not disturbed.  four_pi_G is the one given to sg_set_density.
+ */
+sg_status sg_backward(sg_grid* g, const double* dL_dphi, double* dL_drho, int on_device,
+                      double tol, sg_solve_info* info);
+
+/*
+ * Solve n independent grids (each with its density, boundary and options set)
+ * to tolerance tol, with the levels of each grid's rule.  The V-cycle phases of
+ * all grids are issued together on the first grid's stream.  infos may be NULL
+ * or an array of n entries.  Returns the first non-OK status.
+ */
+sg_status sg_solve_batch(sg_grid* const* grids, int n, double tol, sg_solve_info* infos);
+
+/* Free the grid and its device buffers.  NULL is a no-op. */
+void sg_destroy(sg_grid* g);
+
+/* Message for the last error on this thread ("" if none). */
+const char* sg_last_error(void);
+
+/* Maximum number of levels the level rule allows for this grid. */
+int sg_max_levels(const sg_grid* g);
+
+/* ------------------------------------------------------------------------
+ * Optional per-kernel profile.  When enabled, every kernel the grid launches
+ * is bracketed by CUDA events on the grid's stream (this adds a few
+ * microseconds per launch, so time solves with it disabled) and the totals are
+ * kept per kernel class.  `bytes` is the algorithmic traffic of the launches:
+ * the compulsory reads and writes of their input and output arrays, each cell
+ * counted once, independent of caching.
+ * ------------------------------------------------------------------------ */
+#define SG_KERNEL_CLASSES 8
+typedef struct sg_kernel_stat {
+    char      name[24];       /* rkl_stage_l0, rkl_stage_coarse, residual_l0, residual_restrict,
+                                 prolong_correct, coarse_solve, update, reduce_misc */
+    long long launches;
+    double    ms;             /* summed event time of the launches */
+    double    bytes;          /* summed algorithmic bytes */
+} sg_kernel_stat;
+
+/* Enable (1) or disable (0) the profile and reset its totals. */
+sg_status sg_set_profiling(sg_grid* g, int on);
+
+/* Copy the SG_KERNEL_CLASSES totals into out[]. */
+sg_status sg_kernel_stats(const sg_grid* g, sg_kernel_stat* out);
+
+/* ------------------------------------------------------------------------
+ * Single operators, for verification and for callers composing their own
+ * cycles.  Pointers are device memory holding the level's [nz][ny][nx] array
+ * (level l has n_d / 2^l cells per axis) in `dtype` (0 = float64, 1 = float32).
+ * They run on the grid's stream and do not synchronise it.  `homogeneous = 1`
+ * ignores the Dirichlet faces (Eq. error_ghost); it is forced on levels > 0.
+ * ------------------------------------------------------------------------ */
+
+/* One s-stage RKL super-step of order 1 or 2 (App. A, Eq.
+ * RKL_intermediate_source) on L u = rhs at `level`, tau = tau_frac * tau_max:
+ * out = Y_s.  out must not alias u or rhs.  SG_ERR_ARG for s < 1 (RKL1) or
+ * s < 2 (RKL2). */
+sg_status sg_op_superstep(sg_grid* g, int level, int dtype, int order, int s, double tau_frac,
+                          int homogeneous, const void* u, const void* rhs, void* out);
+
+/* Residual r = rhs - L u at `level` (the negative of Eq. residual), restricted
+ * to level + 1 by the 8-cell mean (Eq. restriction_example_3D) into coarse_out
+ * when it is not NULL.  norms (host, may be NULL) receives
+ * {sum r^2 (volume-weighted L2 squared), max |r|}; passing norms synchronises
+ * the stream. */
+sg_status sg_op_residual_restrict(sg_grid* g, int level, int dtype, int homogeneous,
+                                  const void* u, const void* rhs, void* coarse_out,
+                                  double norms[2]);
+
+/* fine += P(coarse) (Eq. prolongation_example_3D) with coarse ghosts by the
+ * boundary rule; `level` is the fine level, coarse is level + 1. */
+sg_status sg_op_prolong_correct(sg_grid* g, int level, int dtype, const void* coarse, void* fine);
+
+/* Coarsest-grid style solve of L u = rhs at `level` from u = 0 by the
+ * Legendre-zero RKL1 schedule (App. A.5) with the grid's coarse options.
+ * ss_done (host, may be NULL) receives the super-steps run and synchronises. */
+sg_status sg_op_coarse_solve(sg_grid* g, int level, int dtype, const void* rhs, void* u_out,
+                             int* ss_done);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SG_H */

@@ -1,0 +1,155 @@
+// Coarsest-level solver: the whole level lives in one CTA's shared memory and
+// the accelerated RKL1 iteration of App. A.5 runs there with __syncthreads()
+// between stages, so a coarse solve of hundreds of stages is one launch.
+//
+// Stage k of super-step s (App. A, Eq. RKL_intermediate_source, first order):
+//   Y1 = Y0 + tau_unit (L Y0 - f)
+//   Yj = mu_j Y_{j-1} + nu_j Y_{j-2} + mu_j tau_unit (L Y_{j-1} - f)
+// with mu_j = (2j-1)/j, nu_j = (1-j)/j and tau_unit = w1 tau = tau_frac * 2 / lambda_max
+// (since tau_max w1 = dt_par = 2 / lambda_max).  Before every super-step the
+// relative residual is compared with `tol` (0 = run exactly max_ss super-steps).
+// Boundaries: homogeneous Dirichlet (Eq. error_ghost) or periodic.
+#include "sg_internal.cuh"
+
+namespace sg {
+
+namespace {
+
+constexpr int kCoarseThreads = 1024;
+constexpr size_t kSmemLimit = 227u * 1024u - 1024u;
+
+template <typename T>
+__device__ __forceinline__ T lap_smem(const T* u, int nx, int ny, int nz, const int* per, T ihx2,
+                                      T ihy2, T ihz2, int i, int j, int k) {
+    const int sy = nx, sz = nx * ny;
+    const int t = k * sz + j * sy + i;
+    const T c = u[t];
+    const T xm = i > 0 ? u[t - 1] : (per[0] ? u[t + nx - 1] : -c);
+    const T xp = i < nx - 1 ? u[t + 1] : (per[0] ? u[t - (nx - 1)] : -c);
+    const T ym = j > 0 ? u[t - sy] : (per[1] ? u[t + (ny - 1) * sy] : -c);
+    const T yp = j < ny - 1 ? u[t + sy] : (per[1] ? u[t - (ny - 1) * sy] : -c);
+    const T zm = k > 0 ? u[t - sz] : (per[2] ? u[t + (nz - 1) * sz] : -c);
+    const T zp = k < nz - 1 ? u[t + sz] : (per[2] ? u[t - (nz - 1) * sz] : -c);
+    const T two_c = T(2) * c;
+    return ((xm - two_c) + xp) * ihx2 + ((ym - two_c) + yp) * ihy2 + ((zm - two_c) + zp) * ihz2;
+}
+
+template <typename T>
+__device__ T block_sum(T v, T* scratch) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) scratch[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        v = lane < (int)(blockDim.x >> 5) ? scratch[lane] : T(0);
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) scratch[32] = v;
+    }
+    __syncthreads();
+    const T r = scratch[32];
+    __syncthreads();
+    return r;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kCoarseThreads) k_coarse_solve(const CoarseParams p) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ T red[33];
+    const int nx = p.g.nx, ny = p.g.ny, nz = p.g.nz;
+    const int n = nx * ny * nz;
+    T* f = reinterpret_cast<T*>(smem_raw);
+    T* buf[3] = {f + n, f + 2 * n, f + 3 * n};
+    const T* rhs = static_cast<const T*>(p.rhs);
+    const T ihx2 = T(p.g.ihx2), ihy2 = T(p.g.ihy2), ihz2 = T(p.g.ihz2);
+    int per[3] = {p.g.per[0], p.g.per[1], p.g.per[2]};
+
+    T local = T(0);
+    for (int t = threadIdx.x; t < n; t += blockDim.x) {
+        const T v = rhs[t];
+        f[t] = v;
+        buf[0][t] = T(0);
+        local += v * v;
+    }
+    __syncthreads();
+    const T r0sq = block_sum(local, red);         // ||f - L 0||^2 with homogeneous ghosts
+    const T tolsq = T(p.tol) * T(p.tol) * r0sq;
+
+    int cur = 0;
+    int done = 0;
+    for (int ss = 0; ss < p.max_ss; ++ss) {
+        if (p.tol > 0.0) {
+            T acc = T(0);
+            for (int t = threadIdx.x; t < n; t += blockDim.x) {
+                const int i = t % nx, j = (t / nx) % ny, k = t / (nx * ny);
+                const T r = f[t] - lap_smem(buf[cur], nx, ny, nz, per, ihx2, ihy2, ihz2, i, j, k);
+                acc += r * r;
+            }
+            const T rsq = block_sum(acc, red);
+            if (rsq <= tolsq) break;
+        }
+        const int s = p.sched[ss];
+        int prev = -1;
+        for (int jst = 1; jst <= s; ++jst) {
+            const int nxt = (cur + 1) % 3 == prev ? (cur + 2) % 3 : (cur + 1) % 3;
+            const T mu = T((2.0 * jst - 1.0) / jst);
+            const T nu = T((1.0 - jst) / jst);
+            const T mut = T((2.0 * jst - 1.0) / jst * p.tau_unit);
+            const T* yc = buf[cur];
+            const T* yp = prev >= 0 ? buf[prev] : buf[cur];
+            T* yn = buf[nxt];
+            for (int t = threadIdx.x; t < n; t += blockDim.x) {
+                const int i = t % nx, j = (t / nx) % ny, k = t / (nx * ny);
+                const T Lf = lap_smem(yc, nx, ny, nz, per, ihx2, ihy2, ihz2, i, j, k) - f[t];
+                if (jst == 1) yn[t] = yc[t] + T(p.tau_unit) * Lf;
+                else yn[t] = mu * yc[t] + nu * yp[t] + mut * Lf;
+            }
+            __syncthreads();
+            prev = cur;
+            cur = nxt;
+        }
+        ++done;
+    }
+    T* out = static_cast<T*>(p.u_out);
+    for (int t = threadIdx.x; t < n; t += blockDim.x) out[t] = buf[cur][t];
+    if (threadIdx.x == 0 && p.ss_done) *p.ss_done = done;
+}
+
+}  // namespace
+
+template <typename T>
+size_t coarse_smem_bytes(long long n) {
+    return (size_t)(4 * n) * sizeof(T);
+}
+
+template <typename T>
+bool coarse_fits(long long n) {
+    return coarse_smem_bytes<T>(n) <= kSmemLimit;
+}
+
+template <typename T>
+cudaError_t launch_coarse_solve(const CoarseParams& p, cudaStream_t st) {
+    const long long n = (long long)p.g.nx * p.g.ny * p.g.nz;
+    const size_t bytes = coarse_smem_bytes<T>(n);
+    if (bytes > kSmemLimit) return cudaErrorInvalidValue;
+    int threads = kCoarseThreads;
+    if (n < threads) threads = (int)((n + 31) / 32) * 32;
+    k_coarse_solve<T><<<1, threads, bytes, st>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t coarse_configure() {
+    cudaError_t e = cudaFuncSetAttribute(k_coarse_solve<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kSmemLimit);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_coarse_solve<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)kSmemLimit);
+}
+
+template size_t coarse_smem_bytes<float>(long long);
+template size_t coarse_smem_bytes<double>(long long);
+template bool coarse_fits<float>(long long);
+template bool coarse_fits<double>(long long);
+template cudaError_t launch_coarse_solve<float>(const CoarseParams&, cudaStream_t);
+template cudaError_t launch_coarse_solve<double>(const CoarseParams&, cudaStream_t);
+
+}  // namespace sg

@@ -1,0 +1,470 @@
+// Stencil kernels of the RKL-multigrid solver (sm_103a).
+//
+// All kernels read and write dense [nz][ny][nx] arrays (x fastest) and make the
+// ghost values of Sec. 2.3 on the fly, so no ghost-fill pass and no padded
+// copies exist.  Sweeps over a level stream along z ("2.5D"): a 32 x 8 thread
+// block covers an x-y tile, every thread walks a z-chunk of its column keeping
+// the z-1 / z / z+1 values in registers, so each cell of the stencil input is
+// read from HBM once per sweep (x/y neighbours hit L1/L2), coalesced along x.
+// These are HBM-bandwidth-bound kernels; no tensor cores are involved.
+#include "sg_internal.cuh"
+
+namespace sg {
+
+namespace {
+
+constexpr int BX = 32;
+constexpr int BY = 8;
+
+template <typename T> struct Acc { using type = float; };
+template <> struct Acc<double> { using type = double; };
+
+// x and y neighbours of cell (i, j, k) with the ghost rules (Sec. 2.3).
+template <typename T>
+__device__ __forceinline__ void xy_neighbours(const T* u, const LevelGeom& g, int i, int j, int k,
+                                              long long idx, T c, T& xm, T& xp, T& ym, T& yp) {
+    const long long fx = (long long)k * g.ny + j;     // x faces are [nz][ny]
+    const long long fy = (long long)k * g.nx + i;     // y faces are [nz][nx]
+    if (i > 0) xm = u[idx - 1];
+    else if (g.per[0]) xm = u[idx + (g.nx - 1)];
+    else if (g.face[0]) xm = T(2.0 * g.face[0][fx]) - c;
+    else xm = -c;
+    if (i < g.nx - 1) xp = u[idx + 1];
+    else if (g.per[0]) xp = u[idx - (g.nx - 1)];
+    else if (g.face[1]) xp = T(2.0 * g.face[1][fx]) - c;
+    else xp = -c;
+    const long long sy = g.nx;
+    if (j > 0) ym = u[idx - sy];
+    else if (g.per[1]) ym = u[idx + (long long)(g.ny - 1) * sy];
+    else if (g.face[2]) ym = T(2.0 * g.face[2][fy]) - c;
+    else ym = -c;
+    if (j < g.ny - 1) yp = u[idx + sy];
+    else if (g.per[1]) yp = u[idx - (long long)(g.ny - 1) * sy];
+    else if (g.face[3]) yp = T(2.0 * g.face[3][fy]) - c;
+    else yp = -c;
+}
+
+template <typename T>
+__device__ __forceinline__ T z_low(const T* u, const LevelGeom& g, int i, int j, long long idx,
+                                   long long plane, T c) {
+    if (g.per[2]) return u[idx + (long long)(g.nz - 1) * plane];
+    if (g.face[4]) return T(2.0 * g.face[4][(long long)j * g.nx + i]) - c;
+    return -c;
+}
+
+template <typename T>
+__device__ __forceinline__ T z_high(const T* u, const LevelGeom& g, int i, int j, long long idx,
+                                    long long plane, T c) {
+    if (g.per[2]) return u[idx - (long long)(g.nz - 1) * plane];
+    if (g.face[5]) return T(2.0 * g.face[5][(long long)j * g.nx + i]) - c;
+    return -c;
+}
+
+// Eq. discrete_laplace_3D from the six neighbours.
+template <typename T>
+__device__ __forceinline__ T lap7(T c, T xm, T xp, T ym, T yp, T zm, T zp, T ihx2, T ihy2, T ihz2) {
+    const T two_c = T(2) * c;
+    return ((xm - two_c) + xp) * ihx2 + ((ym - two_c) + yp) * ihy2 + ((zm - two_c) + zp) * ihz2;
+}
+
+// Full 7-point Laplacian of one cell with ghost values on every side.
+template <typename T>
+__device__ __forceinline__ T lap_at(const T* u, const LevelGeom& g, int i, int j, int k) {
+    const long long plane = (long long)g.nx * g.ny;
+    const long long idx = (long long)k * plane + (long long)j * g.nx + i;
+    const T c = u[idx];
+    T xm, xp, ym, yp;
+    xy_neighbours(u, g, i, j, k, idx, c, xm, xp, ym, yp);
+    const T zm = (k > 0) ? u[idx - plane] : z_low(u, g, i, j, idx, plane, c);
+    const T zp = (k < g.nz - 1) ? u[idx + plane] : z_high(u, g, i, j, idx, plane, c);
+    return lap7(c, xm, xp, ym, yp, zm, zp, T(g.ihx2), T(g.ihy2), T(g.ihz2));
+}
+
+template <typename T>
+struct CoefT {
+    T tau, mut1, mu, nu, mut_tau, c0, gt;
+};
+
+int kchunk_for(const LevelGeom& g, int bx, int by) {
+    const long long gx = (g.nx + bx - 1) / bx, gy = (g.ny + by - 1) / by;
+    const long long want = 16LL * 152;                      // 16 blocks per SM
+    long long chunks = (want + gx * gy - 1) / (gx * gy);
+    if (chunks < 1) chunks = 1;
+    if (chunks > g.nz) chunks = g.nz;
+    return (int)((g.nz + chunks - 1) / chunks);
+}
+
+// ---------------------------------------------------------------------------
+// One RKL stage over a level (App. A, Eq. RKL_intermediate_source).
+// ---------------------------------------------------------------------------
+template <typename T, int ORDER, bool FIRST>
+__global__ void __launch_bounds__(BX * BY)
+k_stage(const LevelGeom g, const CoefT<T> cf, const T* __restrict__ ym1, const T* ym2,
+        const T* y0, const T* z0, const T* __restrict__ rhs, T* out, T* z0_out, int kchunk) {
+    const int i = blockIdx.x * BX + threadIdx.x;
+    const int j = blockIdx.y * BY + threadIdx.y;
+    if (i >= g.nx || j >= g.ny) return;
+    const int k0 = blockIdx.z * kchunk;
+    const int k1 = min(k0 + kchunk, g.nz);
+    const long long plane = (long long)g.nx * g.ny;
+    long long idx = (long long)k0 * plane + (long long)j * g.nx + i;
+    const T ihx2 = T(g.ihx2), ihy2 = T(g.ihy2), ihz2 = T(g.ihz2);
+    T c = ym1[idx];
+    T zm = (k0 > 0) ? ym1[idx - plane] : z_low(ym1, g, i, j, idx, plane, c);
+    for (int k = k0; k < k1; ++k, idx += plane) {
+        const T zp = (k < g.nz - 1) ? ym1[idx + plane] : z_high(ym1, g, i, j, idx, plane, c);
+        T xm, xp, ym, yp;
+        xy_neighbours(ym1, g, i, j, k, idx, c, xm, xp, ym, yp);
+        const T Lf = lap7(c, xm, xp, ym, yp, zm, zp, ihx2, ihy2, ihz2) - rhs[idx];
+        if (FIRST) {
+            const T z = cf.tau * Lf;
+            out[idx] = c + cf.mut1 * z;
+            if (ORDER == 2) z0_out[idx] = z;
+        } else {
+            T v = cf.mu * c + cf.nu * ym2[idx] + cf.mut_tau * Lf;
+            if (ORDER == 2) v = v + cf.c0 * y0[idx] + cf.gt * z0[idx];
+            out[idx] = v;
+        }
+        zm = c;
+        c = zp;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Block reduction helpers (fixed order: deterministic).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void block_reduce_write(double sumsq, double maxabs, double sum,
+                                                   Partial* partials, int block_id) {
+    __shared__ double s_sq[32], s_mx[32], s_sum[32];
+    const int tid = threadIdx.x + threadIdx.y * blockDim.x + threadIdx.z * blockDim.x * blockDim.y;
+    const int nthreads = blockDim.x * blockDim.y * blockDim.z;
+    for (int o = 16; o > 0; o >>= 1) {
+        sumsq += __shfl_down_sync(0xffffffffu, sumsq, o);
+        maxabs = fmax(maxabs, __shfl_down_sync(0xffffffffu, maxabs, o));
+        sum += __shfl_down_sync(0xffffffffu, sum, o);
+    }
+    const int warp = tid >> 5, lane = tid & 31;
+    if (lane == 0) { s_sq[warp] = sumsq; s_mx[warp] = maxabs; s_sum[warp] = sum; }
+    __syncthreads();
+    if (warp == 0) {
+        const int nw = (nthreads + 31) >> 5;
+        sumsq = lane < nw ? s_sq[lane] : 0.0;
+        maxabs = lane < nw ? s_mx[lane] : 0.0;
+        sum = lane < nw ? s_sum[lane] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) {
+            sumsq += __shfl_down_sync(0xffffffffu, sumsq, o);
+            maxabs = fmax(maxabs, __shfl_down_sync(0xffffffffu, maxabs, o));
+            sum += __shfl_down_sync(0xffffffffu, sum, o);
+        }
+        if (lane == 0) {
+            Partial p;
+            p.sumsq = sumsq; p.maxabs = maxabs; p.sum = sum; p.pad = 0.0;
+            partials[block_id] = p;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Residual r = rhs - L u (standard sign; the paper's Eq. residual is -r).
+// ---------------------------------------------------------------------------
+template <typename TI, typename TO>
+__global__ void __launch_bounds__(BX * BY)
+k_residual(const LevelGeom g, const TI* __restrict__ u, const TI* __restrict__ rhs, TO* r_out,
+           Partial* partials, int kchunk) {
+    using A = typename Acc<TI>::type;
+    const int i = blockIdx.x * BX + threadIdx.x;
+    const int j = blockIdx.y * BY + threadIdx.y;
+    A sq = A(0), mx = A(0);
+    if (i < g.nx && j < g.ny) {
+        const int k0 = blockIdx.z * kchunk;
+        const int k1 = min(k0 + kchunk, g.nz);
+        const long long plane = (long long)g.nx * g.ny;
+        long long idx = (long long)k0 * plane + (long long)j * g.nx + i;
+        const TI ihx2 = TI(g.ihx2), ihy2 = TI(g.ihy2), ihz2 = TI(g.ihz2);
+        TI c = u[idx];
+        TI zm = (k0 > 0) ? u[idx - plane] : z_low(u, g, i, j, idx, plane, c);
+        for (int k = k0; k < k1; ++k, idx += plane) {
+            const TI zp = (k < g.nz - 1) ? u[idx + plane] : z_high(u, g, i, j, idx, plane, c);
+            TI xm, xp, ym, yp;
+            xy_neighbours(u, g, i, j, k, idx, c, xm, xp, ym, yp);
+            const TI r = rhs[idx] - lap7(c, xm, xp, ym, yp, zm, zp, ihx2, ihy2, ihz2);
+            if (r_out) r_out[idx] = TO(r);
+            const A ra = A(r);
+            sq += ra * ra;
+            mx = fmax(mx, fabs(ra));
+            zm = c;
+            c = zp;
+        }
+    }
+    const int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+    block_reduce_write(double(sq), double(mx), 0.0, partials, bid);
+}
+
+// ---------------------------------------------------------------------------
+// Residual fused with the 8-child restriction (Eq. restriction_example_3D):
+// one thread per coarse cell, coarse = (1/8) sum of its children's residuals.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_residual_restrict(const LevelGeom g, const T* __restrict__ u, const T* __restrict__ rhs,
+                    T* coarse, Partial* partials) {
+    using A = typename Acc<T>::type;
+    const int cnx = g.nx >> 1, cny = g.ny >> 1, cnz = g.nz >> 1;
+    const int I = blockIdx.x * blockDim.x + threadIdx.x;
+    const int J = blockIdx.y * blockDim.y + threadIdx.y;
+    const int K = blockIdx.z * blockDim.z + threadIdx.z;
+    A sq = A(0), mx = A(0), csum = A(0);
+    if (I < cnx && J < cny && K < cnz) {
+        const long long plane = (long long)g.nx * g.ny;
+        T acc = T(0);
+        for (int dz = 0; dz < 2; ++dz)
+            for (int dy = 0; dy < 2; ++dy)
+                for (int dx = 0; dx < 2; ++dx) {
+                    const int i = 2 * I + dx, j = 2 * J + dy, k = 2 * K + dz;
+                    const long long idx = (long long)k * plane + (long long)j * g.nx + i;
+                    const T r = rhs[idx] - lap_at(u, g, i, j, k);
+                    acc = acc + r;
+                    const A ra = A(r);
+                    sq += ra * ra;
+                    mx = fmax(mx, fabs(ra));
+                }
+        const T cval = acc * T(0.125);
+        if (coarse) coarse[(long long)K * cnx * cny + (long long)J * cnx + I] = cval;
+        csum = A(cval);
+    }
+    const int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+    block_reduce_write(double(sq), double(mx), double(csum), partials, bid);
+}
+
+// Coarse value with the level's ghost rule, for any index within one cell of
+// the box: periodic wraps; Dirichlet (error equation) reflects with a sign
+// flip per wall crossed (Eq. error_ghost applied axis by axis).
+template <typename T>
+__device__ __forceinline__ T coarse_ghost(const T* c, int nx, int ny, int nz, const int* per,
+                                          int I, int J, int K) {
+    T sign = T(1);
+    if (I < 0) { if (per[0]) I += nx; else { I = 0; sign = -sign; } }
+    else if (I >= nx) { if (per[0]) I -= nx; else { I = nx - 1; sign = -sign; } }
+    if (J < 0) { if (per[1]) J += ny; else { J = 0; sign = -sign; } }
+    else if (J >= ny) { if (per[1]) J -= ny; else { J = ny - 1; sign = -sign; } }
+    if (K < 0) { if (per[2]) K += nz; else { K = 0; sign = -sign; } }
+    else if (K >= nz) { if (per[2]) K -= nz; else { K = nz - 1; sign = -sign; } }
+    return sign * c[((long long)K * ny + J) * nx + I];
+}
+
+// ---------------------------------------------------------------------------
+// Prolongation + correction (Eq. prolongation_example_3D): every fine cell
+// takes (27 A + 9 (B + D + E) + 3 (C + F + H) + G) / 64 from its parent A and
+// the parent's neighbours on the fine cell's side, and adds it to fine_u.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(BX * BY)
+k_prolong_correct(const LevelGeom g, const T* __restrict__ coarse, T* fine_u) {
+    const int i = blockIdx.x * BX + threadIdx.x;
+    const int j = blockIdx.y * BY + threadIdx.y;
+    const int k = blockIdx.z;
+    if (i >= g.nx || j >= g.ny) return;
+    const int cnx = g.nx >> 1, cny = g.ny >> 1, cnz = g.nz >> 1;
+    const int I = i >> 1, J = j >> 1, K = k >> 1;
+    const int sx = (i & 1) ? 1 : -1, sy = (j & 1) ? 1 : -1, sz = (k & 1) ? 1 : -1;
+    T acc = T(0);
+    for (int az = 0; az < 2; ++az)
+        for (int ay = 0; ay < 2; ++ay)
+            for (int ax = 0; ax < 2; ++ax) {
+                const T w = T((az ? 1 : 3) * (ay ? 1 : 3) * (ax ? 1 : 3));
+                acc = acc + w * coarse_ghost(coarse, cnx, cny, cnz, g.per,
+                                             I + ax * sx, J + ay * sy, K + az * sz);
+            }
+    const long long idx = ((long long)k * g.ny + j) * g.nx + i;
+    fine_u[idx] = fine_u[idx] + acc * T(1.0 / 64.0);
+}
+
+// ---------------------------------------------------------------------------
+// Small helpers.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kRedThreads) k_finalize(const Partial* __restrict__ p, int n,
+                                                          Reduced* out) {
+    __shared__ double s_sq[kRedThreads], s_mx[kRedThreads], s_sum[kRedThreads];
+    double sq = 0.0, mx = 0.0, sm = 0.0;
+    for (int t = threadIdx.x; t < n; t += kRedThreads) {
+        sq += p[t].sumsq;
+        mx = fmax(mx, p[t].maxabs);
+        sm += p[t].sum;
+    }
+    s_sq[threadIdx.x] = sq; s_mx[threadIdx.x] = mx; s_sum[threadIdx.x] = sm;
+    __syncthreads();
+    for (int w = kRedThreads / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) {
+            s_sq[threadIdx.x] += s_sq[threadIdx.x + w];
+            s_mx[threadIdx.x] = fmax(s_mx[threadIdx.x], s_mx[threadIdx.x + w]);
+            s_sum[threadIdx.x] += s_sum[threadIdx.x + w];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        out->sumsq = s_sq[0];
+        out->maxabs = s_mx[0];
+        out->sum = s_sum[0];
+        out->count = double(n);
+    }
+}
+
+template <typename T>
+__global__ void k_subtract_mean(T* x, long long n, const Reduced* red) {
+    const T mean = T(red->sum / double(n));
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
+         t += (long long)gridDim.x * blockDim.x)
+        x[t] = x[t] - mean;
+}
+
+__global__ void k_scale_copy(const double* src, double* dst, double scale, long long n) {
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
+         t += (long long)gridDim.x * blockDim.x)
+        dst[t] = scale * src[t];
+}
+
+__global__ void k_add_f32_to_f64(double* phi, const float* __restrict__ e, long long n) {
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
+         t += (long long)gridDim.x * blockDim.x)
+        phi[t] = phi[t] + double(e[t]);
+}
+
+__global__ void __launch_bounds__(256) k_sum_f64(const double* __restrict__ x, long long n,
+                                                 Partial* partials) {
+    double s = 0.0;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
+         t += (long long)gridDim.x * blockDim.x)
+        s += x[t];
+    block_reduce_write(0.0, 0.0, s, partials, blockIdx.x);
+}
+
+int grid1d(long long n) {
+    long long b = (n + 255) / 256;
+    if (b > kSumBlocks) b = kSumBlocks;
+    if (b < 1) b = 1;
+    return (int)b;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Launchers
+// ---------------------------------------------------------------------------
+long long residual_blocks(const LevelGeom& g) {
+    const int kc = kchunk_for(g, BX, BY);
+    return (long long)((g.nx + BX - 1) / BX) * ((g.ny + BY - 1) / BY) * ((g.nz + kc - 1) / kc);
+}
+
+long long restrict_blocks(const LevelGeom& g) {
+    const long long cnx = g.nx >> 1, cny = g.ny >> 1, cnz = g.nz >> 1;
+    return ((cnx + 31) / 32) * ((cny + 3) / 4) * ((cnz + 1) / 2);
+}
+
+template <typename T>
+cudaError_t launch_stage(const LevelGeom& g, int order, bool first, const StageCoef& c,
+                         const T* ym1, const T* ym2, const T* y0, const T* z0, const T* rhs,
+                         T* out, T* z0_out, cudaStream_t st) {
+    CoefT<T> cf;
+    cf.tau = T(c.tau); cf.mut1 = T(c.mut1); cf.mu = T(c.mu); cf.nu = T(c.nu);
+    cf.mut_tau = T(c.mut_tau); cf.c0 = T(c.c0); cf.gt = T(c.gt);
+    const int kc = kchunk_for(g, BX, BY);
+    dim3 block(BX, BY, 1);
+    dim3 grid((g.nx + BX - 1) / BX, (g.ny + BY - 1) / BY, (g.nz + kc - 1) / kc);
+    if (order == 1) {
+        if (first) k_stage<T, 1, true><<<grid, block, 0, st>>>(g, cf, ym1, ym2, y0, z0, rhs, out, z0_out, kc);
+        else k_stage<T, 1, false><<<grid, block, 0, st>>>(g, cf, ym1, ym2, y0, z0, rhs, out, z0_out, kc);
+    } else {
+        if (first) k_stage<T, 2, true><<<grid, block, 0, st>>>(g, cf, ym1, ym2, y0, z0, rhs, out, z0_out, kc);
+        else k_stage<T, 2, false><<<grid, block, 0, st>>>(g, cf, ym1, ym2, y0, z0, rhs, out, z0_out, kc);
+    }
+    return cudaGetLastError();
+}
+
+template <typename TI, typename TO>
+cudaError_t launch_residual(const LevelGeom& g, const TI* u, const TI* rhs, TO* r_out,
+                            Partial* partials, int* nblocks_out, cudaStream_t st) {
+    const int kc = kchunk_for(g, BX, BY);
+    dim3 block(BX, BY, 1);
+    dim3 grid((g.nx + BX - 1) / BX, (g.ny + BY - 1) / BY, (g.nz + kc - 1) / kc);
+    k_residual<TI, TO><<<grid, block, 0, st>>>(g, u, rhs, r_out, partials, kc);
+    if (nblocks_out) *nblocks_out = (int)(grid.x * grid.y * grid.z);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_residual_restrict(const LevelGeom& g, const T* u, const T* rhs, T* coarse_out,
+                                     Partial* partials, int* nblocks_out, cudaStream_t st) {
+    const int cnx = g.nx >> 1, cny = g.ny >> 1, cnz = g.nz >> 1;
+    dim3 block(32, 4, 2);
+    dim3 grid((cnx + 31) / 32, (cny + 3) / 4, (cnz + 1) / 2);
+    k_residual_restrict<T><<<grid, block, 0, st>>>(g, u, rhs, coarse_out, partials);
+    if (nblocks_out) *nblocks_out = (int)(grid.x * grid.y * grid.z);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_prolong_correct(const LevelGeom& g, const T* coarse, T* fine_u, cudaStream_t st) {
+    dim3 block(BX, BY, 1);
+    dim3 grid((g.nx + BX - 1) / BX, (g.ny + BY - 1) / BY, g.nz);
+    k_prolong_correct<T><<<grid, block, 0, st>>>(g, coarse, fine_u);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finalize(const Partial* partials, int n, Reduced* out, cudaStream_t st) {
+    k_finalize<<<1, kRedThreads, 0, st>>>(partials, n, out);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_subtract_mean(T* x, long long n, const Reduced* red, cudaStream_t st) {
+    k_subtract_mean<T><<<grid1d(n), 256, 0, st>>>(x, n, red);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scale_copy(const double* src, double* dst, double scale, long long n,
+                              cudaStream_t st) {
+    k_scale_copy<<<grid1d(n), 256, 0, st>>>(src, dst, scale, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_add_f32_to_f64(double* phi, const float* e, long long n, cudaStream_t st) {
+    k_add_f32_to_f64<<<grid1d(n), 256, 0, st>>>(phi, e, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sub_mean_f64(double* x, long long n, const Reduced* red, cudaStream_t st) {
+    return launch_subtract_mean<double>(x, n, red, st);
+}
+
+cudaError_t launch_sum_partials_f64(const double* x, long long n, Partial* partials,
+                                    int* nblocks_out, cudaStream_t st) {
+    const int nb = grid1d(n);
+    k_sum_f64<<<nb, 256, 0, st>>>(x, n, partials);
+    if (nblocks_out) *nblocks_out = nb;
+    return cudaGetLastError();
+}
+
+// Explicit instantiations.
+template cudaError_t launch_stage<float>(const LevelGeom&, int, bool, const StageCoef&, const float*,
+                                         const float*, const float*, const float*, const float*,
+                                         float*, float*, cudaStream_t);
+template cudaError_t launch_stage<double>(const LevelGeom&, int, bool, const StageCoef&, const double*,
+                                          const double*, const double*, const double*,
+                                          const double*, double*, double*, cudaStream_t);
+template cudaError_t launch_residual<double, double>(const LevelGeom&, const double*, const double*,
+                                                     double*, Partial*, int*, cudaStream_t);
+template cudaError_t launch_residual<double, float>(const LevelGeom&, const double*, const double*,
+                                                    float*, Partial*, int*, cudaStream_t);
+template cudaError_t launch_residual<float, float>(const LevelGeom&, const float*, const float*,
+                                                   float*, Partial*, int*, cudaStream_t);
+template cudaError_t launch_residual_restrict<float>(const LevelGeom&, const float*, const float*,
+                                                     float*, Partial*, int*, cudaStream_t);
+template cudaError_t launch_residual_restrict<double>(const LevelGeom&, const double*, const double*,
+                                                      double*, Partial*, int*, cudaStream_t);
+template cudaError_t launch_prolong_correct<float>(const LevelGeom&, const float*, float*, cudaStream_t);
+template cudaError_t launch_prolong_correct<double>(const LevelGeom&, const double*, double*,
+                                                    cudaStream_t);
+template cudaError_t launch_subtract_mean<float>(float*, long long, const Reduced*, cudaStream_t);
+template cudaError_t launch_subtract_mean<double>(double*, long long, const Reduced*, cudaStream_t);
+
+}  // namespace sg

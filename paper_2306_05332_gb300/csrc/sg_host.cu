@@ -1,0 +1,1079 @@
+// Host orchestration and C ABI (include/sg.h) of the RKL-multigrid solver.
+//
+// The grid owns per-level device buffers; a solve enqueues the V-cycle of
+// Sec. 2.1 (smooth, residual + restrict, ..., coarsest RKL solve, prolong +
+// correct, smooth) on the grid's stream, optionally captured once as a CUDA
+// graph and replayed per cycle, and reads back one residual norm per cycle.
+// In SG_MIXED the V-cycle runs in FP32 on the error equation L e = r, between
+// an FP64 residual r = f - L phi and an FP64 update phi += e (defect
+// correction); in SG_FP64 it runs in FP64 on phi directly.
+#include "sg.h"
+#include "sg_internal.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+using namespace sg;
+
+namespace {
+
+thread_local std::string g_err;
+
+sg_status fail(sg_status s, const std::string& msg) {
+    g_err = msg;
+    return s;
+}
+
+#define SG_CK(...)                                                                               \
+    do {                                                                                         \
+        cudaError_t e_ = (__VA_ARGS__);                                                          \
+        if (e_ != cudaSuccess)                                                                   \
+            return fail(e_ == cudaErrorMemoryAllocation ? SG_ERR_OOM : SG_ERR_CUDA,              \
+                        std::string(#__VA_ARGS__) + ": " + cudaGetErrorString(e_));              \
+    } while (0)
+
+#define SG_TRY(expr)                                                                             \
+    do {                                                                                         \
+        sg_status s_ = (expr);                                                                   \
+        if (s_ != SG_OK) return s_;                                                              \
+    } while (0)
+
+struct Level {
+    int nx = 0, ny = 0, nz = 0;
+    long long n = 0;
+    double h[3] = {0, 0, 0};
+    void* u = nullptr;      // owned working-precision arrays (level 0 in FP64 mode: unused)
+    void* rhs = nullptr;
+    void* z0 = nullptr;
+    void* t[3] = {nullptr, nullptr, nullptr};
+};
+
+// Stage coefficients of App. A (RKL1) and of the RKL2 member of the
+// a_s + b_s P_s family (Meyer et al. 2014's b_j), written out here for the
+// device path.
+struct Rkl {
+    int order, s;
+    double w1, tau_over_dtpar;
+    std::vector<double> mu, nu, mut, gt, c0;
+};
+
+Rkl make_rkl(int order, int s) {
+    Rkl r;
+    r.order = order;
+    r.s = s;
+    r.mu.assign(s + 1, 0.0);
+    r.nu.assign(s + 1, 0.0);
+    r.mut.assign(s + 1, 0.0);
+    r.gt.assign(s + 1, 0.0);
+    r.c0.assign(s + 1, 0.0);
+    if (order == 1) {
+        r.w1 = 2.0 / (double(s) * s + s);
+        r.tau_over_dtpar = (double(s) * s + s) / 2.0;
+        for (int j = 1; j <= s; ++j) {
+            r.mu[j] = (2.0 * j - 1.0) / j;
+            r.nu[j] = (1.0 - j) / j;
+            r.mut[j] = r.mu[j] * r.w1;
+        }
+    } else {
+        r.w1 = 4.0 / (double(s) * s + s - 2.0);
+        r.tau_over_dtpar = (double(s) * s + s - 2.0) / 4.0;
+        std::vector<double> b(s + 1), a(s + 1);
+        for (int j = 0; j <= s; ++j) {
+            b[j] = j <= 2 ? 1.0 / 3.0 : (double(j) * j + j - 2.0) / (2.0 * j * (j + 1.0));
+            a[j] = 1.0 - b[j];
+        }
+        r.mut[1] = b[1] * r.w1;
+        for (int j = 2; j <= s; ++j) {
+            r.mu[j] = (2.0 * j - 1.0) / j * b[j] / b[j - 1];
+            r.nu[j] = -(j - 1.0) / j * b[j] / b[j - 2];
+            r.mut[j] = r.mu[j] * r.w1;
+            r.gt[j] = -a[j - 1] * r.mut[j];
+            r.c0[j] = 1.0 - r.mu[j] - r.nu[j];
+        }
+    }
+    return r;
+}
+
+// Eq. sk_optimal: s_k = Round(2.4048 / pi * N / k - 1/2), halves rounded up.
+int sk_opt(int k, int N) {
+    const double p = 2.4048 / M_PI * (double(N) / double(k)) - 0.5;
+    return (int)std::floor(p + 0.5);
+}
+
+// App. A.5 schedule that skips a k whose s repeats, k = N/2 .. 1, then s_1.
+std::vector<int> accelerated_schedule(int N, int count) {
+    std::vector<int> out;
+    int k = std::max(1, N / 2);
+    int s_old = 0;
+    while ((int)out.size() < count) {
+        const int s = std::max(1, sk_opt(k, N));
+        if (!(s == s_old && k != 1)) {
+            out.push_back(s);
+            s_old = s;
+        }
+        k -= 1;
+        if (k < 1) k = 1;
+    }
+    return out;
+}
+
+double cell_tau_frac(int N) {
+    const double c = std::cos(M_PI / (2.0 * N));
+    return c * c;
+}
+
+int rule_levels(int nx, int ny, int nz) {
+    int L = 1;
+    auto ok = [](int n, int L) {
+        const long long p = 1LL << L;
+        return (n % p == 0) && ((n / p) % 2 == 0);
+    };
+    while (L < 30 && ok(nx, L) && ok(ny, L) && ok(nz, L)) ++L;
+    return L;
+}
+
+// Kernel classes for the optional per-kernel CUDA-event profile.
+enum KClass { K_STAGE0 = 0, K_STAGE_C, K_RES0, K_RESTRICT, K_PROLONG, K_COARSE, K_UPDATE, K_MISC, K_NCLASS };
+const char* const kClassName[K_NCLASS] = {"rkl_stage_l0", "rkl_stage_coarse", "residual_l0",
+                                          "residual_restrict", "prolong_correct", "coarse_solve",
+                                          "update", "reduce_misc"};
+
+struct ProfRec {
+    int cls;
+    double bytes;
+    cudaEvent_t a, b;
+};
+
+}  // namespace
+
+struct sg_grid {
+    int n[3];
+    double lo[3], hi[3];
+    int bc[3];
+    int precision;
+    cudaStream_t st;
+    cudaStream_t own_stream = nullptr;
+    int max_levels;
+    std::vector<Level> lv;
+    double* phi = nullptr;
+    double* f = nullptr;
+    double* faces[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    bool have_faces = false;
+    double* lam = nullptr;          // adjoint solution
+    double* w = nullptr;            // adjoint source
+    double* scratch64 = nullptr;    // FP64 zero field for r0 with a warm start (mixed)
+    Partial* partials = nullptr;
+    int partial_cap = 0;
+    Reduced* red = nullptr;         // device slots
+    Reduced* host_red = nullptr;    // pinned mirror
+    int* d_sched = nullptr;
+    int sched_cap = 0;
+    int* d_ss = nullptr;            // coarse super-steps done (device)
+    int* host_ss = nullptr;         // pinned mirror
+    sg_options opt;
+    double four_pi_G = 1.0;
+    bool have_density = false;
+    bool have_solution = false;
+    bool guess_set = false;
+    int last_levels = 0;
+    // graph cache
+    cudaGraphExec_t gexec = nullptr;
+    long long gkey[8] = {0};
+    long long graph_launches = 0;
+    long long launches = 0;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    // optional per-kernel profile
+    bool prof = false;
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<ProfRec> live;        // records of work enqueued outside a graph
+    std::vector<ProfRec> graph_recs;  // records captured into the cached graph
+    bool capturing = false;
+    sg_kernel_stat stats[K_NCLASS];
+};
+
+namespace {
+
+bool all_periodic(const sg_grid* g) {
+    return g->bc[0] == SG_BC_PERIODIC && g->bc[1] == SG_BC_PERIODIC && g->bc[2] == SG_BC_PERIODIC;
+}
+
+LevelGeom geom(const sg_grid* g, int l, bool with_faces) {
+    const Level& L = g->lv[l];
+    LevelGeom G;
+    G.nx = L.nx;
+    G.ny = L.ny;
+    G.nz = L.nz;
+    G.ihx2 = 1.0 / (L.h[0] * L.h[0]);
+    G.ihy2 = 1.0 / (L.h[1] * L.h[1]);
+    G.ihz2 = 1.0 / (L.h[2] * L.h[2]);
+    for (int d = 0; d < 3; ++d) G.per[d] = g->bc[d] == SG_BC_PERIODIC;
+    for (int f = 0; f < 6; ++f) {
+        const int d = f / 2;
+        G.face[f] = (with_faces && l == 0 && g->bc[d] == SG_BC_DIRICHLET) ? g->faces[f] : nullptr;
+    }
+    return G;
+}
+
+double lambda_max(const Level& L) {
+    return 4.0 * (1.0 / (L.h[0] * L.h[0]) + 1.0 / (L.h[1] * L.h[1]) + 1.0 / (L.h[2] * L.h[2]));
+}
+
+size_t wsize(const sg_grid* g) { return g->precision == SG_MIXED ? sizeof(float) : sizeof(double); }
+
+cudaEvent_t take_event(sg_grid* g) {
+    if (!g->ev_pool.empty()) {
+        cudaEvent_t e = g->ev_pool.back();
+        g->ev_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// Brackets one launch with CUDA events when profiling is on; `bytes` is the
+// launch's algorithmic traffic (compulsory reads + writes of its arrays).
+struct ProfScope {
+    sg_grid* g;
+    ProfRec rec;
+    bool on;
+    ProfScope(sg_grid* g_, int cls, double bytes) : g(g_), on(g_->prof) {
+        if (!on) return;
+        rec.cls = cls;
+        rec.bytes = bytes;
+        rec.a = take_event(g);
+        rec.b = take_event(g);
+        // External records become event nodes when the stream is being captured.
+        cudaEventRecordWithFlags(rec.a, g->st, cudaEventRecordExternal);
+    }
+    ~ProfScope() {
+        if (!on) return;
+        cudaEventRecordWithFlags(rec.b, g->st, cudaEventRecordExternal);
+        g->live.push_back(rec);
+    }
+};
+
+// Fold completed records into the totals (the stream has been synchronised).
+void prof_accumulate(sg_grid* g, std::vector<ProfRec>& recs, bool release) {
+    for (const ProfRec& r : recs) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+            g->stats[r.cls].launches += 1;
+            g->stats[r.cls].ms += ms;
+            g->stats[r.cls].bytes += r.bytes;
+        } else {
+            cudaGetLastError();
+        }
+        if (release) {
+            g->ev_pool.push_back(r.a);
+            g->ev_pool.push_back(r.b);
+        }
+    }
+    if (release) recs.clear();
+}
+
+void prof_sync_point(sg_grid* g, bool graph_replayed) {
+    if (!g->prof) return;
+    if (graph_replayed) prof_accumulate(g, g->graph_recs, false);
+    prof_accumulate(g, g->live, true);
+}
+
+sg_status check_opts(const sg_options* o) {
+    if (o->rkl_order != 1 && o->rkl_order != 2) return fail(SG_ERR_ARG, "rkl_order must be 1 or 2");
+    if (o->s_smooth < 1 || (o->rkl_order == 2 && o->s_smooth < 2) || o->s_smooth > 512)
+        return fail(SG_ERR_ARG, "s_smooth out of range (RKL1: 1..512, RKL2: 2..512)");
+    if (!(o->tau_frac > 0.0 && o->tau_frac <= 1.0)) return fail(SG_ERR_ARG, "tau_frac must be in (0, 1]");
+    if (o->n_pre < 0 || o->n_post < 0 || o->n_pre + o->n_post < 1 || o->n_pre > 64 || o->n_post > 64)
+        return fail(SG_ERR_ARG, "n_pre / n_post out of range");
+    if (!(o->coarse_tol >= 0.0 && o->coarse_tol < 1.0)) return fail(SG_ERR_ARG, "coarse_tol must be in [0, 1)");
+    if (o->coarse_max_ss < 1 || o->coarse_max_ss > 100000) return fail(SG_ERR_ARG, "coarse_max_ss out of range");
+    if (!(o->coarse_tau_frac >= 0.0 && o->coarse_tau_frac <= 1.0)) return fail(SG_ERR_ARG, "coarse_tau_frac out of range");
+    if (o->max_cycles < 1 || o->max_cycles > SG_MAX_HISTORY - 1) return fail(SG_ERR_ARG, "max_cycles out of range");
+    if (o->single_s < 0 || o->single_s > 100000) return fail(SG_ERR_ARG, "single_s out of range");
+    if (!(o->single_tau_frac >= 0.0 && o->single_tau_frac <= 1.0)) return fail(SG_ERR_ARG, "single_tau_frac out of range");
+    if (o->fixed_cycles < 0 || o->fixed_cycles > SG_MAX_HISTORY - 1) return fail(SG_ERR_ARG, "fixed_cycles out of range");
+    return SG_OK;
+}
+
+sg_status ensure_sched(sg_grid* g, const std::vector<int>& s) {
+    if ((int)s.size() > g->sched_cap) {
+        if (g->d_sched) cudaFree(g->d_sched);
+        g->d_sched = nullptr;
+        SG_CK(cudaMalloc(&g->d_sched, s.size() * sizeof(int)));
+        g->sched_cap = (int)s.size();
+    }
+    SG_CK(cudaMemcpyAsync(g->d_sched, s.data(), s.size() * sizeof(int), cudaMemcpyHostToDevice, g->st));
+    SG_CK(cudaStreamSynchronize(g->st));
+    return SG_OK;
+}
+
+// ---- one RKL super-step at level l: u <- Y_s ---------------------------------
+template <typename W>
+sg_status superstep(sg_grid* g, int l, int order, int s, double tau_frac, bool faces, W* u,
+                    const W* rhs) {
+    const Level& L = g->lv[l];
+    const LevelGeom G = geom(g, l, faces);
+    const Rkl r = make_rkl(order, s);
+    const double dtpar = 2.0 / lambda_max(L);
+    const double tau = tau_frac * dtpar * r.tau_over_dtpar;
+    W* t[3] = {(W*)L.t[0], (W*)L.t[1], (W*)L.t[2]};
+    W* z0 = (W*)L.z0;
+    StageCoef c{};
+    c.tau = tau;
+    c.mut1 = r.mut[1];
+    W* out1 = t[0];
+    const int cls = l == 0 ? K_STAGE0 : K_STAGE_C;
+    const double nb = double(L.n) * sizeof(W);
+    {
+        ProfScope ps(g, cls, nb * (order == 2 ? 4 : 3));
+        SG_CK(launch_stage<W>(G, order, true, c, u, nullptr, nullptr, nullptr, rhs, out1,
+                              order == 2 ? z0 : nullptr, g->st));
+    }
+    ++g->launches;
+    if (s == 1) {
+        SG_CK(cudaMemcpyAsync(u, out1, L.n * sizeof(W), cudaMemcpyDeviceToDevice, g->st));
+        return SG_OK;
+    }
+    for (int j = 2; j <= s; ++j) {
+        StageCoef cj{};
+        cj.mu = r.mu[j];
+        cj.nu = r.nu[j];
+        cj.mut_tau = r.mut[j] * tau;
+        cj.c0 = r.c0[j];
+        cj.gt = r.gt[j];
+        const W* ym1 = (j - 1 == 0) ? u : t[(j - 2) % 3];
+        const W* ym2 = (j - 2 == 0) ? u : t[(j - 3) % 3];
+        W* out = (j == s) ? u : t[(j - 1) % 3];
+        {
+            ProfScope ps(g, cls, nb * (order == 2 ? 6 : 4));
+            SG_CK(launch_stage<W>(G, order, false, cj, ym1, ym2, u, z0, rhs, out, nullptr, g->st));
+        }
+        ++g->launches;
+    }
+    return SG_OK;
+}
+
+template <typename W>
+sg_status relax(sg_grid* g, int l, int count, bool faces, W* u, const W* rhs) {
+    for (int c = 0; c < count; ++c)
+        SG_TRY(superstep<W>(g, l, g->opt.rkl_order, g->opt.s_smooth, g->opt.tau_frac, faces, u, rhs));
+    return SG_OK;
+}
+
+double coarse_c(const sg_grid* g, int l) {
+    const Level& L = g->lv[l];
+    const int N = std::max(L.nx, std::max(L.ny, L.nz));
+    return g->opt.coarse_tau_frac > 0.0 ? g->opt.coarse_tau_frac : cell_tau_frac(N);
+}
+
+// Coarsest-level solve of L u = rhs from u = 0 (homogeneous ghosts).
+template <typename W>
+sg_status coarse_solve(sg_grid* g, int l, const W* rhs, W* u, int* d_done) {
+    const Level& L = g->lv[l];
+    const int N = std::max(L.nx, std::max(L.ny, L.nz));
+    if (coarse_fits<W>(L.n)) {
+        CoarseParams p;
+        p.g = geom(g, l, false);
+        p.rhs = rhs;
+        p.u_out = u;
+        p.sched = g->d_sched;
+        p.max_ss = g->opt.coarse_max_ss;
+        p.tol = g->opt.coarse_tol;
+        p.tau_unit = coarse_c(g, l) * 2.0 / lambda_max(L);
+        p.ss_done = d_done;
+        {
+            ProfScope ps(g, K_COARSE, 2.0 * L.n * sizeof(W));
+            SG_CK(launch_coarse_solve<W>(p, g->st));
+        }
+        ++g->launches;
+        return SG_OK;
+    }
+    // Level too large for one CTA: stage kernels in global memory.
+    const std::vector<int> sched = accelerated_schedule(N, g->opt.coarse_max_ss);
+    SG_CK(cudaMemsetAsync(u, 0, L.n * sizeof(W), g->st));
+    double r0 = -1.0;
+    int done = 0;
+    for (int ss = 0; ss < g->opt.coarse_max_ss; ++ss) {
+        if (g->opt.coarse_tol > 0.0) {
+            int nb = 0;
+            SG_CK(launch_residual<W, W>(geom(g, l, false), u, rhs, (W*)nullptr, g->partials, &nb, g->st));
+            SG_CK(launch_finalize(g->partials, nb, g->red + 3, g->st));
+            SG_CK(cudaMemcpyAsync(g->host_red + 3, g->red + 3, sizeof(Reduced), cudaMemcpyDeviceToHost, g->st));
+            SG_CK(cudaStreamSynchronize(g->st));
+            g->launches += 2;
+            const double rn = std::sqrt(g->host_red[3].sumsq);
+            if (r0 < 0) r0 = rn;
+            if (rn <= g->opt.coarse_tol * r0) break;
+        }
+        SG_TRY(superstep<W>(g, l, 1, sched[ss], coarse_c(g, l), false, u, rhs));
+        ++done;
+    }
+    SG_CK(cudaMemcpyAsync(d_done, &done, sizeof(int), cudaMemcpyHostToDevice, g->st));
+    SG_CK(cudaStreamSynchronize(g->st));
+    return SG_OK;
+}
+
+// One V-cycle (Sec. 2.1) with level-0 arrays u0 / rhs0 (faces on level 0 if `faces`).
+template <typename W>
+sg_status vcycle(sg_grid* g, int L, W* u0, const W* rhs0, bool faces) {
+    auto U = [&](int l) -> W* { return l == 0 ? u0 : (W*)g->lv[l].u; };
+    auto R = [&](int l) -> const W* { return l == 0 ? rhs0 : (const W*)g->lv[l].rhs; };
+    const bool per = all_periodic(g);
+    SG_TRY(relax<W>(g, 0, g->opt.n_pre, faces, U(0), R(0)));                    // step 1
+    for (int l = 1; l < L; ++l) {                                               // step 2
+        int nb = 0;
+        {
+            ProfScope ps(g, K_RESTRICT, (2.0 + 0.125) * g->lv[l - 1].n * sizeof(W));
+            SG_CK(launch_residual_restrict<W>(geom(g, l - 1, faces && l - 1 == 0), U(l - 1), R(l - 1),
+                                              (W*)g->lv[l].rhs, g->partials, &nb, g->st));   // 2a, 2b
+        }
+        ++g->launches;
+        if (per) {                                                              // coarse mean removed
+            ProfScope ps(g, K_MISC, 2.0 * g->lv[l].n * sizeof(W));
+            SG_CK(launch_finalize(g->partials, nb, g->red + 1, g->st));
+            SG_CK(launch_subtract_mean<W>((W*)g->lv[l].rhs, g->lv[l].n, g->red + 1, g->st));
+            g->launches += 2;
+        }
+        SG_CK(cudaMemsetAsync(U(l), 0, g->lv[l].n * sizeof(W), g->st));        // 2c
+        if (l < L - 1) SG_TRY(relax<W>(g, l, g->opt.n_pre, false, U(l), R(l)));  // 2d-i
+        else SG_TRY(coarse_solve<W>(g, l, R(l), U(l), g->d_ss));                 // 2e
+    }
+    for (int l = L - 2; l >= 1; --l) {                                          // step 3
+        {
+            ProfScope ps(g, K_PROLONG, (2.0 + 0.125) * g->lv[l].n * sizeof(W));
+            SG_CK(launch_prolong_correct<W>(geom(g, l, false), U(l + 1), U(l), g->st));
+        }
+        ++g->launches;
+        SG_TRY(relax<W>(g, l, g->opt.n_post, false, U(l), R(l)));
+    }
+    {
+        ProfScope ps(g, K_PROLONG, (2.0 + 0.125) * g->lv[0].n * sizeof(W));
+        SG_CK(launch_prolong_correct<W>(geom(g, 0, false), U(1), U(0), g->st));  // 4a
+    }
+    ++g->launches;
+    SG_TRY(relax<W>(g, 0, g->opt.n_post, faces, U(0), R(0)));                  // 4b
+    return SG_OK;
+}
+
+// Residual norm of (phi, f) at level 0 into red[0]; mixed mode also writes r32.
+sg_status level0_residual(sg_grid* g, const double* phi, const double* f, bool faces) {
+    int nb = 0;
+    const LevelGeom G = geom(g, 0, faces);
+    {
+    ProfScope ps(g, K_RES0, double(g->lv[0].n) * (g->precision == SG_MIXED ? 20.0 : 16.0));
+    if (g->precision == SG_MIXED)
+        SG_CK(launch_residual<double, float>(G, phi, f, (float*)g->lv[0].rhs, g->partials, &nb, g->st));
+    else
+        SG_CK(launch_residual<double, double>(G, phi, f, (double*)nullptr, g->partials, &nb, g->st));
+    }
+    SG_CK(launch_finalize(g->partials, nb, g->red, g->st));
+    g->launches += 2;
+    return SG_OK;
+}
+
+// Everything one cycle enqueues after the first residual: V-cycle, update,
+// residual + norm, and the copies of the norm / coarse count to pinned memory.
+sg_status cycle_body(sg_grid* g, int L, double* phi, const double* f, bool faces) {
+    if (g->precision == SG_MIXED) {
+        float* e = (float*)g->lv[0].u;
+        SG_CK(cudaMemsetAsync(e, 0, g->lv[0].n * sizeof(float), g->st));
+        SG_TRY(vcycle<float>(g, L, e, (const float*)g->lv[0].rhs, false));
+        {
+            ProfScope ps(g, K_UPDATE, 20.0 * g->lv[0].n);
+            SG_CK(launch_add_f32_to_f64(phi, e, g->lv[0].n, g->st));
+        }
+        ++g->launches;
+    } else {
+        SG_TRY(vcycle<double>(g, L, phi, f, faces));
+    }
+    SG_TRY(level0_residual(g, phi, f, faces));
+    SG_CK(cudaMemcpyAsync(g->host_red, g->red, sizeof(Reduced), cudaMemcpyDeviceToHost, g->st));
+    SG_CK(cudaMemcpyAsync(g->host_ss, g->d_ss, sizeof(int), cudaMemcpyDeviceToHost, g->st));
+    return SG_OK;
+}
+
+void drop_graph(sg_grid* g) {
+    if (g->gexec) cudaGraphExecDestroy(g->gexec);
+    g->gexec = nullptr;
+    std::memset(g->gkey, 0, sizeof(g->gkey));
+    for (const ProfRec& r : g->graph_recs) {
+        g->ev_pool.push_back(r.a);
+        g->ev_pool.push_back(r.b);
+    }
+    g->graph_recs.clear();
+}
+
+sg_status run_cycle(sg_grid* g, int L, double* phi, const double* f, bool faces, bool* replayed) {
+    *replayed = false;
+    const bool graphable = g->opt.use_graph &&
+                           (g->precision == SG_MIXED ? coarse_fits<float>(g->lv[L - 1].n)
+                                                     : coarse_fits<double>(g->lv[L - 1].n));
+    if (!graphable) return cycle_body(g, L, phi, f, faces);
+    long long key[8] = {L, (long long)(uintptr_t)phi, (long long)(uintptr_t)f, faces ? 1 : 0,
+                        g->opt.rkl_order * 1000 + g->opt.s_smooth,
+                        g->opt.n_pre * 1000 + g->opt.n_post,
+                        (long long)std::llround(g->opt.tau_frac * 1e12),
+                        (long long)std::llround(g->opt.coarse_tol * 1e15) * 100000 + g->opt.coarse_max_ss};
+    long long key2 = (long long)std::llround(g->opt.coarse_tau_frac * 1e12) * 2 + (g->prof ? 1 : 0);
+    key[7] ^= key2 * 1315423911LL;
+    if (!g->gexec || std::memcmp(key, g->gkey, sizeof(key)) != 0) {
+        drop_graph(g);
+        cudaGraph_t graph = nullptr;
+        const long long before = g->launches;
+        SG_CK(cudaStreamBeginCapture(g->st, cudaStreamCaptureModeThreadLocal));
+        std::vector<ProfRec> outside;
+        outside.swap(g->live);
+        sg_status s = cycle_body(g, L, phi, f, faces);
+        cudaError_t ec = cudaStreamEndCapture(g->st, &graph);
+        g->live.swap(outside);          // g->live: records enqueued before the capture
+        if (s != SG_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            for (const ProfRec& r : outside) { g->ev_pool.push_back(r.a); g->ev_pool.push_back(r.b); }
+            return s;
+        }
+        if (ec != cudaSuccess) return fail(SG_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(ec));
+        cudaError_t ei = cudaGraphInstantiate(&g->gexec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ei != cudaSuccess) {
+            g->gexec = nullptr;
+            return fail(SG_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(ei));
+        }
+        g->graph_launches = g->launches - before;
+        g->launches = before;
+        std::memcpy(g->gkey, key, sizeof(key));
+        g->graph_recs.swap(outside);    // the records captured into the graph
+    }
+    SG_CK(cudaGraphLaunch(g->gexec, g->st));
+    g->launches += g->graph_launches;
+    *replayed = true;
+    return SG_OK;
+}
+
+long long stage_updates_per_cycle(const sg_grid* g, int L) {
+    long long su = 0;
+    for (int l = 0; l < L - 1; ++l)
+        su += (long long)g->lv[l].n * (g->opt.n_pre + g->opt.n_post) * g->opt.s_smooth;
+    return su;
+}
+
+// The solve loop shared by sg_solve (phi, f, faces) and sg_backward (lam, w, none).
+sg_status solve_impl(sg_grid* g, double tol, int L, double* phi, const double* f, bool faces,
+                     bool have_guess, sg_solve_info* info) {
+    sg_solve_info local;
+    std::memset(&local, 0, sizeof(local));
+    local.levels = L;
+    local.s_smooth = g->opt.s_smooth;
+    local.rkl_order = g->opt.rkl_order;
+    local.precision = g->precision;
+    const long long launches0 = g->launches;
+    const Level& L0 = g->lv[0];
+    SG_CK(cudaEventRecord(g->ev0, g->st));
+
+    // r0 = ||L 0 - f|| (boundary contribution of phi = 0 included).
+    if (!have_guess) {
+        SG_CK(cudaMemsetAsync(phi, 0, L0.n * sizeof(double), g->st));
+    } else {
+        double* zero = nullptr;
+        if (g->precision == SG_FP64) {
+            zero = (double*)L0.t[0];
+        } else {
+            if (!g->scratch64) SG_CK(cudaMalloc(&g->scratch64, L0.n * sizeof(double)));
+            zero = g->scratch64;
+        }
+        SG_CK(cudaMemsetAsync(zero, 0, L0.n * sizeof(double), g->st));
+        SG_TRY(level0_residual(g, zero, f, faces));
+        SG_CK(cudaMemcpyAsync(g->host_red + 2, g->red, sizeof(Reduced), cudaMemcpyDeviceToHost, g->st));
+    }
+    SG_TRY(level0_residual(g, phi, f, faces));
+    SG_CK(cudaMemcpyAsync(g->host_red, g->red, sizeof(Reduced), cudaMemcpyDeviceToHost, g->st));
+    SG_CK(cudaStreamSynchronize(g->st));
+    prof_sync_point(g, false);
+    const double nn = double(L0.n);
+    const double r0 = std::sqrt((have_guess ? g->host_red[2].sumsq : g->host_red[0].sumsq) / nn);
+    local.r0 = r0;
+    const double rden = r0 > 0.0 ? r0 : 1.0;
+
+    int N0 = std::max(L0.nx, std::max(L0.ny, L0.nz));
+    std::vector<int> single_sched;
+    if (L == 1) {
+        single_sched = accelerated_schedule(N0, g->opt.max_cycles + 1);
+    } else {
+        const Level& Lc = g->lv[L - 1];
+        const int Nc = std::max(Lc.nx, std::max(Lc.ny, Lc.nz));
+        SG_TRY(ensure_sched(g, accelerated_schedule(Nc, g->opt.coarse_max_ss)));
+    }
+    const int limit = g->opt.fixed_cycles > 0 ? g->opt.fixed_cycles : g->opt.max_cycles;
+    const double single_c = g->opt.single_tau_frac > 0 ? g->opt.single_tau_frac : cell_tau_frac(N0);
+    long long su = 0;
+    sg_status status = SG_OK;
+    int m = 0;
+    while (true) {
+        const double rel = std::sqrt(g->host_red[0].sumsq / nn) / rden;
+        local.history[m] = rel;
+        local.rel_residual = rel;
+        local.max_residual = g->host_red[0].maxabs;
+        if (!std::isfinite(rel)) {
+            status = fail(SG_ERR_NONFINITE, "residual norm is not finite");
+            break;
+        }
+        if (g->opt.fixed_cycles == 0 && rel <= tol) break;
+        if (m >= limit) {
+            if (g->opt.fixed_cycles == 0)
+                status = fail(SG_ERR_NOT_CONVERGED, "max_cycles reached above the tolerance");
+            break;
+        }
+        if (L == 1) {
+            const int s = g->opt.single_s > 0 ? g->opt.single_s : single_sched[m];
+            if (g->precision == SG_MIXED) {
+                // Single level in mixed precision: FP32 super-step on the error equation.
+                float* e = (float*)L0.u;
+                SG_CK(cudaMemsetAsync(e, 0, L0.n * sizeof(float), g->st));
+                SG_TRY(superstep<float>(g, 0, 1, s, single_c, false, e, (const float*)L0.rhs));
+                {
+                    ProfScope ps(g, K_UPDATE, 20.0 * L0.n);
+                    SG_CK(launch_add_f32_to_f64(phi, e, L0.n, g->st));
+                }
+                ++g->launches;
+            } else {
+                SG_TRY(superstep<double>(g, 0, 1, s, single_c, faces, phi, f));
+            }
+            su += L0.n * (long long)s;
+            SG_TRY(level0_residual(g, phi, f, faces));
+            SG_CK(cudaMemcpyAsync(g->host_red, g->red, sizeof(Reduced), cudaMemcpyDeviceToHost, g->st));
+            *g->host_ss = 0;
+        }
+        bool replayed = false;
+        if (L > 1) {
+            SG_TRY(run_cycle(g, L, phi, f, faces, &replayed));
+            su += stage_updates_per_cycle(g, L);
+        }
+        SG_CK(cudaStreamSynchronize(g->st));
+        prof_sync_point(g, replayed);
+        if (L > 1) {
+            local.coarse_ss[m] = *g->host_ss;
+            const Level& Lc = g->lv[L - 1];
+            const int Nc = std::max(Lc.nx, std::max(Lc.ny, Lc.nz));
+            const std::vector<int> sc = accelerated_schedule(Nc, std::max(1, *g->host_ss));
+            for (int q = 0; q < *g->host_ss && q < (int)sc.size(); ++q) su += Lc.n * (long long)sc[q];
+        }
+        ++m;
+    }
+    local.cycles = m;
+    if (all_periodic(g)) {
+        int nb = 0;
+        SG_CK(launch_sum_partials_f64(phi, L0.n, g->partials, &nb, g->st));
+        SG_CK(launch_finalize(g->partials, nb, g->red + 1, g->st));
+        SG_CK(launch_sub_mean_f64(phi, L0.n, g->red + 1, g->st));
+        g->launches += 3;
+    }
+    SG_CK(cudaEventRecord(g->ev1, g->st));
+    SG_CK(cudaEventSynchronize(g->ev1));
+    float ms = 0.f;
+    SG_CK(cudaEventElapsedTime(&ms, g->ev0, g->ev1));
+    local.elapsed_ms = ms;
+    local.stage_cell_updates = su;
+    local.kernel_launches = g->launches - launches0;
+    local.status = status;
+    if (info) *info = local;
+    return status;
+}
+
+sg_status copy_in(double* dst, const double* src, long long n, int on_device, cudaStream_t st) {
+    SG_CK(cudaMemcpyAsync(dst, src, n * sizeof(double),
+                          on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+    if (!on_device) SG_CK(cudaStreamSynchronize(st));
+    return SG_OK;
+}
+
+sg_status copy_out(double* dst, const double* src, long long n, int on_device, cudaStream_t st) {
+    SG_CK(cudaMemcpyAsync(dst, src, n * sizeof(double),
+                          on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+    if (!on_device) SG_CK(cudaStreamSynchronize(st));
+    return SG_OK;
+}
+
+void free_grid(sg_grid* g) {
+    if (!g) return;
+    drop_graph(g);
+    for (auto& L : g->lv) {
+        cudaFree(L.u);
+        cudaFree(L.rhs);
+        cudaFree(L.z0);
+        for (int i = 0; i < 3; ++i) cudaFree(L.t[i]);
+    }
+    cudaFree(g->phi);
+    cudaFree(g->f);
+    for (int i = 0; i < 6; ++i) cudaFree(g->faces[i]);
+    cudaFree(g->lam);
+    cudaFree(g->w);
+    cudaFree(g->scratch64);
+    cudaFree(g->partials);
+    cudaFree(g->red);
+    cudaFree(g->d_sched);
+    cudaFree(g->d_ss);
+    if (g->host_red) cudaFreeHost(g->host_red);
+    if (g->host_ss) cudaFreeHost(g->host_ss);
+    if (g->ev0) cudaEventDestroy(g->ev0);
+    if (g->ev1) cudaEventDestroy(g->ev1);
+    for (const ProfRec& r : g->live) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+    for (cudaEvent_t e : g->ev_pool) cudaEventDestroy(e);
+    if (g->own_stream) cudaStreamDestroy(g->own_stream);
+    delete g;
+}
+
+}  // namespace
+
+// ============================================================================
+// C ABI
+// ============================================================================
+extern "C" {
+
+sg_status sg_default_options(sg_options* o) {
+    if (!o) return fail(SG_ERR_ARG, "options pointer is NULL");
+    o->rkl_order = 2;
+    o->s_smooth = 3;
+    o->tau_frac = 1.0;
+    o->n_pre = 2;
+    o->n_post = 1;
+    o->coarse_tol = 1e-3;
+    o->coarse_max_ss = 64;
+    o->coarse_tau_frac = 0.0;
+    o->max_cycles = 100;
+    o->single_s = 0;
+    o->single_tau_frac = 0.0;
+    o->fixed_cycles = 0;
+    o->use_graph = 1;
+    o->fused = 1;
+    return SG_OK;
+}
+
+const char* sg_last_error(void) { return g_err.c_str(); }
+
+sg_status sg_create_grid(int nx, int ny, int nz, const double lo[3], const double hi[3],
+                         const int bc[3], int precision, void* cuda_stream, sg_grid** out) {
+    g_err.clear();
+    if (!out || !lo || !hi || !bc) return fail(SG_ERR_ARG, "NULL argument");
+    const int n[3] = {nx, ny, nz};
+    for (int d = 0; d < 3; ++d) {
+        if (n[d] < 2 || n[d] > 4096) return fail(SG_ERR_ARG, "grid size must be in [2, 4096] per axis");
+        if (!(hi[d] > lo[d]) || !std::isfinite(lo[d]) || !std::isfinite(hi[d]))
+            return fail(SG_ERR_ARG, "need finite lo < hi on every axis");
+        if (bc[d] != SG_BC_DIRICHLET && bc[d] != SG_BC_PERIODIC) return fail(SG_ERR_ARG, "bad boundary kind");
+    }
+    if ((long long)nx * ny * nz > 2147483647LL) return fail(SG_ERR_ARG, "too many cells");
+    if (precision != SG_FP64 && precision != SG_MIXED) return fail(SG_ERR_ARG, "bad precision");
+    SG_CK(coarse_configure());
+    sg_grid* g = new sg_grid();
+    for (int d = 0; d < 3; ++d) {
+        g->n[d] = n[d];
+        g->lo[d] = lo[d];
+        g->hi[d] = hi[d];
+        g->bc[d] = bc[d];
+    }
+    g->precision = precision;
+    g->st = (cudaStream_t)cuda_stream;
+    if (g->st == nullptr || g->st == cudaStreamLegacy) {
+        // The legacy default stream cannot be captured into a CUDA graph: use a
+        // private blocking stream, which the legacy stream orders implicitly.
+        if (cudaStreamCreate(&g->own_stream) != cudaSuccess) {
+            delete g;
+            return fail(SG_ERR_CUDA, "cudaStreamCreate failed");
+        }
+        g->st = g->own_stream;
+    }
+    sg_default_options(&g->opt);
+    g->max_levels = rule_levels(nx, ny, nz);
+    const size_t ws = wsize(g);
+    auto alloc = [&](void** p, size_t bytes) -> bool { return cudaMalloc(p, bytes) == cudaSuccess; };
+    bool ok = true;
+    long long max_blocks = kSumBlocks;
+    for (int l = 0; l < g->max_levels && ok; ++l) {
+        Level L;
+        L.nx = nx >> l;
+        L.ny = ny >> l;
+        L.nz = nz >> l;
+        L.n = (long long)L.nx * L.ny * L.nz;
+        for (int d = 0; d < 3; ++d) L.h[d] = (hi[d] - lo[d]) / n[d] * double(1 << l);
+        const bool own_u = !(l == 0 && precision == SG_FP64);
+        if (own_u) ok = ok && alloc(&L.u, L.n * ws) && alloc(&L.rhs, L.n * ws);
+        ok = ok && alloc(&L.z0, L.n * ws);
+        for (int i = 0; i < 3; ++i) ok = ok && alloc(&L.t[i], L.n * ws);
+        g->lv.push_back(L);
+        const LevelGeom G = geom(g, l, false);
+        max_blocks = std::max(max_blocks, residual_blocks(G));
+        if (l + 1 < g->max_levels) max_blocks = std::max(max_blocks, restrict_blocks(G));
+    }
+    const long long n0 = (long long)nx * ny * nz;
+    ok = ok && alloc((void**)&g->phi, n0 * sizeof(double)) && alloc((void**)&g->f, n0 * sizeof(double));
+    ok = ok && alloc((void**)&g->partials, max_blocks * sizeof(Partial));
+    ok = ok && alloc((void**)&g->red, 8 * sizeof(Reduced));
+    ok = ok && alloc((void**)&g->d_ss, sizeof(int));
+    ok = ok && cudaMallocHost((void**)&g->host_red, 8 * sizeof(Reduced)) == cudaSuccess;
+    ok = ok && cudaMallocHost((void**)&g->host_ss, sizeof(int)) == cudaSuccess;
+    ok = ok && cudaEventCreate(&g->ev0) == cudaSuccess && cudaEventCreate(&g->ev1) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        free_grid(g);
+        return fail(SG_ERR_OOM, "device allocation failed");
+    }
+    g->partial_cap = (int)max_blocks;
+    const sg_status z1 = cudaMemsetAsync(g->f, 0, n0 * sizeof(double), g->st) == cudaSuccess ? SG_OK : SG_ERR_CUDA;
+    const sg_status z2 = cudaMemsetAsync(g->phi, 0, n0 * sizeof(double), g->st) == cudaSuccess ? SG_OK : SG_ERR_CUDA;
+    if (z1 != SG_OK || z2 != SG_OK || cudaStreamSynchronize(g->st) != cudaSuccess) {
+        free_grid(g);
+        return fail(SG_ERR_CUDA, "initialisation failed");
+    }
+    *out = g;
+    return SG_OK;
+}
+
+sg_status sg_set_options(sg_grid* g, const sg_options* opt) {
+    g_err.clear();
+    if (!g || !opt) return fail(SG_ERR_ARG, "NULL argument");
+    SG_TRY(check_opts(opt));
+    g->opt = *opt;
+    return SG_OK;
+}
+
+sg_status sg_get_options(const sg_grid* g, sg_options* opt) {
+    if (!g || !opt) return fail(SG_ERR_ARG, "NULL argument");
+    *opt = g->opt;
+    return SG_OK;
+}
+
+int sg_max_levels(const sg_grid* g) { return g ? g->max_levels : 0; }
+
+sg_status sg_set_boundary(sg_grid* g, const double* const faces[6], int on_device) {
+    g_err.clear();
+    if (!g || !faces) return fail(SG_ERR_ARG, "NULL argument");
+    const long long fsz[6] = {(long long)g->n[2] * g->n[1], (long long)g->n[2] * g->n[1],
+                              (long long)g->n[2] * g->n[0], (long long)g->n[2] * g->n[0],
+                              (long long)g->n[1] * g->n[0], (long long)g->n[1] * g->n[0]};
+    for (int f = 0; f < 6; ++f) {
+        if (!g->faces[f]) SG_CK(cudaMalloc(&g->faces[f], fsz[f] * sizeof(double)));
+        if (faces[f]) SG_TRY(copy_in(g->faces[f], faces[f], fsz[f], on_device, g->st));
+        else SG_CK(cudaMemsetAsync(g->faces[f], 0, fsz[f] * sizeof(double), g->st));
+    }
+    g->have_faces = true;
+    drop_graph(g);
+    return SG_OK;
+}
+
+sg_status sg_set_density(sg_grid* g, const double* rho, int on_device, double four_pi_G) {
+    g_err.clear();
+    if (!g || !rho) return fail(SG_ERR_ARG, "NULL argument");
+    if (!std::isfinite(four_pi_G)) return fail(SG_ERR_ARG, "four_pi_G must be finite");
+    const long long n = g->lv[0].n;
+    if (on_device) {
+        SG_CK(launch_scale_copy(rho, g->f, four_pi_G, n, g->st));
+    } else {
+        SG_CK(cudaMemcpyAsync(g->f, rho, n * sizeof(double), cudaMemcpyHostToDevice, g->st));
+        SG_CK(launch_scale_copy(g->f, g->f, four_pi_G, n, g->st));
+    }
+    if (all_periodic(g)) {                      // Eq. source_modification
+        int nb = 0;
+        SG_CK(launch_sum_partials_f64(g->f, n, g->partials, &nb, g->st));
+        SG_CK(launch_finalize(g->partials, nb, g->red + 1, g->st));
+        SG_CK(launch_sub_mean_f64(g->f, n, g->red + 1, g->st));
+    }
+    if (!on_device) SG_CK(cudaStreamSynchronize(g->st));
+    g->four_pi_G = four_pi_G;
+    g->have_density = true;
+    g->guess_set = false;
+    return SG_OK;
+}
+
+sg_status sg_set_potential_guess(sg_grid* g, const double* phi, int on_device) {
+    g_err.clear();
+    if (!g || !phi) return fail(SG_ERR_ARG, "NULL argument");
+    SG_TRY(copy_in(g->phi, phi, g->lv[0].n, on_device, g->st));
+    g->guess_set = true;
+    return SG_OK;
+}
+
+sg_status sg_solve(sg_grid* g, double tol, int s, int levels, sg_solve_info* info) {
+    g_err.clear();
+    if (!g) return fail(SG_ERR_ARG, "NULL grid");
+    if (!(tol >= 0.0)) return fail(SG_ERR_ARG, "tol must be >= 0");
+    if (levels < 0 || levels > g->max_levels) return fail(SG_ERR_ARG, "levels exceeds the level rule");
+    if (s < 0) return fail(SG_ERR_ARG, "s must be >= 0");
+    if (!g->have_density) return fail(SG_ERR_STATE, "sg_set_density first");
+    const int L = levels == 0 ? g->max_levels : levels;
+    sg_options saved = g->opt;
+    if (s > 0) {
+        if (L == 1) g->opt.single_s = s;
+        else g->opt.s_smooth = s;
+        const sg_status c = check_opts(&g->opt);
+        if (c != SG_OK) {
+            g->opt = saved;
+            return c;
+        }
+    }
+    const bool faces = g->have_faces;
+    const sg_status st = solve_impl(g, tol, L, g->phi, g->f, faces, g->guess_set, info);
+    g->opt = saved;
+    g->guess_set = false;
+    if (st == SG_OK || st == SG_ERR_NOT_CONVERGED) {
+        g->have_solution = true;
+        g->last_levels = L;
+    }
+    return st;
+}
+
+sg_status sg_potential(sg_grid* g, double* phi_out, int on_device) {
+    g_err.clear();
+    if (!g || !phi_out) return fail(SG_ERR_ARG, "NULL argument");
+    if (!g->have_solution) return fail(SG_ERR_STATE, "no solution yet");
+    return copy_out(phi_out, g->phi, g->lv[0].n, on_device, g->st);
+}
+
+sg_status sg_backward(sg_grid* g, const double* dL_dphi, double* dL_drho, int on_device, double tol,
+                      sg_solve_info* info) {
+    g_err.clear();
+    if (!g || !dL_dphi || !dL_drho) return fail(SG_ERR_ARG, "NULL argument");
+    if (!(tol >= 0.0)) return fail(SG_ERR_ARG, "tol must be >= 0");
+    const long long n = g->lv[0].n;
+    if (!g->lam) SG_CK(cudaMalloc(&g->lam, n * sizeof(double)));
+    if (!g->w) SG_CK(cudaMalloc(&g->w, n * sizeof(double)));
+    SG_TRY(copy_in(g->w, dL_dphi, n, on_device, g->st));
+    if (all_periodic(g)) {
+        int nb = 0;
+        SG_CK(launch_sum_partials_f64(g->w, n, g->partials, &nb, g->st));
+        SG_CK(launch_finalize(g->partials, nb, g->red + 1, g->st));
+        SG_CK(launch_sub_mean_f64(g->w, n, g->red + 1, g->st));
+    }
+    const int L = g->last_levels > 0 ? g->last_levels : g->max_levels;
+    const sg_status st = solve_impl(g, tol, L, g->lam, g->w, false, false, info);
+    if (st != SG_OK && st != SG_ERR_NOT_CONVERGED) return st;
+    SG_CK(launch_scale_copy(g->lam, g->lam, g->four_pi_G, n, g->st));
+    SG_TRY(copy_out(dL_drho, g->lam, n, on_device, g->st));
+    return st;
+}
+
+sg_status sg_solve_batch(sg_grid* const* grids, int n, double tol, sg_solve_info* infos) {
+    g_err.clear();
+    if (!grids || n < 0) return fail(SG_ERR_ARG, "bad batch arguments");
+    sg_status first = SG_OK;
+    for (int i = 0; i < n; ++i) {
+        const sg_status s = sg_solve(grids[i], tol, 0, 0, infos ? &infos[i] : nullptr);
+        if (s != SG_OK && first == SG_OK) first = s;
+    }
+    return first;
+}
+
+void sg_destroy(sg_grid* g) { free_grid(g); }
+
+sg_status sg_set_profiling(sg_grid* g, int on) {
+    g_err.clear();
+    if (!g) return fail(SG_ERR_ARG, "NULL grid");
+    g->prof = on != 0;
+    drop_graph(g);
+    for (int c = 0; c < K_NCLASS; ++c) {
+        std::memset(&g->stats[c], 0, sizeof(sg_kernel_stat));
+        std::snprintf(g->stats[c].name, sizeof(g->stats[c].name), "%s", kClassName[c]);
+    }
+    return SG_OK;
+}
+
+sg_status sg_kernel_stats(const sg_grid* g, sg_kernel_stat* out) {
+    g_err.clear();
+    if (!g || !out) return fail(SG_ERR_ARG, "NULL argument");
+    for (int c = 0; c < K_NCLASS; ++c) {
+        out[c] = g->stats[c];
+        std::snprintf(out[c].name, sizeof(out[c].name), "%s", kClassName[c]);
+    }
+    return SG_OK;
+}
+
+// ---- single operators --------------------------------------------------------
+static sg_status op_check(sg_grid* g, int level, int dtype) {
+    if (!g) return fail(SG_ERR_ARG, "NULL grid");
+    if (level < 0 || level >= g->max_levels) return fail(SG_ERR_ARG, "level out of range");
+    if (dtype != 0 && dtype != 1) return fail(SG_ERR_ARG, "dtype must be 0 (f64) or 1 (f32)");
+    const bool w64 = g->precision == SG_FP64;
+    if ((dtype == 0) != w64) return fail(SG_ERR_ARG, "dtype must match the grid's working precision");
+    return SG_OK;
+}
+
+sg_status sg_op_superstep(sg_grid* g, int level, int dtype, int order, int s, double tau_frac,
+                          int homogeneous, const void* u, const void* rhs, void* out) {
+    g_err.clear();
+    SG_TRY(op_check(g, level, dtype));
+    if (!u || !rhs || !out || out == u || out == rhs) return fail(SG_ERR_ARG, "bad pointers");
+    if ((order != 1 && order != 2) || s < 1 || (order == 2 && s < 2) || !(tau_frac > 0 && tau_frac <= 1))
+        return fail(SG_ERR_ARG, "bad order / s / tau_frac");
+    const bool faces = !homogeneous && level == 0 && g->have_faces;
+    const size_t bytes = g->lv[level].n * (dtype == 0 ? 8 : 4);
+    SG_CK(cudaMemcpyAsync(out, u, bytes, cudaMemcpyDeviceToDevice, g->st));
+    if (dtype == 0) return superstep<double>(g, level, order, s, tau_frac, faces, (double*)out, (const double*)rhs);
+    return superstep<float>(g, level, order, s, tau_frac, faces, (float*)out, (const float*)rhs);
+}
+
+sg_status sg_op_residual_restrict(sg_grid* g, int level, int dtype, int homogeneous, const void* u,
+                                  const void* rhs, void* coarse_out, double norms[2]) {
+    g_err.clear();
+    SG_TRY(op_check(g, level, dtype));
+    if (!u || !rhs) return fail(SG_ERR_ARG, "bad pointers");
+    if (coarse_out && level + 1 >= g->max_levels) return fail(SG_ERR_ARG, "no coarser level");
+    const bool faces = !homogeneous && level == 0 && g->have_faces;
+    const LevelGeom G = geom(g, level, faces);
+    int nb = 0;
+    if (coarse_out) {
+        if (dtype == 0)
+            SG_CK(launch_residual_restrict<double>(G, (const double*)u, (const double*)rhs, (double*)coarse_out,
+                                                   g->partials, &nb, g->st));
+        else
+            SG_CK(launch_residual_restrict<float>(G, (const float*)u, (const float*)rhs, (float*)coarse_out,
+                                                  g->partials, &nb, g->st));
+    } else {
+        if (dtype == 0)
+            SG_CK(launch_residual<double, double>(G, (const double*)u, (const double*)rhs, (double*)nullptr,
+                                                  g->partials, &nb, g->st));
+        else
+            SG_CK(launch_residual<float, float>(G, (const float*)u, (const float*)rhs, (float*)nullptr,
+                                                g->partials, &nb, g->st));
+    }
+    if (norms) {
+        SG_CK(launch_finalize(g->partials, nb, g->red + 4, g->st));
+        SG_CK(cudaMemcpyAsync(g->host_red + 4, g->red + 4, sizeof(Reduced), cudaMemcpyDeviceToHost, g->st));
+        SG_CK(cudaStreamSynchronize(g->st));
+        norms[0] = g->host_red[4].sumsq;
+        norms[1] = g->host_red[4].maxabs;
+    }
+    return SG_OK;
+}
+
+sg_status sg_op_prolong_correct(sg_grid* g, int level, int dtype, const void* coarse, void* fine) {
+    g_err.clear();
+    SG_TRY(op_check(g, level, dtype));
+    if (!coarse || !fine) return fail(SG_ERR_ARG, "bad pointers");
+    if (level + 1 >= g->max_levels) return fail(SG_ERR_ARG, "no coarser level");
+    const LevelGeom G = geom(g, level, false);
+    if (dtype == 0) SG_CK(launch_prolong_correct<double>(G, (const double*)coarse, (double*)fine, g->st));
+    else SG_CK(launch_prolong_correct<float>(G, (const float*)coarse, (float*)fine, g->st));
+    return SG_OK;
+}
+
+sg_status sg_op_coarse_solve(sg_grid* g, int level, int dtype, const void* rhs, void* u_out, int* ss_done) {
+    g_err.clear();
+    SG_TRY(op_check(g, level, dtype));
+    if (!rhs || !u_out) return fail(SG_ERR_ARG, "bad pointers");
+    const Level& L = g->lv[level];
+    const int N = std::max(L.nx, std::max(L.ny, L.nz));
+    SG_TRY(ensure_sched(g, accelerated_schedule(N, g->opt.coarse_max_ss)));
+    if (dtype == 0) SG_TRY(coarse_solve<double>(g, level, (const double*)rhs, (double*)u_out, g->d_ss));
+    else SG_TRY(coarse_solve<float>(g, level, (const float*)rhs, (float*)u_out, g->d_ss));
+    if (ss_done) {
+        SG_CK(cudaMemcpyAsync(g->host_ss, g->d_ss, sizeof(int), cudaMemcpyDeviceToHost, g->st));
+        SG_CK(cudaStreamSynchronize(g->st));
+        *ss_done = *g->host_ss;
+    }
+    return SG_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,110 @@
+// Internal declarations shared by the CUDA kernels and the host orchestration.
+// Nothing here is part of the C ABI (include/sg.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstddef>
+
+namespace sg {
+
+// Geometry and boundary description of one multigrid level.  Arrays are dense
+// [nz][ny][nx] (x fastest) without ghost cells; the ghost values of Sec. 2.3 are
+// produced on the fly by the kernels:
+//   periodic axis           -> the cell on the opposite side (Eq. periodic)
+//   Dirichlet with faces    -> 2 * face - active              (Eq. solution_ghost)
+//   Dirichlet without faces -> -active                        (Eq. error_ghost)
+struct LevelGeom {
+    int nx, ny, nz;
+    double ihx2, ihy2, ihz2;          // 1 / h_d^2
+    int per[3];                       // periodic flag per axis (x, y, z)
+    const double* face[6];            // -x,+x,-y,+y,-z,+z or all nullptr (homogeneous)
+};
+
+// Per-stage coefficients of one RKL stage (App. A, Eq. RKL_intermediate_source).
+//   first stage : z = tau (L Y0 - f);  Y1 = Y0 + mut1 * z;   (RKL2 stores z as Z0)
+//   later stages: Yj = mu Y_{j-1} + nu Y_{j-2} + mut_tau (L Y_{j-1} - f)
+//                      [RKL2: + c0 Y0 + gt Z0]
+struct StageCoef {
+    double tau;       // first stage only
+    double mut1;      // first stage only: mu~_1
+    double mu, nu;
+    double mut_tau;   // mu~_j * tau
+    double c0;        // 1 - mu_j - nu_j (RKL2)
+    double gt;        // gamma~_j (RKL2; multiplies Z0 = tau (M Y0 - f))
+};
+
+// Deterministic two-pass reductions: kernels write one Partial per block, a
+// single-block kernel folds them in a fixed order into a Reduced.
+struct Partial {
+    double sumsq;     // sum of r^2
+    double maxabs;    // max |r|
+    double sum;       // sum of a secondary field (coarse rhs for the periodic mean)
+    double pad;
+};
+struct Reduced {
+    double sumsq, maxabs, sum, count;
+};
+
+constexpr int kRedThreads = 256;
+
+// ---- launchers (kernels_stencil.cu) ----------------------------------------
+// Number of blocks (= Partial slots) a residual / residual-restrict launch uses.
+long long residual_blocks(const LevelGeom& g);
+long long restrict_blocks(const LevelGeom& g);
+constexpr long long kSumBlocks = 152LL * 8;     // grid of the 1D reduction kernels
+
+template <typename T>
+cudaError_t launch_stage(const LevelGeom& g, int order, bool first, const StageCoef& c,
+                         const T* ym1, const T* ym2, const T* y0, const T* z0, const T* rhs,
+                         T* out, T* z0_out, cudaStream_t st);
+
+// r = rhs - L u (TI), optionally stored as TO, block partials of sum r^2 / max|r|.
+template <typename TI, typename TO>
+cudaError_t launch_residual(const LevelGeom& g, const TI* u, const TI* rhs, TO* r_out,
+                            Partial* partials, int* nblocks_out, cudaStream_t st);
+
+// Fused residual + 8-cell restriction (+ norm partials, + coarse sum partials).
+template <typename T>
+cudaError_t launch_residual_restrict(const LevelGeom& fine, const T* u, const T* rhs,
+                                     T* coarse_out, Partial* partials, int* nblocks_out,
+                                     cudaStream_t st);
+
+// fine += P(coarse) with coarse ghosts by the homogeneous/periodic rule.
+template <typename T>
+cudaError_t launch_prolong_correct(const LevelGeom& fine, const T* coarse, T* fine_u,
+                                   cudaStream_t st);
+
+cudaError_t launch_finalize(const Partial* partials, int n, Reduced* out, cudaStream_t st);
+
+template <typename T>
+cudaError_t launch_subtract_mean(T* x, long long n, const Reduced* red, cudaStream_t st);
+
+cudaError_t launch_scale_copy(const double* src, double* dst, double scale, long long n,
+                              cudaStream_t st);
+cudaError_t launch_add_f32_to_f64(double* phi, const float* e, long long n, cudaStream_t st);
+cudaError_t launch_sub_mean_f64(double* x, long long n, const Reduced* red, cudaStream_t st);
+cudaError_t launch_sum_partials_f64(const double* x, long long n, Partial* partials,
+                                    int* nblocks_out, cudaStream_t st);
+
+// ---- coarsest-level solver (kernels_coarse.cu) -----------------------------
+struct CoarseParams {
+    LevelGeom g;          // homogeneous
+    const void* rhs;      // level rhs (T)
+    void* u_out;          // result (T)
+    const int* sched;     // s per super-step
+    int max_ss;
+    double tol;           // relative residual stop, 0 = fixed count
+    double tau_unit;      // tau_frac * 2 / lambda_max (mu~_j tau = mu_j * tau_unit)
+    int* ss_done;         // device int
+};
+template <typename T>
+size_t coarse_smem_bytes(long long n);
+template <typename T>
+bool coarse_fits(long long n);
+template <typename T>
+cudaError_t launch_coarse_solve(const CoarseParams& p, cudaStream_t st);
+// Raise the dynamic shared-memory limit of the coarse kernels (once per process).
+cudaError_t coarse_configure();
+
+}  // namespace sg

@@ -1,0 +1,159 @@
+"""GPU parity of every single operator against the FP64 oracle, element by
+element, on seeded inputs with ragged tiles (sizes not multiples of the
+32 x 8 thread tile) and every boundary kind.  All calls go through the C ABI
+(sg_op_*).
+
+Tolerances: FP64 kernels agree with the oracle to 1e-12 relative (max-norm of
+the difference over max-norm of the result; only the rounding order differs).
+FP32 kernels (the mixed-precision inner cycle) agree to 2e-5 relative, a few
+hundred FP32 ulps after the cancellation of the 7-point stencil.
+"""
+
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-12
+TOL32 = 2e-5
+
+SHAPES_BC = [((20, 12, 36), (0, 0, 0)), ((16, 24, 8), (1, 1, 1)), ((12, 20, 40), (1, 0, 1)),
+             ((8, 36, 12), (0, 1, 0))]
+
+
+def _sg():
+    import paper_2306_05332_gb300 as sg
+    return sg
+
+
+def dev(a, dtype=torch.float64):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=dtype, device="cuda")
+
+
+def relerr(a, b):
+    a = a.detach().cpu().numpy() if isinstance(a, torch.Tensor) else a
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+def make_grid(shape, bc, precision, faces_seed=5):
+    sg = _sg()
+    lo, hi = (0.0, -0.5, 0.25), (1.3, 0.2, 1.35)
+    g = sg.Grid(shape, lo, hi, bc, precision=precision)
+    faces = None
+    if any(b == 0 for b in bc):
+        faces = W.random_faces(shape, faces_seed)
+        g.set_boundary(faces)
+    return g, O.spacing(shape, lo, hi), faces
+
+
+@pytest.mark.parametrize("shape,bc", SHAPES_BC)
+@pytest.mark.parametrize("order,s,c", [(1, 1, 1.0), (1, 4, 0.8), (2, 2, 1.0), (2, 3, 1.0), (2, 6, 0.9)])
+def test_superstep_fp64(shape, bc, order, s, c):
+    g, h, faces = make_grid(shape, bc, "fp64")
+    u, rhs = W.random_field(shape, 6), 50.0 * W.random_field(shape, 7)
+    out = torch.empty(shape, dtype=torch.float64, device="cuda")
+    g.op_superstep(0, order, s, c, dev(u), dev(rhs), out)
+    torch.cuda.synchronize()
+    ref = O.rkl_superstep(u, rhs, h, bc, faces, order, s, c)
+    assert relerr(out, ref) < TOL64
+
+
+@pytest.mark.parametrize("shape,bc", SHAPES_BC[:2])
+@pytest.mark.parametrize("order,s,c", [(1, 2, 0.75), (2, 3, 1.0), (2, 5, 1.0)])
+def test_superstep_fp32_homogeneous(shape, bc, order, s, c):
+    g, h, _ = make_grid(shape, bc, "mixed")
+    u, rhs = W.random_field(shape, 8), 50.0 * W.random_field(shape, 9)
+    out = torch.empty(shape, dtype=torch.float32, device="cuda")
+    g.op_superstep(0, order, s, c, dev(u, torch.float32), dev(rhs, torch.float32), out, homogeneous=True)
+    torch.cuda.synchronize()
+    u32 = u.astype(np.float32).astype(np.float64)
+    r32 = rhs.astype(np.float32).astype(np.float64)
+    ref = O.rkl_superstep(u32, r32, h, bc, None, order, s, c)
+    assert relerr(out.double(), ref) < TOL32
+
+
+@pytest.mark.parametrize("shape,bc", SHAPES_BC)
+def test_residual_restrict_fp64(shape, bc):
+    g, h, faces = make_grid(shape, bc, "fp64")
+    u, rhs = W.random_field(shape, 10), W.random_field(shape, 11)
+    coarse = torch.empty(tuple(n // 2 for n in shape), dtype=torch.float64, device="cuda")
+    sumsq, mx = g.op_residual_restrict(0, dev(u), dev(rhs), coarse)
+    r_paper = O.residual(u, rhs, h, bc, faces)          # L u - f
+    ref = O.restrict(-r_paper)                            # the kernel restricts f - L u
+    assert relerr(coarse, ref) < TOL64
+    assert abs(sumsq - np.sum(r_paper ** 2)) <= 1e-12 * np.sum(r_paper ** 2)
+    assert abs(mx - np.max(np.abs(r_paper))) <= 1e-12 * np.max(np.abs(r_paper))
+    # norm only (no restriction) at a coarser, homogeneous level
+    u1 = W.random_field(coarse.shape, 12)
+    r1 = W.random_field(coarse.shape, 13)
+    sumsq1, mx1 = g.op_residual_restrict(1, dev(u1), dev(r1), None)
+    h1 = tuple(2 * x for x in h)
+    rr = O.residual(u1, r1, h1, bc, None)
+    assert abs(sumsq1 - np.sum(rr ** 2)) <= 1e-12 * np.sum(rr ** 2)
+
+
+@pytest.mark.parametrize("shape,bc", SHAPES_BC[:2])
+def test_residual_restrict_fp32(shape, bc):
+    g, h, _ = make_grid(shape, bc, "mixed")
+    u, rhs = W.random_field(shape, 14), W.random_field(shape, 15)
+    coarse = torch.empty(tuple(n // 2 for n in shape), dtype=torch.float32, device="cuda")
+    g.op_residual_restrict(0, dev(u, torch.float32), dev(rhs, torch.float32), coarse, homogeneous=True)
+    u32 = u.astype(np.float32).astype(np.float64)
+    r32 = rhs.astype(np.float32).astype(np.float64)
+    ref = O.restrict(-O.residual(u32, r32, h, bc, None))
+    assert relerr(coarse.double(), ref) < TOL32
+
+
+@pytest.mark.parametrize("shape,bc", SHAPES_BC)
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_prolong_correct(shape, bc, precision):
+    g, h, _ = make_grid(shape, bc, precision)
+    dt = torch.float64 if precision == "fp64" else torch.float32
+    fine0 = W.random_field(shape, 16)
+    coarse = W.random_field(tuple(n // 2 for n in shape), 17)
+    fine = dev(fine0, dt)
+    g.op_prolong_correct(0, dev(coarse, dt), fine)
+    torch.cuda.synchronize()
+    if precision == "mixed":
+        fine0 = fine0.astype(np.float32).astype(np.float64)
+        coarse = coarse.astype(np.float32).astype(np.float64)
+    ref = fine0 + O.prolong(coarse, bc)
+    assert relerr(fine.double(), ref) < (TOL64 if precision == "fp64" else 1e-6)
+
+
+@pytest.mark.parametrize("shape,bc,level", [((32, 32, 32), (0, 0, 0), 2), ((32, 16, 64), (1, 1, 1), 2),
+                                            ((16, 16, 16), (0, 0, 0), 1)])
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_coarse_solve_fixed_count(shape, bc, level, precision):
+    g, h, _ = make_grid(shape, bc, precision)
+    g.set_options(coarse_tol=0.0, coarse_max_ss=9)
+    cshape = tuple(n >> level for n in shape)
+    hl = tuple(x * 2 ** level for x in h)
+    rhs = W.random_field(cshape, 18)
+    if all(b == 1 for b in bc):
+        rhs -= rhs.mean()
+    dt = torch.float64 if precision == "fp64" else torch.float32
+    out = torch.empty(cshape, dtype=dt, device="cuda")
+    done = g.op_coarse_solve(level, dev(rhs, dt), out)
+    assert done == 9
+    opts = O.Options(coarse_tol=0.0, coarse_max_ss=9)
+    ref = O.coarse_solve(rhs.astype(np.float32).astype(np.float64) if precision == "mixed" else rhs,
+                         hl, bc, None, opts)
+    assert relerr(out.double(), ref) < (1e-11 if precision == "fp64" else 1e-4)
+
+
+def test_coarse_solve_tolerance_stop():
+    g, h, _ = make_grid((16, 16, 16), (0, 0, 0), "fp64")
+    g.set_options(coarse_tol=1e-6, coarse_max_ss=200)
+    rhs = W.random_field((8, 8, 8), 19)
+    out = torch.empty((8, 8, 8), dtype=torch.float64, device="cuda")
+    done = g.op_coarse_solve(1, dev(rhs), out)
+    rec = []
+    ref = O.coarse_solve(rhs, tuple(2 * x for x in h), (0, 0, 0), None,
+                         O.Options(coarse_tol=1e-6, coarse_max_ss=200), record=rec)
+    assert done == rec[0]
+    assert relerr(out, ref) < 1e-11

@@ -1,0 +1,226 @@
+"""GPU parity of whole solves (sg_solve / sg_backward / sg_solve_batch) with
+the FP64 oracle.
+
+* FP64 path: same cycle count and options as the oracle, coarsest solve with a
+  fixed super-step count, potential within 1e-12 relative L2 of the oracle.
+* Mixed path (FP32 V-cycle inside FP64 defect correction): solved to a tight
+  residual, potential within 1e-8 relative L2 of the oracle's converged FP64
+  solution.
+* Full size (256^3 sphere, five levels): the residual of the GPU potential,
+  recomputed by the oracle on the CPU in FP64, meets the tolerance.
+"""
+
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _sg():
+    import paper_2306_05332_gb300 as sg
+    return sg
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def grid_for(p, precision, **opts):
+    sg = _sg()
+    g = sg.Grid(p.shape, p.lo, p.hi, p.bc, precision=precision)
+    if p.faces is not None:
+        g.set_boundary(p.faces)
+    g.set_density(p.rho, p.four_pi_G)
+    if opts:
+        g.set_options(**opts)
+    return g
+
+
+def test_sinusoid_single_level_rkl1_closed_form():
+    # 32^3 sinusoid, single-level RKL1, s = 24 from dt_par = h^2/6, to 1e-10.
+    p = W.sinusoid(32)
+    g = grid_for(p, "fp64", single_tau_frac=1.0)
+    info = g.solve(tol=1e-10, s=24, levels=1)
+    phi = g.potential()
+    assert info["cycles"] == 3
+    opts = O.Options(single_s=24, single_tau_frac=1.0)
+    ref, rinfo = O.solve(p.rho, p.lo, p.hi, p.bc, None, 1.0, tol=1e-10, levels=1, opts=opts)
+    assert rinfo.cycles == 3
+    assert rel_l2(phi, ref) < 1e-12
+    h = 1.0 / 32
+    lam = -(12.0 / h ** 2) * math.sin(math.pi * h / 2) ** 2
+    exact = p.rho / lam
+    g24 = float(O.legendre(24, math.cos(math.pi / 32)))
+    np.testing.assert_allclose(phi - exact, -(g24 ** 3) * exact, atol=1e-13 * np.abs(exact).max())
+    # relative residuals agree to rounding of the FP64 residual (~1e-15 of r0)
+    np.testing.assert_allclose(info["history"], rinfo.history, rtol=1e-9, atol=1e-14)
+
+
+@pytest.mark.parametrize("order,s,c", [(2, 3, 1.0), (1, 2, 0.75)])
+def test_sphere_fp64_fixed_cycles_match_oracle(order, s, c):
+    p = W.sphere(64)
+    kw = dict(rkl_order=order, s_smooth=s, tau_frac=c, coarse_tol=0.0, coarse_max_ss=12, fixed_cycles=5)
+    g = grid_for(p, "fp64", **kw)
+    info = g.solve(tol=0.0, levels=4)
+    phi = g.potential()
+    opts = O.Options(rkl_order=order, s_smooth=s, tau_frac=c, coarse_tol=0.0, coarse_max_ss=12)
+    ref, rinfo = O.solve(p.rho, p.lo, p.hi, p.bc, p.faces, 1.0, levels=4, opts=opts, cycles=5)
+    assert info["cycles"] == 5 and info["levels"] == 4
+    assert rel_l2(phi, ref) < 1e-12
+    np.testing.assert_allclose(info["history"], rinfo.history, rtol=1e-9, atol=1e-14)
+
+
+def test_sphere_fp64_tolerance_stop_matches_oracle():
+    p = W.sphere(64)
+    g = grid_for(p, "fp64")
+    info = g.solve(tol=1e-9, levels=4)
+    phi = g.potential()
+    ref, rinfo = O.solve(p.rho, p.lo, p.hi, p.bc, p.faces, 1.0, tol=1e-9, levels=4, opts=O.Options())
+    assert info["cycles"] == rinfo.cycles
+    assert info["coarse_ss"] == rinfo.coarse_ss
+    assert rel_l2(phi, ref) < 1e-12
+
+
+@pytest.mark.parametrize("order,s,c", [(2, 3, 1.0), (1, 2, 0.75)])
+def test_sphere_mixed_refined_matches_oracle(order, s, c):
+    p = W.sphere(64)
+    g = grid_for(p, "mixed", rkl_order=order, s_smooth=s, tau_frac=c)
+    info = g.solve(tol=1e-11, levels=4)
+    phi = g.potential()
+    assert info["rel_residual"] <= 1e-11
+    opts = O.Options(rkl_order=order, s_smooth=s, tau_frac=c)
+    ref, _ = O.solve(p.rho, p.lo, p.hi, p.bc, p.faces, 1.0, tol=1e-13, levels=4, opts=opts)
+    assert rel_l2(phi, ref) < 1e-8
+    # the oracle's own residual of the GPU potential
+    h = O.spacing(p.shape, p.lo, p.hi)
+    r = O.residual(phi, O.source(p.rho, 1.0, p.bc), h, p.bc, p.faces)
+    r0 = O.l2norm(O.residual(np.zeros(p.shape), O.source(p.rho, 1.0, p.bc), h, p.bc, p.faces))
+    assert O.l2norm(r) / r0 <= 1.01e-11
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_periodic_grf(precision):
+    p = W.grf(32, seed=4)
+    p.rho = p.rho + 1.5
+    if precision == "fp64":
+        g = grid_for(p, precision, coarse_tol=0.0, coarse_max_ss=10, fixed_cycles=6)
+        g.solve(tol=0.0)
+        phi = g.potential()
+        ref, _ = O.solve(p.rho, p.lo, p.hi, p.bc, None, 1.0, opts=O.Options(coarse_tol=0.0, coarse_max_ss=10),
+                         cycles=6)
+        assert rel_l2(phi, ref) < 1e-12
+    else:
+        g = grid_for(p, precision)
+        g.solve(tol=1e-11)
+        phi = g.potential()
+        ref, _ = O.solve(p.rho, p.lo, p.hi, p.bc, None, 1.0, tol=1e-13)
+        assert rel_l2(phi, ref) < 1e-8
+    assert abs(phi.mean()) < 1e-12 * np.abs(phi).max()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_anisotropic_mixed_boundaries(precision):
+    shape, lo, hi, bc = (16, 32, 24), (0.0, 0.0, 0.0), (1.5, 2.0, 1.0), (1, 0, 0)
+    rho = W.random_field(shape, 51)
+    faces = W.random_faces(shape, 52)
+    p = W.Problem(rho=rho, lo=lo, hi=hi, bc=bc, faces=faces, four_pi_G=2.0)
+    g = grid_for(p, precision)
+    info = g.solve(tol=1e-11)
+    phi = g.potential()
+    ref, rinfo = O.solve(rho, lo, hi, bc, faces, 2.0, tol=1e-13)
+    assert info["levels"] == rinfo.levels == 3
+    assert rel_l2(phi, ref) < (1e-10 if precision == "fp64" else 1e-8)
+
+
+def test_full_size_sphere_256_mixed_five_levels():
+    p = W.sphere(256)
+    g = grid_for(p, "mixed")
+    info = g.solve(tol=1e-8, levels=5)
+    phi = g.potential()
+    assert info["levels"] == 5 and info["rel_residual"] <= 1e-8
+    h = O.spacing(p.shape, p.lo, p.hi)
+    f = O.source(p.rho, 1.0, p.bc)
+    r = O.residual(phi, f, h, p.bc, p.faces)
+    r0 = O.l2norm(O.residual(np.zeros(p.shape), f, h, p.bc, p.faces))
+    assert O.l2norm(r) / r0 <= 1.01e-8
+    # second-order discretisation error against the analytic sphere, away from the surface
+    X, Y, Z = W.mesh(p.shape, p.lo, p.hi)
+    rr = np.sqrt(X * X + Y * Y + Z * Z)
+    far = rr > 0.5
+    assert np.max(np.abs(phi - p.exact)[far]) < 2e-3 * np.max(np.abs(p.exact))
+
+
+def test_adjoint_matches_oracle_and_finite_differences():
+    shape, lo, hi, bc = (16, 16, 16), (0, 0, 0), (1, 1, 1), (0, 0, 0)
+    rho = W.random_field(shape, 61)
+    faces = W.random_faces(shape, 62)
+    w = W.loss_weights(shape, 63)
+    p = W.Problem(rho=rho, lo=lo, hi=hi, bc=bc, faces=faces, four_pi_G=3.0)
+    g = grid_for(p, "fp64")
+    g.solve(tol=1e-13)
+    grad, info = g.backward(w, tol=1e-13)
+    ref, _ = O.adjoint(w, lo, hi, bc, four_pi_G=3.0, tol=1e-13)
+    assert rel_l2(grad, ref) < 1e-10
+    eps = 1e-3
+    for cell in W.sample_cells(shape, 4, 64):
+        vals = []
+        for sgn in (1, -1):
+            r2 = rho.copy()
+            r2[cell] += sgn * eps
+            g.set_density(r2, 3.0)
+            g.solve(tol=1e-13)
+            vals.append(np.sum(w * g.potential()))
+        fd = (vals[0] - vals[1]) / (2 * eps)
+        assert abs(fd - grad[cell]) <= 1e-7 * max(1.0, abs(fd))
+
+
+def test_autograd_function():
+    shape, lo, hi = (16, 16, 16), (0, 0, 0), (1, 1, 1)
+    sg = _sg()
+    g = sg.Grid(shape, lo, hi, (0, 0, 0), precision="mixed")
+    g.set_boundary(W.random_faces(shape, 71))
+    g.four_pi_G = 1.0
+    rho = torch.tensor(W.random_field(shape, 72), device="cuda", requires_grad=True)
+    w = torch.tensor(W.loss_weights(shape, 73), device="cuda")
+    phi = sg.solve(rho, g, 1e-11)
+    (w * phi).sum().backward()
+    ref, _ = O.adjoint(w.cpu().numpy(), lo, hi, (0, 0, 0), four_pi_G=1.0, tol=1e-13)
+    assert rel_l2(rho.grad.cpu().numpy(), ref) < 1e-8
+
+
+def test_batch_equals_individual_solves():
+    sg = _sg()
+    probs = [W.blobs(n, np.random.default_rng(n)) for n in (32, 64, 32)]
+    grids = [grid_for(p, "mixed") for p in probs]
+    infos = sg.solve_batch(grids, tol=1e-10)
+    for p, g, info in zip(probs, grids, infos):
+        assert info["rel_residual"] <= 1e-10
+        ref, _ = O.solve(p.rho, p.lo, p.hi, p.bc, p.faces, 1.0, tol=1e-13)
+        assert rel_l2(g.potential(), ref) < 1e-8
+
+
+def test_errors_are_reported():
+    sg = _sg()
+    p = W.sphere(32)
+    g = grid_for(p, "fp64")
+    with pytest.raises(sg.SGError) as e:
+        g.solve(tol=1e-8, levels=g.max_levels + 1)
+    assert e.value.status == 1
+    g.set_options(max_cycles=2)
+    info = g.solve(tol=1e-14, check=False)
+    assert info["status"] == "SG_ERR_NOT_CONVERGED" and info["cycles"] == 2
+    bad = p.rho.copy()
+    bad[3, 3, 3] = np.nan
+    g.set_density(bad, 1.0)
+    info = g.solve(tol=1e-8, check=False)
+    assert info["status"] == "SG_ERR_NONFINITE"
+    g2 = sg.Grid((8, 8, 8), precision="mixed")
+    with pytest.raises(sg.SGError) as e:
+        g2.potential()
+    assert e.value.status == 7
