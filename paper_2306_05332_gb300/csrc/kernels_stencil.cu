@@ -167,11 +167,13 @@ __device__ __forceinline__ void block_reduce_write(double sumsq, double maxabs, 
 // ---------------------------------------------------------------------------
 // Residual r = rhs - L u (standard sign; the paper's Eq. residual is -r).
 // ---------------------------------------------------------------------------
-template <typename TI, typename TO>
+template <typename TI, typename TO, bool UNIFORM>
 __global__ void __launch_bounds__(BX * BY)
 k_residual(const LevelGeom g, const TI* __restrict__ u, const TI* __restrict__ rhs, TO* r_out,
            Partial* partials, int kchunk) {
-    using A = typename Acc<TI>::type;
+    // Norms accumulate in the output precision: an FP32 residual needs no FP64
+    // arithmetic beyond the stencil itself (FP64 issue rate is the limit on GB300).
+    using A = typename Acc<TO>::type;
     const int i = blockIdx.x * BX + threadIdx.x;
     const int j = blockIdx.y * BY + threadIdx.y;
     A sq = A(0), mx = A(0);
@@ -181,16 +183,26 @@ k_residual(const LevelGeom g, const TI* __restrict__ u, const TI* __restrict__ r
         const long long plane = (long long)g.nx * g.ny;
         long long idx = (long long)k0 * plane + (long long)j * g.nx + i;
         const TI ihx2 = TI(g.ihx2), ihy2 = TI(g.ihy2), ihz2 = TI(g.ihz2);
+        const TI six = TI(-6), neg_ih2 = -ihx2;
         TI c = u[idx];
         TI zm = (k0 > 0) ? u[idx - plane] : z_low(u, g, i, j, idx, plane, c);
         for (int k = k0; k < k1; ++k, idx += plane) {
             const TI zp = (k < g.nz - 1) ? u[idx + plane] : z_high(u, g, i, j, idx, plane, c);
             TI xm, xp, ym, yp;
             xy_neighbours(u, g, i, j, k, idx, c, xm, xp, ym, yp);
-            const TI r = rhs[idx] - lap7(c, xm, xp, ym, yp, zm, zp, ihx2, ihy2, ihz2);
-            if (r_out) r_out[idx] = TO(r);
-            const A ra = A(r);
-            sq += ra * ra;
+            TI r;
+            if (UNIFORM) {
+                // h equal on all axes: r = f - (sum of 6 neighbours - 6 c) / h^2,
+                // 5 adds and 2 fused multiply-adds.
+                const TI s6 = ((xm + xp) + (ym + yp)) + (zm + zp);
+                r = fma(neg_ih2, fma(six, c, s6), rhs[idx]);
+            } else {
+                r = rhs[idx] - lap7(c, xm, xp, ym, yp, zm, zp, ihx2, ihy2, ihz2);
+            }
+            const TO ro = TO(r);
+            if (r_out) r_out[idx] = ro;
+            const A ra = A(ro);
+            sq = fma(ra, ra, sq);
             mx = fmax(mx, fabs(ra));
             zm = c;
             c = zp;
@@ -386,7 +398,9 @@ cudaError_t launch_residual(const LevelGeom& g, const TI* u, const TI* rhs, TO* 
     const int kc = kchunk_for(g, BX, BY);
     dim3 block(BX, BY, 1);
     dim3 grid((g.nx + BX - 1) / BX, (g.ny + BY - 1) / BY, (g.nz + kc - 1) / kc);
-    k_residual<TI, TO><<<grid, block, 0, st>>>(g, u, rhs, r_out, partials, kc);
+    const bool uniform = g.ihx2 == g.ihy2 && g.ihy2 == g.ihz2;
+    if (uniform) k_residual<TI, TO, true><<<grid, block, 0, st>>>(g, u, rhs, r_out, partials, kc);
+    else k_residual<TI, TO, false><<<grid, block, 0, st>>>(g, u, rhs, r_out, partials, kc);
     if (nblocks_out) *nblocks_out = (int)(grid.x * grid.y * grid.z);
     return cudaGetLastError();
 }

@@ -242,18 +242,23 @@ struct ProfScope {
     sg_grid* g;
     ProfRec rec;
     bool on;
+    // During stream capture an event record must be marked external to become
+    // an event node of the graph (outside capture the flag is not allowed).
+    void record(cudaEvent_t e) {
+        if (g->capturing) cudaEventRecordWithFlags(e, g->st, cudaEventRecordExternal);
+        else cudaEventRecord(e, g->st);
+    }
     ProfScope(sg_grid* g_, int cls, double bytes) : g(g_), on(g_->prof) {
         if (!on) return;
         rec.cls = cls;
         rec.bytes = bytes;
         rec.a = take_event(g);
         rec.b = take_event(g);
-        // External records become event nodes when the stream is being captured.
-        cudaEventRecordWithFlags(rec.a, g->st, cudaEventRecordExternal);
+        record(rec.a);
     }
     ~ProfScope() {
         if (!on) return;
-        cudaEventRecordWithFlags(rec.b, g->st, cudaEventRecordExternal);
+        record(rec.b);
         g->live.push_back(rec);
     }
 };
@@ -528,7 +533,9 @@ sg_status run_cycle(sg_grid* g, int L, double* phi, const double* f, bool faces,
         SG_CK(cudaStreamBeginCapture(g->st, cudaStreamCaptureModeThreadLocal));
         std::vector<ProfRec> outside;
         outside.swap(g->live);
+        g->capturing = true;
         sg_status s = cycle_body(g, L, phi, f, faces);
+        g->capturing = false;
         cudaError_t ec = cudaStreamEndCapture(g->st, &graph);
         g->live.swap(outside);          // g->live: records enqueued before the capture
         if (s != SG_OK) {

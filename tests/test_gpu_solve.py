@@ -224,3 +224,19 @@ def test_errors_are_reported():
     with pytest.raises(sg.SGError) as e:
         g2.potential()
     assert e.value.status == 7
+
+
+def test_kernel_profile_counts_every_class():
+    p = W.sphere(64)
+    g = grid_for(p, "mixed")
+    g.set_profiling(True)
+    info = g.solve(tol=1e-8, levels=4)
+    st = g.kernel_stats()
+    g.set_profiling(False)
+    for name in ("rkl_stage_l0", "rkl_stage_coarse", "residual_l0", "residual_restrict",
+                 "prolong_correct", "coarse_solve", "update"):
+        assert st[name]["launches"] > 0 and st[name]["ms"] > 0, name
+    # one residual per cycle plus the initial one; three restrictions per cycle (4 levels)
+    assert st["residual_l0"]["launches"] == info["cycles"] + 1
+    assert st["residual_restrict"]["launches"] == 3 * info["cycles"]
+    assert st["residual_l0"]["bytes"] == 20.0 * 64 ** 3 * (info["cycles"] + 1)
