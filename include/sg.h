@@ -71,7 +71,7 @@ typedef struct sg_options {
     int    n_pre;           /* smoothing super-steps on the way down (Sec. 4.1)     [2]  */
     int    n_post;          /* smoothing super-steps on the way up                  [1]  */
     double coarse_tol;      /* coarsest solve: stop at this relative residual;
-                               0 runs exactly coarse_max_ss super-steps             [1e-3]*/
+                               0 runs exactly coarse_max_ss super-steps             [1e-2]*/
     int    coarse_max_ss;   /* coarsest solve: cap on super-steps                   [64] */
     double coarse_tau_frac; /* coarsest solve tau / tau_max; 0 = cos^2(pi / 2N)     [0]  */
     int    max_cycles;      /* V-cycle (or single-level super-step) cap             [100]*/

@@ -419,7 +419,7 @@ class Options:
     tau_frac: float = 1.0      # smoother tau / tau_max
     n_pre: int = 2             # Sec. 4.1: N_pre = 2, N_post = 1
     n_post: int = 1
-    coarse_tol: float = 1e-3   # coarsest-level relative residual target (0 = fixed count)
+    coarse_tol: float = 1e-2   # coarsest-level relative residual target (0 = fixed count)
     coarse_max_ss: int = 64    # cap on coarsest-level super-steps
     coarse_tau_frac: float = 0.0   # 0 = coarse_tau_frac(N)
     max_cycles: int = 100

@@ -290,9 +290,11 @@ class Grid:
         return 0 if self.precision == FP64 else 1
 
     def op_superstep(self, level, order, s, tau_frac, u, rhs, out, homogeneous=False):
+        """out = one RKL super-step from u (None: u = 0, fused FP32 path only)."""
         dt = self.dtype_code
         _check(lib().sg_op_superstep(self._h, level, dt, order, s, float(tau_frac), int(homogeneous),
-                                     _dev_ptr(u, dt), _dev_ptr(rhs, dt), _dev_ptr(out, dt)))
+                                     _dev_ptr(u, dt) if u is not None else None, _dev_ptr(rhs, dt),
+                                     _dev_ptr(out, dt)))
 
     def op_residual_restrict(self, level, u, rhs, coarse_out=None, homogeneous=False):
         dt = self.dtype_code

@@ -51,7 +51,11 @@ __device__ T block_sum(T v, T* scratch) {
     return r;
 }
 
-template <typename T>
+// At most kMaxCells cells per thread: the level fits shared memory, so
+// n <= kSmemLimit / (4 sizeof(float)) < kMaxCells * kCoarseThreads.
+constexpr int kMaxCells = 16;
+
+template <typename T, int MAXC>
 __global__ void __launch_bounds__(kCoarseThreads) k_coarse_solve(const CoarseParams p) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ T red[33];
@@ -60,8 +64,19 @@ __global__ void __launch_bounds__(kCoarseThreads) k_coarse_solve(const CoarsePar
     T* f = reinterpret_cast<T*>(smem_raw);
     T* buf[3] = {f + n, f + 2 * n, f + 3 * n};
     const T* rhs = static_cast<const T*>(p.rhs);
-    const T ihx2 = T(p.g.ihx2), ihy2 = T(p.g.ihy2), ihz2 = T(p.g.ihz2);
+    const T ihx2 = ih2x<T>(p.g), ihy2 = ih2y<T>(p.g), ihz2 = ih2z<T>(p.g);
     int per[3] = {p.g.per[0], p.g.per[1], p.g.per[2]};
+
+    // this thread's cells t = tid + m * blockDim, coordinates packed once
+    int cell[MAXC];
+#pragma unroll
+    for (int m = 0; m < MAXC; ++m) {
+        const int t = threadIdx.x + m * blockDim.x;
+        cell[m] = t < n ? ((t % nx) | (((t / nx) % ny) << 10) | ((t / (nx * ny)) << 20)) : -1;
+    }
+    auto lap = [&](const T* y, int c) {
+        return lap_smem(y, nx, ny, nz, per, ihx2, ihy2, ihz2, c & 1023, (c >> 10) & 1023, c >> 20);
+    };
 
     T local = T(0);
     for (int t = threadIdx.x; t < n; t += blockDim.x) {
@@ -72,16 +87,20 @@ __global__ void __launch_bounds__(kCoarseThreads) k_coarse_solve(const CoarsePar
     }
     __syncthreads();
     const T r0sq = block_sum(local, red);         // ||f - L 0||^2 with homogeneous ghosts
-    const T tolsq = T(p.tol) * T(p.tol) * r0sq;
+    const T tol = T(p.tol);                       // converted once; kept in a register
+    const T tau_unit_t = T(p.tau_unit);
+    const T tolsq = tol * tol * r0sq;
 
     int cur = 0;
     int done = 0;
     for (int ss = 0; ss < p.max_ss; ++ss) {
-        if (p.tol > 0.0) {
+        if (tol > T(0)) {
             T acc = T(0);
-            for (int t = threadIdx.x; t < n; t += blockDim.x) {
-                const int i = t % nx, j = (t / nx) % ny, k = t / (nx * ny);
-                const T r = f[t] - lap_smem(buf[cur], nx, ny, nz, per, ihx2, ihy2, ihz2, i, j, k);
+#pragma unroll
+            for (int m = 0; m < MAXC; ++m) {
+                if (cell[m] < 0) break;
+                const int t = threadIdx.x + m * blockDim.x;
+                const T r = f[t] - lap(buf[cur], cell[m]);
                 acc += r * r;
             }
             const T rsq = block_sum(acc, red);
@@ -91,16 +110,20 @@ __global__ void __launch_bounds__(kCoarseThreads) k_coarse_solve(const CoarsePar
         int prev = -1;
         for (int jst = 1; jst <= s; ++jst) {
             const int nxt = (cur + 1) % 3 == prev ? (cur + 2) % 3 : (cur + 1) % 3;
-            const T mu = T((2.0 * jst - 1.0) / jst);
-            const T nu = T((1.0 - jst) / jst);
-            const T mut = T((2.0 * jst - 1.0) / jst * p.tau_unit);
+            // coefficients in the kernel's precision (FP64 issue is 1/64 of FP32 on GB300)
+            const T mu = (T(2) * T(jst) - T(1)) / T(jst);
+            const T nu = (T(1) - T(jst)) / T(jst);
+            const T tu = tau_unit_t;
+            const T mut = mu * tu;
             const T* yc = buf[cur];
             const T* yp = prev >= 0 ? buf[prev] : buf[cur];
             T* yn = buf[nxt];
-            for (int t = threadIdx.x; t < n; t += blockDim.x) {
-                const int i = t % nx, j = (t / nx) % ny, k = t / (nx * ny);
-                const T Lf = lap_smem(yc, nx, ny, nz, per, ihx2, ihy2, ihz2, i, j, k) - f[t];
-                if (jst == 1) yn[t] = yc[t] + T(p.tau_unit) * Lf;
+#pragma unroll
+            for (int m = 0; m < MAXC; ++m) {
+                if (cell[m] < 0) break;
+                const int t = threadIdx.x + m * blockDim.x;
+                const T Lf = lap(yc, cell[m]) - f[t];
+                if (jst == 1) yn[t] = yc[t] + tu * Lf;
                 else yn[t] = mu * yc[t] + nu * yp[t] + mut * Lf;
             }
             __syncthreads();
@@ -123,7 +146,8 @@ size_t coarse_smem_bytes(long long n) {
 
 template <typename T>
 bool coarse_fits(long long n) {
-    return coarse_smem_bytes<T>(n) <= kSmemLimit;
+    // shared-memory capacity, the per-thread cell table, and 10-bit packed coordinates
+    return coarse_smem_bytes<T>(n) <= kSmemLimit && n <= (long long)kMaxCells * kCoarseThreads;
 }
 
 template <typename T>
@@ -133,15 +157,21 @@ cudaError_t launch_coarse_solve(const CoarseParams& p, cudaStream_t st) {
     if (bytes > kSmemLimit) return cudaErrorInvalidValue;
     int threads = kCoarseThreads;
     if (n < threads) threads = (int)((n + 31) / 32) * 32;
-    k_coarse_solve<T><<<1, threads, bytes, st>>>(p);
+    if (n <= 4LL * kCoarseThreads) k_coarse_solve<T, 4><<<1, threads, bytes, st>>>(p);
+    else k_coarse_solve<T, kMaxCells><<<1, threads, bytes, st>>>(p);
     return cudaGetLastError();
 }
 
 cudaError_t coarse_configure() {
-    cudaError_t e = cudaFuncSetAttribute(k_coarse_solve<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)kSmemLimit);
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_coarse_solve<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(k_coarse_solve<float, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)kSmemLimit)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_coarse_solve<float, kMaxCells>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit)) != cudaSuccess)
+        return e;
+    if ((e = cudaFuncSetAttribute(k_coarse_solve<double, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)kSmemLimit)) != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_coarse_solve<double, kMaxCells>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)kSmemLimit);
 }
 

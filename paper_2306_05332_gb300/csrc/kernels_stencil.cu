@@ -20,43 +20,44 @@ template <typename T> struct Acc { using type = float; };
 template <> struct Acc<double> { using type = double; };
 
 // x and y neighbours of cell (i, j, k) with the ghost rules (Sec. 2.3).
-template <typename T>
+// FACES: the level carries Dirichlet data (finest level of an FP64 solve);
+// without it the wall ghost is -centre (Eq. error_ghost).  Grids have fewer
+// than 2^31 cells, so 32-bit offsets suffice.
+template <bool FACES, typename T>
 __device__ __forceinline__ void xy_neighbours(const T* u, const LevelGeom& g, int i, int j, int k,
-                                              long long idx, T c, T& xm, T& xp, T& ym, T& yp) {
-    const long long fx = (long long)k * g.ny + j;     // x faces are [nz][ny]
-    const long long fy = (long long)k * g.nx + i;     // y faces are [nz][nx]
+                                              int idx, T c, T& xm, T& xp, T& ym, T& yp) {
+    const int fx = k * g.ny + j;     // x faces are [nz][ny]
+    const int fy = k * g.nx + i;     // y faces are [nz][nx]
     if (i > 0) xm = u[idx - 1];
     else if (g.per[0]) xm = u[idx + (g.nx - 1)];
-    else if (g.face[0]) xm = T(2.0 * g.face[0][fx]) - c;
+    else if (FACES && g.face[0]) xm = T(2.0 * g.face[0][fx]) - c;
     else xm = -c;
     if (i < g.nx - 1) xp = u[idx + 1];
     else if (g.per[0]) xp = u[idx - (g.nx - 1)];
-    else if (g.face[1]) xp = T(2.0 * g.face[1][fx]) - c;
+    else if (FACES && g.face[1]) xp = T(2.0 * g.face[1][fx]) - c;
     else xp = -c;
-    const long long sy = g.nx;
+    const int sy = g.nx;
     if (j > 0) ym = u[idx - sy];
-    else if (g.per[1]) ym = u[idx + (long long)(g.ny - 1) * sy];
-    else if (g.face[2]) ym = T(2.0 * g.face[2][fy]) - c;
+    else if (g.per[1]) ym = u[idx + (g.ny - 1) * sy];
+    else if (FACES && g.face[2]) ym = T(2.0 * g.face[2][fy]) - c;
     else ym = -c;
     if (j < g.ny - 1) yp = u[idx + sy];
-    else if (g.per[1]) yp = u[idx - (long long)(g.ny - 1) * sy];
-    else if (g.face[3]) yp = T(2.0 * g.face[3][fy]) - c;
+    else if (g.per[1]) yp = u[idx - (g.ny - 1) * sy];
+    else if (FACES && g.face[3]) yp = T(2.0 * g.face[3][fy]) - c;
     else yp = -c;
 }
 
-template <typename T>
-__device__ __forceinline__ T z_low(const T* u, const LevelGeom& g, int i, int j, long long idx,
-                                   long long plane, T c) {
-    if (g.per[2]) return u[idx + (long long)(g.nz - 1) * plane];
-    if (g.face[4]) return T(2.0 * g.face[4][(long long)j * g.nx + i]) - c;
+template <bool FACES, typename T>
+__device__ __forceinline__ T z_low(const T* u, const LevelGeom& g, int i, int j, int idx, int plane, T c) {
+    if (g.per[2]) return u[idx + (g.nz - 1) * plane];
+    if (FACES && g.face[4]) return T(2.0 * g.face[4][j * g.nx + i]) - c;
     return -c;
 }
 
-template <typename T>
-__device__ __forceinline__ T z_high(const T* u, const LevelGeom& g, int i, int j, long long idx,
-                                    long long plane, T c) {
-    if (g.per[2]) return u[idx - (long long)(g.nz - 1) * plane];
-    if (g.face[5]) return T(2.0 * g.face[5][(long long)j * g.nx + i]) - c;
+template <bool FACES, typename T>
+__device__ __forceinline__ T z_high(const T* u, const LevelGeom& g, int i, int j, int idx, int plane, T c) {
+    if (g.per[2]) return u[idx - (g.nz - 1) * plane];
+    if (FACES && g.face[5]) return T(2.0 * g.face[5][j * g.nx + i]) - c;
     return -c;
 }
 
@@ -68,22 +69,30 @@ __device__ __forceinline__ T lap7(T c, T xm, T xp, T ym, T yp, T zm, T zp, T ihx
 }
 
 // Full 7-point Laplacian of one cell with ghost values on every side.
-template <typename T>
+template <bool FACES, typename T>
 __device__ __forceinline__ T lap_at(const T* u, const LevelGeom& g, int i, int j, int k) {
-    const long long plane = (long long)g.nx * g.ny;
-    const long long idx = (long long)k * plane + (long long)j * g.nx + i;
+    const int plane = g.nx * g.ny;
+    const int idx = k * plane + j * g.nx + i;
     const T c = u[idx];
     T xm, xp, ym, yp;
-    xy_neighbours(u, g, i, j, k, idx, c, xm, xp, ym, yp);
-    const T zm = (k > 0) ? u[idx - plane] : z_low(u, g, i, j, idx, plane, c);
-    const T zp = (k < g.nz - 1) ? u[idx + plane] : z_high(u, g, i, j, idx, plane, c);
-    return lap7(c, xm, xp, ym, yp, zm, zp, T(g.ihx2), T(g.ihy2), T(g.ihz2));
+    xy_neighbours<FACES>(u, g, i, j, k, idx, c, xm, xp, ym, yp);
+    const T zm = (k > 0) ? u[idx - plane] : z_low<FACES>(u, g, i, j, idx, plane, c);
+    const T zp = (k < g.nz - 1) ? u[idx + plane] : z_high<FACES>(u, g, i, j, idx, plane, c);
+    return lap7(c, xm, xp, ym, yp, zm, zp, ih2x<T>(g), ih2y<T>(g), ih2z<T>(g));
 }
 
 template <typename T>
 struct CoefT {
     T tau, mut1, mu, nu, mut_tau, c0, gt;
 };
+
+int kchunk_for(const LevelGeom& g, int bx, int by);
+
+// z-chunk with an even length (restriction and prolongation work on plane pairs).
+int even_kchunk(const LevelGeom& g) {
+    const int kc = kchunk_for(g, BX, BY);
+    return kc + (kc & 1);
+}
 
 int kchunk_for(const LevelGeom& g, int bx, int by) {
     const long long gx = (g.nx + bx - 1) / bx, gy = (g.ny + by - 1) / by;
@@ -97,7 +106,7 @@ int kchunk_for(const LevelGeom& g, int bx, int by) {
 // ---------------------------------------------------------------------------
 // One RKL stage over a level (App. A, Eq. RKL_intermediate_source).
 // ---------------------------------------------------------------------------
-template <typename T, int ORDER, bool FIRST>
+template <typename T, int ORDER, bool FIRST, bool FACES>
 __global__ void __launch_bounds__(BX * BY)
 k_stage(const LevelGeom g, const CoefT<T> cf, const T* __restrict__ ym1, const T* ym2,
         const T* y0, const T* z0, const T* __restrict__ rhs, T* out, T* z0_out, int kchunk) {
@@ -106,15 +115,15 @@ k_stage(const LevelGeom g, const CoefT<T> cf, const T* __restrict__ ym1, const T
     if (i >= g.nx || j >= g.ny) return;
     const int k0 = blockIdx.z * kchunk;
     const int k1 = min(k0 + kchunk, g.nz);
-    const long long plane = (long long)g.nx * g.ny;
-    long long idx = (long long)k0 * plane + (long long)j * g.nx + i;
-    const T ihx2 = T(g.ihx2), ihy2 = T(g.ihy2), ihz2 = T(g.ihz2);
+    const int plane = g.nx * g.ny;
+    int idx = k0 * plane + j * g.nx + i;
+    const T ihx2 = ih2x<T>(g), ihy2 = ih2y<T>(g), ihz2 = ih2z<T>(g);
     T c = ym1[idx];
-    T zm = (k0 > 0) ? ym1[idx - plane] : z_low(ym1, g, i, j, idx, plane, c);
+    T zm = (k0 > 0) ? ym1[idx - plane] : z_low<FACES>(ym1, g, i, j, idx, plane, c);
     for (int k = k0; k < k1; ++k, idx += plane) {
-        const T zp = (k < g.nz - 1) ? ym1[idx + plane] : z_high(ym1, g, i, j, idx, plane, c);
+        const T zp = (k < g.nz - 1) ? ym1[idx + plane] : z_high<FACES>(ym1, g, i, j, idx, plane, c);
         T xm, xp, ym, yp;
-        xy_neighbours(ym1, g, i, j, k, idx, c, xm, xp, ym, yp);
+        xy_neighbours<FACES>(ym1, g, i, j, k, idx, c, xm, xp, ym, yp);
         const T Lf = lap7(c, xm, xp, ym, yp, zm, zp, ihx2, ihy2, ihz2) - rhs[idx];
         if (FIRST) {
             const T z = cf.tau * Lf;
@@ -133,9 +142,12 @@ k_stage(const LevelGeom g, const CoefT<T> cf, const T* __restrict__ ym1, const T
 // ---------------------------------------------------------------------------
 // Block reduction helpers (fixed order: deterministic).
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void block_reduce_write(double sumsq, double maxabs, double sum,
-                                                   Partial* partials, int block_id) {
-    __shared__ double s_sq[32], s_mx[32], s_sum[32];
+// Reduction in the kernel's accumulator precision A (FP32 kernels must not
+// spend FP64 issue slots on it: GB300 runs FP64 at 1/64 of the FP32 rate);
+// the block's result is widened to double only when it is stored.
+template <typename A>
+__device__ __forceinline__ void block_reduce_write(A sumsq, A maxabs, A sum, Partial* partials, int block_id) {
+    __shared__ A s_sq[32], s_mx[32], s_sum[32];
     const int tid = threadIdx.x + threadIdx.y * blockDim.x + threadIdx.z * blockDim.x * blockDim.y;
     const int nthreads = blockDim.x * blockDim.y * blockDim.z;
     for (int o = 16; o > 0; o >>= 1) {
@@ -148,9 +160,9 @@ __device__ __forceinline__ void block_reduce_write(double sumsq, double maxabs, 
     __syncthreads();
     if (warp == 0) {
         const int nw = (nthreads + 31) >> 5;
-        sumsq = lane < nw ? s_sq[lane] : 0.0;
-        maxabs = lane < nw ? s_mx[lane] : 0.0;
-        sum = lane < nw ? s_sum[lane] : 0.0;
+        sumsq = lane < nw ? s_sq[lane] : A(0);
+        maxabs = lane < nw ? s_mx[lane] : A(0);
+        sum = lane < nw ? s_sum[lane] : A(0);
         for (int o = 16; o > 0; o >>= 1) {
             sumsq += __shfl_down_sync(0xffffffffu, sumsq, o);
             maxabs = fmax(maxabs, __shfl_down_sync(0xffffffffu, maxabs, o));
@@ -158,7 +170,7 @@ __device__ __forceinline__ void block_reduce_write(double sumsq, double maxabs, 
         }
         if (lane == 0) {
             Partial p;
-            p.sumsq = sumsq; p.maxabs = maxabs; p.sum = sum; p.pad = 0.0;
+            p.sumsq = double(sumsq); p.maxabs = double(maxabs); p.sum = double(sum); p.pad = 0.0;
             partials[block_id] = p;
         }
     }
@@ -167,7 +179,7 @@ __device__ __forceinline__ void block_reduce_write(double sumsq, double maxabs, 
 // ---------------------------------------------------------------------------
 // Residual r = rhs - L u (standard sign; the paper's Eq. residual is -r).
 // ---------------------------------------------------------------------------
-template <typename TI, typename TO, bool UNIFORM>
+template <typename TI, typename TO, bool UNIFORM, bool FACES>
 __global__ void __launch_bounds__(BX * BY)
 k_residual(const LevelGeom g, const TI* __restrict__ u, const TI* __restrict__ rhs, TO* r_out,
            Partial* partials, int kchunk) {
@@ -180,16 +192,16 @@ k_residual(const LevelGeom g, const TI* __restrict__ u, const TI* __restrict__ r
     if (i < g.nx && j < g.ny) {
         const int k0 = blockIdx.z * kchunk;
         const int k1 = min(k0 + kchunk, g.nz);
-        const long long plane = (long long)g.nx * g.ny;
-        long long idx = (long long)k0 * plane + (long long)j * g.nx + i;
-        const TI ihx2 = TI(g.ihx2), ihy2 = TI(g.ihy2), ihz2 = TI(g.ihz2);
+        const int plane = g.nx * g.ny;
+        int idx = k0 * plane + j * g.nx + i;
+        const TI ihx2 = ih2x<TI>(g), ihy2 = ih2y<TI>(g), ihz2 = ih2z<TI>(g);
         const TI six = TI(-6), neg_ih2 = -ihx2;
         TI c = u[idx];
-        TI zm = (k0 > 0) ? u[idx - plane] : z_low(u, g, i, j, idx, plane, c);
+        TI zm = (k0 > 0) ? u[idx - plane] : z_low<FACES>(u, g, i, j, idx, plane, c);
         for (int k = k0; k < k1; ++k, idx += plane) {
-            const TI zp = (k < g.nz - 1) ? u[idx + plane] : z_high(u, g, i, j, idx, plane, c);
+            const TI zp = (k < g.nz - 1) ? u[idx + plane] : z_high<FACES>(u, g, i, j, idx, plane, c);
             TI xm, xp, ym, yp;
-            xy_neighbours(u, g, i, j, k, idx, c, xm, xp, ym, yp);
+            xy_neighbours<FACES>(u, g, i, j, k, idx, c, xm, xp, ym, yp);
             TI r;
             if (UNIFORM) {
                 // h equal on all axes: r = f - (sum of 6 neighbours - 6 c) / h^2,
@@ -209,86 +221,128 @@ k_residual(const LevelGeom g, const TI* __restrict__ u, const TI* __restrict__ r
         }
     }
     const int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
-    block_reduce_write(double(sq), double(mx), 0.0, partials, bid);
+    block_reduce_write<A>(sq, mx, A(0), partials, bid);
 }
 
 // ---------------------------------------------------------------------------
-// Residual fused with the 8-child restriction (Eq. restriction_example_3D):
-// one thread per coarse cell, coarse = (1/8) sum of its children's residuals.
+// Residual fused with the 8-child restriction (Eq. restriction_example_3D).
+// A 32 x 8 block streams fine planes along z (2.5D, z-neighbours in
+// registers); the 2 x 2 x 2 child sum is formed by a lane shuffle (x pair),
+// the register accumulator (z pair) and shared memory (y pair, neighbouring
+// warps), and the coarse value (1/8 of it) is written once.  Needs even
+// nx, ny, nz (true on every level that has a coarser one).
 // ---------------------------------------------------------------------------
-template <typename T>
-__global__ void __launch_bounds__(256)
-k_residual_restrict(const LevelGeom g, const T* __restrict__ u, const T* __restrict__ rhs,
-                    T* coarse, Partial* partials) {
+template <typename T, bool FACES>
+__global__ void __launch_bounds__(BX * BY)
+k_residual_restrict(const LevelGeom g, const T* __restrict__ u, const T* __restrict__ rhs, T* coarse,
+                    Partial* partials, int kchunk) {
     using A = typename Acc<T>::type;
-    const int cnx = g.nx >> 1, cny = g.ny >> 1, cnz = g.nz >> 1;
-    const int I = blockIdx.x * blockDim.x + threadIdx.x;
-    const int J = blockIdx.y * blockDim.y + threadIdx.y;
-    const int K = blockIdx.z * blockDim.z + threadIdx.z;
+    __shared__ T s_acc[BY][BX];
+    const int i = blockIdx.x * BX + threadIdx.x;
+    const int j = blockIdx.y * BY + threadIdx.y;
+    const bool active = i < g.nx && j < g.ny;
+    const int cnx = g.nx >> 1, cny = g.ny >> 1;
+    const int k0 = blockIdx.z * kchunk;                 // even
+    const int k1 = min(k0 + kchunk, g.nz);
+    const int plane = g.nx * g.ny;
+    const T ihx2 = ih2x<T>(g), ihy2 = ih2y<T>(g), ihz2 = ih2z<T>(g);
     A sq = A(0), mx = A(0), csum = A(0);
-    if (I < cnx && J < cny && K < cnz) {
-        const long long plane = (long long)g.nx * g.ny;
-        T acc = T(0);
-        for (int dz = 0; dz < 2; ++dz)
-            for (int dy = 0; dy < 2; ++dy)
-                for (int dx = 0; dx < 2; ++dx) {
-                    const int i = 2 * I + dx, j = 2 * J + dy, k = 2 * K + dz;
-                    const long long idx = (long long)k * plane + (long long)j * g.nx + i;
-                    const T r = rhs[idx] - lap_at(u, g, i, j, k);
-                    acc = acc + r;
-                    const A ra = A(r);
-                    sq += ra * ra;
-                    mx = fmax(mx, fabs(ra));
-                }
-        const T cval = acc * T(0.125);
-        if (coarse) coarse[(long long)K * cnx * cny + (long long)J * cnx + I] = cval;
-        csum = A(cval);
+    int idx = k0 * plane + (active ? j : 0) * g.nx + (active ? i : 0);
+    T c = T(0), zm = T(0);
+    if (active) {
+        c = u[idx];
+        zm = (k0 > 0) ? u[idx - plane] : z_low<FACES>(u, g, i, j, idx, plane, c);
+    }
+    T acc = T(0);
+    for (int k = k0; k < k1; ++k, idx += plane) {
+        T r = T(0);
+        if (active) {
+            const T zp = (k < g.nz - 1) ? u[idx + plane] : z_high<FACES>(u, g, i, j, idx, plane, c);
+            T xm, xp, ym, yp;
+            xy_neighbours<FACES>(u, g, i, j, k, idx, c, xm, xp, ym, yp);
+            r = rhs[idx] - lap7(c, xm, xp, ym, yp, zm, zp, ihx2, ihy2, ihz2);
+            const A ra = A(r);
+            sq += ra * ra;
+            mx = fmax(mx, fabs(ra));
+            zm = c;
+            c = zp;
+        }
+        const T rx = r + __shfl_xor_sync(0xffffffffu, r, 1);      // x pair
+        if ((k & 1) == 0) {
+            acc = rx;                                               // first plane of the z pair
+        } else {
+            acc = acc + rx;                                         // second plane of the z pair
+            s_acc[threadIdx.y][threadIdx.x] = acc;
+            __syncthreads();
+            if (((threadIdx.x | threadIdx.y) & 1) == 0 && active) {
+                const T cval = (s_acc[threadIdx.y][threadIdx.x] + s_acc[threadIdx.y + 1][threadIdx.x]) * T(0.125);
+                const int I = i >> 1, J = j >> 1, K = k >> 1;
+                if (coarse) coarse[(K * cny + J) * cnx + I] = cval;
+                csum += A(cval);
+            }
+            __syncthreads();
+        }
     }
     const int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
-    block_reduce_write(double(sq), double(mx), double(csum), partials, bid);
-}
-
-// Coarse value with the level's ghost rule, for any index within one cell of
-// the box: periodic wraps; Dirichlet (error equation) reflects with a sign
-// flip per wall crossed (Eq. error_ghost applied axis by axis).
-template <typename T>
-__device__ __forceinline__ T coarse_ghost(const T* c, int nx, int ny, int nz, const int* per,
-                                          int I, int J, int K) {
-    T sign = T(1);
-    if (I < 0) { if (per[0]) I += nx; else { I = 0; sign = -sign; } }
-    else if (I >= nx) { if (per[0]) I -= nx; else { I = nx - 1; sign = -sign; } }
-    if (J < 0) { if (per[1]) J += ny; else { J = 0; sign = -sign; } }
-    else if (J >= ny) { if (per[1]) J -= ny; else { J = ny - 1; sign = -sign; } }
-    if (K < 0) { if (per[2]) K += nz; else { K = 0; sign = -sign; } }
-    else if (K >= nz) { if (per[2]) K -= nz; else { K = nz - 1; sign = -sign; } }
-    return sign * c[((long long)K * ny + J) * nx + I];
+    block_reduce_write<A>(sq, mx, csum, partials, bid);
 }
 
 // ---------------------------------------------------------------------------
 // Prolongation + correction (Eq. prolongation_example_3D): every fine cell
 // takes (27 A + 9 (B + D + E) + 3 (C + F + H) + G) / 64 from its parent A and
 // the parent's neighbours on the fine cell's side, and adds it to fine_u.
+// The weights factor as (3, 1) per axis: a thread owns one fine (x, y)
+// column, forms q(K) = sum over its 2 x 2 coarse (x, y) of (3|1)(3|1) C[K]
+// once per coarse plane K, and streams z: fine plane 2K takes
+// 3 q(K) + q(K-1), fine plane 2K+1 takes 3 q(K) + q(K+1), over 64.
+// Coarse ghosts follow Eq. error_ghost axis by axis (index mirrored, sign
+// flipped per wall) or wrap (periodic).
 // ---------------------------------------------------------------------------
 template <typename T>
 __global__ void __launch_bounds__(BX * BY)
-k_prolong_correct(const LevelGeom g, const T* __restrict__ coarse, T* fine_u) {
+k_prolong_correct(const LevelGeom g, const T* __restrict__ coarse, T* fine_u, int kchunk) {
     const int i = blockIdx.x * BX + threadIdx.x;
     const int j = blockIdx.y * BY + threadIdx.y;
-    const int k = blockIdx.z;
     if (i >= g.nx || j >= g.ny) return;
     const int cnx = g.nx >> 1, cny = g.ny >> 1, cnz = g.nz >> 1;
-    const int I = i >> 1, J = j >> 1, K = k >> 1;
-    const int sx = (i & 1) ? 1 : -1, sy = (j & 1) ? 1 : -1, sz = (k & 1) ? 1 : -1;
-    T acc = T(0);
-    for (int az = 0; az < 2; ++az)
-        for (int ay = 0; ay < 2; ++ay)
-            for (int ax = 0; ax < 2; ++ax) {
-                const T w = T((az ? 1 : 3) * (ay ? 1 : 3) * (ax ? 1 : 3));
-                acc = acc + w * coarse_ghost(coarse, cnx, cny, cnz, g.per,
-                                             I + ax * sx, J + ay * sy, K + az * sz);
-            }
-    const long long idx = ((long long)k * g.ny + j) * g.nx + i;
-    fine_u[idx] = fine_u[idx] + acc * T(1.0 / 64.0);
+    const int cplane = cnx * cny;
+    // coarse x / y indices of the parent (a) and the side neighbour (b), with sign
+    const int Ia = i >> 1, Ja = j >> 1;
+    int Ib = Ia + ((i & 1) ? 1 : -1), Jb = Ja + ((j & 1) ? 1 : -1);
+    T sx = T(1), sy = T(1);
+    if (Ib < 0 || Ib >= cnx) {
+        if (g.per[0]) Ib = (Ib + cnx) % cnx;
+        else { Ib = Ia; sx = T(-1); }
+    }
+    if (Jb < 0 || Jb >= cny) {
+        if (g.per[1]) Jb = (Jb + cny) % cny;
+        else { Jb = Ja; sy = T(-1); }
+    }
+    const int oaa = Ja * cnx + Ia, oab = Ja * cnx + Ib;
+    const int oba = Jb * cnx + Ia, obb = Jb * cnx + Ib;
+    auto q = [&](int K) -> T {                          // (x, y) interpolant of coarse plane K
+        T sign = T(1);
+        if (K < 0) { if (g.per[2]) K += cnz; else { K = 0; sign = T(-1); } }
+        else if (K >= cnz) { if (g.per[2]) K -= cnz; else { K = cnz - 1; sign = T(-1); } }
+        const T* cp = coarse + K * cplane;
+        const T v = T(9) * cp[oaa] + T(3) * sx * cp[oab] + T(3) * sy * cp[oba] + sx * sy * cp[obb];
+        return sign * v;
+    };
+    const int k0 = blockIdx.z * kchunk;                 // even
+    const int k1 = min(k0 + kchunk, g.nz);
+    const int plane = g.nx * g.ny;
+    int idx = k0 * plane + j * g.nx + i;
+    int K = k0 >> 1;
+    T qm = q(K - 1), q0 = q(K), qp = q(K + 1);
+    const T w = T(1.0 / 64.0);
+    for (int k = k0; k < k1; k += 2, idx += 2 * plane) {
+        fine_u[idx] = fine_u[idx] + (T(3) * q0 + qm) * w;
+        if (k + 1 < k1) fine_u[idx + plane] = fine_u[idx + plane] + (T(3) * q0 + qp) * w;
+        ++K;
+        qm = q0;
+        q0 = qp;
+        if (k + 2 < k1) qp = q(K + 1);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -323,7 +377,7 @@ __global__ void __launch_bounds__(kRedThreads) k_finalize(const Partial* __restr
 
 template <typename T>
 __global__ void k_subtract_mean(T* x, long long n, const Reduced* red) {
-    const T mean = T(red->sum / double(n));
+    const T mean = T(red->sum) / T(n);            // in T: no FP64 division in FP32 kernels
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
          t += (long long)gridDim.x * blockDim.x)
         x[t] = x[t] - mean;
@@ -347,7 +401,7 @@ __global__ void __launch_bounds__(256) k_sum_f64(const double* __restrict__ x, l
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
          t += (long long)gridDim.x * blockDim.x)
         s += x[t];
-    block_reduce_write(0.0, 0.0, s, partials, blockIdx.x);
+    block_reduce_write<double>(0.0, 0.0, s, partials, blockIdx.x);
 }
 
 int grid1d(long long n) {
@@ -368,8 +422,21 @@ long long residual_blocks(const LevelGeom& g) {
 }
 
 long long restrict_blocks(const LevelGeom& g) {
-    const long long cnx = g.nx >> 1, cny = g.ny >> 1, cnz = g.nz >> 1;
-    return ((cnx + 31) / 32) * ((cny + 3) / 4) * ((cnz + 1) / 2);
+    const int kc = even_kchunk(g);
+    return (long long)((g.nx + BX - 1) / BX) * ((g.ny + BY - 1) / BY) * ((g.nz + kc - 1) / kc);
+}
+
+bool has_faces(const LevelGeom& g) {
+    for (int f = 0; f < 6; ++f)
+        if (g.face[f]) return true;
+    return false;
+}
+
+template <typename T, int ORDER, bool FIRST>
+void launch_stage_f(bool faces, dim3 grid, dim3 block, cudaStream_t st, const LevelGeom& g, const CoefT<T>& cf,
+                    const T* ym1, const T* ym2, const T* y0, const T* z0, const T* rhs, T* out, T* z0_out, int kc) {
+    if (faces) k_stage<T, ORDER, FIRST, true><<<grid, block, 0, st>>>(g, cf, ym1, ym2, y0, z0, rhs, out, z0_out, kc);
+    else k_stage<T, ORDER, FIRST, false><<<grid, block, 0, st>>>(g, cf, ym1, ym2, y0, z0, rhs, out, z0_out, kc);
 }
 
 template <typename T>
@@ -382,12 +449,13 @@ cudaError_t launch_stage(const LevelGeom& g, int order, bool first, const StageC
     const int kc = kchunk_for(g, BX, BY);
     dim3 block(BX, BY, 1);
     dim3 grid((g.nx + BX - 1) / BX, (g.ny + BY - 1) / BY, (g.nz + kc - 1) / kc);
+    const bool faces = has_faces(g);
     if (order == 1) {
-        if (first) k_stage<T, 1, true><<<grid, block, 0, st>>>(g, cf, ym1, ym2, y0, z0, rhs, out, z0_out, kc);
-        else k_stage<T, 1, false><<<grid, block, 0, st>>>(g, cf, ym1, ym2, y0, z0, rhs, out, z0_out, kc);
+        if (first) launch_stage_f<T, 1, true>(faces, grid, block, st, g, cf, ym1, ym2, y0, z0, rhs, out, z0_out, kc);
+        else launch_stage_f<T, 1, false>(faces, grid, block, st, g, cf, ym1, ym2, y0, z0, rhs, out, z0_out, kc);
     } else {
-        if (first) k_stage<T, 2, true><<<grid, block, 0, st>>>(g, cf, ym1, ym2, y0, z0, rhs, out, z0_out, kc);
-        else k_stage<T, 2, false><<<grid, block, 0, st>>>(g, cf, ym1, ym2, y0, z0, rhs, out, z0_out, kc);
+        if (first) launch_stage_f<T, 2, true>(faces, grid, block, st, g, cf, ym1, ym2, y0, z0, rhs, out, z0_out, kc);
+        else launch_stage_f<T, 2, false>(faces, grid, block, st, g, cf, ym1, ym2, y0, z0, rhs, out, z0_out, kc);
     }
     return cudaGetLastError();
 }
@@ -398,9 +466,12 @@ cudaError_t launch_residual(const LevelGeom& g, const TI* u, const TI* rhs, TO* 
     const int kc = kchunk_for(g, BX, BY);
     dim3 block(BX, BY, 1);
     dim3 grid((g.nx + BX - 1) / BX, (g.ny + BY - 1) / BY, (g.nz + kc - 1) / kc);
-    const bool uniform = g.ihx2 == g.ihy2 && g.ihy2 == g.ihz2;
-    if (uniform) k_residual<TI, TO, true><<<grid, block, 0, st>>>(g, u, rhs, r_out, partials, kc);
-    else k_residual<TI, TO, false><<<grid, block, 0, st>>>(g, u, rhs, r_out, partials, kc);
+    const bool uniform = g.ihx2 == g.ihy2 && g.ihy2 == g.ihz2;   // (also true for the FP32 copies)
+    const bool faces = has_faces(g);
+    if (uniform && faces) k_residual<TI, TO, true, true><<<grid, block, 0, st>>>(g, u, rhs, r_out, partials, kc);
+    else if (uniform) k_residual<TI, TO, true, false><<<grid, block, 0, st>>>(g, u, rhs, r_out, partials, kc);
+    else if (faces) k_residual<TI, TO, false, true><<<grid, block, 0, st>>>(g, u, rhs, r_out, partials, kc);
+    else k_residual<TI, TO, false, false><<<grid, block, 0, st>>>(g, u, rhs, r_out, partials, kc);
     if (nblocks_out) *nblocks_out = (int)(grid.x * grid.y * grid.z);
     return cudaGetLastError();
 }
@@ -408,19 +479,21 @@ cudaError_t launch_residual(const LevelGeom& g, const TI* u, const TI* rhs, TO* 
 template <typename T>
 cudaError_t launch_residual_restrict(const LevelGeom& g, const T* u, const T* rhs, T* coarse_out,
                                      Partial* partials, int* nblocks_out, cudaStream_t st) {
-    const int cnx = g.nx >> 1, cny = g.ny >> 1, cnz = g.nz >> 1;
-    dim3 block(32, 4, 2);
-    dim3 grid((cnx + 31) / 32, (cny + 3) / 4, (cnz + 1) / 2);
-    k_residual_restrict<T><<<grid, block, 0, st>>>(g, u, rhs, coarse_out, partials);
+    const int kc = even_kchunk(g);
+    dim3 block(BX, BY, 1);
+    dim3 grid((g.nx + BX - 1) / BX, (g.ny + BY - 1) / BY, (g.nz + kc - 1) / kc);
+    if (has_faces(g)) k_residual_restrict<T, true><<<grid, block, 0, st>>>(g, u, rhs, coarse_out, partials, kc);
+    else k_residual_restrict<T, false><<<grid, block, 0, st>>>(g, u, rhs, coarse_out, partials, kc);
     if (nblocks_out) *nblocks_out = (int)(grid.x * grid.y * grid.z);
     return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_prolong_correct(const LevelGeom& g, const T* coarse, T* fine_u, cudaStream_t st) {
+    const int kc = even_kchunk(g);
     dim3 block(BX, BY, 1);
-    dim3 grid((g.nx + BX - 1) / BX, (g.ny + BY - 1) / BY, g.nz);
-    k_prolong_correct<T><<<grid, block, 0, st>>>(g, coarse, fine_u);
+    dim3 grid((g.nx + BX - 1) / BX, (g.ny + BY - 1) / BY, (g.nz + kc - 1) / kc);
+    k_prolong_correct<T><<<grid, block, 0, st>>>(g, coarse, fine_u, kc);
     return cudaGetLastError();
 }
 

@@ -16,6 +16,8 @@
 #include <cstdlib>
 #include <cstring>
 #include <string>
+#include <type_traits>
+#include <utility>
 #include <vector>
 
 using namespace sg;
@@ -211,6 +213,9 @@ LevelGeom geom(const sg_grid* g, int l, bool with_faces) {
     G.ihx2 = 1.0 / (L.h[0] * L.h[0]);
     G.ihy2 = 1.0 / (L.h[1] * L.h[1]);
     G.ihz2 = 1.0 / (L.h[2] * L.h[2]);
+    G.ihx2f = float(G.ihx2);
+    G.ihy2f = float(G.ihy2);
+    G.ihz2f = float(G.ihz2);
     for (int d = 0; d < 3; ++d) G.per[d] = g->bc[d] == SG_BC_PERIODIC;
     for (int f = 0; f < 6; ++f) {
         const int d = f / 2;
@@ -423,18 +428,81 @@ sg_status coarse_solve(sg_grid* g, int l, const W* rhs, W* u, int* d_done) {
     return SG_OK;
 }
 
-// One V-cycle (Sec. 2.1) with level-0 arrays u0 / rhs0 (faces on level 0 if `faces`).
+// One fused super-step (FP32, homogeneous or periodic ghosts): out = Y_s(y0),
+// y0 == nullptr meaning Y0 = 0.
+sg_status superstep_fused(sg_grid* g, int l, int order, int s, double tau_frac, const float* y0,
+                          const float* rhs, float* out) {
+    const Level& L = g->lv[l];
+    const Rkl r = make_rkl(order, s);
+    const double tau = tau_frac * (2.0 / lambda_max(L)) * r.tau_over_dtpar;
+    FusedCoef cf{};
+    cf.tau = float(tau);
+    cf.mut1 = float(r.mut[1]);
+    for (int j = 2; j <= s; ++j) {
+        cf.mu[j] = float(r.mu[j]);
+        cf.nu[j] = float(r.nu[j]);
+        cf.mut_tau[j] = float(r.mut[j] * tau);
+        cf.c0[j] = float(r.c0[j]);
+        cf.gt[j] = float(r.gt[j]);
+    }
+    {
+        ProfScope ps(g, l == 0 ? K_STAGE0 : K_STAGE_C, double(L.n) * sizeof(float) * (y0 ? 3 : 2));
+        SG_CK(launch_superstep_fused(geom(g, l, false), order, s, y0 == nullptr, cf, y0, rhs, out, g->st));
+    }
+    ++g->launches;
+    return SG_OK;
+}
+
+// The fused super-step streams each tile through all s stages one plane at a
+// time; on small levels that serial chain of planes costs more than it saves
+// in HBM traffic (the level is L2-resident anyway), so only levels with at
+// least kFusedMinCells cells use it.
+constexpr long long kFusedMinCells = 1LL << 21;
+
+bool use_fused(const sg_grid* g, bool faces, int l) {
+    return g->precision == SG_MIXED && g->opt.fused && !faces && fused_supported(g->opt.rkl_order, g->opt.s_smooth) &&
+           g->lv[l].n >= kFusedMinCells;
+}
+
+// One V-cycle (Sec. 2.1) with level-0 arrays u0 / rhs0 (faces on level 0 if
+// `faces`; zero0: u0 is known to be zero, as for the error equation of the
+// mixed-precision loop).  On return *u0_final points at the level-0 result: u0
+// itself, or, with the fused FP32 super-steps (which cannot write in place),
+// whichever of u0 and its ping-pong partner holds it.
 template <typename W>
-sg_status vcycle(sg_grid* g, int L, W* u0, const W* rhs0, bool faces) {
-    auto U = [&](int l) -> W* { return l == 0 ? u0 : (W*)g->lv[l].u; };
+sg_status vcycle(sg_grid* g, int L, W* u0, const W* rhs0, bool faces, bool zero0, W** u0_final) {
+    W* cur[32];
+    W* alt[32];
+    for (int l = 0; l < L; ++l) {
+        cur[l] = l == 0 ? u0 : (W*)g->lv[l].u;
+        alt[l] = (W*)g->lv[l].t[0];
+    }
     auto R = [&](int l) -> const W* { return l == 0 ? rhs0 : (const W*)g->lv[l].rhs; };
     const bool per = all_periodic(g);
-    SG_TRY(relax<W>(g, 0, g->opt.n_pre, faces, U(0), R(0)));                    // step 1
+    // `count` smoothing super-steps at level l; zero_start: the level's u is 0.
+    auto smooth = [&](int l, int count, bool zero_start, bool fc) -> sg_status {
+        if constexpr (std::is_same<W, float>::value) {
+            if (use_fused(g, fc, l)) {
+                for (int c = 0; c < count; ++c) {
+                    const bool z = zero_start && c == 0;
+                    float* out = z ? cur[l] : alt[l];
+                    SG_TRY(superstep_fused(g, l, g->opt.rkl_order, g->opt.s_smooth, g->opt.tau_frac,
+                                           z ? nullptr : cur[l], R(l), out));
+                    if (!z) std::swap(cur[l], alt[l]);
+                }
+                if (zero_start && count == 0) SG_CK(cudaMemsetAsync(cur[l], 0, g->lv[l].n * sizeof(W), g->st));
+                return SG_OK;
+            }
+        }
+        if (zero_start && count > 0) SG_CK(cudaMemsetAsync(cur[l], 0, g->lv[l].n * sizeof(W), g->st));
+        return relax<W>(g, l, count, fc, cur[l], R(l));
+    };
+    SG_TRY(smooth(0, g->opt.n_pre, zero0, faces));                              // step 1
     for (int l = 1; l < L; ++l) {                                               // step 2
         int nb = 0;
         {
             ProfScope ps(g, K_RESTRICT, (2.0 + 0.125) * g->lv[l - 1].n * sizeof(W));
-            SG_CK(launch_residual_restrict<W>(geom(g, l - 1, faces && l - 1 == 0), U(l - 1), R(l - 1),
+            SG_CK(launch_residual_restrict<W>(geom(g, l - 1, faces && l - 1 == 0), cur[l - 1], R(l - 1),
                                               (W*)g->lv[l].rhs, g->partials, &nb, g->st));   // 2a, 2b
         }
         ++g->launches;
@@ -444,24 +512,24 @@ sg_status vcycle(sg_grid* g, int L, W* u0, const W* rhs0, bool faces) {
             SG_CK(launch_subtract_mean<W>((W*)g->lv[l].rhs, g->lv[l].n, g->red + 1, g->st));
             g->launches += 2;
         }
-        SG_CK(cudaMemsetAsync(U(l), 0, g->lv[l].n * sizeof(W), g->st));        // 2c
-        if (l < L - 1) SG_TRY(relax<W>(g, l, g->opt.n_pre, false, U(l), R(l)));  // 2d-i
-        else SG_TRY(coarse_solve<W>(g, l, R(l), U(l), g->d_ss));                 // 2e
+        if (l < L - 1) SG_TRY(smooth(l, g->opt.n_pre, true, false));            // 2c + 2d-i
+        else SG_TRY(coarse_solve<W>(g, l, R(l), cur[l], g->d_ss));              // 2c + 2e
     }
     for (int l = L - 2; l >= 1; --l) {                                          // step 3
         {
             ProfScope ps(g, K_PROLONG, (2.0 + 0.125) * g->lv[l].n * sizeof(W));
-            SG_CK(launch_prolong_correct<W>(geom(g, l, false), U(l + 1), U(l), g->st));
+            SG_CK(launch_prolong_correct<W>(geom(g, l, false), cur[l + 1], cur[l], g->st));
         }
         ++g->launches;
-        SG_TRY(relax<W>(g, l, g->opt.n_post, false, U(l), R(l)));
+        SG_TRY(smooth(l, g->opt.n_post, false, false));
     }
     {
         ProfScope ps(g, K_PROLONG, (2.0 + 0.125) * g->lv[0].n * sizeof(W));
-        SG_CK(launch_prolong_correct<W>(geom(g, 0, false), U(1), U(0), g->st));  // 4a
+        SG_CK(launch_prolong_correct<W>(geom(g, 0, false), cur[1], cur[0], g->st));  // 4a
     }
     ++g->launches;
-    SG_TRY(relax<W>(g, 0, g->opt.n_post, faces, U(0), R(0)));                  // 4b
+    SG_TRY(smooth(0, g->opt.n_post, false, faces));                             // 4b
+    if (u0_final) *u0_final = cur[0];
     return SG_OK;
 }
 
@@ -485,16 +553,17 @@ sg_status level0_residual(sg_grid* g, const double* phi, const double* f, bool f
 // residual + norm, and the copies of the norm / coarse count to pinned memory.
 sg_status cycle_body(sg_grid* g, int L, double* phi, const double* f, bool faces) {
     if (g->precision == SG_MIXED) {
+        // the inner cycle starts from e = 0: its first super-step takes Y0 = 0
         float* e = (float*)g->lv[0].u;
-        SG_CK(cudaMemsetAsync(e, 0, g->lv[0].n * sizeof(float), g->st));
-        SG_TRY(vcycle<float>(g, L, e, (const float*)g->lv[0].rhs, false));
+        float* e_final = e;
+        SG_TRY(vcycle<float>(g, L, e, (const float*)g->lv[0].rhs, false, true, &e_final));
         {
             ProfScope ps(g, K_UPDATE, 20.0 * g->lv[0].n);
-            SG_CK(launch_add_f32_to_f64(phi, e, g->lv[0].n, g->st));
+            SG_CK(launch_add_f32_to_f64(phi, e_final, g->lv[0].n, g->st));
         }
         ++g->launches;
     } else {
-        SG_TRY(vcycle<double>(g, L, phi, f, faces));
+        SG_TRY(vcycle<double>(g, L, phi, f, faces, false, nullptr));
     }
     SG_TRY(level0_residual(g, phi, f, faces));
     SG_CK(cudaMemcpyAsync(g->host_red, g->red, sizeof(Reduced), cudaMemcpyDeviceToHost, g->st));
@@ -747,7 +816,7 @@ sg_status sg_default_options(sg_options* o) {
     o->tau_frac = 1.0;
     o->n_pre = 2;
     o->n_post = 1;
-    o->coarse_tol = 1e-3;
+    o->coarse_tol = 1e-2;
     o->coarse_max_ss = 64;
     o->coarse_tau_frac = 0.0;
     o->max_cycles = 100;
@@ -775,6 +844,7 @@ sg_status sg_create_grid(int nx, int ny, int nz, const double lo[3], const doubl
     if ((long long)nx * ny * nz > 2147483647LL) return fail(SG_ERR_ARG, "too many cells");
     if (precision != SG_FP64 && precision != SG_MIXED) return fail(SG_ERR_ARG, "bad precision");
     SG_CK(coarse_configure());
+    SG_CK(fused_configure());
     sg_grid* g = new sg_grid();
     for (int d = 0; d < 3; ++d) {
         g->n[d] = n[d];
@@ -1011,10 +1081,13 @@ sg_status sg_op_superstep(sg_grid* g, int level, int dtype, int order, int s, do
                           int homogeneous, const void* u, const void* rhs, void* out) {
     g_err.clear();
     SG_TRY(op_check(g, level, dtype));
-    if (!u || !rhs || !out || out == u || out == rhs) return fail(SG_ERR_ARG, "bad pointers");
+    if (!rhs || !out || out == u || out == rhs) return fail(SG_ERR_ARG, "bad pointers");
     if ((order != 1 && order != 2) || s < 1 || (order == 2 && s < 2) || !(tau_frac > 0 && tau_frac <= 1))
         return fail(SG_ERR_ARG, "bad order / s / tau_frac");
     const bool faces = !homogeneous && level == 0 && g->have_faces;
+    if (dtype == 1 && g->opt.fused && !faces && fused_supported(order, s))
+        return superstep_fused(g, level, order, s, tau_frac, (const float*)u, (const float*)rhs, (float*)out);
+    if (!u) return fail(SG_ERR_ARG, "u == NULL (zero initial guess) needs the fused FP32 super-step");
     const size_t bytes = g->lv[level].n * (dtype == 0 ? 8 : 4);
     SG_CK(cudaMemcpyAsync(out, u, bytes, cudaMemcpyDeviceToDevice, g->st));
     if (dtype == 0) return superstep<double>(g, level, order, s, tau_frac, faces, (double*)out, (const double*)rhs);

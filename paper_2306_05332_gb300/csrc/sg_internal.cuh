@@ -17,9 +17,22 @@ namespace sg {
 struct LevelGeom {
     int nx, ny, nz;
     double ihx2, ihy2, ihz2;          // 1 / h_d^2
+    float ihx2f, ihy2f, ihz2f;        // the same in FP32: FP32 kernels must never convert from FP64
+                                      // (GB300 issues FP64 and its conversions at 1/64 of the FP32 rate)
     int per[3];                       // periodic flag per axis (x, y, z)
     const double* face[6];            // -x,+x,-y,+y,-z,+z or all nullptr (homogeneous)
 };
+
+// 1 / h^2 per axis in the kernel's precision.
+template <typename T> __host__ __device__ __forceinline__ T ih2x(const LevelGeom& g);
+template <> __host__ __device__ __forceinline__ float ih2x<float>(const LevelGeom& g) { return g.ihx2f; }
+template <> __host__ __device__ __forceinline__ double ih2x<double>(const LevelGeom& g) { return g.ihx2; }
+template <typename T> __host__ __device__ __forceinline__ T ih2y(const LevelGeom& g);
+template <> __host__ __device__ __forceinline__ float ih2y<float>(const LevelGeom& g) { return g.ihy2f; }
+template <> __host__ __device__ __forceinline__ double ih2y<double>(const LevelGeom& g) { return g.ihy2; }
+template <typename T> __host__ __device__ __forceinline__ T ih2z(const LevelGeom& g);
+template <> __host__ __device__ __forceinline__ float ih2z<float>(const LevelGeom& g) { return g.ihz2f; }
+template <> __host__ __device__ __forceinline__ double ih2z<double>(const LevelGeom& g) { return g.ihz2; }
 
 // Per-stage coefficients of one RKL stage (App. A, Eq. RKL_intermediate_source).
 //   first stage : z = tau (L Y0 - f);  Y1 = Y0 + mut1 * z;   (RKL2 stores z as Z0)
@@ -86,6 +99,21 @@ cudaError_t launch_add_f32_to_f64(double* phi, const float* e, long long n, cuda
 cudaError_t launch_sub_mean_f64(double* x, long long n, const Reduced* red, cudaStream_t st);
 cudaError_t launch_sum_partials_f64(const double* x, long long n, Partial* partials,
                                     int* nblocks_out, cudaStream_t st);
+
+// ---- fused super-step, FP32 (kernels_fused.cu) -----------------------------
+constexpr int kFusedMaxS = 6;
+struct FusedCoef {
+    float tau, mut1;                        // first stage
+    float mu[kFusedMaxS + 1], nu[kFusedMaxS + 1], mut_tau[kFusedMaxS + 1];
+    float c0[kFusedMaxS + 1], gt[kFusedMaxS + 1];
+};
+// True if the fused kernel handles (order, s): 2 <= s <= kFusedMaxS.
+bool fused_supported(int order, int s);
+cudaError_t fused_configure();
+// out = Y_s of one super-step from y0 (nullptr: Y0 = 0) with homogeneous or
+// periodic ghosts; out must not alias y0.
+cudaError_t launch_superstep_fused(const LevelGeom& g, int order, int s, bool zero_y0, const FusedCoef& cf,
+                                   const float* y0, const float* f, float* out, cudaStream_t st);
 
 // ---- coarsest-level solver (kernels_coarse.cu) -----------------------------
 struct CoarseParams {

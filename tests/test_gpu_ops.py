@@ -64,8 +64,10 @@ def test_superstep_fp64(shape, bc, order, s, c):
 
 @pytest.mark.parametrize("shape,bc", SHAPES_BC[:2])
 @pytest.mark.parametrize("order,s,c", [(1, 2, 0.75), (2, 3, 1.0), (2, 5, 1.0)])
-def test_superstep_fp32_homogeneous(shape, bc, order, s, c):
+@pytest.mark.parametrize("fused", [0, 1])
+def test_superstep_fp32_homogeneous(shape, bc, order, s, c, fused):
     g, h, _ = make_grid(shape, bc, "mixed")
+    g.set_options(fused=fused)
     u, rhs = W.random_field(shape, 8), 50.0 * W.random_field(shape, 9)
     out = torch.empty(shape, dtype=torch.float32, device="cuda")
     g.op_superstep(0, order, s, c, dev(u, torch.float32), dev(rhs, torch.float32), out, homogeneous=True)
@@ -157,3 +159,61 @@ def test_coarse_solve_tolerance_stop():
                          O.Options(coarse_tol=1e-6, coarse_max_ss=200), record=rec)
     assert done == rec[0]
     assert relerr(out, ref) < 1e-11
+
+
+# ---------------------------------------------------------------------------
+# Fused (temporally blocked) FP32 super-step: every stage count it supports,
+# both orders, Y0 = 0 and general Y0, every boundary mix, ragged and tiny shapes.
+# ---------------------------------------------------------------------------
+FUSED_SHAPES = [((20, 12, 36), (0, 0, 0)), ((16, 24, 8), (1, 1, 1)), ((12, 20, 40), (1, 0, 1)),
+                ((37, 19, 70), (0, 1, 0)), ((6, 4, 2), (1, 1, 1)), ((4, 6, 10), (0, 0, 0))]
+
+
+@pytest.mark.parametrize("shape,bc", FUSED_SHAPES)
+@pytest.mark.parametrize("order,s", [(1, 2), (1, 5), (2, 2), (2, 3), (2, 4), (2, 6), (1, 6)])
+@pytest.mark.parametrize("zero", [False, True])
+def test_fused_superstep_matches_oracle(shape, bc, order, s, zero):
+    g, h, _ = make_grid(shape, bc, "mixed")
+    assert g.options().fused == 1
+    c = 0.9
+    u = np.zeros(shape) if zero else W.random_field(shape, 20)
+    rhs = 50.0 * W.random_field(shape, 21)
+    out = torch.full(shape, float("nan"), dtype=torch.float32, device="cuda")
+    g.op_superstep(0, order, s, c, None if zero else dev(u, torch.float32), dev(rhs, torch.float32), out,
+                   homogeneous=True)
+    torch.cuda.synchronize()
+    u32 = u.astype(np.float32).astype(np.float64)
+    r32 = rhs.astype(np.float32).astype(np.float64)
+    ref = O.rkl_superstep(u32, r32, h, bc, None, order, s, c)
+    assert torch.isfinite(out).all()
+    assert relerr(out.double(), ref) < 5e-5
+
+
+def test_fused_equals_unfused_fp32():
+    shape, bc = (64, 48, 80), (0, 0, 0)
+    g, h, _ = make_grid(shape, bc, "mixed")
+    u = dev(W.random_field(shape, 22), torch.float32)
+    rhs = dev(W.random_field(shape, 23), torch.float32)
+    a = torch.empty(shape, dtype=torch.float32, device="cuda")
+    b = torch.empty(shape, dtype=torch.float32, device="cuda")
+    g.set_options(fused=1)
+    g.op_superstep(1 - 1, 2, 3, 1.0, u, rhs, a, homogeneous=True)
+    g.set_options(fused=0)
+    g.op_superstep(0, 2, 3, 1.0, u, rhs, b, homogeneous=True)
+    torch.cuda.synchronize()
+    assert relerr(a.double(), b.double().cpu().numpy()) < 1e-5
+
+
+@pytest.mark.parametrize("fused", [0, 1])
+def test_mixed_solve_fused_and_unfused_agree(fused):
+    p = W.sphere(64)
+    sg = pytest.importorskip("paper_2306_05332_gb300")
+    g = sg.Grid(p.shape, p.lo, p.hi, p.bc, precision="mixed")
+    g.set_boundary(p.faces)
+    g.set_density(p.rho, 1.0)
+    g.set_options(fused=fused)
+    info = g.solve(tol=1e-11, levels=4)
+    ref, _ = O.solve(p.rho, p.lo, p.hi, p.bc, p.faces, 1.0, tol=1e-13, levels=4)
+    assert np.linalg.norm(g.potential() - ref) / np.linalg.norm(ref) < 1e-8
+    _, rinfo = O.solve(p.rho, p.lo, p.hi, p.bc, p.faces, 1.0, tol=1e-11, levels=4)
+    assert abs(info["cycles"] - rinfo.cycles) <= 1
