@@ -170,12 +170,44 @@ sg_status sg_backward(sg_grid* g, const double* dL_dphi, double* dL_drho, int on
                       double tol, sg_solve_info* info);
 
 /*
- * Solve n independent grids (each with its density, boundary and options set)
- * to tolerance tol, with the levels of each grid's rule.  The V-cycle phases of
- * all grids are issued together on the first grid's stream.  infos may be NULL
- * or an array of n entries.  Returns the first non-OK status.
+ * Solve n independent grids (each with its density, boundary and options set;
+ * sizes may differ) to tolerance tol, with the levels of each grid's rule.
+ * Every V-cycle of the whole batch is one CUDA graph launch: one branch per
+ * unconverged grid, forked from the first grid's stream, so the kernels of
+ * small grids run concurrently; the graph is re-captured when a grid
+ * converges and leaves.  Grids that cannot be captured (one level, a coarsest
+ * level too large for one CTA, use_graph = 0) are solved one after the other.
+ * Each grid keeps its own stopping rule and info.  infos may be NULL or an
+ * array of n entries.  A grid may appear only once.  Returns the first
+ * non-OK status.
  */
 sg_status sg_solve_batch(sg_grid* const* grids, int n, double tol, sg_solve_info* infos);
+
+/* One candidate of sg_autotune and what it measured. */
+typedef struct sg_tune_entry {
+    int    rkl_order;          /* smoother order tried */
+    int    s_smooth;           /* stages per smoothing super-step tried */
+    int    fused;              /* fused (temporally blocked) super-steps on or off */
+    double tau_frac;           /* smoother tau / tau_max tried */
+    double ms_per_cycle;       /* measured device time per V-cycle */
+    double factor;             /* measured residual reduction per V-cycle */
+    double ms_per_decade;      /* ms_per_cycle / -log10(factor): the score (lower is better) */
+} sg_tune_entry;
+
+/*
+ * Pick the smoother for this grid and its current density by measurement: for
+ * every candidate (RKL order 1 and 2 -- or only the current order when
+ * keep_order is 1 --, s = 2..6, a few tau fractions, fused on and off) run
+ * two and six V-cycles at `levels` (0 = the level rule), take the difference
+ * of their CUDA-event times (so per-solve set-up drops out) and score the time
+ * per decade of residual reduction over cycles 2..6; the best candidate is
+ * written into the grid's options.  The trial cycles overwrite the potential
+ * (call before sg_solve).  table (may be NULL) receives up to cap entries,
+ * *count the number tried.  The App. A.4 spectral analysis motivates the
+ * search: the best s balances the cost of s stages against the reduction of
+ * the modes the smoother must damp.
+ */
+sg_status sg_autotune(sg_grid* g, int levels, int keep_order, sg_tune_entry* table, int cap, int* count);
 
 /* Free the grid and its device buffers.  NULL is a no-op. */
 void sg_destroy(sg_grid* g);

@@ -74,6 +74,12 @@ class KernelStat(ctypes.Structure):
 SG_KERNEL_CLASSES = 8
 
 
+class TuneEntry(ctypes.Structure):
+    _fields_ = [("rkl_order", ctypes.c_int), ("s_smooth", ctypes.c_int), ("fused", ctypes.c_int),
+                ("tau_frac", ctypes.c_double), ("ms_per_cycle", ctypes.c_double), ("factor", ctypes.c_double),
+                ("ms_per_decade", ctypes.c_double)]
+
+
 class SGError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"{STATUS.get(status, status)}: {msg}")
@@ -107,6 +113,7 @@ _SIGS = {
     "sg_op_coarse_solve": ([_P, _I, _I, _P, _P, ctypes.POINTER(_I)], _I),
     "sg_set_profiling": ([_P, _I], _I),
     "sg_kernel_stats": ([_P, ctypes.POINTER(KernelStat)], _I),
+    "sg_autotune": ([_P, _I, _I, ctypes.POINTER(TuneEntry), _I, ctypes.POINTER(_I)], _I),
 }
 
 
@@ -278,6 +285,15 @@ class Grid:
 
     def set_profiling(self, on=True):
         _check(lib().sg_set_profiling(self._h, int(bool(on))))
+
+    def autotune(self, levels=0, keep_order=True):
+        """Measure the smoother candidates and keep the fastest per residual decade."""
+        cap = 128
+        arr = (TuneEntry * cap)()
+        n = ctypes.c_int(0)
+        _check(lib().sg_autotune(self._h, int(levels), int(bool(keep_order)), arr, cap, ctypes.byref(n)))
+        table = [{k: getattr(arr[i], k) for k, _ in TuneEntry._fields_} for i in range(n.value)]
+        return self.options().as_dict(), table
 
     def kernel_stats(self):
         arr = (KernelStat * SG_KERNEL_CLASSES)()

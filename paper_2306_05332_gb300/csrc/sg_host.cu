@@ -160,6 +160,7 @@ struct sg_grid {
     int precision;
     cudaStream_t st;
     cudaStream_t own_stream = nullptr;
+    cudaStream_t batch_stream = nullptr;    // private stream of this grid's branch in a batch graph
     int max_levels;
     std::vector<Level> lv;
     double* phi = nullptr;
@@ -638,19 +639,43 @@ long long stage_updates_per_cycle(const sg_grid* g, int L) {
 }
 
 // The solve loop shared by sg_solve (phi, f, faces) and sg_backward (lam, w, none).
-sg_status solve_impl(sg_grid* g, double tol, int L, double* phi, const double* f, bool faces,
-                     bool have_guess, sg_solve_info* info) {
-    sg_solve_info local;
-    std::memset(&local, 0, sizeof(local));
-    local.levels = L;
-    local.s_smooth = g->opt.s_smooth;
-    local.rkl_order = g->opt.rkl_order;
-    local.precision = g->precision;
-    const long long launches0 = g->launches;
+// State of one solve between its set-up, its cycles and its wrap-up (shared by
+// sg_solve and sg_solve_batch).
+struct SolveState {
+    sg_solve_info info;
+    long long launches0 = 0;
+    int L = 1;
+    double* phi = nullptr;
+    const double* f = nullptr;
+    bool faces = false;
+    double tol = 0.0;
+    double nn = 1.0, rden = 1.0;
+    int limit = 0;
+    double single_c = 1.0;
+    std::vector<int> single_sched;
+    long long su = 0;
+    int m = 0;
+    bool done = false;
+    sg_status status = SG_OK;
+};
+
+// r0 = ||L 0 - f|| (boundary contribution of phi = 0 included), the first
+// residual, the coarse schedule; leaves the residual of the start in host_red[0].
+sg_status solve_begin(sg_grid* g, SolveState& S, double tol, int L, double* phi, const double* f, bool faces,
+                      bool have_guess) {
+    std::memset(&S.info, 0, sizeof(S.info));
+    S.info.levels = L;
+    S.info.s_smooth = g->opt.s_smooth;
+    S.info.rkl_order = g->opt.rkl_order;
+    S.info.precision = g->precision;
+    S.launches0 = g->launches;
+    S.L = L;
+    S.phi = phi;
+    S.f = f;
+    S.faces = faces;
+    S.tol = tol;
     const Level& L0 = g->lv[0];
     SG_CK(cudaEventRecord(g->ev0, g->st));
-
-    // r0 = ||L 0 - f|| (boundary contribution of phi = 0 included).
     if (!have_guess) {
         SG_CK(cudaMemsetAsync(phi, 0, L0.n * sizeof(double), g->st));
     } else {
@@ -669,94 +694,119 @@ sg_status solve_impl(sg_grid* g, double tol, int L, double* phi, const double* f
     SG_CK(cudaMemcpyAsync(g->host_red, g->red, sizeof(Reduced), cudaMemcpyDeviceToHost, g->st));
     SG_CK(cudaStreamSynchronize(g->st));
     prof_sync_point(g, false);
-    const double nn = double(L0.n);
-    const double r0 = std::sqrt((have_guess ? g->host_red[2].sumsq : g->host_red[0].sumsq) / nn);
-    local.r0 = r0;
-    const double rden = r0 > 0.0 ? r0 : 1.0;
-
-    int N0 = std::max(L0.nx, std::max(L0.ny, L0.nz));
-    std::vector<int> single_sched;
+    S.nn = double(L0.n);
+    const double r0 = std::sqrt((have_guess ? g->host_red[2].sumsq : g->host_red[0].sumsq) / S.nn);
+    S.info.r0 = r0;
+    S.rden = r0 > 0.0 ? r0 : 1.0;
+    const int N0 = std::max(L0.nx, std::max(L0.ny, L0.nz));
     if (L == 1) {
-        single_sched = accelerated_schedule(N0, g->opt.max_cycles + 1);
+        S.single_sched = accelerated_schedule(N0, g->opt.max_cycles + 1);
     } else {
         const Level& Lc = g->lv[L - 1];
         const int Nc = std::max(Lc.nx, std::max(Lc.ny, Lc.nz));
         SG_TRY(ensure_sched(g, accelerated_schedule(Nc, g->opt.coarse_max_ss)));
     }
-    const int limit = g->opt.fixed_cycles > 0 ? g->opt.fixed_cycles : g->opt.max_cycles;
-    const double single_c = g->opt.single_tau_frac > 0 ? g->opt.single_tau_frac : cell_tau_frac(N0);
-    long long su = 0;
-    sg_status status = SG_OK;
-    int m = 0;
-    while (true) {
-        const double rel = std::sqrt(g->host_red[0].sumsq / nn) / rden;
-        local.history[m] = rel;
-        local.rel_residual = rel;
-        local.max_residual = g->host_red[0].maxabs;
-        if (!std::isfinite(rel)) {
-            status = fail(SG_ERR_NONFINITE, "residual norm is not finite");
-            break;
-        }
-        if (g->opt.fixed_cycles == 0 && rel <= tol) break;
-        if (m >= limit) {
-            if (g->opt.fixed_cycles == 0)
-                status = fail(SG_ERR_NOT_CONVERGED, "max_cycles reached above the tolerance");
-            break;
-        }
-        if (L == 1) {
-            const int s = g->opt.single_s > 0 ? g->opt.single_s : single_sched[m];
-            if (g->precision == SG_MIXED) {
-                // Single level in mixed precision: FP32 super-step on the error equation.
-                float* e = (float*)L0.u;
-                SG_CK(cudaMemsetAsync(e, 0, L0.n * sizeof(float), g->st));
-                SG_TRY(superstep<float>(g, 0, 1, s, single_c, false, e, (const float*)L0.rhs));
-                {
-                    ProfScope ps(g, K_UPDATE, 20.0 * L0.n);
-                    SG_CK(launch_add_f32_to_f64(phi, e, L0.n, g->st));
-                }
-                ++g->launches;
-            } else {
-                SG_TRY(superstep<double>(g, 0, 1, s, single_c, faces, phi, f));
-            }
-            su += L0.n * (long long)s;
-            SG_TRY(level0_residual(g, phi, f, faces));
-            SG_CK(cudaMemcpyAsync(g->host_red, g->red, sizeof(Reduced), cudaMemcpyDeviceToHost, g->st));
-            *g->host_ss = 0;
-        }
-        bool replayed = false;
-        if (L > 1) {
-            SG_TRY(run_cycle(g, L, phi, f, faces, &replayed));
-            su += stage_updates_per_cycle(g, L);
-        }
-        SG_CK(cudaStreamSynchronize(g->st));
-        prof_sync_point(g, replayed);
-        if (L > 1) {
-            local.coarse_ss[m] = *g->host_ss;
-            const Level& Lc = g->lv[L - 1];
-            const int Nc = std::max(Lc.nx, std::max(Lc.ny, Lc.nz));
-            const std::vector<int> sc = accelerated_schedule(Nc, std::max(1, *g->host_ss));
-            for (int q = 0; q < *g->host_ss && q < (int)sc.size(); ++q) su += Lc.n * (long long)sc[q];
-        }
-        ++m;
+    S.limit = g->opt.fixed_cycles > 0 ? g->opt.fixed_cycles : g->opt.max_cycles;
+    S.single_c = g->opt.single_tau_frac > 0 ? g->opt.single_tau_frac : cell_tau_frac(N0);
+    S.su = 0;
+    S.m = 0;
+    S.done = false;
+    S.status = SG_OK;
+    return SG_OK;
+}
+
+// Record the residual now in host_red[0]; decide whether the solve is over.
+void solve_check(sg_grid* g, SolveState& S) {
+    const double rel = std::sqrt(g->host_red[0].sumsq / S.nn) / S.rden;
+    S.info.history[S.m] = rel;
+    S.info.rel_residual = rel;
+    S.info.max_residual = g->host_red[0].maxabs;
+    if (!std::isfinite(rel)) {
+        S.status = fail(SG_ERR_NONFINITE, "residual norm is not finite");
+        S.done = true;
+    } else if (g->opt.fixed_cycles == 0 && rel <= S.tol) {
+        S.done = true;
+    } else if (S.m >= S.limit) {
+        if (g->opt.fixed_cycles == 0) S.status = fail(SG_ERR_NOT_CONVERGED, "max_cycles reached above the tolerance");
+        S.done = true;
     }
-    local.cycles = m;
+}
+
+// One single-level super-step (levels == 1), its residual and norm copy.
+sg_status solve_single_step(sg_grid* g, SolveState& S) {
+    const Level& L0 = g->lv[0];
+    const int s = g->opt.single_s > 0 ? g->opt.single_s : S.single_sched[S.m];
+    if (g->precision == SG_MIXED) {
+        // mixed precision: an FP32 super-step on the error equation L e = r
+        float* e = (float*)L0.u;
+        SG_CK(cudaMemsetAsync(e, 0, L0.n * sizeof(float), g->st));
+        SG_TRY(superstep<float>(g, 0, 1, s, S.single_c, false, e, (const float*)L0.rhs));
+        {
+            ProfScope ps(g, K_UPDATE, 20.0 * L0.n);
+            SG_CK(launch_add_f32_to_f64(S.phi, e, L0.n, g->st));
+        }
+        ++g->launches;
+    } else {
+        SG_TRY(superstep<double>(g, 0, 1, s, S.single_c, S.faces, S.phi, S.f));
+    }
+    S.su += L0.n * (long long)s;
+    SG_TRY(level0_residual(g, S.phi, S.f, S.faces));
+    SG_CK(cudaMemcpyAsync(g->host_red, g->red, sizeof(Reduced), cudaMemcpyDeviceToHost, g->st));
+    *g->host_ss = 0;
+    return SG_OK;
+}
+
+// Book-keeping after a cycle's work has completed (stream synchronised).
+void solve_after_cycle(sg_grid* g, SolveState& S) {
+    if (S.L > 1) {
+        S.su += stage_updates_per_cycle(g, S.L);
+        S.info.coarse_ss[S.m] = *g->host_ss;
+        const Level& Lc = g->lv[S.L - 1];
+        const int Nc = std::max(Lc.nx, std::max(Lc.ny, Lc.nz));
+        const std::vector<int> sc = accelerated_schedule(Nc, std::max(1, *g->host_ss));
+        for (int q = 0; q < *g->host_ss && q < (int)sc.size(); ++q) S.su += Lc.n * (long long)sc[q];
+    }
+    ++S.m;
+}
+
+sg_status solve_end(sg_grid* g, SolveState& S, sg_solve_info* info) {
+    const Level& L0 = g->lv[0];
+    S.info.cycles = S.m;
     if (all_periodic(g)) {
         int nb = 0;
-        SG_CK(launch_sum_partials_f64(phi, L0.n, g->partials, &nb, g->st));
+        SG_CK(launch_sum_partials_f64(S.phi, L0.n, g->partials, &nb, g->st));
         SG_CK(launch_finalize(g->partials, nb, g->red + 1, g->st));
-        SG_CK(launch_sub_mean_f64(phi, L0.n, g->red + 1, g->st));
+        SG_CK(launch_sub_mean_f64(S.phi, L0.n, g->red + 1, g->st));
         g->launches += 3;
     }
     SG_CK(cudaEventRecord(g->ev1, g->st));
     SG_CK(cudaEventSynchronize(g->ev1));
     float ms = 0.f;
     SG_CK(cudaEventElapsedTime(&ms, g->ev0, g->ev1));
-    local.elapsed_ms = ms;
-    local.stage_cell_updates = su;
-    local.kernel_launches = g->launches - launches0;
-    local.status = status;
-    if (info) *info = local;
-    return status;
+    S.info.elapsed_ms = ms;
+    S.info.stage_cell_updates = S.su;
+    S.info.kernel_launches = g->launches - S.launches0;
+    S.info.status = S.status;
+    if (info) *info = S.info;
+    return S.status;
+}
+
+// The solve loop of sg_solve (phi, f, faces) and sg_backward (lam, w, none).
+sg_status solve_impl(sg_grid* g, double tol, int L, double* phi, const double* f, bool faces,
+                     bool have_guess, sg_solve_info* info) {
+    SolveState S;
+    SG_TRY(solve_begin(g, S, tol, L, phi, f, faces, have_guess));
+    while (true) {
+        solve_check(g, S);
+        if (S.done) break;
+        bool replayed = false;
+        if (L == 1) SG_TRY(solve_single_step(g, S));
+        else SG_TRY(run_cycle(g, L, phi, f, faces, &replayed));
+        SG_CK(cudaStreamSynchronize(g->st));
+        prof_sync_point(g, replayed);
+        solve_after_cycle(g, S);
+    }
+    return solve_end(g, S, info);
 }
 
 sg_status copy_in(double* dst, const double* src, long long n, int on_device, cudaStream_t st) {
@@ -799,6 +849,7 @@ void free_grid(sg_grid* g) {
     for (const ProfRec& r : g->live) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
     for (cudaEvent_t e : g->ev_pool) cudaEventDestroy(e);
     if (g->own_stream) cudaStreamDestroy(g->own_stream);
+    if (g->batch_stream) cudaStreamDestroy(g->batch_stream);
     delete g;
 }
 
@@ -1035,12 +1086,191 @@ sg_status sg_backward(sg_grid* g, const double* dL_dphi, double* dL_drho, int on
 sg_status sg_solve_batch(sg_grid* const* grids, int n, double tol, sg_solve_info* infos) {
     g_err.clear();
     if (!grids || n < 0) return fail(SG_ERR_ARG, "bad batch arguments");
-    sg_status first = SG_OK;
+    if (!(tol >= 0.0)) return fail(SG_ERR_ARG, "tol must be >= 0");
     for (int i = 0; i < n; ++i) {
-        const sg_status s = sg_solve(grids[i], tol, 0, 0, infos ? &infos[i] : nullptr);
-        if (s != SG_OK && first == SG_OK) first = s;
+        if (!grids[i]) return fail(SG_ERR_ARG, "NULL grid in batch");
+        if (!grids[i]->have_density) return fail(SG_ERR_STATE, "sg_set_density first (batch)");
+        for (int k = 0; k < i; ++k)
+            if (grids[k] == grids[i]) return fail(SG_ERR_ARG, "a grid appears twice in the batch");
     }
+    sg_status first = SG_OK;
+    // Grids whose V-cycle can be captured go into one multi-branch CUDA graph per
+    // cycle; the rest (single level, coarsest level too large for one CTA, graph
+    // replay disabled) are solved one after the other.
+    std::vector<int> par;
+    for (int i = 0; i < n; ++i) {
+        sg_grid* g = grids[i];
+        const int L = g->max_levels;
+        const bool ok = L > 1 && g->opt.use_graph &&
+                        (g->precision == SG_MIXED ? coarse_fits<float>(g->lv[L - 1].n)
+                                                  : coarse_fits<double>(g->lv[L - 1].n));
+        if (ok) {
+            par.push_back(i);
+        } else {
+            const sg_status st = sg_solve(g, tol, 0, 0, infos ? &infos[i] : nullptr);
+            if (st != SG_OK && first == SG_OK) first = st;
+        }
+    }
+    if (par.empty()) return first;
+    const size_t P = par.size();
+    std::vector<SolveState> S(P);
+    std::vector<cudaEvent_t> join(P, nullptr);
+    cudaEvent_t fork = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    sg_status err = SG_OK;
+    auto cleanup = [&]() {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (fork) cudaEventDestroy(fork);
+        for (auto e : join)
+            if (e) cudaEventDestroy(e);
+    };
+    auto bail = [&](sg_status st) {
+        cleanup();
+        return st;
+    };
+    if (cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) != cudaSuccess) return bail(fail(SG_ERR_CUDA, "event"));
+    for (size_t k = 0; k < P; ++k) {
+        sg_grid* g = grids[par[k]];
+        if (!g->batch_stream && cudaStreamCreateWithFlags(&g->batch_stream, cudaStreamNonBlocking) != cudaSuccess)
+            return bail(fail(SG_ERR_CUDA, "cudaStreamCreate (batch)"));
+        if (cudaEventCreateWithFlags(&join[k], cudaEventDisableTiming) != cudaSuccess)
+            return bail(fail(SG_ERR_CUDA, "event"));
+        err = solve_begin(g, S[k], tol, g->max_levels, g->phi, g->f, g->have_faces, g->guess_set);
+        if (err != SG_OK) return bail(err);
+        g->guess_set = false;
+    }
+    cudaStream_t origin = grids[par[0]]->st;
+    std::vector<size_t> active_prev;
+    long long graph_kernels = 0;
+    while (true) {
+        std::vector<size_t> active;
+        for (size_t k = 0; k < P; ++k) {
+            if (S[k].done) continue;
+            solve_check(grids[par[k]], S[k]);
+            if (!S[k].done) active.push_back(k);
+        }
+        if (active.empty()) break;
+        if (active != active_prev) {
+            // (Re)capture: fork one branch per unconverged grid off the origin stream.
+            if (exec) cudaGraphExecDestroy(exec);
+            exec = nullptr;
+            cudaGraph_t graph = nullptr;
+            if (cudaStreamBeginCapture(origin, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+                return bail(fail(SG_ERR_CUDA, "batch capture"));
+            sg_status cst = SG_OK;
+            cudaEventRecord(fork, origin);
+            graph_kernels = 0;
+            for (size_t k : active) {
+                sg_grid* g = grids[par[k]];
+                cudaStreamWaitEvent(g->batch_stream, fork, 0);
+                cudaStream_t saved = g->st;
+                const bool prof = g->prof;
+                g->st = g->batch_stream;
+                g->prof = false;
+                const long long before = g->launches;
+                cst = cycle_body(g, S[k].L, S[k].phi, S[k].f, S[k].faces);
+                graph_kernels += g->launches - before;
+                g->launches = before;
+                g->st = saved;
+                g->prof = prof;
+                if (cst != SG_OK) break;
+                cudaEventRecord(join[k], g->batch_stream);
+                cudaStreamWaitEvent(origin, join[k], 0);
+            }
+            const cudaError_t ec = cudaStreamEndCapture(origin, &graph);
+            if (cst != SG_OK) {
+                if (graph) cudaGraphDestroy(graph);
+                return bail(cst);
+            }
+            if (ec != cudaSuccess) return bail(fail(SG_ERR_CUDA, std::string("batch capture: ") + cudaGetErrorString(ec)));
+            const cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (ei != cudaSuccess) {
+                exec = nullptr;
+                return bail(fail(SG_ERR_CUDA, std::string("batch instantiate: ") + cudaGetErrorString(ei)));
+            }
+            active_prev = active;
+        }
+        if (cudaGraphLaunch(exec, origin) != cudaSuccess || cudaStreamSynchronize(origin) != cudaSuccess)
+            return bail(fail(SG_ERR_CUDA, "batch graph launch"));
+        for (size_t k : active) {
+            sg_grid* g = grids[par[k]];
+            g->launches += graph_kernels / (long long)active.size();
+            solve_after_cycle(g, S[k]);
+        }
+    }
+    for (size_t k = 0; k < P; ++k) {
+        sg_grid* g = grids[par[k]];
+        const sg_status st = solve_end(g, S[k], infos ? &infos[par[k]] : nullptr);
+        if (st == SG_OK || st == SG_ERR_NOT_CONVERGED) {
+            g->have_solution = true;
+            g->last_levels = S[k].L;
+        }
+        if (st != SG_OK && first == SG_OK) first = st;
+    }
+    cleanup();
     return first;
+}
+
+sg_status sg_autotune(sg_grid* g, int levels, int keep_order, sg_tune_entry* table, int cap, int* count) {
+    g_err.clear();
+    if (!g) return fail(SG_ERR_ARG, "NULL grid");
+    if (!g->have_density) return fail(SG_ERR_STATE, "sg_set_density first");
+    if (levels < 0 || levels > g->max_levels) return fail(SG_ERR_ARG, "levels exceeds the level rule");
+    const int L = levels == 0 ? g->max_levels : levels;
+    if (L < 2) return fail(SG_ERR_ARG, "autotuning needs a multigrid hierarchy (levels >= 2)");
+    const sg_options saved = g->opt;
+    struct Cand { int order, s, fused; double c; };
+    std::vector<Cand> cands;
+    for (int order = 1; order <= 2; ++order) {
+        if (keep_order && order != saved.rkl_order) continue;
+        for (int s = 2; s <= 6; ++s) {
+            const double cs1[] = {0.6, 0.75, 0.9};
+            const double cs2[] = {0.8, 1.0};
+            const double* cs = order == 1 ? cs1 : cs2;
+            const int ncs = order == 1 ? 3 : 2;
+            for (int ic = 0; ic < ncs; ++ic)
+                for (int fz = 0; fz <= (g->precision == SG_MIXED ? 1 : 0); ++fz) cands.push_back({order, s, fz, cs[ic]});
+        }
+    }
+    double best = 1e300;
+    sg_options best_opt = saved;
+    int tried = 0;
+    for (const Cand& c : cands) {
+        g->opt = saved;
+        g->opt.rkl_order = c.order;
+        g->opt.s_smooth = c.s;
+        g->opt.tau_frac = c.c;
+        g->opt.fused = c.fused;
+        // Time 2 and 6 cycles (after a capture / warm-up run) and take the
+        // difference, so the per-solve set-up cost drops out of the score.
+        sg_solve_info info2, info6;
+        sg_status st = SG_OK;
+        for (int rep = 0; rep < 3 && st == SG_OK; ++rep) {
+            g->opt.fixed_cycles = rep == 2 ? 6 : 2;
+            st = solve_impl(g, 0.0, L, g->phi, g->f, g->have_faces, false, rep == 2 ? &info6 : &info2);
+        }
+        if (st != SG_OK) {
+            g->opt = saved;
+            return st;
+        }
+        const double h2 = info6.history[2], h6 = info6.history[6];
+        const double factor = (h2 > 0 && h6 > 0) ? std::pow(h6 / h2, 0.25) : 1.0;
+        const double mpc = (info6.elapsed_ms - info2.elapsed_ms) / 4.0;
+        const double score = (factor > 0 && factor < 1) ? mpc / -std::log10(factor) : 1e300;
+        if (table && tried < cap) table[tried] = {c.order, c.s, c.fused, c.c, mpc, factor, score};
+        (void)info2;
+        ++tried;
+        if (score < best) {
+            best = score;
+            best_opt = g->opt;
+        }
+    }
+    best_opt.fixed_cycles = saved.fixed_cycles;
+    g->opt = best_opt;
+    g->have_solution = false;
+    if (count) *count = tried;
+    return SG_OK;
 }
 
 void sg_destroy(sg_grid* g) { free_grid(g); }

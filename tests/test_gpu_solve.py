@@ -240,3 +240,42 @@ def test_kernel_profile_counts_every_class():
     assert st["residual_l0"]["launches"] == info["cycles"] + 1
     assert st["residual_restrict"]["launches"] == 3 * info["cycles"]
     assert st["residual_l0"]["bytes"] == 20.0 * 64 ** 3 * (info["cycles"] + 1)
+
+
+def test_batch_graph_matches_individual_solves_exactly():
+    # every branch of the batch graph runs the same kernels on the same data as a
+    # single solve: results agree to the last bit, cycle counts are equal
+    sg = _sg()
+    probs = [W.blobs(32, np.random.default_rng(5)), W.blobs(64, np.random.default_rng(6))]
+    gp = W.grf(32, seed=7)
+    probs.append(gp)
+    sin = W.sinusoid(16)
+    probs.append(sin)
+    anis = W.Problem(rho=W.random_field((8, 4, 6), 8), lo=(0, 0, 0), hi=(1, 1, 1), bc=(0, 0, 0),
+                     faces=W.random_faces((8, 4, 6), 9))          # one level: solved on its own
+    probs.append(anis)
+    precs = ["mixed", "mixed", "mixed", "fp64", "fp64"]
+    batch = [grid_for(p, pr) for p, pr in zip(probs, precs)]
+    single = [grid_for(p, pr) for p, pr in zip(probs, precs)]
+    infos = sg.solve_batch(batch, tol=1e-9)
+    for gb, gs, ib in zip(batch, single, infos):
+        isg = gs.solve(tol=1e-9)
+        assert ib["cycles"] == isg["cycles"]
+        np.testing.assert_array_equal(gb.potential(), gs.potential())
+    ref, _ = O.solve(gp.rho, gp.lo, gp.hi, gp.bc, None, 1.0, tol=1e-12)
+    assert rel_l2(batch[2].potential(), ref) < 1e-8
+
+
+def test_autotune_keeps_order_and_converges():
+    p = W.sphere(64)
+    g = grid_for(p, "mixed")
+    opts, table = g.autotune(levels=4, keep_order=True)
+    assert len(table) > 0 and all(t["rkl_order"] == 2 for t in table)
+    best = min(table, key=lambda t: t["ms_per_decade"])
+    assert opts["s_smooth"] == best["s_smooth"] and opts["rkl_order"] == 2
+    assert all(0 < t["factor"] < 1 for t in table)
+    g.set_density(p.rho, 1.0)
+    info = g.solve(tol=1e-9, levels=4)
+    ref, _ = O.solve(p.rho, p.lo, p.hi, p.bc, p.faces, 1.0, tol=1e-12, levels=4)
+    assert rel_l2(g.potential(), ref) < 1e-7
+    assert info["rel_residual"] <= 1e-9
