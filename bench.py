@@ -67,7 +67,7 @@ def dist_env():
 
 def config(world):
     return {"workload": f"sphere{N}", "grid": [N, N, N], "levels": LEVELS, "tol": TOL,
-            "precision": "mixed (FP32 V-cycle, FP64 residual + defect correction)",
+            "precision": "mixed (FP32 V-cycle; FP64 residual carried by exact recurrence, confirmed in FP64 at the end; FP64 defect correction)",
             "smoother": "RKL2 s=3 tau=tau_max, N_pre=2, N_post=1",
             "coarse": "accelerated RKL1 on 16^3, coarse_tol=1e-2",
             "boundary": "Dirichlet from analytic sphere potential",
@@ -348,7 +348,7 @@ def run_ours(a, world, rank, local):
         peak, src = hbm_peak()
         ach = d["bytes"] / (d["ms"] * 1e-3) / 1e9 if d["ms"] > 0 else 0.0
         per_launch = d["bytes"] / max(1, d["launches"])
-        traffic = ncu_traffic(dom, 1.0) if dom in ("rkl_stage_l0", "residual_l0", "update") else None
+        traffic = ncu_traffic(dom, 1.0) if dom in ("rkl_stage_l0", "residual_l0", "update_residual") else None
         if traffic is not None:
             cells_per_launch = n0
             traffic = traffic * cells_per_launch

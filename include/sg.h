@@ -190,7 +190,10 @@ typedef struct sg_tune_entry {
     int    fused;              /* fused (temporally blocked) super-steps on or off */
     double tau_frac;           /* smoother tau / tau_max tried */
     double ms_per_cycle;       /* measured device time per V-cycle */
-    double factor;             /* measured residual reduction per V-cycle */
+    double factor;             /* residual reduction per V-cycle: measured over cycles 2..6,
+                                  or the smoother's factor on the checkerboard mode raised to
+                                  n_pre + n_post when larger (that mode bounds the asymptotic
+                                  rate: the coarse grid does not see it) */
     double ms_per_decade;      /* ms_per_cycle / -log10(factor): the score (lower is better) */
 } sg_tune_entry;
 
@@ -200,8 +203,9 @@ typedef struct sg_tune_entry {
  * keep_order is 1 --, s = 2..6, a few tau fractions, fused on and off) run
  * two and six V-cycles at `levels` (0 = the level rule), take the difference
  * of their CUDA-event times (so per-solve set-up drops out) and score the time
- * per decade of residual reduction over cycles 2..6; the best candidate is
- * written into the grid's options.  The trial cycles overwrite the potential
+ * per decade of residual reduction over cycles 2..6, bounded below by the
+ * smoother's damping of the checkerboard mode (sg_tune_entry.factor); the best
+ * candidate is written into the grid's options.  The trial cycles overwrite the potential
  * (call before sg_solve).  table (may be NULL) receives up to cap entries,
  * *count the number tried.  The App. A.4 spectral analysis motivates the
  * search: the best s balances the cost of s stages against the reduction of

@@ -182,7 +182,7 @@ __device__ __forceinline__ void block_reduce_write(A sumsq, A maxabs, A sum, Par
 template <typename TI, typename TO, bool UNIFORM, bool FACES>
 __global__ void __launch_bounds__(BX * BY)
 k_residual(const LevelGeom g, const TI* __restrict__ u, const TI* __restrict__ rhs, TO* r_out,
-           Partial* partials, int kchunk) {
+           TI* r_full, Partial* partials, int kchunk) {
     // Norms accumulate in the output precision: an FP32 residual needs no FP64
     // arithmetic beyond the stencil itself (FP64 issue rate is the limit on GB300).
     using A = typename Acc<TO>::type;
@@ -213,6 +213,7 @@ k_residual(const LevelGeom g, const TI* __restrict__ u, const TI* __restrict__ r
             }
             const TO ro = TO(r);
             if (r_out) r_out[idx] = ro;
+            if (r_full) r_full[idx] = r;
             const A ra = A(ro);
             sq = fma(ra, ra, sq);
             mx = fmax(mx, fabs(ra));
@@ -346,6 +347,110 @@ k_prolong_correct(const LevelGeom g, const T* __restrict__ coarse, T* fine_u, in
 }
 
 // ---------------------------------------------------------------------------
+// Defect-correction update with the FP64 residual carried by recurrence.
+// For phi <- phi + e (e: the FP32 correction of the inner V-cycle),
+//   r = f - A phi   <-   r - A_0 e,
+// where A_0 is the Laplacian with homogeneous ghosts (the Dirichlet data enter
+// A affinely, so they cancel in A(phi + e) - A phi).  A_0 e is evaluated
+// without rounding error that matters: the seven terms are summed in FP32
+// with error-free transformations (TwoSum, and an FMA for the error of the
+// product 6 e_c), giving hi + lo to about 2^-48 of the largest term; hi and lo
+// then enter the FP64 residual with one FMA each.  Float <-> double
+// conversions are done on the bit patterns (IEEE 754 fields, integer pipe):
+// on GB300 every FP64-pipe instruction, conversions included, issues at 1/64
+// of the FP32 rate, and this kernel keeps three of them per cell (phi + e and
+// the two FMAs).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& err) {
+    s = a + b;
+    const float bb = s - a;
+    err = (a - (s - bb)) + (b - bb);
+}
+
+// float -> double from the IEEE fields (subnormal floats, below 1.2e-38, become 0).
+__device__ __forceinline__ double f2d_bits(float x) {
+    const unsigned u = __float_as_uint(x);
+    const unsigned sgn = u & 0x80000000u, ex = (u >> 23) & 0xffu, m = u & 0x7fffffu;
+    unsigned hi, lo;
+    if (ex == 0u) { hi = sgn; lo = 0u; }
+    else if (ex == 255u) { hi = sgn | 0x7ff00000u | (m >> 3); lo = m << 29; }
+    else { hi = sgn | ((ex + 896u) << 20) | (m >> 3); lo = m << 29; }
+    return __hiloint2double((int)hi, (int)lo);
+}
+
+// double -> float by truncating the significand (within one FP32 ulp; values
+// below 2^-126 become 0, beyond the FP32 range +-inf).
+__device__ __forceinline__ float d2f_bits(double x) {
+    const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+    const unsigned sgn = hi & 0x80000000u, ex = (hi >> 20) & 0x7ffu, mh = hi & 0xfffffu;
+    if (ex <= 896u) return __uint_as_float(sgn);
+    if (ex >= 1151u) return __uint_as_float(sgn | 0x7f800000u | ((ex == 2047u && (mh | lo)) ? 0x400000u : 0u));
+    return __uint_as_float(sgn | ((ex - 896u) << 23) | (mh << 3) | (lo >> 29));
+}
+
+template <bool UNIFORM>
+__global__ void __launch_bounds__(BX * BY)
+k_update_residual(const LevelGeom g, double* __restrict__ phi, const float* __restrict__ e,
+                  double* __restrict__ r64, float* __restrict__ r32, Partial* partials, int kchunk) {
+    const int i = blockIdx.x * BX + threadIdx.x;
+    const int j = blockIdx.y * BY + threadIdx.y;
+    float sq = 0.0f, mx = 0.0f;
+    if (i < g.nx && j < g.ny) {
+        const int k0 = blockIdx.z * kchunk;
+        const int k1 = min(k0 + kchunk, g.nz);
+        const int plane = g.nx * g.ny;
+        int idx = k0 * plane + j * g.nx + i;
+        float c = e[idx];
+        float zm = (k0 > 0) ? e[idx - plane] : z_low<false>(e, g, i, j, idx, plane, c);
+        for (int k = k0; k < k1; ++k, idx += plane) {
+            const float zp = (k < g.nz - 1) ? e[idx + plane] : z_high<false>(e, g, i, j, idx, plane, c);
+            float xm, xp, ym, yp;
+            xy_neighbours<false>(e, g, i, j, k, idx, c, xm, xp, ym, yp);
+            double r = r64[idx];
+            if (UNIFORM) {
+                // sum of the six neighbours minus 6 c, compensated
+                const float p = -6.0f * c;
+                const float perr = fmaf(-6.0f, c, -p);          // -6 c = p + perr exactly
+                float s = xm, comp = perr, t;
+                two_sum(s, xp, s, t); comp += t;
+                two_sum(s, ym, s, t); comp += t;
+                two_sum(s, yp, s, t); comp += t;
+                two_sum(s, zm, s, t); comp += t;
+                two_sum(s, zp, s, t); comp += t;
+                two_sum(s, p, s, t); comp += t;
+                const double nih2 = -g.ihx2;
+                r = fma(nih2, f2d_bits(s), r);
+                r = fma(nih2, f2d_bits(comp), r);
+            } else {
+                // per-axis second differences (-2 c is exact), compensated
+                const float m2 = -2.0f * c;
+                const float a[3][2] = {{xm, xp}, {ym, yp}, {zm, zp}};
+                const double ih[3] = {g.ihx2, g.ihy2, g.ihz2};
+#pragma unroll
+                for (int d = 0; d < 3; ++d) {
+                    float s, comp, t;
+                    two_sum(a[d][0], a[d][1], s, comp);
+                    two_sum(s, m2, s, t);
+                    comp += t;
+                    r = fma(-ih[d], f2d_bits(s), r);
+                    r = fma(-ih[d], f2d_bits(comp), r);
+                }
+            }
+            r64[idx] = r;
+            phi[idx] = phi[idx] + f2d_bits(c);
+            const float rf = d2f_bits(r);
+            r32[idx] = rf;
+            sq = fmaf(rf, rf, sq);
+            mx = fmaxf(mx, fabsf(rf));
+            zm = c;
+            c = zp;
+        }
+    }
+    const int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+    block_reduce_write<float>(sq, mx, 0.0f, partials, bid);
+}
+
+// ---------------------------------------------------------------------------
 // Small helpers.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kRedThreads) k_finalize(const Partial* __restrict__ p, int n,
@@ -462,16 +567,16 @@ cudaError_t launch_stage(const LevelGeom& g, int order, bool first, const StageC
 
 template <typename TI, typename TO>
 cudaError_t launch_residual(const LevelGeom& g, const TI* u, const TI* rhs, TO* r_out,
-                            Partial* partials, int* nblocks_out, cudaStream_t st) {
+                            Partial* partials, int* nblocks_out, cudaStream_t st, TI* r_full) {
     const int kc = kchunk_for(g, BX, BY);
     dim3 block(BX, BY, 1);
     dim3 grid((g.nx + BX - 1) / BX, (g.ny + BY - 1) / BY, (g.nz + kc - 1) / kc);
     const bool uniform = g.ihx2 == g.ihy2 && g.ihy2 == g.ihz2;   // (also true for the FP32 copies)
     const bool faces = has_faces(g);
-    if (uniform && faces) k_residual<TI, TO, true, true><<<grid, block, 0, st>>>(g, u, rhs, r_out, partials, kc);
-    else if (uniform) k_residual<TI, TO, true, false><<<grid, block, 0, st>>>(g, u, rhs, r_out, partials, kc);
-    else if (faces) k_residual<TI, TO, false, true><<<grid, block, 0, st>>>(g, u, rhs, r_out, partials, kc);
-    else k_residual<TI, TO, false, false><<<grid, block, 0, st>>>(g, u, rhs, r_out, partials, kc);
+    if (uniform && faces) k_residual<TI, TO, true, true><<<grid, block, 0, st>>>(g, u, rhs, r_out, r_full, partials, kc);
+    else if (uniform) k_residual<TI, TO, true, false><<<grid, block, 0, st>>>(g, u, rhs, r_out, r_full, partials, kc);
+    else if (faces) k_residual<TI, TO, false, true><<<grid, block, 0, st>>>(g, u, rhs, r_out, r_full, partials, kc);
+    else k_residual<TI, TO, false, false><<<grid, block, 0, st>>>(g, u, rhs, r_out, r_full, partials, kc);
     if (nblocks_out) *nblocks_out = (int)(grid.x * grid.y * grid.z);
     return cudaGetLastError();
 }
@@ -494,6 +599,18 @@ cudaError_t launch_prolong_correct(const LevelGeom& g, const T* coarse, T* fine_
     dim3 block(BX, BY, 1);
     dim3 grid((g.nx + BX - 1) / BX, (g.ny + BY - 1) / BY, (g.nz + kc - 1) / kc);
     k_prolong_correct<T><<<grid, block, 0, st>>>(g, coarse, fine_u, kc);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_update_residual(const LevelGeom& g, double* phi, const float* e, double* r64, float* r32,
+                                  Partial* partials, int* nblocks_out, cudaStream_t st) {
+    const int kc = kchunk_for(g, BX, BY);
+    dim3 block(BX, BY, 1);
+    dim3 grid((g.nx + BX - 1) / BX, (g.ny + BY - 1) / BY, (g.nz + kc - 1) / kc);
+    const bool uniform = g.ihx2 == g.ihy2 && g.ihy2 == g.ihz2;
+    if (uniform) k_update_residual<true><<<grid, block, 0, st>>>(g, phi, e, r64, r32, partials, kc);
+    else k_update_residual<false><<<grid, block, 0, st>>>(g, phi, e, r64, r32, partials, kc);
+    if (nblocks_out) *nblocks_out = (int)(grid.x * grid.y * grid.z);
     return cudaGetLastError();
 }
 
@@ -539,11 +656,11 @@ template cudaError_t launch_stage<double>(const LevelGeom&, int, bool, const Sta
                                           const double*, const double*, const double*,
                                           const double*, double*, double*, cudaStream_t);
 template cudaError_t launch_residual<double, double>(const LevelGeom&, const double*, const double*,
-                                                     double*, Partial*, int*, cudaStream_t);
+                                                     double*, Partial*, int*, cudaStream_t, double*);
 template cudaError_t launch_residual<double, float>(const LevelGeom&, const double*, const double*,
-                                                    float*, Partial*, int*, cudaStream_t);
+                                                    float*, Partial*, int*, cudaStream_t, double*);
 template cudaError_t launch_residual<float, float>(const LevelGeom&, const float*, const float*,
-                                                   float*, Partial*, int*, cudaStream_t);
+                                                   float*, Partial*, int*, cudaStream_t, float*);
 template cudaError_t launch_residual_restrict<float>(const LevelGeom&, const float*, const float*,
                                                      float*, Partial*, int*, cudaStream_t);
 template cudaError_t launch_residual_restrict<double>(const LevelGeom&, const double*, const double*,

@@ -72,10 +72,11 @@ cudaError_t launch_stage(const LevelGeom& g, int order, bool first, const StageC
                          const T* ym1, const T* ym2, const T* y0, const T* z0, const T* rhs,
                          T* out, T* z0_out, cudaStream_t st);
 
-// r = rhs - L u (TI), optionally stored as TO, block partials of sum r^2 / max|r|.
+// r = rhs - L u (TI), optionally stored as TO (r_out) and in full precision
+// (r_full), block partials of sum r^2 / max|r|.
 template <typename TI, typename TO>
 cudaError_t launch_residual(const LevelGeom& g, const TI* u, const TI* rhs, TO* r_out,
-                            Partial* partials, int* nblocks_out, cudaStream_t st);
+                            Partial* partials, int* nblocks_out, cudaStream_t st, TI* r_full = nullptr);
 
 // Fused residual + 8-cell restriction (+ norm partials, + coarse sum partials).
 template <typename T>
@@ -89,6 +90,11 @@ cudaError_t launch_prolong_correct(const LevelGeom& fine, const T* coarse, T* fi
                                    cudaStream_t st);
 
 cudaError_t launch_finalize(const Partial* partials, int n, Reduced* out, cudaStream_t st);
+
+// phi += e (FP64) and r64 -= A_0 e (FP64 residual by recurrence, A_0 e summed
+// error-free in FP32), r32 = r64 rounded, block partials of |r32|.
+cudaError_t launch_update_residual(const LevelGeom& g, double* phi, const float* e, double* r64, float* r32,
+                                  Partial* partials, int* nblocks_out, cudaStream_t st);
 
 template <typename T>
 cudaError_t launch_subtract_mean(T* x, long long n, const Reduced* red, cudaStream_t st);

@@ -234,12 +234,16 @@ def test_kernel_profile_counts_every_class():
     st = g.kernel_stats()
     g.set_profiling(False)
     for name in ("rkl_stage_l0", "rkl_stage_coarse", "residual_l0", "residual_restrict",
-                 "prolong_correct", "coarse_solve", "update"):
+                 "prolong_correct", "coarse_solve", "update_residual"):
         assert st[name]["launches"] > 0 and st[name]["ms"] > 0, name
-    # one residual per cycle plus the initial one; three restrictions per cycle (4 levels)
-    assert st["residual_l0"]["launches"] == info["cycles"] + 1
+    # mixed precision: the true FP64 residual at the start and once to confirm
+    # convergence; the recurrence update after every cycle; three restrictions
+    # per cycle (4 levels)
+    assert st["residual_l0"]["launches"] == 2
+    assert st["update_residual"]["launches"] == info["cycles"]
     assert st["residual_restrict"]["launches"] == 3 * info["cycles"]
-    assert st["residual_l0"]["bytes"] == 20.0 * 64 ** 3 * (info["cycles"] + 1)
+    assert st["residual_l0"]["bytes"] == 20.0 * 64 ** 3 * 2
+    assert st["update_residual"]["bytes"] == 40.0 * 64 ** 3 * info["cycles"]
 
 
 def test_batch_graph_matches_individual_solves_exactly():
@@ -273,7 +277,13 @@ def test_autotune_keeps_order_and_converges():
     assert len(table) > 0 and all(t["rkl_order"] == 2 for t in table)
     best = min(table, key=lambda t: t["ms_per_decade"])
     assert opts["s_smooth"] == best["s_smooth"] and opts["rkl_order"] == 2
-    assert all(0 < t["factor"] < 1 for t in table)
+    assert all(0 < t["factor"] <= 1 + 1e-9 for t in table)
+    # RKL2 with even s at tau_max does not damp the checkerboard mode, which
+    # the coarse grid cannot see: such candidates never converge and score last
+    for t in table:
+        if t["s_smooth"] % 2 == 0 and t["tau_frac"] == 1.0:
+            assert t["factor"] > 0.999
+    assert not (opts["s_smooth"] % 2 == 0 and opts["tau_frac"] == 1.0)
     g.set_density(p.rho, 1.0)
     info = g.solve(tol=1e-9, levels=4)
     ref, _ = O.solve(p.rho, p.lo, p.hi, p.bc, p.faces, 1.0, tol=1e-12, levels=4)

@@ -386,6 +386,34 @@ def test_vcycle_fixed_point():
     np.testing.assert_allclose(out, exact, atol=1e-11 * np.abs(exact).max())
 
 
+@pytest.mark.parametrize("order,s,c", [(2, 2, 1.0), (2, 4, 1.0), (2, 3, 1.0), (2, 2, 0.8),
+                                       (1, 3, 1.0), (1, 2, 0.75)])
+@pytest.mark.parametrize("bc", [(0, 0, 0), (1, 1, 1)])
+def test_vcycle_leaves_checkerboard_to_the_smoother(order, s, c, bc):
+    # (-1)^(i+j+k) is an eigenvector of the homogeneous Dirichlet and of the
+    # periodic operator (even sizes) with the top eigenvalue -4 sum 1/h^2, and
+    # its 8-child means vanish, so the coarse correction is zero and one
+    # V-cycle (f = 0) scales it by the smoother alone: tau = c tau_max puts it
+    # at x = 1 - 2c of the stability polynomial, R = P_s(x) (RKL1) or
+    # a_s + b_s P_s(x) (RKL2), applied n_pre + n_post times.  For RKL2 with
+    # even s and c = 1 that factor is exactly 1.
+    shape = (8, 12, 16)
+    h = O.spacing(shape, (0, 0, 0), (1.0, 1.5, 2.4))
+    k, j, i = np.meshgrid(*(np.arange(n) for n in shape), indexing="ij")
+    u0 = np.where((i + j + k) % 2 == 0, 1.0, -1.0)
+    opts = O.Options(rkl_order=order, s_smooth=s, tau_frac=c)
+    out = O.vcycle(u0.copy(), np.zeros(shape), h, bc, None, 3, opts)
+    x = 1.0 - 2.0 * c
+    if order == 1:
+        R = P(s, x)
+    else:
+        b = (s * s + s - 2.0) / (2.0 * s * (s + 1.0)) if s > 2 else 1.0 / 3.0
+        R = (1.0 - b) + b * P(s, x)
+    np.testing.assert_allclose(out, R ** (opts.n_pre + opts.n_post) * u0, atol=1e-12, rtol=0)
+    if order == 2 and s % 2 == 0 and c == 1.0:
+        np.testing.assert_allclose(out, u0, atol=1e-12, rtol=0)
+
+
 # ---------------------------------------------------------------------------
 # Behaviour printed in the paper
 # ---------------------------------------------------------------------------
