@@ -279,6 +279,52 @@ sg_status sg_op_prolong_correct(sg_grid* g, int level, int dtype, const void* co
 sg_status sg_op_coarse_solve(sg_grid* g, int level, int dtype, const void* rhs, void* u_out,
                              int* ss_done);
 
+/* ------------------------------------------------------------------------
+ * Allocation-free residual.  The paper has no counterpart: this computes what
+ * sg_op_residual_restrict computes (r = rhs - L u, the negative of Eq.
+ * residual, its 8-cell mean of Eq. restriction_example_3D, and the norms) and
+ * only changes where the reduction's scratch lives.
+ *
+ * For callers that may not allocate device memory while they run -- a job
+ * whose device memory is all reserved up front (a caching allocator holding
+ * the device, a real-time loop), or a host that owns only its own arrays and
+ * wants no grid object (sg_create_grid allocates every multigrid level).  It
+ * takes the finest-level geometry directly, runs the same kernels, and keeps
+ * the per-block partial norms in one array compiled into this library: 8192
+ * block slots, 256 KiB per device.  It calls no cudaMalloc, cudaFree or other
+ * allocating routine.
+ *
+ * nx, ny, nz, lo, hi, bc: as for sg_create_grid (the grid of u).  faces: NULL
+ * for the homogeneous rule ghost = -active (Eq. error_ghost), else six DEVICE
+ * pointers laid out as for sg_set_boundary (a NULL entry is a zero face;
+ * entries of periodic axes are ignored).  dtype: 0 = float64, 1 = float32.
+ * u, rhs: device [nz][ny][nx] arrays of dtype on the current device.
+ * coarse_out: device (nz/2, ny/2, nx/2) array of dtype receiving the 8-cell
+ * mean of r (every size even), or NULL.  norms: host, receives {sum r^2,
+ * max |r|} and synchronises the stream, or NULL; coarse_out and norms are not
+ * both NULL.  cuda_stream: a cudaStream_t (NULL = the legacy default stream).
+ *
+ * Limit: one slot per thread block of the launch, about ceil(nx/32) *
+ * ceil(ny/8) * (z chunks).  Every cube up to 1024^3 fits; a grid needing more
+ * than 8192 slots returns SG_ERR_ARG (with the count) before any launch.
+ *
+ * Set-up: the first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current; this may load the
+ * library's kernels onto the device) and caches it.  Make that first call
+ * before any stream capture begins.  Nothing in the array needs clearing:
+ * each block writes its own slot before the fold reads it, and the fold
+ * writes the whole result.
+ *
+ * The array is shared by every call on a device: calls whose work overlaps
+ * on one device (different streams, or threads without ordering) race on it
+ * and return wrong norms.  Serialise them (one stream, or an event between).
+ * Errors: SG_ERR_ARG, SG_ERR_CUDA.
+ */
+sg_status sg_residual_restrict_noalloc(int nx, int ny, int nz, const double lo[3], const double hi[3],
+                                       const int bc[3], const double* const faces[6], int dtype,
+                                       const void* u, const void* rhs, void* coarse_out,
+                                       double norms[2], void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -114,6 +114,8 @@ _SIGS = {
     "sg_set_profiling": ([_P, _I], _I),
     "sg_kernel_stats": ([_P, ctypes.POINTER(KernelStat)], _I),
     "sg_autotune": ([_P, _I, _I, ctypes.POINTER(TuneEntry), _I, ctypes.POINTER(_I)], _I),
+    "sg_residual_restrict_noalloc": ([_I, _I, _I, ctypes.POINTER(_D), ctypes.POINTER(_D), ctypes.POINTER(_I),
+                                      ctypes.POINTER(_P), _I, _P, _P, _P, ctypes.POINTER(_D), _P], _I),
 }
 
 
@@ -331,6 +333,32 @@ class Grid:
         _check(lib().sg_op_coarse_solve(self._h, level, dt, _dev_ptr(rhs, dt), _dev_ptr(out, dt),
                                         ctypes.byref(done)))
         return done.value
+
+
+def residual_restrict_noalloc(shape, lo, hi, bc, u, rhs, coarse_out=None, faces=None, norms=True,
+                              stream=None):
+    """Residual r = rhs - L u of the CUDA tensors u, rhs (shape (nz, ny, nx) on
+    the box [lo, hi], boundary kinds bc, all in x, y, z order) without a Grid
+    and without allocating device memory: its 8-cell mean into coarse_out (or
+    None) and, when norms is true, returns (sum r^2, max |r|).  faces: None
+    (homogeneous ghosts) or six CUDA float64 face tensors (None entries are
+    zero faces).  Runs on `stream` (a cudaStream_t as int; default: torch's
+    current stream).  Calls on one device must not overlap: they share one
+    scratch array."""
+    torch = _torch()
+    dt = 0 if u.dtype == torch.float64 else 1
+    nz, ny, nx = (int(v) for v in shape)
+    fp = None
+    if faces is not None:
+        fp = (_P * 6)(*[None if f is None else _dev_ptr(f, 0).value for f in faces])
+    out = (_D * 2)() if norms else None
+    if stream is None:
+        stream = torch.cuda.current_stream(u.device).cuda_stream
+    _check(lib().sg_residual_restrict_noalloc(nx, ny, nz, (_D * 3)(*lo), (_D * 3)(*hi), (_I * 3)(*bc), fp, dt,
+                                              _dev_ptr(u, dt), _dev_ptr(rhs, dt),
+                                              _dev_ptr(coarse_out, dt) if coarse_out is not None else None,
+                                              out, stream))
+    return (out[0], out[1]) if norms else None
 
 
 def solve_batch(grids, tol=1e-8):

@@ -15,6 +15,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <type_traits>
 #include <utility>
@@ -1428,3 +1429,130 @@ sg_status sg_op_coarse_solve(sg_grid* g, int level, int dtype, const void* rhs, 
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free residual, restriction and norms (sg_residual_restrict_noalloc).
+//
+// Some callers may not allocate device memory while they run: a job whose
+// memory is reserved up front (a caching allocator holding the whole device, a
+// real-time loop), or a host that owns only its arrays and wants no grid object
+// (creating one allocates every multigrid level).  This entry point runs the
+// same residual / residual-restrict and norm-fold kernels as
+// sg_op_residual_restrict, but the per-block partial norms and the folded
+// result live in one array compiled into this library, so it calls no
+// allocating routine.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int kStaticSlots = 8192;                                 // per-block partial norms
+constexpr size_t kStaticRedOffset = size_t(kStaticSlots) * sizeof(Partial);
+constexpr size_t kStaticBytes = kStaticRedOffset + 256;            // + the folded Reduced
+static_assert(kStaticRedOffset % 256 == 0 && sizeof(Reduced) <= 256, "static scratch layout");
+constexpr int kStaticMaxDevices = 64;
+
+}  // namespace
+
+// 256 KiB + 256 B per device, shared by every call on that device.
+static __device__ __align__(256) unsigned char sg_static_scratch[kStaticBytes];
+
+namespace {
+
+std::mutex g_static_mu;
+unsigned char* g_static_addr[kStaticMaxDevices] = {};
+
+// Device address of the scratch on the current device; looked up once per
+// device (the lookup may load this library's kernels onto that device).
+sg_status static_scratch(unsigned char** out) {
+    int dev = -1;
+    SG_CK(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kStaticMaxDevices) return fail(SG_ERR_ARG, "device ordinal beyond 63");
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    if (!g_static_addr[dev]) {
+        void* p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, sg_static_scratch);
+        if (e != cudaSuccess || !p)
+            return fail(SG_ERR_CUDA, std::string("cudaGetSymbolAddress(static scratch): ") + cudaGetErrorString(e));
+        g_static_addr[dev] = static_cast<unsigned char*>(p);
+    }
+    *out = g_static_addr[dev];
+    return SG_OK;
+}
+
+}  // namespace
+
+extern "C" sg_status sg_residual_restrict_noalloc(int nx, int ny, int nz, const double lo[3], const double hi[3],
+                                                  const int bc[3], const double* const faces[6], int dtype,
+                                                  const void* u, const void* rhs, void* coarse_out, double norms[2],
+                                                  void* cuda_stream) {
+    g_err.clear();
+    if (!lo || !hi || !bc) return fail(SG_ERR_ARG, "NULL lo, hi or bc");
+    const int n[3] = {nx, ny, nz};
+    for (int d = 0; d < 3; ++d) {
+        if (n[d] < 2 || n[d] > 4096) return fail(SG_ERR_ARG, "grid size must be in [2, 4096] per axis");
+        if (!(hi[d] > lo[d]) || !std::isfinite(lo[d]) || !std::isfinite(hi[d]))
+            return fail(SG_ERR_ARG, "need finite lo < hi on every axis");
+        if (bc[d] != SG_BC_DIRICHLET && bc[d] != SG_BC_PERIODIC) return fail(SG_ERR_ARG, "bad boundary kind");
+    }
+    if ((long long)nx * ny * nz > 2147483647LL) return fail(SG_ERR_ARG, "too many cells");
+    if (dtype != 0 && dtype != 1) return fail(SG_ERR_ARG, "dtype must be 0 (float64) or 1 (float32)");
+    if (!u || !rhs) return fail(SG_ERR_ARG, "bad pointers");
+    if (!coarse_out && !norms) return fail(SG_ERR_ARG, "nothing to compute: coarse_out and norms are both NULL");
+    if (coarse_out && ((nx | ny | nz) & 1)) return fail(SG_ERR_ARG, "restriction needs even sizes on every axis");
+
+    LevelGeom G;
+    G.nx = nx;
+    G.ny = ny;
+    G.nz = nz;
+    double ih2[3];
+    for (int d = 0; d < 3; ++d) {
+        const double h = (hi[d] - lo[d]) / n[d];
+        ih2[d] = 1.0 / (h * h);
+        G.per[d] = bc[d] == SG_BC_PERIODIC;
+    }
+    G.ihx2 = ih2[0];
+    G.ihy2 = ih2[1];
+    G.ihz2 = ih2[2];
+    G.ihx2f = float(G.ihx2);
+    G.ihy2f = float(G.ihy2);
+    G.ihz2f = float(G.ihz2);
+    for (int f = 0; f < 6; ++f) G.face[f] = (faces && bc[f / 2] == SG_BC_DIRICHLET) ? faces[f] : nullptr;
+
+    const long long need = coarse_out ? restrict_blocks(G) : residual_blocks(G);
+    if (need > kStaticSlots)
+        return fail(SG_ERR_ARG, "this grid needs " + std::to_string(need) + " block slots; the static scratch holds " +
+                                    std::to_string(kStaticSlots));
+
+    unsigned char* base = nullptr;
+    SG_TRY(static_scratch(&base));
+    Partial* partials = reinterpret_cast<Partial*>(base);
+    Reduced* red = reinterpret_cast<Reduced*>(base + kStaticRedOffset);
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+
+    // Every launched block writes its own slot before the fold reads it, and
+    // the fold writes the whole result: nothing here needs clearing.
+    int nb = 0;
+    if (coarse_out) {
+        if (dtype == 0)
+            SG_CK(launch_residual_restrict<double>(G, (const double*)u, (const double*)rhs, (double*)coarse_out,
+                                                   partials, &nb, st));
+        else
+            SG_CK(launch_residual_restrict<float>(G, (const float*)u, (const float*)rhs, (float*)coarse_out,
+                                                  partials, &nb, st));
+    } else {
+        if (dtype == 0)
+            SG_CK(launch_residual<double, double>(G, (const double*)u, (const double*)rhs, (double*)nullptr,
+                                                  partials, &nb, st));
+        else
+            SG_CK(launch_residual<float, float>(G, (const float*)u, (const float*)rhs, (float*)nullptr,
+                                                partials, &nb, st));
+    }
+    if (norms) {
+        SG_CK(launch_finalize(partials, nb, red, st));
+        Reduced h{};
+        SG_CK(cudaMemcpyAsync(&h, red, sizeof(Reduced), cudaMemcpyDeviceToHost, st));
+        SG_CK(cudaStreamSynchronize(st));
+        norms[0] = h.sumsq;
+        norms[1] = h.maxabs;
+    }
+    return SG_OK;
+}
