@@ -55,6 +55,9 @@ def args_():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-profile", action="store_true")
     ap.add_argument("--no-extra", action="store_true")
+    ap.add_argument("--profile-solves", type=int, default=0,
+                    help="only run this many solves of the sphere workload (for ncu captures; no JSON line)")
+    ap.add_argument("--n", type=int, default=N, help="grid size of --profile-solves")
     return ap.parse_args()
 
 
@@ -452,9 +455,31 @@ def run_ours(a, world, rank, local):
         dist.destroy_process_group()
 
 
+def run_profile_solves(a):
+    """A bare sequence of solves of the n^3 sphere workload with the bench's
+    solver settings, for profiler captures: no timing contract, no extras."""
+    import torch
+    import paper_2306_05332_gb300 as sg
+    import workloads as W
+    p = W.sphere(a.n)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    g = sg.Grid(p.shape, p.lo, p.hi, p.bc, precision="mixed", stream=stream.cuda_stream)
+    g.set_boundary(p.faces)
+    g.set_options(**SOLVER)
+    rho = torch.tensor(p.rho, device="cuda")
+    for k in range(a.profile_solves):
+        g.set_density(rho, 1.0)
+        info = g.solve(tol=TOL, levels=LEVELS)
+        print(k, info["cycles"], round(info["elapsed_ms"], 3), info["coarse_ss"][:5], flush=True)
+
+
 def main():
     a = args_()
     world, rank, local = dist_env()
+    if a.profile_solves > 0:
+        run_profile_solves(a)
+        return
     if a.impl == "reference":
         run_reference(a, world, rank)
         return
