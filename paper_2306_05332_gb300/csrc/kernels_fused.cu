@@ -400,8 +400,7 @@ cudaError_t fused_configure() {
     int dev = 0;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-    if ((e = configure_s<2>()) != cudaSuccess) return e;
-    if ((e = configure_s<3>()) != cudaSuccess) return e;
+    if ((e = lean_configure()) != cudaSuccess) return e;       // s = 2, 3 (kernels_superstep.cu)
     if ((e = configure_s<4>()) != cudaSuccess) return e;
     if ((e = configure_s<5>()) != cudaSuccess) return e;
     return configure_s<6>();
@@ -410,8 +409,8 @@ cudaError_t fused_configure() {
 cudaError_t launch_superstep_fused(const LevelGeom& g, int order, int s, bool zero_y0, const FusedCoef& cf,
                                    const float* y0, const float* f, float* out, cudaStream_t st) {
     switch (s) {
-        case 2: return dispatch<2>(order, zero_y0, g, cf, y0, f, out, st);
-        case 3: return dispatch<3>(order, zero_y0, g, cf, y0, f, out, st);
+        case 2:
+        case 3: return launch_superstep_lean(g, order, s, zero_y0, cf, y0, f, out, st);
         case 4: return dispatch<4>(order, zero_y0, g, cf, y0, f, out, st);
         case 5: return dispatch<5>(order, zero_y0, g, cf, y0, f, out, st);
         case 6: return dispatch<6>(order, zero_y0, g, cf, y0, f, out, st);

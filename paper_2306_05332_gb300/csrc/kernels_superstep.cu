@@ -1,0 +1,592 @@
+// Fused RKL super-step for s = 2 and 3 stages (App. A, Eq.
+// RKL_intermediate_source): all stages in one pass over HBM, FP32, for the
+// error equation of the mixed-precision V-cycle (homogeneous Dirichlet or
+// periodic ghosts).
+//
+// Work split.  A CTA owns a 32 x 16 column of the level, widened by a halo
+// (4 cells in x, s cells in y), and streams it along z.  Stage j is computed
+// on the tile widened by s - j cells in strips of four x cells; every thread
+// owns ONE strip of ONE stage for the whole stream, and each stage's strips
+// fill whole warps, so every warp does one strip per phase.  In phase t,
+// stage j works on plane t - (2j - 1): it reads only planes finished in
+// earlier phases, so one barrier per phase suffices.
+//
+// Boundaries without branches.  For a Dirichlet axis the halo outside the box
+// is loaded as the odd reflection of the interior (cell -1-k holds -cell k,
+// repeated with period 2n), for a periodic axis as the periodic image.  The
+// 7-point stencil and the stage recurrence commute with that reflection
+// exactly (negation and operand order are exact in IEEE arithmetic), so every
+// stage computes the odd extension of the solution and the ghost rule of Eq.
+// error_ghost (ghost = -active) holds at the walls with no per-cell test.
+// Loads arrive by cp.async; a thread negates the reflected cells it loaded.
+//
+// Shared-memory traffic.  A thread keeps its strip of the planes p - 1 and p
+// of its input stage in registers (it reads plane p + 1 as it walks z), takes
+// its x neighbours from the adjacent lanes by shuffles, and reads only the
+// y neighbours and one combined source field from shared memory.  The first
+// stage folds everything later stages take from Y0, Z0 = tau (L Y0 - f), f and
+// Y1 into one field per stage:
+//   Y_j = mu_j Y_{j-1} + mu~_j tau L Y_{j-1} + W_j,
+//   W_j = nu_j Y_{j-2} + c0_j Y0 + gamma~_j Z0 - mu~_j tau f   (RKL1: c0 = gamma~ = 0)
+// and with Y0 = 0 every W_j is a multiple of f.
+//
+// Ring depths divide 8 and the phase loop is unrolled by 8, so every ring
+// slot is a compile-time constant and shared-memory addresses are immediate
+// offsets from one per-thread register.
+//
+// Latency.  Planes are staged into shared memory two phases before their
+// first use, and prefetched into L2 kPrefetch planes ahead, so a phase waits
+// on an L2 hit rather than on HBM.
+//
+// HBM traffic per super-step: read Y0 + read f + write Y_s (12 B/cell; 8 B/cell
+// when Y0 = 0).  Halo cells are re-read from L2 by neighbouring tiles.
+#include "sg_internal.cuh"
+
+#include <algorithm>
+#include <cstdint>
+#include <type_traits>
+
+namespace sg {
+
+namespace {
+
+__device__ __forceinline__ void cpa4(float* smem, const float* gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cpa16(float* smem, const float* gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cpa_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cpa_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+__device__ __forceinline__ void cpa_wait_prev() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+__device__ __forceinline__ void prefetch_l2(const float* p) { asm volatile("prefetch.global.L2 [%0];\n" ::"l"(p)); }
+
+// Index of cell v of an axis of n cells in the stored array and its sign:
+// periodic image, or odd reflection about both walls (period 2n).
+__host__ __device__ __forceinline__ int map_axis(int v, int n, bool periodic, int* sign) {
+    if (v >= 0 && v < n) {                  // inside the box: no integer division
+        *sign = 1;
+        return v;
+    }
+    if (periodic) {
+        *sign = 1;
+        const int m = v % n;
+        return m < 0 ? m + n : m;
+    }
+    int m = v % (2 * n);
+    if (m < 0) m += 2 * n;
+    if (m < n) {
+        *sign = 1;
+        return m;
+    }
+    *sign = -1;
+    return 2 * n - 1 - m;
+}
+
+template <int S, bool ZERO>
+struct Lean {
+    static constexpr int TX = 32, TY = 16, HX = 4;
+    static constexpr int W = TX + 2 * HX;            // plane row (floats)
+    static constexpr int H = TY + 2 * S;             // plane rows
+    static constexpr int Q = W / 4;                  // strips per row
+    static constexpr int P = W * H;                  // floats per plane
+    static constexpr int HQ = H * Q;                 // strips per plane
+    // planes store the even rows, then the odd rows, so that the first rows of
+    // consecutive row pairs are contiguous (conflict-free quarter-warp accesses)
+    __host__ __device__ static constexpr int rowoff(int r) { return (r & 1) * (H / 2) * W + (r >> 1) * W; }
+    // stage j covers rows [j, H - j) (an even count) and strips [qlo(j), qhi(j));
+    // one item = the strips of rows r and r + 1 at one q
+    __host__ __device__ static constexpr int qlo(int j) { return (HX - (S - j)) / 4; }
+    __host__ __device__ static constexpr int qhi(int j) { return (HX + TX + (S - j) + 3) / 4; }
+    __host__ __device__ static constexpr int nq(int j) { return qhi(j) - qlo(j); }
+    __host__ __device__ static constexpr int items(int j) { return nq(j) * ((H - 2 * j) / 2); }
+    __host__ __device__ static constexpr int warps(int j) { return (items(j) + 31) / 32; }
+    static constexpr int T2 = 32 * warps(1);         // first thread of stage 2
+    static constexpr int T3 = T2 + 32 * warps(2);    // first thread of stage 3 (or end)
+    static constexpr int TS = S == 2 ? T3 : T3 + 32 * warps(3);   // threads with stage work
+    static constexpr int TL = 32 * ((HQ + 31) / 32); // threads [0, HQ) stage one strip of Y0 and of f
+    static constexpr int NT = TS > TL ? TS : TL;
+    // ring depths (planes, powers of two)
+    static constexpr int RY0 = ZERO ? 0 : 4;         // Y0: p, p + 1 read, p + 2 in flight
+    static constexpr int RF = ZERO ? 8 : 4;          // f (Y0 = 0: read by every stage, lag up to 2s - 1)
+    static constexpr int RY = 4;                     // Y_j, j < s
+    static constexpr int RW2 = ZERO ? 0 : 4;         // W_2: written at lag 1, read at lag 3
+    static constexpr int RW3 = (ZERO || S < 3) ? 0 : 8;   // W_3: written at lag 1, read at lag 5
+    static constexpr int OY0 = 0;
+    static constexpr int OF = OY0 + RY0 * P;
+    static constexpr int OY = OF + RF * P;           // ring of Y_j at OY + (j - 1) RY P
+    static constexpr int OW2 = OY + (S - 1) * RY * P;
+    static constexpr int OW3 = OW2 + RW2 * P;
+    static constexpr int NFLOATS = OW3 + RW3 * P;
+    static constexpr size_t BYTES = size_t(NFLOATS) * sizeof(float);
+    static_assert(S == 2 || S == 3, "lean super-step covers s = 2, 3");
+    static_assert(HX >= S - 1 && HX % 4 == 0, "x halo");
+    static_assert(TY % 2 == 0 && H % 2 == 0, "row pairs");
+    static_assert(BYTES <= 227u * 1024u, "rings exceed the shared memory of one CTA");
+    static_assert(NT <= 1024, "block size");
+};
+
+// Coefficients, all FP32 (the kernel never converts from FP64).
+struct LeanCoef {
+    float ax[4], ay[4], az[4], b[4];    // stage j >= 2: Y_j = ax sx + ay sy + az sz + b c + W_j
+    float ihx2, ihy2, ihz2, m2s;        // stage 1: Lf = ihx2 sx + ihy2 sy + ihz2 sz + m2s c - f
+    float m1t;                          //          Y1 = c + m1t Lf
+    float k2y0, k2z, k2f;               //          W2 = k2y0 c + k2z Lf + k2f f
+    float k3y1, k3y0, k3z, k3f;         //          W3 = k3y1 Y1 + k3y0 c + k3z Lf + k3f f
+    float kz[4];                        // Y0 = 0: Y1 = kz[1] f, W_j = kz[j] f
+};
+
+// Source of one 4-cell strip of a staged plane.
+struct LoadDesc {
+    int dst;        // offset in the plane (floats); -1: this thread loads nothing
+    int row;        // source row offset (y index * nx)
+    int x01, x23;   // source x of the four cells, 16 bits each
+    int flags;      // bit 4: one 16-byte copy; bits 0-3: cells negated by the x/y reflection
+};
+
+__device__ __forceinline__ LoadDesc make_desc(int k, int X0, int Yt, const LevelGeom& g, bool vec_ok, int W, int Q,
+                                              int H) {
+    LoadDesc d;
+    const int r = k / Q, q = k % Q;
+    d.dst = (r & 1) * (H / 2) * W + (r >> 1) * W + 4 * q;
+    int sy;
+    const int yy = map_axis(Yt + r, g.ny, g.per[1] != 0, &sy);
+    d.row = yy * g.nx;
+    int xs[4], mask = 0;
+    bool contiguous = true;
+    for (int e = 0; e < 4; ++e) {
+        int sx;
+        xs[e] = map_axis(X0 + 4 * q + e, g.nx, g.per[0] != 0, &sx);
+        if (sx * sy < 0) mask |= 1 << e;
+        if (sx < 0 || xs[e] != xs[0] + e) contiguous = false;
+    }
+    d.x01 = xs[0] | (xs[1] << 16);
+    d.x23 = xs[2] | (xs[3] << 16);
+    const bool vec = vec_ok && contiguous && (xs[0] & 3) == 0;
+    d.flags = mask | (vec ? 16 : 0);
+    return d;
+}
+
+__device__ __forceinline__ void issue(const LoadDesc& d, float* plane_dst, const float* plane_src) {
+    if (d.dst < 0) return;
+    const float* s = plane_src + d.row;
+    if (d.flags & 16) {
+        cpa16(plane_dst + d.dst, s + (d.x01 & 0xffff));
+    } else {
+        cpa4(plane_dst + d.dst + 0, s + (d.x01 & 0xffff));
+        cpa4(plane_dst + d.dst + 1, s + (d.x01 >> 16));
+        cpa4(plane_dst + d.dst + 2, s + (d.x23 & 0xffff));
+        cpa4(plane_dst + d.dst + 3, s + (d.x23 >> 16));
+    }
+}
+
+// After the thread's copies arrived: negate the cells whose reflection sign
+// (x, y and the plane's z sign) is negative.
+__device__ __forceinline__ void fixup(const LoadDesc& d, float* plane_dst, int zsign) {
+    if (d.dst < 0) return;
+    const int m = zsign < 0 ? (~d.flags & 15) : (d.flags & 15);
+    if (m == 0) return;
+    float4* p = reinterpret_cast<float4*>(plane_dst + d.dst);
+    float4 v = *p;
+    if (m & 1) v.x = -v.x;
+    if (m & 2) v.y = -v.y;
+    if (m & 4) v.z = -v.z;
+    if (m & 8) v.w = -v.w;
+    *p = v;
+}
+
+__device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
+__device__ __forceinline__ void st4(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
+
+constexpr int kPrefetch = 8;      // planes between the L2 prefetch and the first use
+
+// One strip of stage j >= 2: Y_j = ax sx + ay sy + az sz + b c + W_j.
+__device__ __forceinline__ float4 later_strip(float4 c, float4 n, float4 s, float4 d, float4 u, float l, float r,
+                                              float ax, float ay, float az, float bb, float4 w) {
+    float4 v;
+    v.x = fmaf(ax, l + c.y, fmaf(ay, n.x + s.x, fmaf(az, d.x + u.x, fmaf(bb, c.x, w.x))));
+    v.y = fmaf(ax, c.x + c.z, fmaf(ay, n.y + s.y, fmaf(az, d.y + u.y, fmaf(bb, c.y, w.y))));
+    v.z = fmaf(ax, c.y + c.w, fmaf(ay, n.z + s.z, fmaf(az, d.z + u.z, fmaf(bb, c.z, w.z))));
+    v.w = fmaf(ax, c.z + r, fmaf(ay, n.w + s.w, fmaf(az, d.w + u.w, fmaf(bb, c.w, w.w))));
+    return v;
+}
+
+// One strip of stage 1: Lf = L Y0 - f, Y1 = c + mu~_1 tau Lf and the combined
+// fields W_2 (and W_3 for s = 3).
+template <int S>
+__device__ __forceinline__ void first_strip(const LeanCoef& k, float4 c, float4 n, float4 s, float4 d, float4 u,
+                                            float l, float r, float4 f, float4& y1, float4& w2, float4& w3) {
+    const float sx[4] = {l + c.y, c.x + c.z, c.y + c.w, c.z + r};
+    const float sy[4] = {n.x + s.x, n.y + s.y, n.z + s.z, n.w + s.w};
+    const float sz[4] = {d.x + u.x, d.y + u.y, d.z + u.z, d.w + u.w};
+    const float cc[4] = {c.x, c.y, c.z, c.w};
+    const float ff[4] = {f.x, f.y, f.z, f.w};
+    float a[4], b[4], e3[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        const float lf = fmaf(k.ihx2, sx[e], fmaf(k.ihy2, sy[e], fmaf(k.ihz2, sz[e], fmaf(k.m2s, cc[e], -ff[e]))));
+        a[e] = fmaf(k.m1t, lf, cc[e]);
+        b[e] = fmaf(k.k2y0, cc[e], fmaf(k.k2z, lf, k.k2f * ff[e]));
+        if (S == 3) e3[e] = fmaf(k.k3y1, a[e], fmaf(k.k3y0, cc[e], fmaf(k.k3z, lf, k.k3f * ff[e])));
+    }
+    y1 = make_float4(a[0], a[1], a[2], a[3]);
+    w2 = make_float4(b[0], b[1], b[2], b[3]);
+    w3 = make_float4(e3[0], e3[1], e3[2], e3[3]);
+}
+
+__device__ __forceinline__ float4 scale4(float k, float4 v) { return make_float4(k * v.x, k * v.y, k * v.z, k * v.w); }
+
+__device__ __forceinline__ void store_out(float* dst, float4 v, bool vec, int n) {
+    if (vec) {
+        st4(dst, v);
+    } else {
+        dst[0] = v.x;
+        if (n > 1) dst[1] = v.y;
+        if (n > 2) dst[2] = v.z;
+        if (n > 3) dst[3] = v.w;
+    }
+}
+
+template <int S, int ORDER, bool ZERO>
+__global__ void __launch_bounds__(Lean<S, ZERO>::NT, 2)
+k_superstep_lean(const __grid_constant__ LevelGeom g, const __grid_constant__ LeanCoef k,
+                 const float* __restrict__ y0g, const float* __restrict__ fg, float* __restrict__ outg,
+                 int kchunk, int vec_ok) {
+    using C = Lean<S, ZERO>;
+    constexpr int W = C::W, P = C::P, Q = C::Q, HQ = C::HQ;
+    extern __shared__ __align__(16) float sm[];
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int X0 = blockIdx.x * C::TX - C::HX;          // global x of local column 0
+    const int Yt = blockIdx.y * C::TY - S;              // global y of local row 0
+    const int nx = g.nx, ny = g.ny, nz = g.nz, plane = nx * ny;
+    const bool pz = g.per[2] != 0;
+
+    // ---- this thread's stage and row pair (fixed for the whole stream; J = 0: loads only)
+    int J, item;
+    if (tid < C::T2) { J = 1; item = tid; }
+    else if (tid < C::T3) { J = 2; item = tid - C::T2; }
+    else if (S == 3 && tid < C::TS) { J = 3; item = tid - C::T3; }
+    else { J = 0; item = 0; }
+    const int Jr = J > 0 ? J : 1;
+    const int nqj = Jr == 1 ? C::nq(1) : (Jr == 2 ? C::nq(2) : C::nq(3));
+    const int qloj = Jr == 1 ? C::qlo(1) : (Jr == 2 ? C::qlo(2) : C::qlo(3));
+    const int nitems = J == 1 ? C::items(1) : (J == 2 ? C::items(2) : (J == 3 ? C::items(3) : 0));
+    const bool active = item < nitems;
+    const int it = active ? item : 0;
+    const int row = Jr + 2 * (it / nqj), q = qloj + it % nqj;   // rows row, row + 1
+    const int o = C::rowoff(row) + 4 * q;               // row `row` of the strip
+    const int d1 = C::rowoff(row + 1) + 4 * q - o;      // row + 1 relative to o; row - 1 is d1 - W, row + 2 is W
+    const bool fix_l = (it % nqj == 0) || lane == 0;
+    const bool fix_r = (it % nqj == nqj - 1) || lane == 31 || !active;
+    const int L = 2 * J - 1;                            // lag: stage J works on plane t - L
+    // stage J >= 2: coefficients, input ring, combined-field ring, output ring
+    float ax = 0.f, ay = 0.f, az = 0.f, bb = 0.f, kw = 0.f;
+    const float* in_b = sm + o;
+    const float* w_b = sm + o;
+    float* out_b = sm + o;
+    int w_mask = 3;
+    if (J >= 2) {
+        ax = J == 2 ? k.ax[2] : k.ax[3];
+        ay = J == 2 ? k.ay[2] : k.ay[3];
+        az = J == 2 ? k.az[2] : k.az[3];
+        bb = J == 2 ? k.b[2] : k.b[3];
+        kw = J == 2 ? k.kz[2] : k.kz[3];
+        in_b = sm + C::OY + (J - 2) * C::RY * P + o;
+        out_b = sm + C::OY + (J - 1) * C::RY * P + o;
+        if (ZERO) {
+            w_b = sm + C::OF + o;
+            w_mask = C::RF - 1;
+        } else if (J == 2) {
+            w_b = sm + C::OW2 + o;
+            w_mask = C::RW2 - 1;
+        } else {
+            w_b = sm + C::OW3 + o;
+            w_mask = (C::RW3 > 0 ? C::RW3 : 1) - 1;
+        }
+    }
+    // output cells of stage s (rows row, row + 1)
+    int st0 = -1, st1 = -1, st_n = 0;
+    bool st_vec = false;
+    if (J == S && active) {
+        const int gy = Yt + row, gx0 = X0 + 4 * q;
+        if (gx0 < nx) {
+            if (gy < ny) st0 = gy * nx + gx0;
+            if (gy + 1 < ny) st1 = (gy + 1) * nx + gx0;
+            st_n = min(4, nx - gx0);
+            st_vec = vec_ok && st_n == 4;
+        }
+    }
+    // staged-plane loads: thread k < HQ stages strip k of Y0 and of f
+    LoadDesc ld;
+    ld.dst = -1;
+    if (tid < HQ) ld = make_desc(tid, X0, Yt, g, vec_ok != 0, W, Q, C::H);
+    // L2 prefetch: three points of each staged row (first, middle and last cell of
+    // the row's part inside the box), per field
+    int pf = -1;
+    const float* pf_src = fg;
+    {
+        constexpr int NPF = 3 * C::H;
+        const int fld = tid / NPF, rem = tid % NPF;
+        if (fld < (ZERO ? 1 : 2)) {
+            int sy;
+            const int yy = map_axis(Yt + rem / 3, ny, g.per[1] != 0, &sy);
+            const int xlo = max(X0, 0), xhi = min(X0 + W, nx) - 1;
+            const int kq = rem % 3;
+            pf = yy * nx + (kq == 0 ? xlo : (kq == 1 ? (xlo + xhi) / 2 : xhi));
+            pf_src = (ZERO || fld == 1) ? fg : y0g;
+        }
+    }
+
+    const int kz0 = blockIdx.z * kchunk;
+    const int kz1 = min(kz0 + kchunk, nz);
+    const int t_first = kz0 - S + 2;                    // stage 1 computes plane t - 1
+    const int nph = (kz1 - kz0) + 3 * S - 3;            // phases
+    const int nload = kz1 + S - t_first;                // planes t_first + v, v < nload, are staged
+    const int u_store0 = kz0 - t_first + 2 * S - 1;     // phases whose stage-s plane lies in [kz0, kz1)
+    const int u_store1 = kz1 - t_first + 2 * S - 1;
+    // plane t_first + v of a ring with R slots sits in slot (v & (R - 1))
+    auto stage_plane = [&](int v, int* zsign) {
+        const int src = map_axis(t_first + v, nz, pz, zsign) * plane;
+        if constexpr (!ZERO) issue(ld, sm + C::OY0 + (v & 3) * P, y0g + src);
+        issue(ld, sm + C::OF + (v & (C::RF - 1)) * P, fg + src);
+    };
+    auto fix_plane = [&](int v, int zsign) {
+        if constexpr (!ZERO) fixup(ld, sm + C::OY0 + (v & 3) * P, zsign);
+        fixup(ld, sm + C::OF + (v & (C::RF - 1)) * P, zsign);
+    };
+
+    // ---- prologue: planes t_first - 2 .. t_first; t_first + 1 stays in flight
+    int zs0, zs1, zs2, zs_next = 1;
+    stage_plane(-2, &zs0);
+    stage_plane(-1, &zs1);
+    stage_plane(0, &zs2);
+    cpa_commit();
+    cpa_wait_all();
+    fix_plane(-2, zs0);
+    fix_plane(-1, zs1);
+    fix_plane(0, zs2);
+    if (1 < nload) stage_plane(1, &zs_next);
+    cpa_commit();
+    if (pf >= 0)
+        for (int v = 2; v < kPrefetch && v < nload; ++v) {
+            int zsg;
+            prefetch_l2(pf_src + map_axis(t_first + v, nz, pz, &zsg) * plane + pf);
+        }
+    __syncthreads();
+
+    // z window of the thread's two strips: planes p - 1 (dn) and p (cen)
+    float4 dn0 = make_float4(0.f, 0.f, 0.f, 0.f), cen0 = dn0, dn1 = dn0, cen1 = dn0;
+    if (!ZERO && J == 1) {
+        dn0 = ld4(sm + C::OY0 + (-2 & 3) * P + o);
+        dn1 = ld4(sm + C::OY0 + (-2 & 3) * P + o + d1);
+        cen0 = ld4(sm + C::OY0 + (-1 & 3) * P + o);
+        cen1 = ld4(sm + C::OY0 + (-1 & 3) * P + o + d1);
+    }
+
+    for (int u = 0; u < nph; ++u) {
+        // stage plane t + 2 into shared memory, prefetch plane t + kPrefetch into L2
+        const int zs_cur = zs_next;
+        if (u + 2 < nload) stage_plane(u + 2, &zs_next);
+        cpa_commit();
+        if (pf >= 0 && u + kPrefetch < nload) {
+            int zsg;
+            prefetch_l2(pf_src + map_axis(t_first + u + kPrefetch, nz, pz, &zsg) * plane + pf);
+        }
+
+        if (J == 1) {
+            // ---- stage 1 on plane t - 1
+            const int sp = (u - 1) & 3;
+            if (ZERO) {
+                const float* fp = sm + C::OF + ((u - 1) & (C::RF - 1)) * P + o;
+                const float kk = k.kz[1];
+                if (active) {
+                    st4(sm + C::OY + sp * P + o, scale4(kk, ld4(fp)));
+                    st4(sm + C::OY + sp * P + o + d1, scale4(kk, ld4(fp + d1)));
+                }
+            } else {
+                const float* yc = sm + C::OY0 + sp * P + o;
+                const float* yu = sm + C::OY0 + (u & 3) * P + o;
+                const float* fp = sm + C::OF + ((u - 1) & 3) * P + o;
+                const float4 up0 = ld4(yu), up1 = ld4(yu + d1);
+                const float4 nn = ld4(yc + d1 - W), ss = ld4(yc + W);
+                const float4 f0 = ld4(fp), f1 = ld4(fp + d1);
+                float l0 = __shfl_up_sync(0xffffffffu, cen0.w, 1);
+                float r0 = __shfl_down_sync(0xffffffffu, cen0.x, 1);
+                float l1 = __shfl_up_sync(0xffffffffu, cen1.w, 1);
+                float r1 = __shfl_down_sync(0xffffffffu, cen1.x, 1);
+                if (fix_l) { l0 = yc[-1]; l1 = yc[d1 - 1]; }
+                if (fix_r) { r0 = yc[4]; r1 = yc[d1 + 4]; }
+                float4 y1a, w2a, w3a, y1b, w2b, w3b;
+                first_strip<S>(k, cen0, nn, cen1, dn0, up0, l0, r0, f0, y1a, w2a, w3a);
+                first_strip<S>(k, cen1, cen0, ss, dn1, up1, l1, r1, f1, y1b, w2b, w3b);
+                if (active) {
+                    float* y1p = sm + C::OY + sp * P + o;
+                    float* w2p = sm + C::OW2 + sp * P + o;
+                    st4(y1p, y1a);
+                    st4(y1p + d1, y1b);
+                    st4(w2p, w2a);
+                    st4(w2p + d1, w2b);
+                    if (S == 3) {
+                        float* w3p = sm + C::OW3 + ((u - 1) & 7) * P + o;
+                        st4(w3p, w3a);
+                        st4(w3p + d1, w3b);
+                    }
+                }
+                dn0 = cen0; cen0 = up0;
+                dn1 = cen1; cen1 = up1;
+            }
+        } else if (J >= 2) {
+            // ---- stage J on plane p = t - L
+            const int sp = (u - L) & 3;
+            const float* yc = in_b + sp * P;
+            const float* yu = in_b + ((u - L + 1) & 3) * P;
+            const float* wp = w_b + ((u - L) & w_mask) * P;
+            const float4 up0 = ld4(yu), up1 = ld4(yu + d1);
+            const float4 nn = ld4(yc + d1 - W), ss = ld4(yc + W);
+            float l0 = __shfl_up_sync(0xffffffffu, cen0.w, 1);
+            float r0 = __shfl_down_sync(0xffffffffu, cen0.x, 1);
+            float l1 = __shfl_up_sync(0xffffffffu, cen1.w, 1);
+            float r1 = __shfl_down_sync(0xffffffffu, cen1.x, 1);
+            if (fix_l) { l0 = yc[-1]; l1 = yc[d1 - 1]; }
+            if (fix_r) { r0 = yc[4]; r1 = yc[d1 + 4]; }
+            float4 wa = ld4(wp), wb = ld4(wp + d1);
+            if (ZERO) {
+                wa = scale4(kw, wa);
+                wb = scale4(kw, wb);
+            }
+            const float4 va = later_strip(cen0, nn, cen1, dn0, up0, l0, r0, ax, ay, az, bb, wa);
+            const float4 vb = later_strip(cen1, cen0, ss, dn1, up1, l1, r1, ax, ay, az, bb, wb);
+            if (J < S) {
+                if (active) {
+                    st4(out_b + sp * P, va);
+                    st4(out_b + sp * P + d1, vb);
+                }
+            } else if (u >= u_store0 && u < u_store1) {
+                float* ob = outg + (t_first + u - L) * plane;
+                if (st0 >= 0) store_out(ob + st0, va, st_vec, st_n);
+                if (st1 >= 0) store_out(ob + st1, vb, st_vec, st_n);
+            }
+            dn0 = cen0; cen0 = up0;
+            dn1 = cen1; cen1 = up1;
+        }
+
+        // plane t + 1 (staged in the previous phase) has landed: fix its reflected cells
+        cpa_wait_prev();
+        if (u + 1 < nload) fix_plane(u + 1, zs_cur);
+        __syncthreads();
+    }
+}
+
+int g_lean_sms = 152;
+
+template <int S, int ORDER, bool ZERO>
+struct LeanResident {
+    static int per_sm;
+};
+template <int S, int ORDER, bool ZERO>
+int LeanResident<S, ORDER, ZERO>::per_sm = 1;
+
+LeanCoef make_lean_coef(const LevelGeom& g, int order, int s, const FusedCoef& cf) {
+    LeanCoef k{};
+    const double hx = g.ihx2f, hy = g.ihy2f, hz = g.ihz2f;
+    const double tau = cf.tau;
+    for (int j = 2; j <= s; ++j) {
+        const double mt = cf.mut_tau[j];
+        k.ax[j] = float(mt * hx);
+        k.ay[j] = float(mt * hy);
+        k.az[j] = float(mt * hz);
+        k.b[j] = float(double(cf.mu[j]) - 2.0 * mt * (hx + hy + hz));
+    }
+    k.ihx2 = g.ihx2f;
+    k.ihy2 = g.ihy2f;
+    k.ihz2 = g.ihz2f;
+    k.m2s = float(-2.0 * (hx + hy + hz));
+    k.m1t = float(double(cf.mut1) * tau);
+    const double c0_2 = order == 2 ? cf.c0[2] : 0.0, gt_2 = order == 2 ? cf.gt[2] : 0.0;
+    k.k2y0 = float(double(cf.nu[2]) + c0_2);
+    k.k2z = float(gt_2 * tau);
+    k.k2f = float(-double(cf.mut_tau[2]));
+    if (s >= 3) {
+        const double c0_3 = order == 2 ? cf.c0[3] : 0.0, gt_3 = order == 2 ? cf.gt[3] : 0.0;
+        k.k3y1 = cf.nu[3];
+        k.k3y0 = float(c0_3);
+        k.k3z = float(gt_3 * tau);
+        k.k3f = float(-double(cf.mut_tau[3]));
+    }
+    // Y0 = 0: Z0 = -tau f, Y1 = -mu~_1 tau f
+    const double y1 = -double(cf.mut1) * tau;
+    k.kz[1] = float(y1);
+    k.kz[2] = float(-gt_2 * tau - double(cf.mut_tau[2]));
+    if (s >= 3) {
+        const double gt_3 = order == 2 ? cf.gt[3] : 0.0;
+        k.kz[3] = float(double(cf.nu[3]) * y1 - gt_3 * tau - double(cf.mut_tau[3]));
+    }
+    return k;
+}
+
+template <int S, int ORDER, bool ZERO>
+cudaError_t lean_one(const LevelGeom& g, const LeanCoef& k, const float* y0, const float* f, float* out,
+                     cudaStream_t st) {
+    using C = Lean<S, ZERO>;
+    const long long gx = (g.nx + C::TX - 1) / C::TX, gy = (g.ny + C::TY - 1) / C::TY;
+    // all CTAs resident in one wave; a chunk adds 3s - 3 pipeline phases, so keep it >= 4s planes
+    const long long slots = (long long)g_lean_sms * LeanResident<S, ORDER, ZERO>::per_sm;
+    long long chunks = std::max(1LL, slots / (gx * gy));
+    chunks = std::min<long long>(chunks, std::max(1, g.nz / (4 * S)));
+    const int kchunk = (int)((g.nz + chunks - 1) / chunks);
+    const bool aligned = ((reinterpret_cast<uintptr_t>(y0) | reinterpret_cast<uintptr_t>(f) |
+                           reinterpret_cast<uintptr_t>(out)) & 15) == 0;
+    const int vec_ok = ((g.nx & 3) == 0 && aligned) ? 1 : 0;
+    dim3 grid((unsigned)gx, (unsigned)gy, (unsigned)((g.nz + kchunk - 1) / kchunk));
+    k_superstep_lean<S, ORDER, ZERO><<<grid, C::NT, C::BYTES, st>>>(g, k, y0, f, out, kchunk, vec_ok);
+    return cudaGetLastError();
+}
+
+template <int S, int ORDER, bool ZERO>
+cudaError_t lean_configure_one() {
+    using C = Lean<S, ZERO>;
+    auto kern = k_superstep_lean<S, ORDER, ZERO>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::BYTES);
+    if (e != cudaSuccess) return e;
+    int n = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, C::NT, C::BYTES);
+    if (e != cudaSuccess) return e;
+    LeanResident<S, ORDER, ZERO>::per_sm = n > 0 ? n : 1;
+    return cudaSuccess;
+}
+
+template <int S>
+cudaError_t lean_dispatch(int order, bool zero, const LevelGeom& g, const LeanCoef& k, const float* y0,
+                          const float* f, float* out, cudaStream_t st) {
+    if (order == 1) return zero ? lean_one<S, 1, true>(g, k, y0, f, out, st) : lean_one<S, 1, false>(g, k, y0, f, out, st);
+    return zero ? lean_one<S, 2, true>(g, k, y0, f, out, st) : lean_one<S, 2, false>(g, k, y0, f, out, st);
+}
+
+}  // namespace
+
+cudaError_t lean_configure() {
+    cudaError_t e;
+    int dev = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&g_lean_sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if ((e = lean_configure_one<2, 1, false>()) != cudaSuccess) return e;
+    if ((e = lean_configure_one<2, 1, true>()) != cudaSuccess) return e;
+    if ((e = lean_configure_one<2, 2, false>()) != cudaSuccess) return e;
+    if ((e = lean_configure_one<2, 2, true>()) != cudaSuccess) return e;
+    if ((e = lean_configure_one<3, 1, false>()) != cudaSuccess) return e;
+    if ((e = lean_configure_one<3, 1, true>()) != cudaSuccess) return e;
+    if ((e = lean_configure_one<3, 2, false>()) != cudaSuccess) return e;
+    return lean_configure_one<3, 2, true>();
+}
+
+cudaError_t launch_superstep_lean(const LevelGeom& g, int order, int s, bool zero_y0, const FusedCoef& cf,
+                                  const float* y0, const float* f, float* out, cudaStream_t st) {
+    const LeanCoef k = make_lean_coef(g, order, s, cf);
+    if (s == 2) return lean_dispatch<2>(order, zero_y0, g, k, y0, f, out, st);
+    if (s == 3) return lean_dispatch<3>(order, zero_y0, g, k, y0, f, out, st);
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace sg

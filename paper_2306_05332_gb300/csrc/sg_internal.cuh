@@ -120,6 +120,10 @@ cudaError_t fused_configure();
 // periodic ghosts; out must not alias y0.
 cudaError_t launch_superstep_fused(const LevelGeom& g, int order, int s, bool zero_y0, const FusedCoef& cf,
                                    const float* y0, const float* f, float* out, cudaStream_t st);
+// s = 2, 3: stage-balanced variant with reflected halos (kernels_superstep.cu).
+cudaError_t lean_configure();
+cudaError_t launch_superstep_lean(const LevelGeom& g, int order, int s, bool zero_y0, const FusedCoef& cf,
+                                  const float* y0, const float* f, float* out, cudaStream_t st);
 
 // ---- coarsest-level solver (kernels_coarse.cu) -----------------------------
 struct CoarseParams {
