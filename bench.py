@@ -153,10 +153,12 @@ def hbm_peak():
 
 
 def kernel_source_hash():
+    """Hash of the device-code sources (kernels_*.cu and the shared header):
+    DRAM counters taken on other kernel code are not reported."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2306_05332_gb300", "csrc")
     for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh")):
+        if (f.startswith("kernels_") and f.endswith(".cu")) or f.endswith(".cuh"):
             h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
 
