@@ -68,6 +68,39 @@ def dist_env():
     return world, rank, local
 
 
+class Ranks:
+    """Cross-rank reductions of the timing figures (identities with one rank).
+    `dist` is torch.distributed with an initialised process group, or None."""
+
+    def __init__(self, dist=None, device="cpu"):
+        self.dist = dist
+        self.device = device
+
+    def barrier(self):
+        if self.dist is not None:
+            self.dist.barrier()
+
+    def _reduce(self, x, op):
+        if self.dist is None:
+            return float(x)
+        import torch
+        t = torch.tensor([float(x)], dtype=torch.float64, device=self.device)
+        self.dist.all_reduce(t, op=op)
+        return float(t.item())
+
+    def max(self, x):
+        return self._reduce(x, None if self.dist is None else self.dist.ReduceOp.MAX)
+
+    def sum(self, x):
+        return self._reduce(x, None if self.dist is None else self.dist.ReduceOp.SUM)
+
+
+def throughput(world, steps, max_total_ms):
+    """Whole-job solves/s: every rank solves `steps` instances, and the job
+    takes as long as its slowest rank."""
+    return world * steps / (max_total_ms * 1e-3)
+
+
 def config(world):
     return {"workload": f"sphere{N}", "grid": [N, N, N], "levels": LEVELS, "tol": TOL,
             "precision": "mixed (FP32 V-cycle; FP64 residual carried by exact recurrence, confirmed in FP64 at the end; FP64 defect correction)",
@@ -207,7 +240,12 @@ def cpu_baseline_obj(p, cycles):
 # ---------------------------------------------------------------------------
 # Reference arm: the oracle, timed on the host cores
 # ---------------------------------------------------------------------------
-CYCLES_PER_SOLVE_REF = 18
+def oracle_cycles_per_solve():
+    """V-cycles the FP64 oracle needs on this workload, written by
+    tests/golden/make_oracle_cycles.py (a run of the oracle itself)."""
+    path = os.path.join(ROOT, "tests", "golden", "oracle_cycles_sphere256.json")
+    with open(path) as f:
+        return int(json.load(f)["cycles"])
 
 
 def run_reference(a, world, rank):
@@ -218,7 +256,8 @@ def run_reference(a, world, rank):
     for _ in range(a.warmup):
         oracle_vcycle_seconds(p, 1)
     ts = [oracle_vcycle_seconds(p, 1) for _ in range(a.steps)]
-    t = statistics.mean(ts) * CYCLES_PER_SOLVE_REF
+    cycles = oracle_cycles_per_solve()
+    t = statistics.mean(ts) * cycles
     value = 1.0 / t
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
             "steps": a.steps, "warmup": a.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
@@ -226,7 +265,7 @@ def run_reference(a, world, rank):
             "config": config(world),
             "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle",
                              "sample": f"each step: 1 V-cycle + residual of the numpy FP64 oracle at {N}^3, "
-                                       f"x {CYCLES_PER_SOLVE_REF} cycles per solve"},
+                                       f"x {cycles} cycles per solve (the oracle's count on this workload)"},
             "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -248,23 +287,8 @@ def run_ours(a, world, rank, local):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
 
-    def barrier():
-        if dist is not None:
-            dist.barrier()
-
-    def max_ranks(x):
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
-
-    def sum_ranks(x):
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        return float(t.item())
+    ranks = Ranks(dist, dev)
+    barrier, max_ranks, sum_ranks = ranks.barrier, ranks.max, ranks.sum
 
     p = W.sphere(N)
     stream = torch.cuda.Stream(dev)
@@ -312,7 +336,7 @@ def run_ours(a, world, rank, local):
     step_ms = [e0[k].elapsed_time(e1[k]) for k in range(a.steps)]
     total_ms = max_ranks(sum(step_ms))
     ms_per_step = total_ms / a.steps
-    value = world * 1000.0 / ms_per_step
+    value = throughput(world, a.steps, total_ms)
     cycles = infos[-1]["cycles"]
     su = statistics.mean(i["stage_cell_updates"] for i in infos)
     launches = int(sum(i["kernel_launches"] for i in infos) + a.steps)   # + one source kernel per step

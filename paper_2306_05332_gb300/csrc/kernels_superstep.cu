@@ -202,19 +202,46 @@ __device__ __forceinline__ void st4(float* p, float4 v) { *reinterpret_cast<floa
 
 constexpr int kPrefetch = 8;      // planes between the L2 prefetch and the first use
 
+// Packed FP32 pairs (Blackwell f32x2 instructions): each call is two
+// independent FP32 operations with the rounding of the scalar ones.
+__device__ __forceinline__ unsigned long long pk(float2 v) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(v.x), "f"(v.y));
+    return r;
+}
+__device__ __forceinline__ float2 upk(unsigned long long r) {
+    float2 v;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(v.x), "=f"(v.y) : "l"(r));
+    return v;
+}
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
+    unsigned long long d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(pk(a)), "l"(pk(b)), "l"(pk(c)));
+    return upk(d);
+}
+__device__ __forceinline__ float2 add2(float2 a, float2 b) {
+    unsigned long long d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(pk(a)), "l"(pk(b)));
+    return upk(d);
+}
+__device__ __forceinline__ float2 lo2(float4 v) { return make_float2(v.x, v.y); }
+__device__ __forceinline__ float2 hi2(float4 v) { return make_float2(v.z, v.w); }
+__device__ __forceinline__ float2 dup2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float4 cat4(float2 a, float2 b) { return make_float4(a.x, a.y, b.x, b.y); }
+
 // One strip of stage j >= 2: Y_j = ax sx + ay sy + az sz + b c + W_j.
 __device__ __forceinline__ float4 later_strip(float4 c, float4 n, float4 s, float4 d, float4 u, float l, float r,
-                                              float ax, float ay, float az, float bb, float4 w) {
-    float4 v;
-    v.x = fmaf(ax, l + c.y, fmaf(ay, n.x + s.x, fmaf(az, d.x + u.x, fmaf(bb, c.x, w.x))));
-    v.y = fmaf(ax, c.x + c.z, fmaf(ay, n.y + s.y, fmaf(az, d.y + u.y, fmaf(bb, c.y, w.y))));
-    v.z = fmaf(ax, c.y + c.w, fmaf(ay, n.z + s.z, fmaf(az, d.z + u.z, fmaf(bb, c.z, w.z))));
-    v.w = fmaf(ax, c.z + r, fmaf(ay, n.w + s.w, fmaf(az, d.w + u.w, fmaf(bb, c.w, w.w))));
-    return v;
+                                              float2 ax, float2 ay, float2 az, float2 bb, float4 w) {
+    const float2 sx01 = make_float2(l + c.y, c.x + c.z), sx23 = make_float2(c.y + c.w, c.z + r);
+    const float2 v01 = fma2(ax, sx01, fma2(ay, add2(lo2(n), lo2(s)), fma2(az, add2(lo2(d), lo2(u)), fma2(bb, lo2(c), lo2(w)))));
+    const float2 v23 = fma2(ax, sx23, fma2(ay, add2(hi2(n), hi2(s)), fma2(az, add2(hi2(d), hi2(u)), fma2(bb, hi2(c), hi2(w)))));
+    return cat4(v01, v23);
 }
 
 // One strip of stage 1: Lf = L Y0 - f, Y1 = c + mu~_1 tau Lf and the combined
-// fields W_2 (and W_3 for s = 3).
+// fields W_2 (and W_3 for s = 3).  Scalar FP32: the chain Lf -> Y1 -> W_3 is
+// long, and four independent cells per strip hide its latency better than
+// two packed pairs.
 template <int S>
 __device__ __forceinline__ void first_strip(const LeanCoef& k, float4 c, float4 n, float4 s, float4 d, float4 u,
                                             float l, float r, float4 f, float4& y1, float4& w2, float4& w3) {
@@ -282,16 +309,17 @@ k_superstep_lean(const __grid_constant__ LevelGeom g, const __grid_constant__ Le
     const bool fix_r = (it % nqj == nqj - 1) || lane == 31 || !active;
     const int L = 2 * J - 1;                            // lag: stage J works on plane t - L
     // stage J >= 2: coefficients, input ring, combined-field ring, output ring
-    float ax = 0.f, ay = 0.f, az = 0.f, bb = 0.f, kw = 0.f;
+    float2 ax = dup2(0.f), ay = ax, az = ax, bb = ax;
+    float kw = 0.f;
     const float* in_b = sm + o;
     const float* w_b = sm + o;
     float* out_b = sm + o;
     int w_mask = 3;
     if (J >= 2) {
-        ax = J == 2 ? k.ax[2] : k.ax[3];
-        ay = J == 2 ? k.ay[2] : k.ay[3];
-        az = J == 2 ? k.az[2] : k.az[3];
-        bb = J == 2 ? k.b[2] : k.b[3];
+        ax = dup2(J == 2 ? k.ax[2] : k.ax[3]);
+        ay = dup2(J == 2 ? k.ay[2] : k.ay[3]);
+        az = dup2(J == 2 ? k.az[2] : k.az[3]);
+        bb = dup2(J == 2 ? k.b[2] : k.b[3]);
         kw = J == 2 ? k.kz[2] : k.kz[3];
         in_b = sm + C::OY + (J - 2) * C::RY * P + o;
         out_b = sm + C::OY + (J - 1) * C::RY * P + o;

@@ -556,7 +556,7 @@ sg_status level0_residual(sg_grid* g, const double* phi, const double* f, bool f
     int nb = 0;
     const LevelGeom G = geom(g, 0, faces);
     {
-    ProfScope ps(g, K_RES0, double(g->lv[0].n) * (g->precision == SG_MIXED ? 20.0 : 16.0));
+    ProfScope ps(g, K_RES0, double(g->lv[0].n) * (g->precision == SG_MIXED ? 28.0 : 16.0));
     if (g->precision == SG_MIXED)
         SG_CK(launch_residual<double, float>(G, phi, f, (float*)g->lv[0].rhs, g->partials, &nb, g->st, g->r64));
     else

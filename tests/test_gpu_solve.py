@@ -242,7 +242,7 @@ def test_kernel_profile_counts_every_class():
     assert st["residual_l0"]["launches"] == 2
     assert st["update_residual"]["launches"] == info["cycles"]
     assert st["residual_restrict"]["launches"] == 3 * info["cycles"]
-    assert st["residual_l0"]["bytes"] == 20.0 * 64 ** 3 * 2
+    assert st["residual_l0"]["bytes"] == 28.0 * 64 ** 3 * 2
     assert st["update_residual"]["bytes"] == 40.0 * 64 ** 3 * info["cycles"]
 
 
