@@ -137,6 +137,126 @@ __global__ void __launch_bounds__(kCoarseThreads) k_coarse_solve(const CoarsePar
     if (threadIdx.x == 0 && p.ss_done) *p.ss_done = done;
 }
 
+// Levels of at most kSmallCells cells: every buffer carries a one-cell ghost
+// layer, (nx+2)(ny+2)(nz+2), so the stencil reads fixed offsets with no
+// boundary test.  The thread that writes a boundary cell also writes the
+// ghost that mirrors it (-v across a Dirichlet wall, Eq. error_ghost; v on the
+// opposite side of a periodic axis, Eq. periodic), so each ghost has one
+// writer and a stage needs one barrier.  Each thread keeps its cells' padded
+// indices, face flags and right-hand side in registers.
+constexpr int kSmallCells = 4 * kCoarseThreads;
+
+template <typename T>
+__global__ void __launch_bounds__(kCoarseThreads) k_coarse_small(const CoarseParams p) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ T red[33];
+    const int nx = p.g.nx, ny = p.g.ny, nz = p.g.nz;
+    const int n = nx * ny * nz;
+    const int px = nx + 2, pxy = px * (ny + 2), np = pxy * (nz + 2);
+    T* const b0 = reinterpret_cast<T*>(smem_raw);
+    const T ihx2 = ih2x<T>(p.g), ihy2 = ih2y<T>(p.g), ihz2 = ih2z<T>(p.g);
+    const T diag = T(2) * (ihx2 + ihy2 + ihz2);
+    const bool perx = p.g.per[0] != 0, pery = p.g.per[1] != 0, perz = p.g.per[2] != 0;
+    const T* rhs = static_cast<const T*>(p.rhs);
+
+    // this thread's cells t = tid + m * blockDim: padded index, face flags, f
+    int pc[4];
+    unsigned faces = 0u;                  // 6 bits per cell: -x +x -y +y -z +z
+    T fv[4];
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        const int t = threadIdx.x + m * blockDim.x;
+        pc[m] = -1;
+        fv[m] = T(0);
+        if (t < n) {
+            const int i = t % nx, j = (t / nx) % ny, k = t / (nx * ny);
+            pc[m] = (k + 1) * pxy + (j + 1) * px + (i + 1);
+            const unsigned fl = (i == 0 ? 1u : 0u) | (i == nx - 1 ? 2u : 0u) | (j == 0 ? 4u : 0u) |
+                                (j == ny - 1 ? 8u : 0u) | (k == 0 ? 16u : 0u) | (k == nz - 1 ? 32u : 0u);
+            faces |= fl << (6 * m);
+            fv[m] = rhs[t];
+        }
+    }
+    for (int idx = threadIdx.x; idx < 3 * np; idx += blockDim.x) b0[idx] = T(0);
+    __syncthreads();
+
+    auto lap = [&](const T* y, int q) {
+        return ihx2 * (y[q - 1] + y[q + 1]) + ihy2 * (y[q - px] + y[q + px]) + ihz2 * (y[q - pxy] + y[q + pxy]) -
+               diag * y[q];
+    };
+    // store v at cell m of y and at the ghosts that mirror it
+    auto put = [&](T* y, int m, T v) {
+        const int q = pc[m];
+        y[q] = v;
+        const unsigned fl = (faces >> (6 * m)) & 63u;
+        if (fl) {
+            if (fl & 1u) y[perx ? q + nx : q - 1] = perx ? v : -v;
+            if (fl & 2u) y[perx ? q - nx : q + 1] = perx ? v : -v;
+            if (fl & 4u) y[pery ? q + ny * px : q - px] = pery ? v : -v;
+            if (fl & 8u) y[pery ? q - ny * px : q + px] = pery ? v : -v;
+            if (fl & 16u) y[perz ? q + nz * pxy : q - pxy] = perz ? v : -v;
+            if (fl & 32u) y[perz ? q - nz * pxy : q + pxy] = perz ? v : -v;
+        }
+    };
+
+    T local = T(0);
+#pragma unroll
+    for (int m = 0; m < 4; ++m) local += fv[m] * fv[m];
+    const T r0sq = block_sum(local, red);         // ||f - L 0||^2 with homogeneous ghosts
+    const T tol = T(p.tol);
+    const T tu = T(p.tau_unit);
+    const T tolsq = tol * tol * r0sq;
+
+    T* y_cur = b0;                                // all zero, ghosts included
+    T* y_prev = b0 + np;
+    T* y_free = b0 + 2 * np;
+    int done = 0;
+    for (int ss = 0; ss < p.max_ss; ++ss) {
+        if (tol > T(0)) {
+            T acc = T(0);
+#pragma unroll
+            for (int m = 0; m < 4; ++m) {
+                if (pc[m] < 0) break;
+                const T r = fv[m] - lap(y_cur, pc[m]);
+                acc += r * r;
+            }
+            const T rsq = block_sum(acc, red);
+            if (rsq <= tolsq) break;
+        }
+        const int s = p.sched[ss];
+        for (int jst = 1; jst <= s; ++jst) {
+            const T mu = (T(2) * T(jst) - T(1)) / T(jst);
+            const T nu = (T(1) - T(jst)) / T(jst);
+            const T mut = mu * tu;
+            T* const y_new = y_free;
+#pragma unroll
+            for (int m = 0; m < 4; ++m) {
+                if (pc[m] < 0) break;
+                const int q = pc[m];
+                const T Lf = lap(y_cur, q) - fv[m];
+                put(y_new, m, jst == 1 ? y_cur[q] + tu * Lf : mu * y_cur[q] + nu * y_prev[q] + mut * Lf);
+            }
+            __syncthreads();
+            y_free = y_prev;
+            y_prev = y_cur;
+            y_cur = y_new;
+        }
+        ++done;
+    }
+    T* out = static_cast<T*>(p.u_out);
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        const int t = threadIdx.x + m * blockDim.x;
+        if (pc[m] >= 0) out[t] = y_cur[pc[m]];
+    }
+    if (threadIdx.x == 0 && p.ss_done) *p.ss_done = done;
+}
+
+template <typename T>
+size_t coarse_small_bytes(int nx, int ny, int nz) {
+    return (size_t)3 * (size_t)(nx + 2) * (ny + 2) * (nz + 2) * sizeof(T);
+}
+
 }  // namespace
 
 template <typename T>
@@ -157,6 +277,11 @@ cudaError_t launch_coarse_solve(const CoarseParams& p, cudaStream_t st) {
     if (bytes > kSmemLimit) return cudaErrorInvalidValue;
     int threads = kCoarseThreads;
     if (n < threads) threads = (int)((n + 31) / 32) * 32;
+    const size_t small = coarse_small_bytes<T>(p.g.nx, p.g.ny, p.g.nz);
+    if (n <= kSmallCells && small <= kSmemLimit) {
+        k_coarse_small<T><<<1, threads, small, st>>>(p);
+        return cudaGetLastError();
+    }
     if (n <= 4LL * kCoarseThreads) k_coarse_solve<T, 4><<<1, threads, bytes, st>>>(p);
     else k_coarse_solve<T, kMaxCells><<<1, threads, bytes, st>>>(p);
     return cudaGetLastError();
@@ -164,6 +289,10 @@ cudaError_t launch_coarse_solve(const CoarseParams& p, cudaStream_t st) {
 
 cudaError_t coarse_configure() {
     cudaError_t e;
+    if ((e = cudaFuncSetAttribute(k_coarse_small<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)kSmemLimit)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_coarse_small<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)kSmemLimit)) != cudaSuccess) return e;
     if ((e = cudaFuncSetAttribute(k_coarse_solve<float, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)kSmemLimit)) != cudaSuccess) return e;
     if ((e = cudaFuncSetAttribute(k_coarse_solve<float, kMaxCells>,
