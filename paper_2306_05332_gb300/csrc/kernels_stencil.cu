@@ -9,6 +9,8 @@
 // These are HBM-bandwidth-bound kernels; no tensor cores are involved.
 #include "sg_internal.cuh"
 
+#include <cstdint>
+
 namespace sg {
 
 namespace {
@@ -388,6 +390,45 @@ __device__ __forceinline__ float d2f_bits(double x) {
     return __uint_as_float(sgn | ((ex - 896u) << 23) | (mh << 3) | (lo >> 29));
 }
 
+// r -= (A_0 e) for one cell, A_0 the homogeneous operator, formed without
+// rounding: the FP32 neighbour sum is split by TwoSum into a value and its
+// exact error (products by -6 and -2 are exact up to one FMA term), and both
+// enter r through FP64 FMAs.
+template <bool UNIFORM>
+__device__ __forceinline__ double update_r(const LevelGeom& g, float c, float xm, float xp, float ym, float yp,
+                                           float zm, float zp, double r) {
+    if (UNIFORM) {
+        // sum of the six neighbours minus 6 c, compensated
+        const float p = -6.0f * c;
+        const float perr = fmaf(-6.0f, c, -p);          // -6 c = p + perr exactly
+        float s = xm, comp = perr, t;
+        two_sum(s, xp, s, t); comp += t;
+        two_sum(s, ym, s, t); comp += t;
+        two_sum(s, yp, s, t); comp += t;
+        two_sum(s, zm, s, t); comp += t;
+        two_sum(s, zp, s, t); comp += t;
+        two_sum(s, p, s, t); comp += t;
+        const double nih2 = -g.ihx2;
+        r = fma(nih2, f2d_bits(s), r);
+        r = fma(nih2, f2d_bits(comp), r);
+    } else {
+        // per-axis second differences (-2 c is exact), compensated
+        const float m2 = -2.0f * c;
+        const float a[3][2] = {{xm, xp}, {ym, yp}, {zm, zp}};
+        const double ih[3] = {g.ihx2, g.ihy2, g.ihz2};
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            float s, comp, t;
+            two_sum(a[d][0], a[d][1], s, comp);
+            two_sum(s, m2, s, t);
+            comp += t;
+            r = fma(-ih[d], f2d_bits(s), r);
+            r = fma(-ih[d], f2d_bits(comp), r);
+        }
+    }
+    return r;
+}
+
 template <bool UNIFORM>
 __global__ void __launch_bounds__(BX * BY)
 k_update_residual(const LevelGeom g, double* __restrict__ phi, const float* __restrict__ e,
@@ -406,42 +447,70 @@ k_update_residual(const LevelGeom g, double* __restrict__ phi, const float* __re
             const float zp = (k < g.nz - 1) ? e[idx + plane] : z_high<false>(e, g, i, j, idx, plane, c);
             float xm, xp, ym, yp;
             xy_neighbours<false>(e, g, i, j, k, idx, c, xm, xp, ym, yp);
-            double r = r64[idx];
-            if (UNIFORM) {
-                // sum of the six neighbours minus 6 c, compensated
-                const float p = -6.0f * c;
-                const float perr = fmaf(-6.0f, c, -p);          // -6 c = p + perr exactly
-                float s = xm, comp = perr, t;
-                two_sum(s, xp, s, t); comp += t;
-                two_sum(s, ym, s, t); comp += t;
-                two_sum(s, yp, s, t); comp += t;
-                two_sum(s, zm, s, t); comp += t;
-                two_sum(s, zp, s, t); comp += t;
-                two_sum(s, p, s, t); comp += t;
-                const double nih2 = -g.ihx2;
-                r = fma(nih2, f2d_bits(s), r);
-                r = fma(nih2, f2d_bits(comp), r);
-            } else {
-                // per-axis second differences (-2 c is exact), compensated
-                const float m2 = -2.0f * c;
-                const float a[3][2] = {{xm, xp}, {ym, yp}, {zm, zp}};
-                const double ih[3] = {g.ihx2, g.ihy2, g.ihz2};
-#pragma unroll
-                for (int d = 0; d < 3; ++d) {
-                    float s, comp, t;
-                    two_sum(a[d][0], a[d][1], s, comp);
-                    two_sum(s, m2, s, t);
-                    comp += t;
-                    r = fma(-ih[d], f2d_bits(s), r);
-                    r = fma(-ih[d], f2d_bits(comp), r);
-                }
-            }
+            const double r = update_r<UNIFORM>(g, c, xm, xp, ym, yp, zm, zp, r64[idx]);
             r64[idx] = r;
             phi[idx] = phi[idx] + f2d_bits(c);
             const float rf = d2f_bits(r);
             r32[idx] = rf;
             sq = fmaf(rf, rf, sq);
             mx = fmaxf(mx, fabsf(rf));
+            zm = c;
+            c = zp;
+        }
+    }
+    const int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+    block_reduce_write<float>(sq, mx, 0.0f, partials, bid);
+}
+
+// The same update on strips of four x cells (nx % 4 == 0, 16-byte aligned
+// arrays): one 16-byte load of e per neighbour row and 16-byte loads and
+// stores of phi and r, the z neighbours carried in registers, the z loop
+// unrolled by two so the next plane's loads overlap the current arithmetic.
+__device__ __forceinline__ float4 ld_f4(const float* p) { return *reinterpret_cast<const float4*>(p); }
+__device__ __forceinline__ double2 ld_d2(const double* p) { return *reinterpret_cast<const double2*>(p); }
+__device__ __forceinline__ float4 neg_f4(float4 v) { return make_float4(-v.x, -v.y, -v.z, -v.w); }
+
+template <bool UNIFORM>
+__global__ void __launch_bounds__(BX * BY)
+k_update_residual4(const LevelGeom g, double* __restrict__ phi, const float* __restrict__ e,
+                   double* __restrict__ r64, float* __restrict__ r32, Partial* partials, int kchunk) {
+    const int q = blockIdx.x * BX + threadIdx.x;        // strip: cells 4q .. 4q + 3
+    const int j = blockIdx.y * BY + threadIdx.y;
+    const int nx = g.nx, ny = g.ny, nz = g.nz;
+    float sq = 0.0f, mx = 0.0f;
+    if (4 * q < nx && j < ny) {
+        const int i0 = 4 * q, plane = nx * ny;
+        const bool px = g.per[0] != 0, py = g.per[1] != 0, pz = g.per[2] != 0;
+        const int k0 = blockIdx.z * kchunk;
+        const int k1 = min(k0 + kchunk, nz);
+        int idx = k0 * plane + j * nx + i0;
+        float4 c = ld_f4(e + idx);
+        float4 zm = k0 > 0 ? ld_f4(e + idx - plane) : (pz ? ld_f4(e + idx + (nz - 1) * plane) : neg_f4(c));
+#pragma unroll 2
+        for (int k = k0; k < k1; ++k, idx += plane) {
+            const float4 zp = k < nz - 1 ? ld_f4(e + idx + plane) : (pz ? ld_f4(e + idx - (nz - 1) * plane) : neg_f4(c));
+            const float4 ym = j > 0 ? ld_f4(e + idx - nx) : (py ? ld_f4(e + idx + (ny - 1) * nx) : neg_f4(c));
+            const float4 yp = j < ny - 1 ? ld_f4(e + idx + nx) : (py ? ld_f4(e + idx - (ny - 1) * nx) : neg_f4(c));
+            const float xl = i0 > 0 ? e[idx - 1] : (px ? e[idx + nx - 1] : -c.x);
+            const float xr = i0 + 4 < nx ? e[idx + 4] : (px ? e[idx + 4 - nx] : -c.w);
+            double2 ra = ld_d2(r64 + idx), rb = ld_d2(r64 + idx + 2);
+            double2 pa = ld_d2(phi + idx), pb = ld_d2(phi + idx + 2);
+            ra.x = update_r<UNIFORM>(g, c.x, xl, c.y, ym.x, yp.x, zm.x, zp.x, ra.x);
+            ra.y = update_r<UNIFORM>(g, c.y, c.x, c.z, ym.y, yp.y, zm.y, zp.y, ra.y);
+            rb.x = update_r<UNIFORM>(g, c.z, c.y, c.w, ym.z, yp.z, zm.z, zp.z, rb.x);
+            rb.y = update_r<UNIFORM>(g, c.w, c.z, xr, ym.w, yp.w, zm.w, zp.w, rb.y);
+            *reinterpret_cast<double2*>(r64 + idx) = ra;
+            *reinterpret_cast<double2*>(r64 + idx + 2) = rb;
+            pa.x += f2d_bits(c.x);
+            pa.y += f2d_bits(c.y);
+            pb.x += f2d_bits(c.z);
+            pb.y += f2d_bits(c.w);
+            *reinterpret_cast<double2*>(phi + idx) = pa;
+            *reinterpret_cast<double2*>(phi + idx + 2) = pb;
+            const float4 rf = make_float4(d2f_bits(ra.x), d2f_bits(ra.y), d2f_bits(rb.x), d2f_bits(rb.y));
+            *reinterpret_cast<float4*>(r32 + idx) = rf;
+            sq = fmaf(rf.x, rf.x, fmaf(rf.y, rf.y, fmaf(rf.z, rf.z, fmaf(rf.w, rf.w, sq))));
+            mx = fmaxf(mx, fmaxf(fmaxf(fabsf(rf.x), fabsf(rf.y)), fmaxf(fabsf(rf.z), fabsf(rf.w))));
             zm = c;
             c = zp;
         }
@@ -604,6 +673,21 @@ cudaError_t launch_prolong_correct(const LevelGeom& g, const T* coarse, T* fine_
 
 cudaError_t launch_update_residual(const LevelGeom& g, double* phi, const float* e, double* r64, float* r32,
                                   Partial* partials, int* nblocks_out, cudaStream_t st) {
+    const bool uniform4 = g.ihx2 == g.ihy2 && g.ihy2 == g.ihz2;
+    const bool aligned = ((reinterpret_cast<uintptr_t>(phi) | reinterpret_cast<uintptr_t>(e) |
+                           reinterpret_cast<uintptr_t>(r64) | reinterpret_cast<uintptr_t>(r32)) & 15) == 0;
+    if ((g.nx & 3) == 0 && aligned) {
+        // as many blocks as the scalar residual launch at most (the partials buffer)
+        const long long gx = (g.nx / 4 + BX - 1) / BX, gy = (g.ny + BY - 1) / BY;
+        const long long chunks = std::min<long long>(g.nz, std::max(1LL, residual_blocks(g) / (gx * gy)));
+        const int kc = (int)((g.nz + chunks - 1) / chunks);
+        dim3 block(BX, BY, 1);
+        dim3 grid((unsigned)gx, (unsigned)gy, (unsigned)((g.nz + kc - 1) / kc));
+        if (uniform4) k_update_residual4<true><<<grid, block, 0, st>>>(g, phi, e, r64, r32, partials, kc);
+        else k_update_residual4<false><<<grid, block, 0, st>>>(g, phi, e, r64, r32, partials, kc);
+        if (nblocks_out) *nblocks_out = (int)(grid.x * grid.y * grid.z);
+        return cudaGetLastError();
+    }
     const int kc = kchunk_for(g, BX, BY);
     dim3 block(BX, BY, 1);
     dim3 grid((g.nx + BX - 1) / BX, (g.ny + BY - 1) / BY, (g.nz + kc - 1) / kc);
