@@ -615,7 +615,8 @@ sg_status run_cycle(sg_grid* g, int L, double* phi, const double* f, bool faces,
                         g->opt.n_pre * 1000 + g->opt.n_post,
                         (long long)std::llround(g->opt.tau_frac * 1e12),
                         (long long)std::llround(g->opt.coarse_tol * 1e15) * 100000 + g->opt.coarse_max_ss};
-    long long key2 = (long long)std::llround(g->opt.coarse_tau_frac * 1e12) * 2 + (g->prof ? 1 : 0);
+    long long key2 = ((long long)std::llround(g->opt.coarse_tau_frac * 1e12) * 2 + (g->prof ? 1 : 0)) * 2 +
+                     (g->opt.fused ? 1 : 0);
     key[7] ^= key2 * 1315423911LL;
     if (!g->gexec || std::memcmp(key, g->gkey, sizeof(key)) != 0) {
         drop_graph(g);

@@ -217,3 +217,24 @@ def test_mixed_solve_fused_and_unfused_agree(fused):
     assert np.linalg.norm(g.potential() - ref) / np.linalg.norm(ref) < 1e-8
     _, rinfo = O.solve(p.rho, p.lo, p.hi, p.bc, p.faces, 1.0, tol=1e-11, levels=4)
     assert abs(info["cycles"] - rinfo.cycles) <= 1
+
+
+def test_fused_option_change_takes_effect_on_the_same_grid():
+    # the cycle graph is cached per option set: switching the fused super-step
+    # off and on must re-capture (level 0 of 128^3 has 2^21 cells, the fused size)
+    p = W.sphere(128)
+    sg = pytest.importorskip("paper_2306_05332_gb300")
+    g = sg.Grid(p.shape, p.lo, p.hi, p.bc, precision="mixed")
+    g.set_boundary(p.faces)
+    g.set_options(rkl_order=2, s_smooth=3, fused=1, fixed_cycles=2)
+    counts = {}
+    for fused in (1, 0, 1):
+        g.set_options(fused=fused)
+        g.set_density(p.rho, 1.0)
+        g.set_profiling(True)
+        g.solve(tol=0.0, levels=4)
+        counts.setdefault(fused, []).append(g.kernel_stats()["rkl_stage_l0"]["launches"])
+        g.set_profiling(False)
+    # fused: one launch per super-step (3 per cycle); unfused: one per stage
+    assert counts[1] == [2 * 3, 2 * 3]
+    assert counts[0] == [2 * 3 * 3]
