@@ -10,6 +10,7 @@
 #include "sg_internal.cuh"
 
 #include <cstdint>
+#include <type_traits>
 
 namespace sg {
 
@@ -62,6 +63,11 @@ __device__ __forceinline__ T z_high(const T* u, const LevelGeom& g, int i, int j
     if (FACES && g.face[5]) return T(2.0 * g.face[5][j * g.nx + i]) - c;
     return -c;
 }
+
+// 16-byte vector loads (callers guarantee the alignment).
+__device__ __forceinline__ float4 ld_f4(const float* p) { return *reinterpret_cast<const float4*>(p); }
+__device__ __forceinline__ double2 ld_d2(const double* p) { return *reinterpret_cast<const double2*>(p); }
+__device__ __forceinline__ float4 neg_f4(float4 v) { return make_float4(-v.x, -v.y, -v.z, -v.w); }
 
 // Eq. discrete_laplace_3D from the six neighbours.
 template <typename T>
@@ -290,6 +296,72 @@ k_residual_restrict(const LevelGeom g, const T* __restrict__ u, const T* __restr
     block_reduce_write<A>(sq, mx, csum, partials, bid);
 }
 
+// FP32 residual + restriction on homogeneous ghosts, for nx % 4 == 0 and
+// 16-byte aligned arrays: a thread owns a strip of four x cells on a pair of
+// rows (2J, 2J + 1) and streams z, so each 2 x 2 x 2 block of the 8-cell mean
+// (Eq. restriction_example_3D) is summed in its registers, with no shared
+// memory or barrier; the z neighbours are carried in registers.
+__global__ void __launch_bounds__(BX * BY)
+k_residual_restrict4(const LevelGeom g, const float* __restrict__ u, const float* __restrict__ rhs,
+                     float* __restrict__ coarse, Partial* partials, int kchunk) {
+    const int q = blockIdx.x * BX + threadIdx.x;        // cells 4q .. 4q + 3
+    const int jp = blockIdx.y * BY + threadIdx.y;       // rows 2 jp, 2 jp + 1
+    const int nx = g.nx, ny = g.ny, nz = g.nz;
+    float sq = 0.0f, mx = 0.0f, csum = 0.0f;
+    if (4 * q < nx && 2 * jp < ny) {
+        const int i0 = 4 * q, j0 = 2 * jp, plane = nx * ny;
+        const int cnx = nx >> 1, cny = ny >> 1;
+        const bool px = g.per[0] != 0, py = g.per[1] != 0, pz = g.per[2] != 0;
+        const float hx = g.ihx2f, hy = g.ihy2f, hz = g.ihz2f;
+        const int k0 = blockIdx.z * kchunk;             // even
+        const int k1 = min(k0 + kchunk, nz);
+        int idx = k0 * plane + j0 * nx + i0;
+        float4 ca = ld_f4(u + idx), cb = ld_f4(u + idx + nx);
+        float4 za = k0 > 0 ? ld_f4(u + idx - plane) : (pz ? ld_f4(u + idx + (nz - 1) * plane) : neg_f4(ca));
+        float4 zb = k0 > 0 ? ld_f4(u + idx + nx - plane) : (pz ? ld_f4(u + idx + nx + (nz - 1) * plane) : neg_f4(cb));
+        float2 acc = make_float2(0.0f, 0.0f);
+        for (int k = k0; k < k1; ++k, idx += plane) {
+            const bool top = k == nz - 1;
+            const float4 zpa = !top ? ld_f4(u + idx + plane) : (pz ? ld_f4(u + idx - (nz - 1) * plane) : neg_f4(ca));
+            const float4 zpb = !top ? ld_f4(u + idx + nx + plane) : (pz ? ld_f4(u + idx + nx - (nz - 1) * plane) : neg_f4(cb));
+            const float4 ym = j0 > 0 ? ld_f4(u + idx - nx) : (py ? ld_f4(u + idx + (ny - 1) * nx) : neg_f4(ca));
+            const float4 yp = j0 + 2 < ny ? ld_f4(u + idx + 2 * nx) : (py ? ld_f4(u + idx + (2 - ny) * nx) : neg_f4(cb));
+            const float xla = i0 > 0 ? u[idx - 1] : (px ? u[idx + nx - 1] : -ca.x);
+            const float xra = i0 + 4 < nx ? u[idx + 4] : (px ? u[idx + 4 - nx] : -ca.w);
+            const float xlb = i0 > 0 ? u[idx + nx - 1] : (px ? u[idx + 2 * nx - 1] : -cb.x);
+            const float xrb = i0 + 4 < nx ? u[idx + nx + 4] : (px ? u[idx + 4] : -cb.w);
+            const float4 fa = ld_f4(rhs + idx), fb = ld_f4(rhs + idx + nx);
+            // row a: y neighbours ym (row 2J - 1) and cb (row 2J + 1); row b: ca and yp
+            const float r0 = fa.x - lap7(ca.x, xla, ca.y, ym.x, cb.x, za.x, zpa.x, hx, hy, hz);
+            const float r1 = fa.y - lap7(ca.y, ca.x, ca.z, ym.y, cb.y, za.y, zpa.y, hx, hy, hz);
+            const float r2 = fa.z - lap7(ca.z, ca.y, ca.w, ym.z, cb.z, za.z, zpa.z, hx, hy, hz);
+            const float r3 = fa.w - lap7(ca.w, ca.z, xra, ym.w, cb.w, za.w, zpa.w, hx, hy, hz);
+            const float r4 = fb.x - lap7(cb.x, xlb, cb.y, ca.x, yp.x, zb.x, zpb.x, hx, hy, hz);
+            const float r5 = fb.y - lap7(cb.y, cb.x, cb.z, ca.y, yp.y, zb.y, zpb.y, hx, hy, hz);
+            const float r6 = fb.z - lap7(cb.z, cb.y, cb.w, ca.z, yp.z, zb.z, zpb.z, hx, hy, hz);
+            const float r7 = fb.w - lap7(cb.w, cb.z, xrb, ca.w, yp.w, zb.w, zpb.w, hx, hy, hz);
+            sq = fmaf(r0, r0, fmaf(r1, r1, fmaf(r2, r2, fmaf(r3, r3, sq))));
+            sq = fmaf(r4, r4, fmaf(r5, r5, fmaf(r6, r6, fmaf(r7, r7, sq))));
+            mx = fmaxf(mx, fmaxf(fmaxf(fmaxf(fabsf(r0), fabsf(r1)), fmaxf(fabsf(r2), fabsf(r3))),
+                                 fmaxf(fmaxf(fabsf(r4), fabsf(r5)), fmaxf(fabsf(r6), fabsf(r7)))));
+            const float2 s2 = make_float2((r0 + r1) + (r4 + r5), (r2 + r3) + (r6 + r7));
+            if ((k & 1) == 0) {
+                acc = s2;
+            } else {
+                const float2 cv = make_float2((acc.x + s2.x) * 0.125f, (acc.y + s2.y) * 0.125f);
+                if (coarse) *reinterpret_cast<float2*>(coarse + ((k >> 1) * cny + jp) * cnx + 2 * q) = cv;
+                csum += cv.x + cv.y;
+            }
+            za = ca;
+            ca = zpa;
+            zb = cb;
+            cb = zpb;
+        }
+    }
+    const int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+    block_reduce_write<float>(sq, mx, csum, partials, bid);
+}
+
 // ---------------------------------------------------------------------------
 // Prolongation + correction (Eq. prolongation_example_3D): every fine cell
 // takes (27 A + 9 (B + D + E) + 3 (C + F + H) + G) / 64 from its parent A and
@@ -345,6 +417,81 @@ k_prolong_correct(const LevelGeom g, const T* __restrict__ coarse, T* fine_u, in
         qm = q0;
         q0 = qp;
         if (k + 2 < k1) qp = q(K + 1);
+    }
+}
+
+// The same prolongation + correction for FP32, nx % 4 == 0 and aligned
+// arrays: a thread owns a strip of four fine x cells on a pair of fine rows
+// (2J, 2J + 1).  Per coarse plane it reads coarse x = 2q - 1 .. 2q + 2 on rows
+// J - 1 .. J + 1 (ghosts by the same rules), forms the x interpolants (3, 1),
+// then the y interpolants of its two rows, and streams z with 16-byte
+// read-modify-writes of the fine strips.
+__global__ void __launch_bounds__(BX * BY)
+k_prolong_correct4(const LevelGeom g, const float* __restrict__ coarse, float* __restrict__ fine_u, int kchunk) {
+    const int q = blockIdx.x * BX + threadIdx.x;
+    const int J = blockIdx.y * BY + threadIdx.y;
+    const int nx = g.nx, ny = g.ny, nz = g.nz;
+    if (4 * q >= nx || 2 * J >= ny) return;
+    const int cnx = nx >> 1, cny = ny >> 1, cnz = nz >> 1, cplane = cnx * cny;
+    const bool px = g.per[0] != 0, py = g.per[1] != 0, pz = g.per[2] != 0;
+    // coarse x = 2q - 1 and 2q + 2 with their ghost rule; rows J - 1, J + 1 likewise
+    int xl = 2 * q - 1, xr = 2 * q + 2;
+    float sl = 1.0f, sr = 1.0f;
+    if (xl < 0) { if (px) xl += cnx; else { xl = 0; sl = -1.0f; } }
+    if (xr >= cnx) { if (px) xr -= cnx; else { xr = cnx - 1; sr = -1.0f; } }
+    int ym = J - 1, yp = J + 1;
+    float sym = 1.0f, syp = 1.0f;
+    if (ym < 0) { if (py) ym += cny; else { ym = 0; sym = -1.0f; } }
+    if (yp >= cny) { if (py) yp -= cny; else { yp = cny - 1; syp = -1.0f; } }
+    const int rm = ym * cnx, r0 = J * cnx, rp = yp * cnx;
+    // (x, y) interpolants of coarse plane K for fine rows a = 2J and b = 2J + 1
+    auto interp = [&](int K, float4& qa, float4& qb) {
+        float sz = 1.0f;
+        if (K < 0) { if (pz) K += cnz; else { K = 0; sz = -1.0f; } }
+        else if (K >= cnz) { if (pz) K -= cnz; else { K = cnz - 1; sz = -1.0f; } }
+        const float* cp = coarse + K * cplane;
+        float4 x[3];
+        const int rows[3] = {rm, r0, rp};
+        const float ys[3] = {sym, 1.0f, syp};
+#pragma unroll
+        for (int t = 0; t < 3; ++t) {
+            const float* row = cp + rows[t];
+            const float2 c2 = *reinterpret_cast<const float2*>(row + 2 * q);
+            const float cl = sl * row[xl], cr = sr * row[xr];
+            const float sg = ys[t] * sz;
+            x[t] = make_float4(sg * (3.0f * c2.x + cl), sg * (3.0f * c2.x + c2.y), sg * (3.0f * c2.y + c2.x),
+                               sg * (3.0f * c2.y + cr));
+        }
+        qa = make_float4(3.0f * x[1].x + x[0].x, 3.0f * x[1].y + x[0].y, 3.0f * x[1].z + x[0].z, 3.0f * x[1].w + x[0].w);
+        qb = make_float4(3.0f * x[1].x + x[2].x, 3.0f * x[1].y + x[2].y, 3.0f * x[1].z + x[2].z, 3.0f * x[1].w + x[2].w);
+    };
+    const int k0 = blockIdx.z * kchunk;                 // even
+    const int k1 = min(k0 + kchunk, nz);
+    const int plane = nx * ny;
+    int idx = k0 * plane + 2 * J * nx + 4 * q;
+    int K = k0 >> 1;
+    float4 qma, qmb, q0a, q0b, qpa, qpb;
+    interp(K - 1, qma, qmb);
+    interp(K, q0a, q0b);
+    interp(K + 1, qpa, qpb);
+    const float w = 1.0f / 64.0f;
+    auto add = [&](float* p, float4 a, float4 b) {      // p += (3 a + b) / 64
+        float4 v = ld_f4(p);
+        v.x += (3.0f * a.x + b.x) * w;
+        v.y += (3.0f * a.y + b.y) * w;
+        v.z += (3.0f * a.z + b.z) * w;
+        v.w += (3.0f * a.w + b.w) * w;
+        *reinterpret_cast<float4*>(p) = v;
+    };
+    for (int k = k0; k < k1; k += 2, idx += 2 * plane) {
+        add(fine_u + idx, q0a, qma);
+        add(fine_u + idx + nx, q0b, qmb);
+        add(fine_u + idx + plane, q0a, qpa);
+        add(fine_u + idx + plane + nx, q0b, qpb);
+        ++K;
+        qma = q0a; qmb = q0b;
+        q0a = qpa; q0b = qpb;
+        if (k + 2 < k1) interp(K + 1, qpa, qpb);
     }
 }
 
@@ -466,9 +613,6 @@ k_update_residual(const LevelGeom g, double* __restrict__ phi, const float* __re
 // arrays): one 16-byte load of e per neighbour row and 16-byte loads and
 // stores of phi and r, the z neighbours carried in registers, the z loop
 // unrolled by two so the next plane's loads overlap the current arithmetic.
-__device__ __forceinline__ float4 ld_f4(const float* p) { return *reinterpret_cast<const float4*>(p); }
-__device__ __forceinline__ double2 ld_d2(const double* p) { return *reinterpret_cast<const double2*>(p); }
-__device__ __forceinline__ float4 neg_f4(float4 v) { return make_float4(-v.x, -v.y, -v.z, -v.w); }
 
 template <bool UNIFORM>
 __global__ void __launch_bounds__(BX * BY)
@@ -653,6 +797,22 @@ cudaError_t launch_residual(const LevelGeom& g, const TI* u, const TI* rhs, TO* 
 template <typename T>
 cudaError_t launch_residual_restrict(const LevelGeom& g, const T* u, const T* rhs, T* coarse_out,
                                      Partial* partials, int* nblocks_out, cudaStream_t st) {
+    if constexpr (std::is_same<T, float>::value) {
+        const bool aligned = ((reinterpret_cast<uintptr_t>(u) | reinterpret_cast<uintptr_t>(rhs) |
+                               reinterpret_cast<uintptr_t>(coarse_out)) & 15) == 0;
+        if (!has_faces(g) && (g.nx & 3) == 0 && (g.ny & 1) == 0 && (g.nz & 1) == 0 && aligned) {
+            // as many blocks as the scalar launch at most (the partials buffer)
+            const long long gx = (g.nx / 4 + BX - 1) / BX, gy = (g.ny / 2 + BY - 1) / BY;
+            const long long chunks = std::min<long long>(g.nz / 2, std::max(1LL, restrict_blocks(g) / (gx * gy)));
+            int kc = (int)((g.nz + chunks - 1) / chunks);
+            kc += kc & 1;
+            dim3 block(BX, BY, 1);
+            dim3 grid((unsigned)gx, (unsigned)gy, (unsigned)((g.nz + kc - 1) / kc));
+            k_residual_restrict4<<<grid, block, 0, st>>>(g, u, rhs, coarse_out, partials, kc);
+            if (nblocks_out) *nblocks_out = (int)(grid.x * grid.y * grid.z);
+            return cudaGetLastError();
+        }
+    }
     const int kc = even_kchunk(g);
     dim3 block(BX, BY, 1);
     dim3 grid((g.nx + BX - 1) / BX, (g.ny + BY - 1) / BY, (g.nz + kc - 1) / kc);
@@ -664,6 +824,19 @@ cudaError_t launch_residual_restrict(const LevelGeom& g, const T* u, const T* rh
 
 template <typename T>
 cudaError_t launch_prolong_correct(const LevelGeom& g, const T* coarse, T* fine_u, cudaStream_t st) {
+    if constexpr (std::is_same<T, float>::value) {
+        const bool aligned = ((reinterpret_cast<uintptr_t>(coarse) | reinterpret_cast<uintptr_t>(fine_u)) & 15) == 0;
+        if ((g.nx & 3) == 0 && (g.ny & 1) == 0 && (g.nz & 1) == 0 && aligned) {
+            const long long gx = (g.nx / 4 + BX - 1) / BX, gy = (g.ny / 2 + BY - 1) / BY;
+            const long long chunks = std::min<long long>(g.nz / 2, std::max(1LL, 16LL * 152 / (gx * gy)));
+            int kc = (int)((g.nz + chunks - 1) / chunks);
+            kc += kc & 1;
+            dim3 block(BX, BY, 1);
+            dim3 grid((unsigned)gx, (unsigned)gy, (unsigned)((g.nz + kc - 1) / kc));
+            k_prolong_correct4<<<grid, block, 0, st>>>(g, coarse, fine_u, kc);
+            return cudaGetLastError();
+        }
+    }
     const int kc = even_kchunk(g);
     dim3 block(BX, BY, 1);
     dim3 grid((g.nx + BX - 1) / BX, (g.ny + BY - 1) / BY, (g.nz + kc - 1) / kc);
