@@ -413,7 +413,10 @@ k_superstep_lean(const __grid_constant__ LevelGeom g, const __grid_constant__ Le
         cen1 = ld4(sm + C::OY0 + (-1 & 3) * P + o + d1);
     }
 
-    for (int u = 0; u < nph; ++u) {
+    // One phase.  (dn, cen) hold the thread's strips of planes p - 1 and p of its
+    // input stage; the strips of plane p + 1 are loaded into `nxt`.  The loop
+    // below rotates the three register sets by renaming (unrolled by three).
+    auto phase = [&](int u, float4& dn0, float4& cen0, float4& nxt0, float4& dn1, float4& cen1, float4& nxt1) {
         // stage plane t + 2 into shared memory, prefetch plane t + kPrefetch into L2
         const int zs_cur = zs_next;
         if (u + 2 < nload) stage_plane(u + 2, &zs_next);
@@ -437,7 +440,9 @@ k_superstep_lean(const __grid_constant__ LevelGeom g, const __grid_constant__ Le
                 const float* yc = sm + C::OY0 + sp * P + o;
                 const float* yu = sm + C::OY0 + (u & 3) * P + o;
                 const float* fp = sm + C::OF + ((u - 1) & 3) * P + o;
-                const float4 up0 = ld4(yu), up1 = ld4(yu + d1);
+                nxt0 = ld4(yu);
+                nxt1 = ld4(yu + d1);
+                const float4 up0 = nxt0, up1 = nxt1;
                 const float4 nn = ld4(yc + d1 - W), ss = ld4(yc + W);
                 const float4 f0 = ld4(fp), f1 = ld4(fp + d1);
                 float l0 = __shfl_up_sync(0xffffffffu, cen0.w, 1);
@@ -462,8 +467,6 @@ k_superstep_lean(const __grid_constant__ LevelGeom g, const __grid_constant__ Le
                         st4(w3p + d1, w3b);
                     }
                 }
-                dn0 = cen0; cen0 = up0;
-                dn1 = cen1; cen1 = up1;
             }
         } else if (J >= 2) {
             // ---- stage J on plane p = t - L
@@ -471,7 +474,9 @@ k_superstep_lean(const __grid_constant__ LevelGeom g, const __grid_constant__ Le
             const float* yc = in_b + sp * P;
             const float* yu = in_b + ((u - L + 1) & 3) * P;
             const float* wp = w_b + ((u - L) & w_mask) * P;
-            const float4 up0 = ld4(yu), up1 = ld4(yu + d1);
+            nxt0 = ld4(yu);
+            nxt1 = ld4(yu + d1);
+            const float4 up0 = nxt0, up1 = nxt1;
             const float4 nn = ld4(yc + d1 - W), ss = ld4(yc + W);
             float l0 = __shfl_up_sync(0xffffffffu, cen0.w, 1);
             float r0 = __shfl_down_sync(0xffffffffu, cen0.x, 1);
@@ -496,14 +501,21 @@ k_superstep_lean(const __grid_constant__ LevelGeom g, const __grid_constant__ Le
                 if (st0 >= 0) store_out(ob + st0, va, st_vec, st_n);
                 if (st1 >= 0) store_out(ob + st1, vb, st_vec, st_n);
             }
-            dn0 = cen0; cen0 = up0;
-            dn1 = cen1; cen1 = up1;
         }
 
         // plane t + 1 (staged in the previous phase) has landed: fix its reflected cells
         cpa_wait_prev();
         if (u + 1 < nload) fix_plane(u + 1, zs_cur);
         __syncthreads();
+    };
+
+    float4 nx0 = make_float4(0.f, 0.f, 0.f, 0.f), nx1 = nx0;
+    for (int u = 0; u < nph; u += 3) {              // nph is uniform: every thread takes the same exits
+        phase(u, dn0, cen0, nx0, dn1, cen1, nx1);
+        if (u + 1 >= nph) break;
+        phase(u + 1, cen0, nx0, dn0, cen1, nx1, dn1);
+        if (u + 2 >= nph) break;
+        phase(u + 2, nx0, dn0, cen0, nx1, dn1, cen1);
     }
 }
 
