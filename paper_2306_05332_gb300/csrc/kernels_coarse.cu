@@ -11,6 +11,9 @@
 // Boundaries: homogeneous Dirichlet (Eq. error_ghost) or periodic.
 #include "sg_internal.cuh"
 
+#include <cstdint>
+#include <type_traits>
+
 namespace sg {
 
 namespace {
@@ -252,6 +255,118 @@ __global__ void __launch_bounds__(kCoarseThreads) k_coarse_small(const CoarsePar
     if (threadIdx.x == 0 && p.ss_done) *p.ss_done = done;
 }
 
+// FP32 levels with nx % 4 == 0 and at most kCoarseThreads strips of four x
+// cells: one strip per thread, 16-byte loads and stores.  Rows are padded to
+// nx + 8 floats with the interior at offset 4 (16-byte aligned) and the x
+// ghosts at offsets 3 and nx + 4; y and z ghost rows and planes as above.
+__device__ __forceinline__ float4 cld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
+__device__ __forceinline__ void cst4(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
+
+__global__ void __launch_bounds__(kCoarseThreads) k_coarse_strips(const CoarseParams p) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ float red[33];
+    const int nx = p.g.nx, ny = p.g.ny, nz = p.g.nz;
+    const int nq = nx >> 2, nstrips = nq * ny * nz;
+    const int rs = nx + 8, ps = rs * (ny + 2), np = ps * (nz + 2);
+    float* const b0 = reinterpret_cast<float*>(smem_raw);
+    const float hx = p.g.ihx2f, hy = p.g.ihy2f, hz = p.g.ihz2f;
+    const float diag = 2.0f * (hx + hy + hz);
+    const bool perx = p.g.per[0] != 0, pery = p.g.per[1] != 0, perz = p.g.per[2] != 0;
+    const float* rhs = static_cast<const float*>(p.rhs);
+
+    const int sidx = threadIdx.x;
+    const bool mine = sidx < nstrips;
+    int q = 0, j = 0, k = 0;
+    if (mine) {
+        q = sidx % nq;
+        j = (sidx / nq) % ny;
+        k = sidx / (nq * ny);
+    }
+    const int pc = (k + 1) * ps + (j + 1) * rs + 4 + 4 * q;     // padded index of the strip
+    const int t = (k * ny + j) * nx + 4 * q;                     // unpadded index
+    float4 fv = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (mine) fv = cld4(rhs + t);
+    for (int idx = threadIdx.x; idx < 3 * np; idx += blockDim.x) b0[idx] = 0.0f;
+    __syncthreads();
+
+    auto lap = [&](const float* y) {
+        const float4 c = cld4(y + pc);
+        const float l = y[pc - 1], r = y[pc + 4];
+        const float4 ym = cld4(y + pc - rs), yp = cld4(y + pc + rs);
+        const float4 zm = cld4(y + pc - ps), zp = cld4(y + pc + ps);
+        float4 o;
+        o.x = hx * (l + c.y) + hy * (ym.x + yp.x) + hz * (zm.x + zp.x) - diag * c.x;
+        o.y = hx * (c.x + c.z) + hy * (ym.y + yp.y) + hz * (zm.y + zp.y) - diag * c.y;
+        o.z = hx * (c.y + c.w) + hy * (ym.z + yp.z) + hz * (zm.z + zp.z) - diag * c.z;
+        o.w = hx * (c.z + r) + hy * (ym.w + yp.w) + hz * (zm.w + zp.w) - diag * c.w;
+        return o;
+    };
+    // store the strip and the ghosts that mirror it (Eq. error_ghost / Eq. periodic)
+    auto put = [&](float* y, float4 v) {
+        cst4(y + pc, v);
+        const float4 nv = make_float4(-v.x, -v.y, -v.z, -v.w);
+        if (q == 0) y[perx ? pc + nx : pc - 1] = perx ? v.x : -v.x;
+        if (q == nq - 1) y[perx ? pc + 3 - nx : pc + 4] = perx ? v.w : -v.w;
+        if (j == 0) cst4(y + (pery ? pc + ny * rs : pc - rs), pery ? v : nv);
+        if (j == ny - 1) cst4(y + (pery ? pc - ny * rs : pc + rs), pery ? v : nv);
+        if (k == 0) cst4(y + (perz ? pc + nz * ps : pc - ps), perz ? v : nv);
+        if (k == nz - 1) cst4(y + (perz ? pc - nz * ps : pc + ps), perz ? v : nv);
+    };
+
+    const float r0sq = block_sum(mine ? fv.x * fv.x + fv.y * fv.y + fv.z * fv.z + fv.w * fv.w : 0.0f, red);
+    const float tol = float(p.tol);
+    const float tu = float(p.tau_unit);
+    const float tolsq = tol * tol * r0sq;
+
+    float* y_cur = b0;
+    float* y_prev = b0 + np;
+    float* y_free = b0 + 2 * np;
+    int done = 0;
+    for (int ss = 0; ss < p.max_ss; ++ss) {
+        if (tol > 0.0f) {
+            float acc = 0.0f;
+            if (mine) {
+                const float4 L = lap(y_cur);
+                const float4 r = make_float4(fv.x - L.x, fv.y - L.y, fv.z - L.z, fv.w - L.w);
+                acc = r.x * r.x + r.y * r.y + r.z * r.z + r.w * r.w;
+            }
+            if (block_sum(acc, red) <= tolsq) break;
+        }
+        const int s = p.sched[ss];
+        for (int jst = 1; jst <= s; ++jst) {
+            const float inv = 1.0f / float(jst);
+            const float mu = 2.0f - inv, nu = inv - 1.0f;   // (2j - 1) / j, (1 - j) / j
+            const float mut = mu * tu;
+            float* const y_new = y_free;
+            if (mine) {
+                const float4 L = lap(y_cur);
+                const float4 c = cld4(y_cur + pc);
+                float4 v;
+                if (jst == 1) {
+                    v = make_float4(c.x + tu * (L.x - fv.x), c.y + tu * (L.y - fv.y), c.z + tu * (L.z - fv.z),
+                                    c.w + tu * (L.w - fv.w));
+                } else {
+                    const float4 pv = cld4(y_prev + pc);
+                    v = make_float4(mu * c.x + nu * pv.x + mut * (L.x - fv.x), mu * c.y + nu * pv.y + mut * (L.y - fv.y),
+                                    mu * c.z + nu * pv.z + mut * (L.z - fv.z), mu * c.w + nu * pv.w + mut * (L.w - fv.w));
+                }
+                put(y_new, v);
+            }
+            __syncthreads();
+            y_free = y_prev;
+            y_prev = y_cur;
+            y_cur = y_new;
+        }
+        ++done;
+    }
+    if (mine) cst4(static_cast<float*>(p.u_out) + t, cld4(y_cur + pc));
+    if (threadIdx.x == 0 && p.ss_done) *p.ss_done = done;
+}
+
+size_t coarse_strips_bytes(int nx, int ny, int nz) {
+    return (size_t)3 * (size_t)(nx + 8) * (ny + 2) * (nz + 2) * sizeof(float);
+}
+
 template <typename T>
 size_t coarse_small_bytes(int nx, int ny, int nz) {
     return (size_t)3 * (size_t)(nx + 2) * (ny + 2) * (nz + 2) * sizeof(T);
@@ -277,6 +392,15 @@ cudaError_t launch_coarse_solve(const CoarseParams& p, cudaStream_t st) {
     if (bytes > kSmemLimit) return cudaErrorInvalidValue;
     int threads = kCoarseThreads;
     if (n < threads) threads = (int)((n + 31) / 32) * 32;
+    if constexpr (std::is_same<T, float>::value) {
+        const size_t sb = coarse_strips_bytes(p.g.nx, p.g.ny, p.g.nz);
+        const bool aligned = ((reinterpret_cast<uintptr_t>(p.rhs) | reinterpret_cast<uintptr_t>(p.u_out)) & 15) == 0;
+        if ((p.g.nx & 3) == 0 && n / 4 <= kCoarseThreads && sb <= kSmemLimit && aligned) {
+            const int strips = (int)(n / 4);
+            k_coarse_strips<<<1, ((strips + 31) / 32) * 32, sb, st>>>(p);
+            return cudaGetLastError();
+        }
+    }
     const size_t small = coarse_small_bytes<T>(p.g.nx, p.g.ny, p.g.nz);
     if (n <= kSmallCells && small <= kSmemLimit) {
         k_coarse_small<T><<<1, threads, small, st>>>(p);
@@ -289,6 +413,8 @@ cudaError_t launch_coarse_solve(const CoarseParams& p, cudaStream_t st) {
 
 cudaError_t coarse_configure() {
     cudaError_t e;
+    if ((e = cudaFuncSetAttribute(k_coarse_strips, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)kSmemLimit)) != cudaSuccess) return e;
     if ((e = cudaFuncSetAttribute(k_coarse_small<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)kSmemLimit)) != cudaSuccess) return e;
     if ((e = cudaFuncSetAttribute(k_coarse_small<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
