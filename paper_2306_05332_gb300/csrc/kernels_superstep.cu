@@ -280,15 +280,18 @@ template <int S, int ORDER, bool ZERO>
 __global__ void __launch_bounds__(Lean<S, ZERO>::NT, 2)
 k_superstep_lean(const __grid_constant__ LevelGeom g, const __grid_constant__ LeanCoef k,
                  const float* __restrict__ y0g, const float* __restrict__ fg, float* __restrict__ outg,
-                 int kchunk, int vec_ok) {
+                 int tiles_x, int kchunk, int vec_ok) {
     using C = Lean<S, ZERO>;
     constexpr int W = C::W, P = C::P, Q = C::Q, HQ = C::HQ;
     extern __shared__ __align__(16) float sm[];
     const int tid = threadIdx.x, lane = tid & 31;
-    const int X0 = blockIdx.x * C::TX - C::HX;          // global x of local column 0
-    const int Yt = blockIdx.y * C::TY - S;              // global y of local row 0
     const int nx = g.nx, ny = g.ny, nz = g.nz, plane = nx * ny;
     const bool pz = g.per[2] != 0;
+
+    // ---- one segment of the stream: tile (bx, by), planes [kz0, kz1)
+    auto segment = [&](int bx, int by, int kz0, int kz1) {
+    const int X0 = bx * C::TX - C::HX;                  // global x of local column 0
+    const int Yt = by * C::TY - S;                      // global y of local row 0
 
     // ---- this thread's stage and row pair (fixed for the whole stream; J = 0: loads only)
     int J, item;
@@ -367,8 +370,6 @@ k_superstep_lean(const __grid_constant__ LevelGeom g, const __grid_constant__ Le
         }
     }
 
-    const int kz0 = blockIdx.z * kchunk;
-    const int kz1 = min(kz0 + kchunk, nz);
     const int t_first = kz0 - S + 2;                    // stage 1 computes plane t - 1
     const int nph = (kz1 - kz0) + 3 * S - 3;            // phases
     const int nload = kz1 + S - t_first;                // planes t_first + v, v < nload, are staged
@@ -517,6 +518,30 @@ k_superstep_lean(const __grid_constant__ LevelGeom g, const __grid_constant__ Le
         if (u + 2 >= nph) break;
         phase(u + 2, nx0, dn0, cen0, nx1, dn1, cen1);
     }
+    };
+
+    const long long tiles = (long long)tiles_x * ((ny + C::TY - 1) / C::TY);
+    if (kchunk > 0) {
+        // tile-aligned chunks: CTA b streams planes [c kchunk, (c + 1) kchunk) of one tile
+        const int cpt = (nz + kchunk - 1) / kchunk;
+        const int tile = blockIdx.x / cpt, c = blockIdx.x % cpt;
+        segment(tile % tiles_x, tile / tiles_x, c * kchunk, min(nz, (c + 1) * kchunk));
+        return;
+    }
+    // balanced: the (tile, plane) units of the level, tiles outermost, split
+    // evenly over the CTAs; a CTA streams its range as one segment per tile it
+    // touches, each with its own pipeline
+    const long long total = tiles * nz;
+    long long w = total * blockIdx.x / gridDim.x;
+    const long long w_end = total * (blockIdx.x + 1) / gridDim.x;
+    while (w < w_end) {                                 // uniform over the CTA
+        const long long tile = w / nz;
+        const int kz0 = (int)(w - tile * nz);
+        const int kz1 = (int)std::min<long long>(nz, kz0 + (w_end - w));
+        segment((int)(tile % tiles_x), (int)(tile / tiles_x), kz0, kz1);
+        w += kz1 - kz0;
+        __syncthreads();                                // the next segment reuses the rings
+    }
 }
 
 int g_lean_sms = 152;
@@ -571,16 +596,25 @@ cudaError_t lean_one(const LevelGeom& g, const LeanCoef& k, const float* y0, con
                      cudaStream_t st) {
     using C = Lean<S, ZERO>;
     const long long gx = (g.nx + C::TX - 1) / C::TX, gy = (g.ny + C::TY - 1) / C::TY;
-    // all CTAs resident in one wave; a chunk adds 3s - 3 pipeline phases, so keep it >= 4s planes
+    // One resident wave.  Either every tile is cut into equal z chunks (at
+    // least 4s planes, a segment costs 3s - 3 extra phases), or the (tile,
+    // plane) units are shared evenly and a CTA may stream two segments:
+    // take the schedule with the shorter longest CTA.
     const long long slots = (long long)g_lean_sms * LeanResident<S, ORDER, ZERO>::per_sm;
-    long long chunks = std::max(1LL, slots / (gx * gy));
+    const long long tiles = gx * gy, fill = 3 * S - 3;
+    long long chunks = std::max(1LL, slots / tiles);
     chunks = std::min<long long>(chunks, std::max(1, g.nz / (4 * S)));
     const int kchunk = (int)((g.nz + chunks - 1) / chunks);
+    const long long aligned_phases = kchunk + fill;
+    const long long ncta_bal = std::max(1LL, std::min(slots, tiles * g.nz / (4 * S)));
+    const long long balanced_phases = (tiles * g.nz + ncta_bal - 1) / ncta_bal + 2 * fill;
+    const bool balanced = balanced_phases < aligned_phases;
+    const long long ncta = balanced ? ncta_bal : tiles * ((g.nz + kchunk - 1) / kchunk);
     const bool aligned = ((reinterpret_cast<uintptr_t>(y0) | reinterpret_cast<uintptr_t>(f) |
                            reinterpret_cast<uintptr_t>(out)) & 15) == 0;
     const int vec_ok = ((g.nx & 3) == 0 && aligned) ? 1 : 0;
-    dim3 grid((unsigned)gx, (unsigned)gy, (unsigned)((g.nz + kchunk - 1) / kchunk));
-    k_superstep_lean<S, ORDER, ZERO><<<grid, C::NT, C::BYTES, st>>>(g, k, y0, f, out, kchunk, vec_ok);
+    k_superstep_lean<S, ORDER, ZERO><<<(unsigned)ncta, C::NT, C::BYTES, st>>>(g, k, y0, f, out, (int)gx,
+                                                                              balanced ? 0 : kchunk, vec_ok);
     return cudaGetLastError();
 }
 
