@@ -3,7 +3,7 @@
 // error equation of the mixed-precision V-cycle (homogeneous Dirichlet or
 // periodic ghosts).
 //
-// Work split.  A CTA owns a 32 x 16 column of the level, widened by a halo
+// Work split.  A CTA owns a 32 x 16 (or 32 x 14) column of the level, widened by a halo
 // (4 cells in x, s cells in y), and streams it along z.  Stage j is computed
 // on the tile widened by s - j cells in strips of four x cells; every thread
 // owns ONE strip of ONE stage for the whole stream, and each stage's strips
@@ -30,9 +30,10 @@
 //   W_j = nu_j Y_{j-2} + c0_j Y0 + gamma~_j Z0 - mu~_j tau f   (RKL1: c0 = gamma~ = 0)
 // and with Y0 = 0 every W_j is a multiple of f.
 //
-// Ring depths divide 8 and the phase loop is unrolled by 8, so every ring
-// slot is a compile-time constant and shared-memory addresses are immediate
-// offsets from one per-thread register.
+// Ring depths are powers of two (a slot is a mask of the phase index), and the
+// phase loop is unrolled by three so that the z window rotates by register
+// renaming.  A launch cuts every tile into the same z chunks, so neighbouring
+// tiles stream the same planes at about the same time and share halos in L2.
 //
 // Latency.  Planes are staged into shared memory two phases before their
 // first use, and prefetched into L2 kPrefetch planes ahead, so a phase waits
@@ -85,9 +86,9 @@ __host__ __device__ __forceinline__ int map_axis(int v, int n, bool periodic, in
     return 2 * n - 1 - m;
 }
 
-template <int S, bool ZERO>
+template <int S, bool ZERO, int TYV>
 struct Lean {
-    static constexpr int TX = 32, TY = 16, HX = 4;
+    static constexpr int TX = 32, TY = TYV, HX = 4;
     static constexpr int W = TX + 2 * HX;            // plane row (floats)
     static constexpr int H = TY + 2 * S;             // plane rows
     static constexpr int Q = W / 4;                  // strips per row
@@ -276,12 +277,12 @@ __device__ __forceinline__ void store_out(float* dst, float4 v, bool vec, int n)
     }
 }
 
-template <int S, int ORDER, bool ZERO>
-__global__ void __launch_bounds__(Lean<S, ZERO>::NT, 2)
+template <int S, int ORDER, bool ZERO, int TY>
+__global__ void __launch_bounds__(Lean<S, ZERO, TY>::NT, 2)
 k_superstep_lean(const __grid_constant__ LevelGeom g, const __grid_constant__ LeanCoef k,
                  const float* __restrict__ y0g, const float* __restrict__ fg, float* __restrict__ outg,
                  int tiles_x, int kchunk, int vec_ok) {
-    using C = Lean<S, ZERO>;
+    using C = Lean<S, ZERO, TY>;
     constexpr int W = C::W, P = C::P, Q = C::Q, HQ = C::HQ;
     extern __shared__ __align__(16) float sm[];
     const int tid = threadIdx.x, lane = tid & 31;
@@ -520,38 +521,22 @@ k_superstep_lean(const __grid_constant__ LevelGeom g, const __grid_constant__ Le
     }
     };
 
-    const long long tiles = (long long)tiles_x * ((ny + C::TY - 1) / C::TY);
-    if (kchunk > 0) {
-        // tile-aligned chunks: CTA b streams planes [c kchunk, (c + 1) kchunk) of one tile
-        const int cpt = (nz + kchunk - 1) / kchunk;
-        const int tile = blockIdx.x / cpt, c = blockIdx.x % cpt;
-        segment(tile % tiles_x, tile / tiles_x, c * kchunk, min(nz, (c + 1) * kchunk));
-        return;
-    }
-    // balanced: the (tile, plane) units of the level, tiles outermost, split
-    // evenly over the CTAs; a CTA streams its range as one segment per tile it
-    // touches, each with its own pipeline
-    const long long total = tiles * nz;
-    long long w = total * blockIdx.x / gridDim.x;
-    const long long w_end = total * (blockIdx.x + 1) / gridDim.x;
-    while (w < w_end) {                                 // uniform over the CTA
-        const long long tile = w / nz;
-        const int kz0 = (int)(w - tile * nz);
-        const int kz1 = (int)std::min<long long>(nz, kz0 + (w_end - w));
-        segment((int)(tile % tiles_x), (int)(tile / tiles_x), kz0, kz1);
-        w += kz1 - kz0;
-        __syncthreads();                                // the next segment reuses the rings
-    }
+    // CTA b streams planes [c kchunk, (c + 1) kchunk) of one tile: all tiles
+    // share the chunk boundaries, so neighbouring tiles stream the same planes
+    // at about the same time and their halo rows are served from L2
+    const int cpt = (nz + kchunk - 1) / kchunk;
+    const int tile = blockIdx.x / cpt, c = blockIdx.x % cpt;
+    segment(tile % tiles_x, tile / tiles_x, c * kchunk, min(nz, (c + 1) * kchunk));
 }
 
 int g_lean_sms = 152;
 
-template <int S, int ORDER, bool ZERO>
+template <int S, int ORDER, bool ZERO, int TY>
 struct LeanResident {
     static int per_sm;
 };
-template <int S, int ORDER, bool ZERO>
-int LeanResident<S, ORDER, ZERO>::per_sm = 1;
+template <int S, int ORDER, bool ZERO, int TY>
+int LeanResident<S, ORDER, ZERO, TY>::per_sm = 1;
 
 LeanCoef make_lean_coef(const LevelGeom& g, int order, int s, const FusedCoef& cf) {
     LeanCoef k{};
@@ -591,44 +576,71 @@ LeanCoef make_lean_coef(const LevelGeom& g, int order, int s, const FusedCoef& c
     return k;
 }
 
-template <int S, int ORDER, bool ZERO>
-cudaError_t lean_one(const LevelGeom& g, const LeanCoef& k, const float* y0, const float* f, float* out,
-                     cudaStream_t st) {
-    using C = Lean<S, ZERO>;
+// A launch plan: every tile cut into equal z chunks (at least 4s planes; a
+// chunk costs 3s - 3 extra pipeline phases), one resident wave of CTAs.
+struct LeanPlan {
+    long long tiles_x = 0, ncta = 0;
+    int kchunk = 0;
+    double cost = 0;     // the longest SM: CTAs per SM x phases x strip items per phase
+};
+
+template <int S, int ORDER, bool ZERO, int TY>
+LeanPlan lean_plan(const LevelGeom& g) {
+    using C = Lean<S, ZERO, TY>;
+    LeanPlan p;
     const long long gx = (g.nx + C::TX - 1) / C::TX, gy = (g.ny + C::TY - 1) / C::TY;
-    // One resident wave.  Either every tile is cut into equal z chunks (at
-    // least 4s planes, a segment costs 3s - 3 extra phases), or the (tile,
-    // plane) units are shared evenly and a CTA may stream two segments:
-    // take the schedule with the shorter longest CTA.
-    const long long slots = (long long)g_lean_sms * LeanResident<S, ORDER, ZERO>::per_sm;
-    const long long tiles = gx * gy, fill = 3 * S - 3;
-    long long chunks = std::max(1LL, slots / tiles);
+    const long long slots = (long long)g_lean_sms * LeanResident<S, ORDER, ZERO, TY>::per_sm;
+    long long chunks = std::max(1LL, slots / (gx * gy));
     chunks = std::min<long long>(chunks, std::max(1, g.nz / (4 * S)));
-    const int kchunk = (int)((g.nz + chunks - 1) / chunks);
-    const long long aligned_phases = kchunk + fill;
-    const long long ncta_bal = std::max(1LL, std::min(slots, tiles * g.nz / (4 * S)));
-    const long long balanced_phases = (tiles * g.nz + ncta_bal - 1) / ncta_bal + 2 * fill;
-    const bool balanced = balanced_phases < aligned_phases;
-    const long long ncta = balanced ? ncta_bal : tiles * ((g.nz + kchunk - 1) / kchunk);
-    const bool aligned = ((reinterpret_cast<uintptr_t>(y0) | reinterpret_cast<uintptr_t>(f) |
-                           reinterpret_cast<uintptr_t>(out)) & 15) == 0;
-    const int vec_ok = ((g.nx & 3) == 0 && aligned) ? 1 : 0;
-    k_superstep_lean<S, ORDER, ZERO><<<(unsigned)ncta, C::NT, C::BYTES, st>>>(g, k, y0, f, out, (int)gx,
-                                                                              balanced ? 0 : kchunk, vec_ok);
+    p.tiles_x = gx;
+    p.kchunk = (int)((g.nz + chunks - 1) / chunks);
+    p.ncta = gx * gy * ((g.nz + p.kchunk - 1) / p.kchunk);
+    const long long per_sm = (p.ncta + g_lean_sms - 1) / g_lean_sms;
+    const int items = C::items(1) + C::items(2) + (S == 3 ? C::items(3) : 0);
+    p.cost = double(per_sm) * double(p.kchunk + 3 * S - 3) * double(items);
+    return p;
+}
+
+template <int S, int ORDER, bool ZERO, int TY>
+cudaError_t lean_launch(const LeanPlan& p, const LevelGeom& g, const LeanCoef& k, const float* y0, const float* f,
+                        float* out, int vec_ok, cudaStream_t st) {
+    using C = Lean<S, ZERO, TY>;
+    k_superstep_lean<S, ORDER, ZERO, TY><<<(unsigned)p.ncta, C::NT, C::BYTES, st>>>(g, k, y0, f, out, (int)p.tiles_x,
+                                                                                   p.kchunk, vec_ok);
     return cudaGetLastError();
 }
 
+// Tiles 16 or 14 rows high: the shorter tile costs more halo per cell but can
+// fill every CTA slot (256^3: 152 tiles x 2 chunks = 2 CTAs on each of 152
+// SMs); the plan with the cheaper longest SM is launched.
 template <int S, int ORDER, bool ZERO>
+cudaError_t lean_one(const LevelGeom& g, const LeanCoef& k, const float* y0, const float* f, float* out,
+                     cudaStream_t st) {
+    const bool aligned = ((reinterpret_cast<uintptr_t>(y0) | reinterpret_cast<uintptr_t>(f) |
+                           reinterpret_cast<uintptr_t>(out)) & 15) == 0;
+    const int vec_ok = ((g.nx & 3) == 0 && aligned) ? 1 : 0;
+    const LeanPlan a = lean_plan<S, ORDER, ZERO, 16>(g), b = lean_plan<S, ORDER, ZERO, 14>(g);
+    if (b.cost < a.cost) return lean_launch<S, ORDER, ZERO, 14>(b, g, k, y0, f, out, vec_ok, st);
+    return lean_launch<S, ORDER, ZERO, 16>(a, g, k, y0, f, out, vec_ok, st);
+}
+
+template <int S, int ORDER, bool ZERO, int TY>
 cudaError_t lean_configure_one() {
-    using C = Lean<S, ZERO>;
-    auto kern = k_superstep_lean<S, ORDER, ZERO>;
+    using C = Lean<S, ZERO, TY>;
+    auto kern = k_superstep_lean<S, ORDER, ZERO, TY>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::BYTES);
     if (e != cudaSuccess) return e;
     int n = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, C::NT, C::BYTES);
     if (e != cudaSuccess) return e;
-    LeanResident<S, ORDER, ZERO>::per_sm = n > 0 ? n : 1;
+    LeanResident<S, ORDER, ZERO, TY>::per_sm = n > 0 ? n : 1;
     return cudaSuccess;
+}
+
+template <int S, int ORDER, bool ZERO>
+cudaError_t lean_configure_ty() {
+    cudaError_t e = lean_configure_one<S, ORDER, ZERO, 16>();
+    return e != cudaSuccess ? e : lean_configure_one<S, ORDER, ZERO, 14>();
 }
 
 template <int S>
@@ -645,14 +657,14 @@ cudaError_t lean_configure() {
     int dev = 0;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&g_lean_sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-    if ((e = lean_configure_one<2, 1, false>()) != cudaSuccess) return e;
-    if ((e = lean_configure_one<2, 1, true>()) != cudaSuccess) return e;
-    if ((e = lean_configure_one<2, 2, false>()) != cudaSuccess) return e;
-    if ((e = lean_configure_one<2, 2, true>()) != cudaSuccess) return e;
-    if ((e = lean_configure_one<3, 1, false>()) != cudaSuccess) return e;
-    if ((e = lean_configure_one<3, 1, true>()) != cudaSuccess) return e;
-    if ((e = lean_configure_one<3, 2, false>()) != cudaSuccess) return e;
-    return lean_configure_one<3, 2, true>();
+    if ((e = lean_configure_ty<2, 1, false>()) != cudaSuccess) return e;
+    if ((e = lean_configure_ty<2, 1, true>()) != cudaSuccess) return e;
+    if ((e = lean_configure_ty<2, 2, false>()) != cudaSuccess) return e;
+    if ((e = lean_configure_ty<2, 2, true>()) != cudaSuccess) return e;
+    if ((e = lean_configure_ty<3, 1, false>()) != cudaSuccess) return e;
+    if ((e = lean_configure_ty<3, 1, true>()) != cudaSuccess) return e;
+    if ((e = lean_configure_ty<3, 2, false>()) != cudaSuccess) return e;
+    return lean_configure_ty<3, 2, true>();
 }
 
 cudaError_t launch_superstep_lean(const LevelGeom& g, int order, int s, bool zero_y0, const FusedCoef& cf,
