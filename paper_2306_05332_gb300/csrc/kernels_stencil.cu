@@ -233,6 +233,71 @@ k_residual(const LevelGeom g, const TI* __restrict__ u, const TI* __restrict__ r
     block_reduce_write<A>(sq, mx, A(0), partials, bid);
 }
 
+// The same residual for u = 0 (a solve that starts from a zero potential):
+// every neighbour is zero except the ghosts of a Dirichlet wall with face data
+// (2 g, Eq. solution_ghost), so r = f away from such walls.  Next to them the
+// sums are formed in the order of k_residual (the same value bit for bit, up
+// to the sign of an exact zero).  Whether a cell touches such a wall is
+// decided per column and per end plane, outside the z loop, so cells away
+// from the walls do no FP64 stencil arithmetic and u is never read.
+template <typename TO, bool UNIFORM, bool FACES>
+__global__ void __launch_bounds__(BX * BY)
+k_residual_zero(const LevelGeom g, const double* __restrict__ rhs, TO* r_out, double* r_full, Partial* partials,
+                int kchunk) {
+    using A = typename Acc<TO>::type;
+    const int i = blockIdx.x * BX + threadIdx.x;
+    const int j = blockIdx.y * BY + threadIdx.y;
+    A sq = A(0), mx = A(0);
+    if (i < g.nx && j < g.ny) {
+        const int k0 = blockIdx.z * kchunk;
+        const int k1 = min(k0 + kchunk, g.nz);
+        const int plane = g.nx * g.ny;
+        const bool dx = !g.per[0], dy = !g.per[1], dz = !g.per[2];
+        auto emit = [&](int idx, double r) {
+            const TO ro = TO(r);
+            if (r_out) r_out[idx] = ro;
+            if (r_full) r_full[idx] = r;
+            const A ra = A(ro);
+            sq = fma(ra, ra, sq);
+            mx = fmax(mx, fabs(ra));
+        };
+        // a cell next to a Dirichlet wall with face data: f minus the face terms
+        auto wall_cell = [&](int k) {
+            const int idx = (k * g.ny + j) * g.nx + i;
+            double xm = 0.0, xp = 0.0, ym = 0.0, yp = 0.0, zm = 0.0, zp = 0.0;
+            const int fx = k * g.ny + j, fy = k * g.nx + i, fz = j * g.nx + i;
+            if (dx && i == 0 && g.face[0]) xm = 2.0 * g.face[0][fx];
+            if (dx && i == g.nx - 1 && g.face[1]) xp = 2.0 * g.face[1][fx];
+            if (dy && j == 0 && g.face[2]) ym = 2.0 * g.face[2][fy];
+            if (dy && j == g.ny - 1 && g.face[3]) yp = 2.0 * g.face[3][fy];
+            if (dz && k == 0 && g.face[4]) zm = 2.0 * g.face[4][fz];
+            if (dz && k == g.nz - 1 && g.face[5]) zp = 2.0 * g.face[5][fz];
+            double r;
+            if (UNIFORM) {
+                const double s6 = ((xm + xp) + (ym + yp)) + (zm + zp);
+                r = fma(-g.ihx2, fma(-6.0, 0.0, s6), rhs[idx]);
+            } else {
+                r = rhs[idx] - lap7(0.0, xm, xp, ym, yp, zm, zp, g.ihx2, g.ihy2, g.ihz2);
+            }
+            emit(idx, r);
+        };
+        const bool wall_xy = FACES && ((dx && (i == 0 || i == g.nx - 1)) || (dy && (j == 0 || j == g.ny - 1)));
+        if (wall_xy) {
+            for (int k = k0; k < k1; ++k) wall_cell(k);
+        } else {
+            // the planes next to a z wall with face data take the face terms
+            const bool zlo = FACES && dz && k0 == 0, zhi = FACES && dz && k1 == g.nz;
+            const int a = zlo ? 1 : k0, b = zhi ? g.nz - 1 : k1;
+            if (zlo) wall_cell(0);
+            int idx = a * plane + j * g.nx + i;
+            for (int k = a; k < b; ++k, idx += plane) emit(idx, rhs[idx]);
+            if (zhi) wall_cell(g.nz - 1);
+        }
+    }
+    const int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+    block_reduce_write<A>(sq, mx, A(0), partials, bid);
+}
+
 // ---------------------------------------------------------------------------
 // Residual fused with the 8-child restriction (Eq. restriction_example_3D).
 // A 32 x 8 block streams fine planes along z (2.5D, z-neighbours in
@@ -778,6 +843,22 @@ cudaError_t launch_stage(const LevelGeom& g, int order, bool first, const StageC
     return cudaGetLastError();
 }
 
+template <typename TO>
+cudaError_t launch_residual_zero(const LevelGeom& g, const double* rhs, TO* r_out, Partial* partials,
+                                 int* nblocks_out, cudaStream_t st, double* r_full) {
+    const int kc = kchunk_for(g, BX, BY);                        // the blocks of launch_residual
+    dim3 block(BX, BY, 1);
+    dim3 grid((g.nx + BX - 1) / BX, (g.ny + BY - 1) / BY, (g.nz + kc - 1) / kc);
+    const bool uniform = g.ihx2 == g.ihy2 && g.ihy2 == g.ihz2;
+    const bool faces = has_faces(g);
+    if (uniform && faces) k_residual_zero<TO, true, true><<<grid, block, 0, st>>>(g, rhs, r_out, r_full, partials, kc);
+    else if (uniform) k_residual_zero<TO, true, false><<<grid, block, 0, st>>>(g, rhs, r_out, r_full, partials, kc);
+    else if (faces) k_residual_zero<TO, false, true><<<grid, block, 0, st>>>(g, rhs, r_out, r_full, partials, kc);
+    else k_residual_zero<TO, false, false><<<grid, block, 0, st>>>(g, rhs, r_out, r_full, partials, kc);
+    if (nblocks_out) *nblocks_out = (int)(grid.x * grid.y * grid.z);
+    return cudaGetLastError();
+}
+
 template <typename TI, typename TO>
 cudaError_t launch_residual(const LevelGeom& g, const TI* u, const TI* rhs, TO* r_out,
                             Partial* partials, int* nblocks_out, cudaStream_t st, TI* r_full) {
@@ -912,6 +993,10 @@ template cudaError_t launch_stage<float>(const LevelGeom&, int, bool, const Stag
 template cudaError_t launch_stage<double>(const LevelGeom&, int, bool, const StageCoef&, const double*,
                                           const double*, const double*, const double*,
                                           const double*, double*, double*, cudaStream_t);
+template cudaError_t launch_residual_zero<double>(const LevelGeom&, const double*, double*, Partial*, int*,
+                                                  cudaStream_t, double*);
+template cudaError_t launch_residual_zero<float>(const LevelGeom&, const double*, float*, Partial*, int*,
+                                                 cudaStream_t, double*);
 template cudaError_t launch_residual<double, double>(const LevelGeom&, const double*, const double*,
                                                      double*, Partial*, int*, cudaStream_t, double*);
 template cudaError_t launch_residual<double, float>(const LevelGeom&, const double*, const double*,

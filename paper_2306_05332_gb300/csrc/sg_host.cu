@@ -185,7 +185,6 @@ struct sg_grid {
     bool have_faces = false;
     double* lam = nullptr;          // adjoint solution
     double* w = nullptr;            // adjoint source
-    double* scratch64 = nullptr;    // FP64 zero field for r0 with a warm start (mixed)
     double* r64 = nullptr;          // FP64 residual f - A phi carried by recurrence (mixed)
     Partial* partials = nullptr;
     int partial_cap = 0;
@@ -567,6 +566,22 @@ sg_status level0_residual(sg_grid* g, const double* phi, const double* f, bool f
     return SG_OK;
 }
 
+// level0_residual for phi = 0 (no read of phi, no FP64 stencil).
+sg_status level0_residual_zero(sg_grid* g, const double* f, bool faces) {
+    int nb = 0;
+    const LevelGeom G = geom(g, 0, faces);
+    {
+    ProfScope ps(g, K_RES0, double(g->lv[0].n) * (g->precision == SG_MIXED ? 20.0 : 8.0));
+    if (g->precision == SG_MIXED)
+        SG_CK(launch_residual_zero<float>(G, f, (float*)g->lv[0].rhs, g->partials, &nb, g->st, g->r64));
+    else
+        SG_CK(launch_residual_zero<double>(G, f, (double*)nullptr, g->partials, &nb, g->st));
+    }
+    SG_CK(launch_finalize(g->partials, nb, g->red, g->st));
+    g->launches += 2;
+    return SG_OK;
+}
+
 // Everything one cycle enqueues after the first residual: V-cycle, update,
 // residual + norm, and the copies of the norm / coarse count to pinned memory.
 sg_status cycle_body(sg_grid* g, int L, double* phi, const double* f, bool faces) {
@@ -700,19 +715,13 @@ sg_status solve_begin(sg_grid* g, SolveState& S, double tol, int L, double* phi,
     SG_CK(cudaEventRecord(g->ev0, g->st));
     if (!have_guess) {
         SG_CK(cudaMemsetAsync(phi, 0, L0.n * sizeof(double), g->st));
+        SG_TRY(level0_residual_zero(g, f, faces));
     } else {
-        double* zero = nullptr;
-        if (g->precision == SG_FP64) {
-            zero = (double*)L0.t[0];
-        } else {
-            if (!g->scratch64) SG_CK(cudaMalloc(&g->scratch64, L0.n * sizeof(double)));
-            zero = g->scratch64;
-        }
-        SG_CK(cudaMemsetAsync(zero, 0, L0.n * sizeof(double), g->st));
-        SG_TRY(level0_residual(g, zero, f, faces));
+        // r0 = ||L 0 - f|| for the relative stopping test, then the guess's residual
+        SG_TRY(level0_residual_zero(g, f, faces));
         SG_CK(cudaMemcpyAsync(g->host_red + 2, g->red, sizeof(Reduced), cudaMemcpyDeviceToHost, g->st));
+        SG_TRY(level0_residual(g, phi, f, faces));
     }
-    SG_TRY(level0_residual(g, phi, f, faces));
     SG_CK(cudaMemcpyAsync(g->host_red, g->red, sizeof(Reduced), cudaMemcpyDeviceToHost, g->st));
     SG_CK(cudaStreamSynchronize(g->st));
     prof_sync_point(g, false);
@@ -870,7 +879,6 @@ void free_grid(sg_grid* g) {
     for (int i = 0; i < 6; ++i) cudaFree(g->faces[i]);
     cudaFree(g->lam);
     cudaFree(g->w);
-    cudaFree(g->scratch64);
     cudaFree(g->r64);
     cudaFree(g->partials);
     cudaFree(g->red);

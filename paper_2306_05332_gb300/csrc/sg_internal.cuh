@@ -77,6 +77,10 @@ cudaError_t launch_stage(const LevelGeom& g, int order, bool first, const StageC
 template <typename TI, typename TO>
 cudaError_t launch_residual(const LevelGeom& g, const TI* u, const TI* rhs, TO* r_out,
                             Partial* partials, int* nblocks_out, cudaStream_t st, TI* r_full = nullptr);
+// The same for u = 0 (FP64 rhs): r = rhs - L 0, the face terms only.
+template <typename TO>
+cudaError_t launch_residual_zero(const LevelGeom& g, const double* rhs, TO* r_out, Partial* partials,
+                                 int* nblocks_out, cudaStream_t st, double* r_full = nullptr);
 
 // Fused residual + 8-cell restriction (+ norm partials, + coarse sum partials).
 template <typename T>

@@ -242,7 +242,8 @@ def test_kernel_profile_counts_every_class():
     assert st["residual_l0"]["launches"] == 2
     assert st["update_residual"]["launches"] == info["cycles"]
     assert st["residual_restrict"]["launches"] == 3 * info["cycles"]
-    assert st["residual_l0"]["bytes"] == 28.0 * 64 ** 3 * 2
+    # the start (phi = 0: f and the face terms, 20 B/cell) and the confirmation (28 B/cell)
+    assert st["residual_l0"]["bytes"] == (20.0 + 28.0) * 64 ** 3
     assert st["update_residual"]["bytes"] == 40.0 * 64 ** 3 * info["cycles"]
 
 
