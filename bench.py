@@ -185,14 +185,18 @@ def hbm_peak():
         return FALLBACK_HBM_GBS, "fallback"
 
 
+# Source files of the kernel whose DRAM bytes `roofline.traffic` reports (the
+# fused level-0 super-step) and the header it includes.
+TRAFFIC_SOURCES = ("kernels_superstep.cu", "sg_internal.cuh")
+
+
 def kernel_source_hash():
-    """Hash of the device-code sources (kernels_*.cu and the shared header):
-    DRAM counters taken on other kernel code are not reported."""
+    """Hash of the dominant kernel's sources: DRAM counters taken on other
+    code of that kernel are not reported."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2306_05332_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        if (f.startswith("kernels_") and f.endswith(".cu")) or f.endswith(".cuh"):
-            h.update(open(os.path.join(csrc, f), "rb").read())
+    for f in TRAFFIC_SOURCES:
+        h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
 
 

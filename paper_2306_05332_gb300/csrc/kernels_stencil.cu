@@ -22,6 +22,15 @@ constexpr int BY = 8;
 template <typename T> struct Acc { using type = float; };
 template <> struct Acc<double> { using type = double; };
 
+// Norm arithmetic in the accumulator's own precision (FP32 accumulators must
+// not go through the double-precision functions).
+__device__ __forceinline__ float acc_fma(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double acc_fma(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float acc_max(float a, float b) { return fmaxf(a, b); }
+__device__ __forceinline__ double acc_max(double a, double b) { return fmax(a, b); }
+__device__ __forceinline__ float acc_abs(float a) { return fabsf(a); }
+__device__ __forceinline__ double acc_abs(double a) { return fabs(a); }
+
 // x and y neighbours of cell (i, j, k) with the ghost rules (Sec. 2.3).
 // FACES: the level carries Dirichlet data (finest level of an FP64 solve);
 // without it the wall ghost is -centre (Eq. error_ghost).  Grids have fewer
@@ -160,7 +169,7 @@ __device__ __forceinline__ void block_reduce_write(A sumsq, A maxabs, A sum, Par
     const int nthreads = blockDim.x * blockDim.y * blockDim.z;
     for (int o = 16; o > 0; o >>= 1) {
         sumsq += __shfl_down_sync(0xffffffffu, sumsq, o);
-        maxabs = fmax(maxabs, __shfl_down_sync(0xffffffffu, maxabs, o));
+        maxabs = acc_max(maxabs, __shfl_down_sync(0xffffffffu, maxabs, o));
         sum += __shfl_down_sync(0xffffffffu, sum, o);
     }
     const int warp = tid >> 5, lane = tid & 31;
@@ -173,7 +182,7 @@ __device__ __forceinline__ void block_reduce_write(A sumsq, A maxabs, A sum, Par
         sum = lane < nw ? s_sum[lane] : A(0);
         for (int o = 16; o > 0; o >>= 1) {
             sumsq += __shfl_down_sync(0xffffffffu, sumsq, o);
-            maxabs = fmax(maxabs, __shfl_down_sync(0xffffffffu, maxabs, o));
+            maxabs = acc_max(maxabs, __shfl_down_sync(0xffffffffu, maxabs, o));
             sum += __shfl_down_sync(0xffffffffu, sum, o);
         }
         if (lane == 0) {
@@ -223,8 +232,8 @@ k_residual(const LevelGeom g, const TI* __restrict__ u, const TI* __restrict__ r
             if (r_out) r_out[idx] = ro;
             if (r_full) r_full[idx] = r;
             const A ra = A(ro);
-            sq = fma(ra, ra, sq);
-            mx = fmax(mx, fabs(ra));
+            sq = acc_fma(ra, ra, sq);
+            mx = acc_max(mx, acc_abs(ra));
             zm = c;
             c = zp;
         }
@@ -258,8 +267,8 @@ k_residual_zero(const LevelGeom g, const double* __restrict__ rhs, TO* r_out, do
             if (r_out) r_out[idx] = ro;
             if (r_full) r_full[idx] = r;
             const A ra = A(ro);
-            sq = fma(ra, ra, sq);
-            mx = fmax(mx, fabs(ra));
+            sq = acc_fma(ra, ra, sq);
+            mx = acc_max(mx, acc_abs(ra));
         };
         // a cell next to a Dirichlet wall with face data: f minus the face terms
         auto wall_cell = [&](int k) {
@@ -337,7 +346,7 @@ k_residual_restrict(const LevelGeom g, const T* __restrict__ u, const T* __restr
             r = rhs[idx] - lap7(c, xm, xp, ym, yp, zm, zp, ihx2, ihy2, ihz2);
             const A ra = A(r);
             sq += ra * ra;
-            mx = fmax(mx, fabs(ra));
+            mx = acc_max(mx, acc_abs(ra));
             zm = c;
             c = zp;
         }
