@@ -28,7 +28,9 @@
 // Y1 into one field per stage:
 //   Y_j = mu_j Y_{j-1} + mu~_j tau L Y_{j-1} + W_j,
 //   W_j = nu_j Y_{j-2} + c0_j Y0 + gamma~_j Z0 - mu~_j tau f   (RKL1: c0 = gamma~ = 0)
-// and with Y0 = 0 every W_j is a multiple of f.
+// and with Y0 = 0 every W_j is a multiple of f.  So is Y1 = -mu~_1 tau f then:
+// the pipeline starts at stage 2, a stencil of f with that factor folded into
+// its coefficients, and runs s - 1 stencil stages on a halo of s - 1 cells.
 //
 // Ring depths are powers of two (a slot is a mask of the phase index), and the
 // phase loop is unrolled by three so that the z window rotates by register
@@ -88,43 +90,57 @@ __host__ __device__ __forceinline__ int map_axis(int v, int n, bool periodic, in
 
 template <int S, bool ZERO, int TYV>
 struct Lean {
+    // pipeline stages: with Y0 = 0 the first RKL stage is Y1 = mu~_1 tau (-f),
+    // so RKL stage 2 is a stencil of f itself and the pipeline runs stages
+    // 2 .. s (pipeline stage j computes RKL stage j + 1)
+    static constexpr int NS = ZERO ? S - 1 : S;
     static constexpr int TX = 32, TY = TYV, HX = 4;
     static constexpr int W = TX + 2 * HX;            // plane row (floats)
-    static constexpr int H = TY + 2 * S;             // plane rows
+    static constexpr int H = TY + 2 * NS;            // plane rows
     static constexpr int Q = W / 4;                  // strips per row
     static constexpr int P = W * H;                  // floats per plane
     static constexpr int HQ = H * Q;                 // strips per plane
     // planes store the even rows, then the odd rows, so that the first rows of
     // consecutive row pairs are contiguous (conflict-free quarter-warp accesses)
     __host__ __device__ static constexpr int rowoff(int r) { return (r & 1) * (H / 2) * W + (r >> 1) * W; }
-    // stage j covers rows [j, H - j) (an even count) and strips [qlo(j), qhi(j));
-    // one item = the strips of rows r and r + 1 at one q
-    __host__ __device__ static constexpr int qlo(int j) { return (HX - (S - j)) / 4; }
-    __host__ __device__ static constexpr int qhi(int j) { return (HX + TX + (S - j) + 3) / 4; }
+    // pipeline stage j covers rows [j, H - j) (an even count) and strips
+    // [qlo(j), qhi(j)); one item = the strips of rows r and r + 1 at one q
+    __host__ __device__ static constexpr int qlo(int j) { return (HX - (NS - j)) / 4; }
+    __host__ __device__ static constexpr int qhi(int j) { return (HX + TX + (NS - j) + 3) / 4; }
     __host__ __device__ static constexpr int nq(int j) { return qhi(j) - qlo(j); }
-    __host__ __device__ static constexpr int items(int j) { return nq(j) * ((H - 2 * j) / 2); }
+    __host__ __device__ static constexpr int items(int j) { return j > NS ? 0 : nq(j) * ((H - 2 * j) / 2); }
     __host__ __device__ static constexpr int warps(int j) { return (items(j) + 31) / 32; }
-    static constexpr int T2 = 32 * warps(1);         // first thread of stage 2
-    static constexpr int T3 = T2 + 32 * warps(2);    // first thread of stage 3 (or end)
-    static constexpr int TS = S == 2 ? T3 : T3 + 32 * warps(3);   // threads with stage work
+    static constexpr int T2 = 32 * warps(1);         // first thread of pipeline stage 2 (or end)
+    static constexpr int T3 = T2 + 32 * warps(2);    // first thread of pipeline stage 3 (or end)
+    static constexpr int TS = T3 + 32 * warps(3);    // threads with stage work
     static constexpr int TL = 32 * ((HQ + 31) / 32); // threads [0, HQ) stage one strip of Y0 and of f
     static constexpr int NT = TS > TL ? TS : TL;
+    // Registers per thread that let `ctas` CTAs share an SM: the register file
+    // is split over four scheduler partitions of 16384 registers, a warp sits
+    // on one partition and holds a multiple of 8 registers per thread.
+    __host__ __device__ static constexpr int reg_cap(int ctas) {
+        return (16384 / ((((ctas * NT / 32) + 3) / 4) * 32)) / 8 * 8;
+    }
+    // CTAs per SM the registers are budgeted for: two; three for the lighter
+    // Y0 = 0 variant where that leaves at least 88 registers per thread
+    static constexpr int CTAS = (ZERO && reg_cap(3) >= 88) ? 3 : 2;
     // ring depths (planes, powers of two)
     static constexpr int RY0 = ZERO ? 0 : 4;         // Y0: p, p + 1 read, p + 2 in flight
-    static constexpr int RF = ZERO ? 8 : 4;          // f (Y0 = 0: read by every stage, lag up to 2s - 1)
-    static constexpr int RY = 4;                     // Y_j, j < s
+    static constexpr int RF = ZERO ? 8 : 4;          // f (Y0 = 0: read by every stage, lag up to 2 NS - 1)
+    static constexpr int RY = 4;                     // Y_j, j < NS
     static constexpr int RW2 = ZERO ? 0 : 4;         // W_2: written at lag 1, read at lag 3
     static constexpr int RW3 = (ZERO || S < 3) ? 0 : 8;   // W_3: written at lag 1, read at lag 5
     static constexpr int OY0 = 0;
     static constexpr int OF = OY0 + RY0 * P;
-    static constexpr int OY = OF + RF * P;           // ring of Y_j at OY + (j - 1) RY P
-    static constexpr int OW2 = OY + (S - 1) * RY * P;
+    static constexpr int OY = OF + RF * P;           // ring of pipeline stage j at OY + (j - 1) RY P
+    static constexpr int OW2 = OY + (NS - 1) * RY * P;
     static constexpr int OW3 = OW2 + RW2 * P;
     static constexpr int NFLOATS = OW3 + RW3 * P;
     static constexpr size_t BYTES = size_t(NFLOATS) * sizeof(float);
     static_assert(S == 2 || S == 3, "lean super-step covers s = 2, 3");
-    static_assert(HX >= S - 1 && HX % 4 == 0, "x halo");
+    static_assert(HX >= NS - 1 && HX % 4 == 0, "x halo");
     static_assert(TY % 2 == 0 && H % 2 == 0, "row pairs");
+    static_assert(!ZERO || RF >= 2 * NS + 2, "f ring spans the staged planes and the oldest read");
     static_assert(BYTES <= 227u * 1024u, "rings exceed the shared memory of one CTA");
     static_assert(NT <= 1024, "block size");
 };
@@ -135,8 +151,10 @@ struct LeanCoef {
     float ihx2, ihy2, ihz2, m2s;        // stage 1: Lf = ihx2 sx + ihy2 sy + ihz2 sz + m2s c - f
     float m1t;                          //          Y1 = c + m1t Lf
     float k2y0, k2z, k2f;               //          W2 = k2y0 c + k2z Lf + k2f f
-    float k3y1, k3y0, k3z, k3f;         //          W3 = k3y1 Y1 + k3y0 c + k3z Lf + k3f f
+    float k3c, k3l, k3f;                //          W3 = nu_3 Y1 + c0_3 c + gamma~_3 tau Lf - mu~_3 tau f
+                                        //             = k3c c + k3l Lf + k3f f  (Y1 = c + m1t Lf)
     float kz[4];                        // Y0 = 0: Y1 = kz[1] f, W_j = kz[j] f
+    float zx, zy, zz, zb;               // Y0 = 0: Y2 = zx sx(f) + zy sy(f) + zz sz(f) + zb f
 };
 
 // Source of one 4-cell strip of a staged plane.
@@ -257,7 +275,7 @@ __device__ __forceinline__ void first_strip(const LeanCoef& k, float4 c, float4 
         const float lf = fmaf(k.ihx2, sx[e], fmaf(k.ihy2, sy[e], fmaf(k.ihz2, sz[e], fmaf(k.m2s, cc[e], -ff[e]))));
         a[e] = fmaf(k.m1t, lf, cc[e]);
         b[e] = fmaf(k.k2y0, cc[e], fmaf(k.k2z, lf, k.k2f * ff[e]));
-        if (S == 3) e3[e] = fmaf(k.k3y1, a[e], fmaf(k.k3y0, cc[e], fmaf(k.k3z, lf, k.k3f * ff[e])));
+        if (S == 3) e3[e] = fmaf(k.k3c, cc[e], fmaf(k.k3l, lf, k.k3f * ff[e]));
     }
     y1 = make_float4(a[0], a[1], a[2], a[3]);
     w2 = make_float4(b[0], b[1], b[2], b[3]);
@@ -278,12 +296,12 @@ __device__ __forceinline__ void store_out(float* dst, float4 v, bool vec, int n)
 }
 
 template <int S, int ORDER, bool ZERO, int TY>
-__global__ void __launch_bounds__(Lean<S, ZERO, TY>::NT, 2)
+__global__ void __launch_bounds__(Lean<S, ZERO, TY>::NT, Lean<S, ZERO, TY>::CTAS)
 k_superstep_lean(const __grid_constant__ LevelGeom g, const __grid_constant__ LeanCoef k,
                  const float* __restrict__ y0g, const float* __restrict__ fg, float* __restrict__ outg,
                  int tiles_x, int kchunk, int vec_ok) {
     using C = Lean<S, ZERO, TY>;
-    constexpr int W = C::W, P = C::P, Q = C::Q, HQ = C::HQ;
+    constexpr int W = C::W, P = C::P, Q = C::Q, HQ = C::HQ, NS = C::NS;
     extern __shared__ __align__(16) float sm[];
     const int tid = threadIdx.x, lane = tid & 31;
     const int nx = g.nx, ny = g.ny, nz = g.nz, plane = nx * ny;
@@ -292,13 +310,14 @@ k_superstep_lean(const __grid_constant__ LevelGeom g, const __grid_constant__ Le
     // ---- one segment of the stream: tile (bx, by), planes [kz0, kz1)
     auto segment = [&](int bx, int by, int kz0, int kz1) {
     const int X0 = bx * C::TX - C::HX;                  // global x of local column 0
-    const int Yt = by * C::TY - S;                      // global y of local row 0
+    const int Yt = by * C::TY - NS;                     // global y of local row 0
 
-    // ---- this thread's stage and row pair (fixed for the whole stream; J = 0: loads only)
+    // ---- this thread's pipeline stage and row pair (fixed for the whole
+    // stream; J = 0: loads only)
     int J, item;
     if (tid < C::T2) { J = 1; item = tid; }
-    else if (tid < C::T3) { J = 2; item = tid - C::T2; }
-    else if (S == 3 && tid < C::TS) { J = 3; item = tid - C::T3; }
+    else if (NS >= 2 && tid < C::T3) { J = 2; item = tid - C::T2; }
+    else if (NS == 3 && tid < C::TS) { J = 3; item = tid - C::T3; }
     else { J = 0; item = 0; }
     const int Jr = J > 0 ? J : 1;
     const int nqj = Jr == 1 ? C::nq(1) : (Jr == 2 ? C::nq(2) : C::nq(3));
@@ -312,25 +331,40 @@ k_superstep_lean(const __grid_constant__ LevelGeom g, const __grid_constant__ Le
     const bool fix_l = (it % nqj == 0) || lane == 0;
     const bool fix_r = (it % nqj == nqj - 1) || lane == 31 || !active;
     const int L = 2 * J - 1;                            // lag: stage J works on plane t - L
-    // stage J >= 2: coefficients, input ring, combined-field ring, output ring
+    // stencil stages (every pipeline stage with Y0 = 0, J >= 2 otherwise):
+    // coefficients, input ring, combined-field ring, output ring
     float2 ax = dup2(0.f), ay = ax, az = ax, bb = ax;
     float kw = 0.f;
     const float* in_b = sm + o;
     const float* w_b = sm + o;
     float* out_b = sm + o;
     int w_mask = 3;
-    if (J >= 2) {
+    if (ZERO && J == 1) {
+        // RKL stage 2 from f: Y1 = kz[1] f folded into the coefficients, no W
+        ax = dup2(k.zx);
+        ay = dup2(k.zy);
+        az = dup2(k.zz);
+        bb = dup2(k.zb);
+        in_b = sm + C::OF + o;
+        out_b = sm + C::OY + o;
+    } else if (ZERO && J == 2) {
+        // RKL stage 3 from Y2: W_3 = kz[3] f
+        ax = dup2(k.ax[3]);
+        ay = dup2(k.ay[3]);
+        az = dup2(k.az[3]);
+        bb = dup2(k.b[3]);
+        kw = k.kz[3];
+        in_b = sm + C::OY + o;
+        w_b = sm + C::OF + o;
+        w_mask = C::RF - 1;
+    } else if (J >= 2) {
         ax = dup2(J == 2 ? k.ax[2] : k.ax[3]);
         ay = dup2(J == 2 ? k.ay[2] : k.ay[3]);
         az = dup2(J == 2 ? k.az[2] : k.az[3]);
         bb = dup2(J == 2 ? k.b[2] : k.b[3]);
-        kw = J == 2 ? k.kz[2] : k.kz[3];
         in_b = sm + C::OY + (J - 2) * C::RY * P + o;
         out_b = sm + C::OY + (J - 1) * C::RY * P + o;
-        if (ZERO) {
-            w_b = sm + C::OF + o;
-            w_mask = C::RF - 1;
-        } else if (J == 2) {
+        if (J == 2) {
             w_b = sm + C::OW2 + o;
             w_mask = C::RW2 - 1;
         } else {
@@ -338,10 +372,10 @@ k_superstep_lean(const __grid_constant__ LevelGeom g, const __grid_constant__ Le
             w_mask = (C::RW3 > 0 ? C::RW3 : 1) - 1;
         }
     }
-    // output cells of stage s (rows row, row + 1)
+    // output cells of the last stage (rows row, row + 1)
     int st0 = -1, st1 = -1, st_n = 0;
     bool st_vec = false;
-    if (J == S && active) {
+    if (J == NS && active) {
         const int gy = Yt + row, gx0 = X0 + 4 * q;
         if (gx0 < nx) {
             if (gy < ny) st0 = gy * nx + gx0;
@@ -371,11 +405,11 @@ k_superstep_lean(const __grid_constant__ LevelGeom g, const __grid_constant__ Le
         }
     }
 
-    const int t_first = kz0 - S + 2;                    // stage 1 computes plane t - 1
-    const int nph = (kz1 - kz0) + 3 * S - 3;            // phases
-    const int nload = kz1 + S - t_first;                // planes t_first + v, v < nload, are staged
-    const int u_store0 = kz0 - t_first + 2 * S - 1;     // phases whose stage-s plane lies in [kz0, kz1)
-    const int u_store1 = kz1 - t_first + 2 * S - 1;
+    const int t_first = kz0 - NS + 2;                   // stage 1 computes plane t - 1
+    const int nph = (kz1 - kz0) + 3 * NS - 3;           // phases
+    const int nload = kz1 + NS - t_first;               // planes t_first + v, v < nload, are staged
+    const int u_store0 = kz0 - t_first + 2 * NS - 1;    // phases whose last-stage plane lies in [kz0, kz1)
+    const int u_store1 = kz1 - t_first + 2 * NS - 1;
     // plane t_first + v of a ring with R slots sits in slot (v & (R - 1))
     auto stage_plane = [&](int v, int* zsign) {
         const int src = map_axis(t_first + v, nz, pz, zsign) * plane;
@@ -408,11 +442,13 @@ k_superstep_lean(const __grid_constant__ LevelGeom g, const __grid_constant__ Le
 
     // z window of the thread's two strips: planes p - 1 (dn) and p (cen)
     float4 dn0 = make_float4(0.f, 0.f, 0.f, 0.f), cen0 = dn0, dn1 = dn0, cen1 = dn0;
-    if (!ZERO && J == 1) {
-        dn0 = ld4(sm + C::OY0 + (-2 & 3) * P + o);
-        dn1 = ld4(sm + C::OY0 + (-2 & 3) * P + o + d1);
-        cen0 = ld4(sm + C::OY0 + (-1 & 3) * P + o);
-        cen1 = ld4(sm + C::OY0 + (-1 & 3) * P + o + d1);
+    if (J == 1) {            // stage 1 reads the staged planes -2 and -1 (Y0, or f when Y0 = 0)
+        const float* base = ZERO ? sm + C::OF + o : sm + C::OY0 + o;
+        const int mask = ZERO ? C::RF - 1 : 3;
+        dn0 = ld4(base + (-2 & mask) * P);
+        dn1 = ld4(base + (-2 & mask) * P + d1);
+        cen0 = ld4(base + (-1 & mask) * P);
+        cen1 = ld4(base + (-1 & mask) * P + d1);
     }
 
     // One phase.  (dn, cen) hold the thread's strips of planes p - 1 and p of its
@@ -428,54 +464,44 @@ k_superstep_lean(const __grid_constant__ LevelGeom g, const __grid_constant__ Le
             prefetch_l2(pf_src + map_axis(t_first + u + kPrefetch, nz, pz, &zsg) * plane + pf);
         }
 
-        if (J == 1) {
+        if (!ZERO && J == 1) {
             // ---- stage 1 on plane t - 1
             const int sp = (u - 1) & 3;
-            if (ZERO) {
-                const float* fp = sm + C::OF + ((u - 1) & (C::RF - 1)) * P + o;
-                const float kk = k.kz[1];
-                if (active) {
-                    st4(sm + C::OY + sp * P + o, scale4(kk, ld4(fp)));
-                    st4(sm + C::OY + sp * P + o + d1, scale4(kk, ld4(fp + d1)));
-                }
-            } else {
-                const float* yc = sm + C::OY0 + sp * P + o;
-                const float* yu = sm + C::OY0 + (u & 3) * P + o;
-                const float* fp = sm + C::OF + ((u - 1) & 3) * P + o;
-                nxt0 = ld4(yu);
-                nxt1 = ld4(yu + d1);
-                const float4 up0 = nxt0, up1 = nxt1;
-                const float4 nn = ld4(yc + d1 - W), ss = ld4(yc + W);
-                const float4 f0 = ld4(fp), f1 = ld4(fp + d1);
-                float l0 = __shfl_up_sync(0xffffffffu, cen0.w, 1);
-                float r0 = __shfl_down_sync(0xffffffffu, cen0.x, 1);
-                float l1 = __shfl_up_sync(0xffffffffu, cen1.w, 1);
-                float r1 = __shfl_down_sync(0xffffffffu, cen1.x, 1);
-                if (fix_l) { l0 = yc[-1]; l1 = yc[d1 - 1]; }
-                if (fix_r) { r0 = yc[4]; r1 = yc[d1 + 4]; }
-                float4 y1a, w2a, w3a, y1b, w2b, w3b;
-                first_strip<S>(k, cen0, nn, cen1, dn0, up0, l0, r0, f0, y1a, w2a, w3a);
-                first_strip<S>(k, cen1, cen0, ss, dn1, up1, l1, r1, f1, y1b, w2b, w3b);
-                if (active) {
-                    float* y1p = sm + C::OY + sp * P + o;
-                    float* w2p = sm + C::OW2 + sp * P + o;
-                    st4(y1p, y1a);
-                    st4(y1p + d1, y1b);
-                    st4(w2p, w2a);
-                    st4(w2p + d1, w2b);
-                    if (S == 3) {
-                        float* w3p = sm + C::OW3 + ((u - 1) & 7) * P + o;
-                        st4(w3p, w3a);
-                        st4(w3p + d1, w3b);
-                    }
+            const float* yc = sm + C::OY0 + sp * P + o;
+            const float* yu = sm + C::OY0 + (u & 3) * P + o;
+            const float* fp = sm + C::OF + ((u - 1) & 3) * P + o;
+            nxt0 = ld4(yu);
+            nxt1 = ld4(yu + d1);
+            const float4 up0 = nxt0, up1 = nxt1;
+            const float4 nn = ld4(yc + d1 - W), ss = ld4(yc + W);
+            const float4 f0 = ld4(fp), f1 = ld4(fp + d1);
+            float l0 = __shfl_up_sync(0xffffffffu, cen0.w, 1);
+            float r0 = __shfl_down_sync(0xffffffffu, cen0.x, 1);
+            float l1 = __shfl_up_sync(0xffffffffu, cen1.w, 1);
+            float r1 = __shfl_down_sync(0xffffffffu, cen1.x, 1);
+            if (fix_l) { l0 = yc[-1]; l1 = yc[d1 - 1]; }
+            if (fix_r) { r0 = yc[4]; r1 = yc[d1 + 4]; }
+            float4 y1a, w2a, w3a, y1b, w2b, w3b;
+            first_strip<S>(k, cen0, nn, cen1, dn0, up0, l0, r0, f0, y1a, w2a, w3a);
+            first_strip<S>(k, cen1, cen0, ss, dn1, up1, l1, r1, f1, y1b, w2b, w3b);
+            if (active) {
+                float* y1p = sm + C::OY + sp * P + o;
+                float* w2p = sm + C::OW2 + sp * P + o;
+                st4(y1p, y1a);
+                st4(y1p + d1, y1b);
+                st4(w2p, w2a);
+                st4(w2p + d1, w2b);
+                if (S == 3) {
+                    float* w3p = sm + C::OW3 + ((u - 1) & 7) * P + o;
+                    st4(w3p, w3a);
+                    st4(w3p + d1, w3b);
                 }
             }
-        } else if (J >= 2) {
-            // ---- stage J on plane p = t - L
-            const int sp = (u - L) & 3;
-            const float* yc = in_b + sp * P;
-            const float* yu = in_b + ((u - L + 1) & 3) * P;
-            const float* wp = w_b + ((u - L) & w_mask) * P;
+        } else if (J >= 1) {
+            // ---- stencil stage J on plane p = t - L
+            const int in_mask = (ZERO && J == 1) ? C::RF - 1 : 3;
+            const float* yc = in_b + ((u - L) & in_mask) * P;
+            const float* yu = in_b + ((u - L + 1) & in_mask) * P;
             nxt0 = ld4(yu);
             nxt1 = ld4(yu + d1);
             const float4 up0 = nxt0, up1 = nxt1;
@@ -486,17 +512,23 @@ k_superstep_lean(const __grid_constant__ LevelGeom g, const __grid_constant__ Le
             float r1 = __shfl_down_sync(0xffffffffu, cen1.x, 1);
             if (fix_l) { l0 = yc[-1]; l1 = yc[d1 - 1]; }
             if (fix_r) { r0 = yc[4]; r1 = yc[d1 + 4]; }
-            float4 wa = ld4(wp), wb = ld4(wp + d1);
-            if (ZERO) {
-                wa = scale4(kw, wa);
-                wb = scale4(kw, wb);
+            float4 wa = make_float4(0.f, 0.f, 0.f, 0.f), wb = wa;
+            if (!ZERO || J >= 2) {
+                const float* wp = w_b + ((u - L) & w_mask) * P;
+                wa = ld4(wp);
+                wb = ld4(wp + d1);
+                if (ZERO) {
+                    wa = scale4(kw, wa);
+                    wb = scale4(kw, wb);
+                }
             }
             const float4 va = later_strip(cen0, nn, cen1, dn0, up0, l0, r0, ax, ay, az, bb, wa);
             const float4 vb = later_strip(cen1, cen0, ss, dn1, up1, l1, r1, ax, ay, az, bb, wb);
-            if (J < S) {
+            if (J < NS) {
                 if (active) {
-                    st4(out_b + sp * P, va);
-                    st4(out_b + sp * P + d1, vb);
+                    const int op = ((u - L) & 3) * P;
+                    st4(out_b + op, va);
+                    st4(out_b + op + d1, vb);
                 }
             } else if (u >= u_store0 && u < u_store1) {
                 float* ob = outg + (t_first + u - L) * plane;
@@ -560,15 +592,24 @@ LeanCoef make_lean_coef(const LevelGeom& g, int order, int s, const FusedCoef& c
     k.k2f = float(-double(cf.mut_tau[2]));
     if (s >= 3) {
         const double c0_3 = order == 2 ? cf.c0[3] : 0.0, gt_3 = order == 2 ? cf.gt[3] : 0.0;
-        k.k3y1 = cf.nu[3];
-        k.k3y0 = float(c0_3);
-        k.k3z = float(gt_3 * tau);
+        const double nu3 = cf.nu[3];
+        k.k3c = float(nu3 + c0_3);
+        k.k3l = float(nu3 * double(cf.mut1) * tau + gt_3 * tau);
         k.k3f = float(-double(cf.mut_tau[3]));
     }
     // Y0 = 0: Z0 = -tau f, Y1 = -mu~_1 tau f
     const double y1 = -double(cf.mut1) * tau;
     k.kz[1] = float(y1);
-    k.kz[2] = float(-gt_2 * tau - double(cf.mut_tau[2]));
+    const double kz2 = -gt_2 * tau - double(cf.mut_tau[2]);
+    k.kz[2] = float(kz2);
+    // Y2 = mu~_2 tau (hx sx + hy sy + hz sz) Y1 + b_2 Y1 + kz2 f with Y1 = y1 f
+    {
+        const double mt = cf.mut_tau[2];
+        k.zx = float(mt * hx * y1);
+        k.zy = float(mt * hy * y1);
+        k.zz = float(mt * hz * y1);
+        k.zb = float((double(cf.mu[2]) - 2.0 * mt * (hx + hy + hz)) * y1 + kz2);
+    }
     if (s >= 3) {
         const double gt_3 = order == 2 ? cf.gt[3] : 0.0;
         k.kz[3] = float(double(cf.nu[3]) * y1 - gt_3 * tau - double(cf.mut_tau[3]));
@@ -591,13 +632,13 @@ LeanPlan lean_plan(const LevelGeom& g) {
     const long long gx = (g.nx + C::TX - 1) / C::TX, gy = (g.ny + C::TY - 1) / C::TY;
     const long long slots = (long long)g_lean_sms * LeanResident<S, ORDER, ZERO, TY>::per_sm;
     long long chunks = std::max(1LL, slots / (gx * gy));
-    chunks = std::min<long long>(chunks, std::max(1, g.nz / (4 * S)));
+    chunks = std::min<long long>(chunks, std::max(1, g.nz / (4 * C::NS)));
     p.tiles_x = gx;
     p.kchunk = (int)((g.nz + chunks - 1) / chunks);
     p.ncta = gx * gy * ((g.nz + p.kchunk - 1) / p.kchunk);
     const long long per_sm = (p.ncta + g_lean_sms - 1) / g_lean_sms;
-    const int items = C::items(1) + C::items(2) + (S == 3 ? C::items(3) : 0);
-    p.cost = double(per_sm) * double(p.kchunk + 3 * S - 3) * double(items);
+    const int items = C::items(1) + C::items(2) + C::items(3);
+    p.cost = double(per_sm) * double(p.kchunk + 3 * C::NS - 3) * double(items);
     return p;
 }
 
@@ -605,8 +646,7 @@ template <int S, int ORDER, bool ZERO, int TY>
 cudaError_t lean_launch(const LeanPlan& p, const LevelGeom& g, const LeanCoef& k, const float* y0, const float* f,
                         float* out, int vec_ok, cudaStream_t st) {
     using C = Lean<S, ZERO, TY>;
-    k_superstep_lean<S, ORDER, ZERO, TY><<<(unsigned)p.ncta, C::NT, C::BYTES, st>>>(g, k, y0, f, out, (int)p.tiles_x,
-                                                                                   p.kchunk, vec_ok);
+    k_superstep_lean<S, ORDER, ZERO, TY><<<(unsigned)p.ncta, C::NT, C::BYTES, st>>>(g, k, y0, f, out, (int)p.tiles_x, p.kchunk, vec_ok);
     return cudaGetLastError();
 }
 
