@@ -230,10 +230,11 @@ int sg_max_levels(const sg_grid* g);
  * the compulsory reads and writes of their input and output arrays, each cell
  * counted once, independent of caching.
  * ------------------------------------------------------------------------ */
-#define SG_KERNEL_CLASSES 8
+#define SG_KERNEL_CLASSES 9
 typedef struct sg_kernel_stat {
     char      name[24];       /* rkl_stage_l0, rkl_stage_coarse, residual_l0, residual_restrict,
-                                 prolong_correct, coarse_solve, update, reduce_misc */
+                                 prolong_correct, coarse_solve, update, reduce_misc,
+                                 bottom_levels (the two coarsest levels in one launch) */
     long long launches;
     double    ms;             /* summed event time of the launches */
     double    bytes;          /* summed algorithmic bytes */

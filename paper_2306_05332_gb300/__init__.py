@@ -71,7 +71,7 @@ class KernelStat(ctypes.Structure):
                 ("bytes", ctypes.c_double)]
 
 
-SG_KERNEL_CLASSES = 8
+SG_KERNEL_CLASSES = 9
 
 
 class TuneEntry(ctypes.Structure):

@@ -742,27 +742,51 @@ k_update_residual4(const LevelGeom g, double* __restrict__ phi, const float* __r
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kRedThreads) k_finalize(const Partial* __restrict__ p, int n,
                                                           Reduced* out) {
-    __shared__ double s_sq[kRedThreads], s_mx[kRedThreads], s_sum[kRedThreads];
+    // Fixed order (deterministic): thread t folds partials t, t + 256, ...
+    // four at a time so that their loads are in flight together, then the
+    // warps fold by shuffles and warp 0 folds the eight warp results.
+    __shared__ double s_sq[kRedThreads / 32], s_mx[kRedThreads / 32], s_sum[kRedThreads / 32];
     double sq = 0.0, mx = 0.0, sm = 0.0;
-    for (int t = threadIdx.x; t < n; t += kRedThreads) {
+    int t = threadIdx.x;
+    for (; t + 3 * kRedThreads < n; t += 4 * kRedThreads) {
+        Partial a[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) a[e] = p[t + e * kRedThreads];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            sq += a[e].sumsq;
+            mx = fmax(mx, a[e].maxabs);
+            sm += a[e].sum;
+        }
+    }
+    for (; t < n; t += kRedThreads) {
         sq += p[t].sumsq;
         mx = fmax(mx, p[t].maxabs);
         sm += p[t].sum;
     }
-    s_sq[threadIdx.x] = sq; s_mx[threadIdx.x] = mx; s_sum[threadIdx.x] = sm;
-    __syncthreads();
-    for (int w = kRedThreads / 2; w > 0; w >>= 1) {
-        if (threadIdx.x < w) {
-            s_sq[threadIdx.x] += s_sq[threadIdx.x + w];
-            s_mx[threadIdx.x] = fmax(s_mx[threadIdx.x], s_mx[threadIdx.x + w]);
-            s_sum[threadIdx.x] += s_sum[threadIdx.x + w];
-        }
-        __syncthreads();
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        sq += __shfl_down_sync(0xffffffffu, sq, o);
+        mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, o));
+        sm += __shfl_down_sync(0xffffffffu, sm, o);
     }
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) {
+        s_sq[w] = sq;
+        s_mx[w] = mx;
+        s_sum[w] = sm;
+    }
+    __syncthreads();
     if (threadIdx.x == 0) {
-        out->sumsq = s_sq[0];
-        out->maxabs = s_mx[0];
-        out->sum = s_sum[0];
+        double a = s_sq[0], b = s_mx[0], c = s_sum[0];
+        for (int k = 1; k < kRedThreads / 32; ++k) {
+            a += s_sq[k];
+            b = fmax(b, s_mx[k]);
+            c += s_sum[k];
+        }
+        out->sumsq = a;
+        out->maxabs = b;
+        out->sum = c;
         out->count = double(n);
     }
 }

@@ -156,10 +156,10 @@ int rule_levels(int nx, int ny, int nz) {
 }
 
 // Kernel classes for the optional per-kernel CUDA-event profile.
-enum KClass { K_STAGE0 = 0, K_STAGE_C, K_RES0, K_RESTRICT, K_PROLONG, K_COARSE, K_UPDATE, K_MISC, K_NCLASS };
+enum KClass { K_STAGE0 = 0, K_STAGE_C, K_RES0, K_RESTRICT, K_PROLONG, K_COARSE, K_UPDATE, K_MISC, K_BOTTOM, K_NCLASS };
 const char* const kClassName[K_NCLASS] = {"rkl_stage_l0", "rkl_stage_coarse", "residual_l0",
                                           "residual_restrict", "prolong_correct", "coarse_solve",
-                                          "update_residual", "reduce_misc"};
+                                          "update_residual", "reduce_misc", "bottom_levels"};
 
 struct ProfRec {
     int cls;
@@ -481,6 +481,66 @@ bool use_fused(const sg_grid* g, bool faces, int l) {
            g->lv[l].n >= kFusedMinCells;
 }
 
+// The two coarsest levels B = L - 2 >= 1 and C = L - 1 of the FP32 V-cycle
+// in one cluster launch (kernels_cluster.cu): the cluster size, or 0 where the
+// level-by-level kernels run them.
+int bottom_nc(const sg_grid* g, int L, int* threads, size_t* bytes) {
+    const int B = L - 2;
+    if (g->precision != SG_MIXED || !g->opt.fused || B < 1) return 0;
+    const Level& lb = g->lv[B];
+    return bottom_plan(lb.nx, lb.ny, lb.nz, g->opt.s_smooth, threads, bytes);
+}
+
+// e_B from f_B: B's pre-smoothing, the restriction to C, C's coarse solve, the
+// prolongation to B and B's post-smoothing, with the coefficients and the
+// schedule of the level-by-level path.
+sg_status bottom_levels(sg_grid* g, int B, const float* rhs, float* u, int nc, int threads, size_t bytes) {
+    const Level& lb = g->lv[B];
+    const Level& lc = g->lv[B + 1];
+    const LevelGeom gb = geom(g, B, false), gc = geom(g, B + 1, false);
+    const int order = g->opt.rkl_order, s = g->opt.s_smooth;
+    const Rkl r = make_rkl(order, s);
+    const double tau = g->opt.tau_frac * (2.0 / lambda_max(lb)) * r.tau_over_dtpar;
+    BottomParams p{};
+    p.nx = lb.nx;
+    p.ny = lb.ny;
+    p.nz = lb.nz;
+    for (int d = 0; d < 3; ++d) p.per[d] = gb.per[d];
+    p.hx = gb.ihx2f;
+    p.hy = gb.ihy2f;
+    p.hz = gb.ihz2f;
+    p.chx = gc.ihx2f;
+    p.chy = gc.ihy2f;
+    p.chz = gc.ihz2f;
+    p.order = order;
+    p.s = s;
+    p.n_pre = g->opt.n_pre;
+    p.n_post = g->opt.n_post;
+    p.tau = float(tau);
+    p.mut1 = float(r.mut[1]);
+    for (int j = 2; j <= s; ++j) {
+        p.mu[j] = float(r.mu[j]);
+        p.nu[j] = float(r.nu[j]);
+        p.mut_tau[j] = float(r.mut[j] * tau);
+        p.c0[j] = float(r.c0[j]);
+        p.gt[j] = float(r.gt[j]);
+    }
+    p.remove_mean = all_periodic(g) ? 1 : 0;
+    p.sched = g->d_sched;
+    p.max_ss = g->opt.coarse_max_ss;
+    p.tol = float(g->opt.coarse_tol);
+    p.tau_unit = float(coarse_c(g, B + 1) * 2.0 / lambda_max(lc));
+    p.rhs = rhs;
+    p.u_out = u;
+    p.ss_done = g->d_ss;
+    {
+        ProfScope ps(g, K_BOTTOM, 2.0 * lb.n * sizeof(float));
+        SG_CK(launch_bottom(p, nc, threads, bytes, g->st));
+    }
+    ++g->launches;
+    return SG_OK;
+}
+
 // One V-cycle (Sec. 2.1) with level-0 arrays u0 / rhs0 (faces on level 0 if
 // `faces`; zero0: u0 is known to be zero, as for the error equation of the
 // mixed-precision loop).  On return *u0_final points at the level-0 result: u0
@@ -514,8 +574,12 @@ sg_status vcycle(sg_grid* g, int L, W* u0, const W* rhs0, bool faces, bool zero0
         if (zero_start && count > 0) SG_CK(cudaMemsetAsync(cur[l], 0, g->lv[l].n * sizeof(W), g->st));
         return relax<W>(g, l, count, fc, cur[l], R(l));
     };
+    int bottom_threads = 0;
+    size_t bottom_bytes = 0;
+    const int bottom = std::is_same<W, float>::value ? bottom_nc(g, L, &bottom_threads, &bottom_bytes) : 0;
     SG_TRY(smooth(0, g->opt.n_pre, zero0, faces));                              // step 1
     for (int l = 1; l < L; ++l) {                                               // step 2
+        if (bottom && l == L - 1) break;        // restricted into C inside the cluster launch
         int nb = 0;
         {
             ProfScope ps(g, K_RESTRICT, (2.0 + 0.125) * g->lv[l - 1].n * sizeof(W));
@@ -529,10 +593,17 @@ sg_status vcycle(sg_grid* g, int L, W* u0, const W* rhs0, bool faces, bool zero0
             SG_CK(launch_subtract_mean<W>((W*)g->lv[l].rhs, g->lv[l].n, g->red + 1, g->st));
             g->launches += 2;
         }
+        if constexpr (std::is_same<W, float>::value) {
+            if (bottom && l == L - 2) {                                          // levels L - 2 and L - 1
+                SG_TRY(bottom_levels(g, l, R(l), cur[l], bottom, bottom_threads, bottom_bytes));
+                continue;
+            }
+        }
         if (l < L - 1) SG_TRY(smooth(l, g->opt.n_pre, true, false));            // 2c + 2d-i
         else SG_TRY(coarse_solve<W>(g, l, R(l), cur[l], g->d_ss));              // 2c + 2e
     }
     for (int l = L - 2; l >= 1; --l) {                                          // step 3
+        if (bottom && l == L - 2) continue;     // prolonged and post-smoothed in the cluster launch
         {
             ProfScope ps(g, K_PROLONG, (2.0 + 0.125) * g->lv[l].n * sizeof(W));
             SG_CK(launch_prolong_correct<W>(geom(g, l, false), cur[l + 1], cur[l], g->st));
@@ -736,6 +807,9 @@ sg_status solve_begin(sg_grid* g, SolveState& S, double tol, int L, double* phi,
         const Level& Lc = g->lv[L - 1];
         const int Nc = std::max(Lc.nx, std::max(Lc.ny, Lc.nz));
         SG_TRY(ensure_sched(g, accelerated_schedule(Nc, g->opt.coarse_max_ss)));
+        int bt = 0;
+        size_t bb = 0;
+        (void)bottom_nc(g, L, &bt, &bb);          // plan the cluster launch before any capture
     }
     S.limit = g->opt.fixed_cycles > 0 ? g->opt.fixed_cycles : g->opt.max_cycles;
     S.single_c = g->opt.single_tau_frac > 0 ? g->opt.single_tau_frac : cell_tau_frac(N0);
@@ -938,6 +1012,7 @@ sg_status sg_create_grid(int nx, int ny, int nz, const double lo[3], const doubl
     if (precision != SG_FP64 && precision != SG_MIXED) return fail(SG_ERR_ARG, "bad precision");
     SG_CK(coarse_configure());
     SG_CK(fused_configure());
+    SG_CK(bottom_configure());
     sg_grid* g = new sg_grid();
     for (int d = 0; d < 3; ++d) {
         g->n[d] = n[d];

@@ -149,4 +149,29 @@ cudaError_t launch_coarse_solve(const CoarseParams& p, cudaStream_t st);
 // Raise the dynamic shared-memory limit of the coarse kernels (once per process).
 cudaError_t coarse_configure();
 
+// ---- the two coarsest levels in one cluster launch (kernels_cluster.cu) ------
+constexpr int kBottomMaxS = 32;          // smoothing stages the coefficient table holds
+struct BottomParams {
+    int nx, ny, nz;                      // level B; level C = B + 1 has half of each
+    int per[3];                          // periodic flag per axis
+    float hx, hy, hz;                    // 1 / h^2 of level B
+    float chx, chy, chz;                 // 1 / h^2 of level C
+    int order, s, n_pre, n_post;         // smoothing of level B
+    float tau, mut1;                     // first stage: z = tau (L Y0 - f), Y1 = Y0 + mut1 z
+    float mu[kBottomMaxS + 1], nu[kBottomMaxS + 1], mut_tau[kBottomMaxS + 1];
+    float c0[kBottomMaxS + 1], gt[kBottomMaxS + 1];
+    int remove_mean;                     // every axis periodic: f_C -= mean(f_C)
+    const int* sched;                    // coarse solve: s per super-step (device)
+    int max_ss;
+    float tol;                           // relative residual stop, 0 = fixed count
+    float tau_unit;                      // coarse: mu~_j tau = mu_j * tau_unit
+    const float* rhs;                    // f_B (device)
+    float* u_out;                        // e_B (device)
+    int* ss_done;                        // coarse super-steps done (device int)
+};
+cudaError_t bottom_configure();
+// Cluster size (0: not possible), block size and shared memory for level B.
+int bottom_plan(int nx, int ny, int nz, int s, int* threads, size_t* bytes);
+cudaError_t launch_bottom(const BottomParams& p, int nc, int threads, size_t bytes, cudaStream_t st);
+
 }  // namespace sg

@@ -234,14 +234,18 @@ def test_kernel_profile_counts_every_class():
     st = g.kernel_stats()
     g.set_profiling(False)
     for name in ("rkl_stage_l0", "rkl_stage_coarse", "residual_l0", "residual_restrict",
-                 "prolong_correct", "coarse_solve", "update_residual"):
+                 "prolong_correct", "bottom_levels", "update_residual"):
         assert st[name]["launches"] > 0 and st[name]["ms"] > 0, name
     # mixed precision: the true FP64 residual at the start and once to confirm
-    # convergence; the recurrence update after every cycle; three restrictions
-    # per cycle (4 levels)
+    # convergence; the recurrence update after every cycle; of the three
+    # restrictions per cycle (4 levels) the last one runs inside the cluster
+    # launch of the two coarsest levels (16^3 and 8^3), which also holds the
+    # coarse solve
     assert st["residual_l0"]["launches"] == 2
     assert st["update_residual"]["launches"] == info["cycles"]
-    assert st["residual_restrict"]["launches"] == 3 * info["cycles"]
+    assert st["bottom_levels"]["launches"] == info["cycles"]
+    assert st["residual_restrict"]["launches"] == 2 * info["cycles"]
+    assert st["coarse_solve"]["launches"] == 0
     # the start (phi = 0: f and the face terms, 20 B/cell) and the confirmation (28 B/cell)
     assert st["residual_l0"]["bytes"] == (20.0 + 28.0) * 64 ** 3
     assert st["update_residual"]["bytes"] == 40.0 * 64 ** 3 * info["cycles"]
