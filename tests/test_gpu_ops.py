@@ -189,6 +189,32 @@ def test_fused_superstep_matches_oracle(shape, bc, order, s, zero):
     assert relerr(out.double(), ref) < 5e-5
 
 
+# The plane-streaming super-step at sizes where it runs several z chunks per
+# tile column: ragged tiles in y and z, and an x extent that is not a multiple
+# of four (scalar plane loads).
+LEAN_SHAPES = [((168, 160, 160), (0, 0, 0)), ((170, 160, 162), (1, 0, 1))]
+
+
+@pytest.mark.parametrize("shape,bc", LEAN_SHAPES)
+@pytest.mark.parametrize("order,s", [(2, 3), (1, 2)])
+@pytest.mark.parametrize("zero", [False, True])
+def test_plane_streaming_superstep_matches_oracle(shape, bc, order, s, zero):
+    assert shape[0] * shape[1] * shape[2] >= 1 << 22
+    g, h, _ = make_grid(shape, bc, "mixed")
+    c = 1.0
+    u = np.zeros(shape) if zero else W.random_field(shape, 30)
+    rhs = 50.0 * W.random_field(shape, 31)
+    out = torch.full(shape, float("nan"), dtype=torch.float32, device="cuda")
+    g.op_superstep(0, order, s, c, None if zero else dev(u, torch.float32), dev(rhs, torch.float32), out,
+                   homogeneous=True)
+    torch.cuda.synchronize()
+    u32 = u.astype(np.float32).astype(np.float64)
+    r32 = rhs.astype(np.float32).astype(np.float64)
+    ref = O.rkl_superstep(u32, r32, h, bc, None, order, s, c)
+    assert torch.isfinite(out).all()
+    assert relerr(out.double(), ref) < 5e-5
+
+
 def test_fused_equals_unfused_fp32():
     shape, bc = (64, 48, 80), (0, 0, 0)
     g, h, _ = make_grid(shape, bc, "mixed")
