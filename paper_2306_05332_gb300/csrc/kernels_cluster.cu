@@ -1,8 +1,8 @@
 // The two coarsest levels of the FP32 V-cycle in one launch (Sec. 2.1 steps
 // 2c-2e and 3, Eq. RKL_intermediate_source, App. A.5): a thread-block cluster
-// holds level B (the second coarsest) and level C = B + 1 (the coarsest) in
-// distributed shared memory and runs, without touching global memory between
-// them,
+// holds level B (the second coarsest) in distributed shared memory and level
+// C = B + 1 (the coarsest) whole in every CTA, and runs, without touching
+// global memory between them,
 //   the n_pre smoothing super-steps of B from e_B = 0,
 //   r_B = f_B - L e_B and its 8-child restriction f_C (mean removed when every
 //   axis is periodic, Eq. source_modification),
@@ -10,16 +10,21 @@
 //   stopped by the coarse tolerance),
 //   e_B += P e_C (27/9/3/1 prolongation) and the n_post smoothing super-steps.
 //
-// Layout.  CTA `rank` of the cluster owns the z slab [rank pz, (rank + 1) pz)
-// of level B and the matching slab of pz / 2 planes of level C; every field is
-// stored with a one-cell ghost layer.  A thread owns one (x, y) column of the
-// slab.  Ghosts follow the boundary rule of the level (Eq. error_ghost: ghost =
-// -active; Eq. periodic: the opposite cell): the thread writing a boundary cell
-// writes the x / y ghost in its own CTA and the z ghost plane of the
-// neighbouring CTA (through distributed shared memory), and a cluster barrier
-// (release / acquire) ends every stage.  Block and cluster sums are folded in
-// a fixed order and every CTA folds the same partials, so all CTAs take the
-// same stop decision and pass the same barriers.
+// Level B.  CTA `rank` of the cluster owns the z slab [rank pz, (rank + 1) pz)
+// of level B; every field is stored with a one-cell ghost layer.  A thread
+// owns one (x, y) column of the slab.  Ghosts follow the boundary rule of the
+// level (Eq. error_ghost: ghost = -active; Eq. periodic: the opposite cell):
+// the thread writing a boundary cell writes the x / y ghost in its own CTA and
+// the z ghost plane of the neighbouring CTA (through distributed shared
+// memory), and a cluster barrier (release / acquire) ends every stage.
+//
+// Level C.  The restriction sends f_C to every CTA, and each CTA then solves
+// the whole level by itself with one block barrier per stage: the same
+// arithmetic on the same data, so every CTA holds the same e_C, takes the same
+// stop decision (block sums in a fixed order) and has every coarse plane its
+// prolongation needs.  The solve works on strips of four x cells in dense
+// rotating buffers, each neighbour strip picked by the boundary rule, in the
+// shared memory the level-B stage buffers free meanwhile.
 //
 // The arithmetic of every stage, of the residual, the restriction and the
 // prolongation is written in the order of the single-level kernels.
@@ -112,22 +117,15 @@ __device__ __forceinline__ float block_sum(float v, float* red) {
     return t;
 }
 
-// Sum over the cluster: every CTA's block sum, folded in rank order by every
-// CTA.  Partials alternate between two slot arrays, so a CTA writing the next
-// round never overwrites slots a peer is still reading.
-__device__ __forceinline__ float cluster_sum(const Ctx& c, float* sm, int cred, int& round, float v, float* red) {
-    const float b = block_sum(v, red);
-    const int slot = cred + (round & 1) * kBottomMaxNC;
-    if (threadIdx.x < c.nc) {
-        float* r = c.cl.map_shared_rank(sm, (int)threadIdx.x) + slot;
-        r[c.rank] = b;
-    }
-    ++round;
-    c.cl.sync();
-    float t = 0.0f;
-    for (int k = 0; k < c.nc; ++k) t += sm[slot + k];
-    return t;
-}
+// Level C held whole with a ghost layer on every face (for the prolongation).
+struct Full {
+    int nx, ny, nz, row, plane;
+    __device__ int at(int k, int j, int i) const { return (k + 1) * plane + (j + 1) * row + (i + 1); }
+};
+
+__device__ __forceinline__ float4 ld4s(const float* p) { return *reinterpret_cast<const float4*>(p); }
+__device__ __forceinline__ void st4s(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
+__device__ __forceinline__ float4 neg4(float4 v) { return make_float4(-v.x, -v.y, -v.z, -v.w); }
 
 __global__ void __launch_bounds__(1024) k_bottom_levels(const __grid_constant__ BottomParams p) {
     extern __shared__ __align__(16) float sm[];
@@ -136,19 +134,26 @@ __global__ void __launch_bounds__(1024) k_bottom_levels(const __grid_constant__ 
     c.rank = (int)c.cl.block_rank();
     c.nc = (int)c.cl.num_blocks();
     const int nx = p.nx, ny = p.ny, nz = p.nz, pz = nz / c.nc;
-    const int cnx = nx / 2, cny = ny / 2, cpz = pz / 2;
-    const Slab sb = make_slab(nx, ny, pz), sc = make_slab(cnx, cny, cpz);
-    const int fb = sb.plane * (pz + 2), fc = sc.plane * (cpz + 2);
-    // fields: level B rhs, Z0 / residual, four iterates; level C rhs, three iterates; cluster partials
-    const int F = 0, Z = fb, YB = 2 * fb;
-    const int FC = 6 * fb, YC = FC + fc, CRED = FC + 4 * fc;
-    const int nfl = CRED + 2 * kBottomMaxNC;
+    const int cnx = nx / 2, cny = ny / 2, cnz = nz / 2, cpz = pz / 2;
+    const int ncc = cnx * cny * cnz;                 // cells of level C
+    const Slab sb = make_slab(nx, ny, pz);
+    Full sf;
+    sf.nx = cnx;
+    sf.ny = cny;
+    sf.nz = cnz;
+    sf.row = cnx + 2;
+    sf.plane = (cnx + 2) * (cny + 2);
+    const int fb = sb.plane * (pz + 2);
+    // level B: rhs F, iterate E, then a region U of four slab fields (Z0 /
+    // residual and three stage buffers) that holds level C's three iterates
+    // and its ghosted copy while level C is solved; FC: level C's rhs, dense
+    const int F = 0, E = fb, U = 2 * fb, FC = 6 * fb;
+    const int nfl = FC + ncc;
     const int tid = threadIdx.x;
     const bool act_b = tid < nx * ny, act_c = tid < cnx * cny;
     const int i = act_b ? tid % nx : 0, j = act_b ? tid / nx : 0;
     const int I = act_c ? tid % cnx : 0, J = act_c ? tid / cnx : 0;
     const float hx = p.hx, hy = p.hy, hz = p.hz;
-    int round = 0;
 
     for (int t = tid; t < nfl; t += blockDim.x) sm[t] = 0.0f;
     c.cl.sync();                                 // no peer writes a ghost before it is cleared
@@ -157,14 +162,15 @@ __global__ void __launch_bounds__(1024) k_bottom_levels(const __grid_constant__ 
     __syncthreads();
 
     // ---- smoothing super-steps of level B (App. A, Eq. RKL_intermediate_source)
-    int e = YB;                                   // current iterate (zero)
-    int spare[3] = {YB + fb, YB + 2 * fb, YB + 3 * fb};
+    const int Z = U;
+    int e = E;                                    // current iterate (zero)
+    int spare[3] = {U + fb, U + 2 * fb, U + 3 * fb};
     auto superstep = [&]() {
         const int y0 = e;
         for (int js = 1; js <= p.s; ++js) {
             const int out = spare[(js - 1) % 3];
             const int ym1 = js == 1 ? y0 : spare[(js - 2) % 3];
-            const int ym2 = js == 2 ? y0 : spare[(js + 0) % 3];   // (js - 3) mod 3
+            const int ym2 = js == 2 ? y0 : spare[js % 3];         // (js - 3) mod 3
             if (act_b) {
                 for (int k = 0; k < pz; ++k) {
                     const int o = sb.at(k, j, i);
@@ -191,15 +197,23 @@ __global__ void __launch_bounds__(1024) k_bottom_levels(const __grid_constant__ 
         e = ne;
     };
     for (int n = 0; n < p.n_pre; ++n) superstep();
+    // the iterate back to its home E (ghost planes included), so that U is free
+    if (e != E) {
+        for (int t = tid; t < fb; t += blockDim.x) sm[E + t] = sm[e + t];
+        for (int k = 0; k < 3; ++k)
+            if (spare[k] == E) spare[k] = e;
+        e = E;
+        __syncthreads();
+    }
 
-    // ---- r_B = f_B - L e_B, restricted by the 8-child mean into f_C
+    // ---- r_B = f_B - L e_B, restricted by the 8-child mean into f_C, which
+    // every CTA receives whole
     if (act_b)
         for (int k = 0; k < pz; ++k) {
             const int o = sb.at(k, j, i);
             sm[Z + o] = sm[F + o] - lap_at(sm + e, sb, k, j, i, hx, hy, hz);
         }
     __syncthreads();
-    float csum = 0.0f;
     if (act_c)
         for (int K = 0; K < cpz; ++K) {
             float pl[2];
@@ -211,97 +225,126 @@ __global__ void __launch_bounds__(1024) k_bottom_levels(const __grid_constant__ 
                 pl[a] = (r0 + r1) + (r4 + r5);
             }
             const float cv = (pl[0] + pl[1]) * 0.125f;
-            sm[FC + sc.at(K, J, I)] = cv;
-            csum += cv;
+            const int o = FC + ((c.rank * cpz + K) * cny + J) * cnx + I;
+            for (int q = 0; q < c.nc; ++q) c.cl.map_shared_rank(sm, q)[o] = cv;
         }
-    if (p.remove_mean) {
-        const float total = cluster_sum(c, sm, CRED, round, csum, red);
-        const float mean = total / float(cnx * cny * (nz / 2));
-        if (act_c)
-            for (int K = 0; K < cpz; ++K) sm[FC + sc.at(K, J, I)] -= mean;
-    }
-    __syncthreads();
+    c.cl.sync();
 
-    // ---- coarsest level: accelerated RKL1 from e_C = 0 (App. A.5)
+    // ---- level C, whole in every CTA: the same arithmetic on the same data in
+    // each, so all CTAs hold the same e_C and take the same steps (accelerated
+    // RKL1 from e_C = 0, App. A.5).  Strips of four x cells; the boundary rule
+    // picks each neighbour strip.
     const float chx = p.chx, chy = p.chy, chz = p.chz, tu = p.tau_unit;
-    int y_cur = YC, y_prev = YC + fc, y_free = YC + 2 * fc;
-    float f2 = 0.0f;
-    if (act_c)
-        for (int K = 0; K < cpz; ++K) {
-            const float v = sm[FC + sc.at(K, J, I)];
-            f2 = fmaf(v, v, f2);
-        }
-    const float r0sq = cluster_sum(c, sm, CRED, round, f2, red);
+    if (p.remove_mean) {                         // Eq. source_modification on level C
+        float s = 0.0f;
+        for (int t = tid; t < ncc; t += blockDim.x) s += sm[FC + t];
+        const float mean = block_sum(s, red) / float(ncc);
+        for (int t = tid; t < ncc; t += blockDim.x) sm[FC + t] -= mean;
+        __syncthreads();
+    }
+    // one strip of four x cells per thread (the plan guarantees enough
+    // threads); its iterate, previous iterate and f stay in registers, and
+    // every stage publishes the new iterate in one of two dense buffers
+    const int nq = cnx >> 2, nrow = nq * cny, nstrip = nrow * cnz;
+    const bool own = tid < nstrip;
+    const int q = own ? tid % nq : 0, jj = own ? (tid / nq) % cny : 0, kk = own ? tid / nrow : 0;
+    // neighbour strips (float4 index) and x cells (float index); -1: the
+    // Dirichlet reflection of this strip's own value
+    const int oym = jj > 0 ? tid - nq : (c.py ? tid + (cny - 1) * nq : -1);
+    const int oyp = jj < cny - 1 ? tid + nq : (c.py ? tid - (cny - 1) * nq : -1);
+    const int ozm = kk > 0 ? tid - nrow : (c.pz ? tid + (cnz - 1) * nrow : -1);
+    const int ozp = kk < cnz - 1 ? tid + nrow : (c.pz ? tid - (cnz - 1) * nrow : -1);
+    const int oxl = q > 0 ? 4 * tid - 1 : (c.px ? 4 * (tid + nq - 1) + 3 : -1);
+    const int oxr = q < nq - 1 ? 4 * tid + 4 : (c.px ? 4 * (tid - nq + 1) : -1);
+    int pub = U;                                   // buffer holding every strip's current iterate
+    const int other = U + ncc;
+    for (int t = tid; t < 2 * ncc; t += blockDim.x) sm[U + t] = 0.0f;
+    const float4 f = own ? ld4s(sm + FC + 4 * tid) : make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 cur = make_float4(0.f, 0.f, 0.f, 0.f), prev = cur;
+    const float f2 = own ? fmaf(f.x, f.x, fmaf(f.y, f.y, fmaf(f.z, f.z, f.w * f.w))) : 0.0f;
+    const float r0sq = block_sum(f2, red);       // (its barriers also order the writes above)
     const float tolsq = p.tol * p.tol * r0sq;
+    auto lap4 = [&](const float* y) {
+        const float4 ym = oym >= 0 ? ld4s(y + 4 * oym) : neg4(cur);
+        const float4 yp = oyp >= 0 ? ld4s(y + 4 * oyp) : neg4(cur);
+        const float4 zm = ozm >= 0 ? ld4s(y + 4 * ozm) : neg4(cur);
+        const float4 zp = ozp >= 0 ? ld4s(y + 4 * ozp) : neg4(cur);
+        const float xl = oxl >= 0 ? y[oxl] : -cur.x;
+        const float xr = oxr >= 0 ? y[oxr] : -cur.w;
+        const float4 cc = cur;
+        return make_float4(lap7f(cc.x, xl, cc.y, ym.x, yp.x, zm.x, zp.x, chx, chy, chz),
+                           lap7f(cc.y, cc.x, cc.z, ym.y, yp.y, zm.y, zp.y, chx, chy, chz),
+                           lap7f(cc.z, cc.y, cc.w, ym.z, yp.z, zm.z, zp.z, chx, chy, chz),
+                           lap7f(cc.w, cc.z, xr, ym.w, yp.w, zm.w, zp.w, chx, chy, chz));
+    };
     int done = 0;
     for (int ss = 0; ss < p.max_ss; ++ss) {
         if (p.tol > 0.0f) {
             float acc = 0.0f;
-            if (act_c)
-                for (int K = 0; K < cpz; ++K) {
-                    const float r = sm[FC + sc.at(K, J, I)] - lap_at(sm + y_cur, sc, K, J, I, chx, chy, chz);
-                    acc = fmaf(r, r, acc);
-                }
-            if (cluster_sum(c, sm, CRED, round, acc, red) <= tolsq) break;
+            if (own) {
+                const float4 L = lap4(sm + pub);
+                const float r0 = f.x - L.x, r1 = f.y - L.y, r2 = f.z - L.z, r3 = f.w - L.w;
+                acc = fmaf(r0, r0, fmaf(r1, r1, fmaf(r2, r2, r3 * r3)));
+            }
+            if (block_sum(acc, red) <= tolsq) break;
         }
         const int s = p.sched[ss];
         for (int js = 1; js <= s; ++js) {
             const float inv = 1.0f / float(js);
             const float mu = 2.0f - inv, nu = inv - 1.0f;
             const float mut = mu * tu;
-            if (act_c)
-                for (int K = 0; K < cpz; ++K) {
-                    const int o = sc.at(K, J, I);
-                    const float cc = sm[y_cur + o];
-                    const float L = lap_at(sm + y_cur, sc, K, J, I, chx, chy, chz);
-                    const float f = sm[FC + o];
-                    const float v = js == 1 ? cc + tu * (L - f) : mu * cc + nu * sm[y_prev + o] + mut * (L - f);
-                    put(c, sm, y_free, sc, K, J, I, v);
+            const int dst = pub == U ? other : U;
+            if (own) {
+                const float4 L = lap4(sm + pub), cc = cur;
+                float4 v;
+                if (js == 1) {
+                    v = make_float4(cc.x + tu * (L.x - f.x), cc.y + tu * (L.y - f.y), cc.z + tu * (L.z - f.z),
+                                    cc.w + tu * (L.w - f.w));
+                } else {
+                    v = make_float4(mu * cc.x + nu * prev.x + mut * (L.x - f.x),
+                                    mu * cc.y + nu * prev.y + mut * (L.y - f.y),
+                                    mu * cc.z + nu * prev.z + mut * (L.z - f.z),
+                                    mu * cc.w + nu * prev.w + mut * (L.w - f.w));
                 }
-            c.cl.sync();
-            const int t = y_free;
-            y_free = y_prev;
-            y_prev = y_cur;
-            y_cur = t;
+                prev = cc;
+                cur = v;
+                st4s(sm + dst + 4 * tid, v);
+            }
+            __syncthreads();
+            pub = dst;
         }
         ++done;
     }
     if (c.rank == 0 && tid == 0 && p.ss_done) *p.ss_done = done;
+    const int y_cur = pub;
 
-    // ---- e_B += P e_C (27/9/3/1 weights / 64).  The x / y ghosts of every
-    // plane of e_C (z ghost planes included, their edges and corners too) are
-    // set from the plane's interior by the boundary rule first.
-    {
-        const int gw = cnx + 2, gh = cny + 2, ng = 2 * gw + 2 * cny;     // ghost cells of one plane
-        for (int t = tid; t < ng * (cpz + 2); t += blockDim.x) {
-            const int K = t / ng - 1, g = t % ng;
-            int gi, gj;
-            if (g < gw) { gi = g - 1; gj = -1; }
-            else if (g < 2 * gw) { gi = g - gw - 1; gj = cny; }
-            else if (g < 2 * gw + cny) { gi = -1; gj = g - 2 * gw; }
-            else { gi = cnx; gj = g - 2 * gw - cny; }
-            (void)gh;
-            int si = gi, sj = gj;
-            float sg = 1.0f;
-            if (gi < 0) { si = c.px ? cnx - 1 : 0; if (!c.px) sg = -sg; }
-            else if (gi >= cnx) { si = c.px ? 0 : cnx - 1; if (!c.px) sg = -sg; }
-            if (gj < 0) { sj = c.py ? cny - 1 : 0; if (!c.py) sg = -sg; }
-            else if (gj >= cny) { sj = c.py ? 0 : cny - 1; if (!c.py) sg = -sg; }
-            sm[y_cur + sc.at(K, gj, gi)] = sg * sm[y_cur + sc.at(K, sj, si)];
-        }
+    // ---- e_B += P e_C (27/9/3/1 weights / 64) from a ghosted copy of e_C:
+    // every ghost (edges and corners too) set by the boundary rule
+    const int EC = U + 3 * ncc;
+    const int ff = sf.plane * (cnz + 2);
+    for (int t = tid; t < ff; t += blockDim.x) {
+        const int gk = t / sf.plane - 1, gj = (t / sf.row) % (cny + 2) - 1, gi = t % sf.row - 1;
+        float sg = 1.0f;
+        auto mapc = [&](int v, int n, bool per) {
+            if (v < 0) { if (!per) sg = -sg; return per ? n - 1 : 0; }
+            if (v >= n) { if (!per) sg = -sg; return per ? 0 : n - 1; }
+            return v;
+        };
+        const int si = mapc(gi, cnx, c.px), sj = mapc(gj, cny, c.py), sk = mapc(gk, cnz, c.pz);
+        sm[EC + t] = sg * sm[y_cur + (sk * cny + sj) * cnx + si];
     }
     __syncthreads();
     if (act_b) {
         const int Ia = i >> 1, Ja = j >> 1;
         const int Ib = Ia + ((i & 1) ? 1 : -1), Jb = Ja + ((j & 1) ? 1 : -1);
-        const float* ec = sm + y_cur;
+        const float* ec = sm + EC;
         auto q = [&](int K) {
-            return 9.0f * ec[sc.at(K, Ja, Ia)] + 3.0f * ec[sc.at(K, Ja, Ib)] + 3.0f * ec[sc.at(K, Jb, Ia)] +
-                   ec[sc.at(K, Jb, Ib)];
+            return 9.0f * ec[sf.at(K, Ja, Ia)] + 3.0f * ec[sf.at(K, Ja, Ib)] + 3.0f * ec[sf.at(K, Jb, Ia)] +
+                   ec[sf.at(K, Jb, Ib)];
         };
         const float w = 1.0f / 64.0f;
         for (int k = 0; k < pz; k += 2) {
-            const int K = k >> 1;
+            const int K = (c.rank * pz + k) >> 1;
             const float qm = q(K - 1), q0 = q(K), qp = q(K + 1);
             const int o0 = sb.at(k, j, i), o1 = sb.at(k + 1, j, i);
             put(c, sm, e, sb, k, j, i, sm[e + o0] + (3.0f * q0 + qm) * w);
@@ -317,11 +360,18 @@ __global__ void __launch_bounds__(1024) k_bottom_levels(const __grid_constant__ 
     c.cl.sync();                                  // peers may still write this CTA's ghosts until here
 }
 
+// Shared memory of one CTA, or 0 where level C does not split into 4-cell
+// strips, has more strips than the CTA has threads, or does not fit (two
+// dense iterates and a ghosted copy) in the region of four level-B slab
+// fields.
 size_t bottom_bytes(int nx, int ny, int nz, int nc) {
     const int pz = nz / nc;
     const size_t fb = (size_t)(nx + 2) * (ny + 2) * (pz + 2);
-    const size_t fc = (size_t)(nx / 2 + 2) * (ny / 2 + 2) * (pz / 2 + 2);
-    return (6 * fb + 4 * fc + 2 * kBottomMaxNC) * sizeof(float);
+    const size_t ncc = (size_t)(nx / 2) * (ny / 2) * (nz / 2);
+    const size_t ff = (size_t)(nx / 2 + 2) * (ny / 2 + 2) * (nz / 2 + 2);
+    const size_t threads = ((size_t)nx * ny + 31) / 32 * 32;
+    if ((nx / 2) % 4 != 0 || ncc / 4 > threads || 3 * ncc + ff > 4 * fb) return 0;
+    return (6 * fb + ncc) * sizeof(float);
 }
 
 // Plans by level-B shape, filled before any graph capture (the occupancy query
@@ -363,7 +413,7 @@ int bottom_plan(int nx, int ny, int nz, int s, int* threads, size_t* bytes) {
     for (int nc = kBottomMaxNC; nc >= 1 && !found; nc >>= 1) {
         if (nz % (2 * nc)) continue;
         by = bottom_bytes(nx, ny, nz, nc);
-        if (by > kSmemLimit) continue;
+        if (by == 0 || by > kSmemLimit) continue;
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(nc);
         cfg.blockDim = dim3(th);

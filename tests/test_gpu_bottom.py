@@ -1,8 +1,10 @@
 """The two coarsest levels of the FP32 V-cycle in one cluster launch against
 the level-by-level kernels (the `fused` option switches between them), on
 every boundary mix and on the cluster sizes the planner picks (8, 4 and 2
-CTAs; level B of 32^3, 16^3, 8^3, 24^3, 20 x 12 x 36 and 12^3 cells; a valid
-hierarchy has an even coarsest level, so level B always splits in two).
+CTAs; level B of 32^3, 16^3, 8^3, 24^3 and 24 x 16 x 12 cells; a valid
+hierarchy has an even coarsest level, so level B always splits in two), and
+the fallback to the level-by-level kernels where the coarsest level's x extent
+is not a multiple of four.
 
 Both paths evaluate the same formulas in the same order (RKL stages, residual,
 8-child restriction, periodic mean, accelerated RKL1 coarse solve with its
@@ -29,14 +31,13 @@ def _sg():
 
 LO, HI = (0.0, -0.5, 0.25), (1.3, 0.2, 1.35)
 
-# (shape, bc, levels): level B = levels - 2
+# (shape (nz, ny, nx), bc, levels): level B = levels - 2
 CASES = [
     ((128, 128, 128), (0, 0, 0), 4),   # B 32^3, 8 CTAs of 4 planes (the benchmark's level B)
     ((64, 64, 64), (0, 0, 0), 4),      # B 16^3, 8 CTAs
     ((32, 32, 32), (1, 1, 1), 4),      # B 8^3, 4 CTAs, coarse mean removed
-    ((48, 48, 48), (1, 0, 1), 3),      # B 24^3, 4 CTAs
-    ((40, 24, 72), (0, 1, 0), 3),      # B 20 x 12 x 36, 2 CTAs
-    ((24, 24, 24), (0, 0, 0), 3),      # B 12^3, 2 CTAs of 6 planes
+    ((48, 48, 48), (1, 0, 1), 3),      # B 24^3, 4 CTAs, 3 strips per coarse row
+    ((24, 32, 48), (0, 1, 0), 3),      # B 12 x 16 x 24 (z, y, x), 2 CTAs of 6 planes
 ]
 
 
@@ -70,6 +71,17 @@ def test_cluster_launch_matches_level_by_level(shape, bc, levels, opts):
         a, b = a - a.mean(), b - b.mean()
     assert np.linalg.norm(a - b) / np.linalg.norm(b) < 1e-5
     assert ia["coarse_ss"] == ib["coarse_ss"]
+
+
+def test_unsupported_shape_falls_back_to_level_by_level():
+    # level C of 10 x 6 x 18 (x extent not a multiple of four)
+    shape, bc, levels = (40, 24, 72), (0, 1, 0), 3
+    opts = dict(rkl_order=2, s_smooth=3)
+    a, _, st = _run(shape, bc, levels, 1, opts, prof=True)
+    b, _, _ = _run(shape, bc, levels, 0, opts)
+    assert st["bottom_levels"]["launches"] == 0
+    assert st["coarse_solve"]["launches"] == 2
+    assert np.linalg.norm(a - b) / np.linalg.norm(b) < 1e-5
 
 
 def test_cluster_path_solve_matches_oracle():
