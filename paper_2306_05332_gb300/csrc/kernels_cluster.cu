@@ -123,6 +123,37 @@ struct Full {
     __device__ int at(int k, int j, int i) const { return (k + 1) * plane + (j + 1) * row + (i + 1); }
 };
 
+// Packed FP32 pairs (f32x2): two independent FP32 operations per instruction,
+// each rounded as the scalar one.
+__device__ __forceinline__ unsigned long long pk2(float2 v) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(v.x), "f"(v.y));
+    return r;
+}
+__device__ __forceinline__ float2 upk2(unsigned long long r) {
+    float2 v;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(v.x), "=f"(v.y) : "l"(r));
+    return v;
+}
+__device__ __forceinline__ float2 fma2f(float2 a, float2 b, float2 c) {
+    unsigned long long d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(pk2(a)), "l"(pk2(b)), "l"(pk2(c)));
+    return upk2(d);
+}
+__device__ __forceinline__ float2 add2f(float2 a, float2 b) {
+    unsigned long long d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(pk2(a)), "l"(pk2(b)));
+    return upk2(d);
+}
+__device__ __forceinline__ float2 mul2f(float2 a, float2 b) {
+    unsigned long long d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(pk2(a)), "l"(pk2(b)));
+    return upk2(d);
+}
+__device__ __forceinline__ float2 lo2f(float4 v) { return make_float2(v.x, v.y); }
+__device__ __forceinline__ float2 hi2f(float4 v) { return make_float2(v.z, v.w); }
+__device__ __forceinline__ float2 dupf(float a) { return make_float2(a, a); }
+
 __device__ __forceinline__ float4 ld4s(const float* p) { return *reinterpret_cast<const float4*>(p); }
 __device__ __forceinline__ void st4s(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
 __device__ __forceinline__ float4 neg4(float4 v) { return make_float4(-v.x, -v.y, -v.z, -v.w); }
@@ -264,7 +295,11 @@ __global__ void __launch_bounds__(1024) k_bottom_levels(const __grid_constant__ 
     const float f2 = own ? fmaf(f.x, f.x, fmaf(f.y, f.y, fmaf(f.z, f.z, f.w * f.w))) : 0.0f;
     const float r0sq = block_sum(f2, red);       // (its barriers also order the writes above)
     const float tolsq = p.tol * p.tol * r0sq;
-    auto lap4 = [&](const float* y) {
+    // L of the thread's strip as two packed pairs: h_x (x neighbours) +
+    // h_y (y neighbours) + h_z (z neighbours) - 2 (h_x + h_y + h_z) c
+    const float2 hx2 = dupf(chx), hy2 = dupf(chy), hz2 = dupf(chz), md2 = dupf(-2.0f * (chx + chy + chz));
+    const float2 nf01 = make_float2(-f.x, -f.y), nf23 = make_float2(-f.z, -f.w);
+    auto lap_minus_f = [&](const float* y, float2& d01, float2& d23) {     // L cur - f
         const float4 ym = oym >= 0 ? ld4s(y + 4 * oym) : neg4(cur);
         const float4 yp = oyp >= 0 ? ld4s(y + 4 * oyp) : neg4(cur);
         const float4 zm = ozm >= 0 ? ld4s(y + 4 * ozm) : neg4(cur);
@@ -272,19 +307,23 @@ __global__ void __launch_bounds__(1024) k_bottom_levels(const __grid_constant__ 
         const float xl = oxl >= 0 ? y[oxl] : -cur.x;
         const float xr = oxr >= 0 ? y[oxr] : -cur.w;
         const float4 cc = cur;
-        return make_float4(lap7f(cc.x, xl, cc.y, ym.x, yp.x, zm.x, zp.x, chx, chy, chz),
-                           lap7f(cc.y, cc.x, cc.z, ym.y, yp.y, zm.y, zp.y, chx, chy, chz),
-                           lap7f(cc.z, cc.y, cc.w, ym.z, yp.z, zm.z, zp.z, chx, chy, chz),
-                           lap7f(cc.w, cc.z, xr, ym.w, yp.w, zm.w, zp.w, chx, chy, chz));
+        const float2 sx01 = add2f(make_float2(xl, cc.x), make_float2(cc.y, cc.z));
+        const float2 sx23 = add2f(make_float2(cc.y, cc.z), make_float2(cc.w, xr));
+        const float2 L01 = fma2f(hx2, sx01, fma2f(hy2, add2f(lo2f(ym), lo2f(yp)),
+                                                  fma2f(hz2, add2f(lo2f(zm), lo2f(zp)), mul2f(md2, lo2f(cc)))));
+        const float2 L23 = fma2f(hx2, sx23, fma2f(hy2, add2f(hi2f(ym), hi2f(yp)),
+                                                  fma2f(hz2, add2f(hi2f(zm), hi2f(zp)), mul2f(md2, hi2f(cc)))));
+        d01 = add2f(L01, nf01);
+        d23 = add2f(L23, nf23);
     };
     int done = 0;
     for (int ss = 0; ss < p.max_ss; ++ss) {
         if (p.tol > 0.0f) {
             float acc = 0.0f;
             if (own) {
-                const float4 L = lap4(sm + pub);
-                const float r0 = f.x - L.x, r1 = f.y - L.y, r2 = f.z - L.z, r3 = f.w - L.w;
-                acc = fmaf(r0, r0, fmaf(r1, r1, fmaf(r2, r2, r3 * r3)));
+                float2 d01, d23;
+                lap_minus_f(sm + pub, d01, d23);
+                acc = fmaf(d01.x, d01.x, fmaf(d01.y, d01.y, fmaf(d23.x, d23.x, d23.y * d23.y)));
             }
             if (block_sum(acc, red) <= tolsq) break;
         }
@@ -292,23 +331,23 @@ __global__ void __launch_bounds__(1024) k_bottom_levels(const __grid_constant__ 
         for (int js = 1; js <= s; ++js) {
             const float inv = 1.0f / float(js);
             const float mu = 2.0f - inv, nu = inv - 1.0f;
-            const float mut = mu * tu;
             const int dst = pub == U ? other : U;
             if (own) {
-                const float4 L = lap4(sm + pub), cc = cur;
-                float4 v;
-                if (js == 1) {
-                    v = make_float4(cc.x + tu * (L.x - f.x), cc.y + tu * (L.y - f.y), cc.z + tu * (L.z - f.z),
-                                    cc.w + tu * (L.w - f.w));
-                } else {
-                    v = make_float4(mu * cc.x + nu * prev.x + mut * (L.x - f.x),
-                                    mu * cc.y + nu * prev.y + mut * (L.y - f.y),
-                                    mu * cc.z + nu * prev.z + mut * (L.z - f.z),
-                                    mu * cc.w + nu * prev.w + mut * (L.w - f.w));
+                float2 d01, d23;
+                lap_minus_f(sm + pub, d01, d23);
+                const float4 cc = cur;
+                float2 v01, v23;
+                if (js == 1) {                     // Y1 = Y0 + tau_unit (L Y0 - f)
+                    v01 = fma2f(dupf(tu), d01, lo2f(cc));
+                    v23 = fma2f(dupf(tu), d23, hi2f(cc));
+                } else {                           // Y_j = mu Y_{j-1} + nu Y_{j-2} + mu tau_unit (L Y_{j-1} - f)
+                    const float2 mu2 = dupf(mu), nu2 = dupf(nu), mt2 = dupf(mu * tu);
+                    v01 = fma2f(mt2, d01, fma2f(nu2, lo2f(prev), mul2f(mu2, lo2f(cc))));
+                    v23 = fma2f(mt2, d23, fma2f(nu2, hi2f(prev), mul2f(mu2, hi2f(cc))));
                 }
                 prev = cc;
-                cur = v;
-                st4s(sm + dst + 4 * tid, v);
+                cur = make_float4(v01.x, v01.y, v23.x, v23.y);
+                st4s(sm + dst + 4 * tid, cur);
             }
             __syncthreads();
             pub = dst;
