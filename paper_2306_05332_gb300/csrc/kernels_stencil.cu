@@ -375,7 +375,7 @@ k_residual_restrict(const LevelGeom g, const T* __restrict__ u, const T* __restr
 // rows (2J, 2J + 1) and streams z, so each 2 x 2 x 2 block of the 8-cell mean
 // (Eq. restriction_example_3D) is summed in its registers, with no shared
 // memory or barrier; the z neighbours are carried in registers.
-__global__ void __launch_bounds__(BX * BY)
+__global__ void __launch_bounds__(BX * BY, 4)
 k_residual_restrict4(const LevelGeom g, const float* __restrict__ u, const float* __restrict__ rhs,
                      float* __restrict__ coarse, Partial* partials, int kchunk) {
     const int q = blockIdx.x * BX + threadIdx.x;        // cells 4q .. 4q + 3
@@ -549,8 +549,11 @@ k_prolong_correct4(const LevelGeom g, const float* __restrict__ coarse, float* _
     interp(K, q0a, q0b);
     interp(K + 1, qpa, qpb);
     const float w = 1.0f / 64.0f;
-    auto add = [&](float* p, float4 a, float4 b) {      // p += (3 a + b) / 64
-        float4 v = ld_f4(p);
+    // the four fine rows of the next plane pair are loaded before the current
+    // pair is corrected, so two pairs' loads are in flight
+    float4 va = ld_f4(fine_u + idx), vb = ld_f4(fine_u + idx + nx);
+    float4 vc = ld_f4(fine_u + idx + plane), vd = ld_f4(fine_u + idx + plane + nx);
+    auto put = [&](float* p, float4 v, float4 a, float4 b) {      // p = v + (3 a + b) / 64
         v.x += (3.0f * a.x + b.x) * w;
         v.y += (3.0f * a.y + b.y) * w;
         v.z += (3.0f * a.z + b.z) * w;
@@ -558,14 +561,23 @@ k_prolong_correct4(const LevelGeom g, const float* __restrict__ coarse, float* _
         *reinterpret_cast<float4*>(p) = v;
     };
     for (int k = k0; k < k1; k += 2, idx += 2 * plane) {
-        add(fine_u + idx, q0a, qma);
-        add(fine_u + idx + nx, q0b, qmb);
-        add(fine_u + idx + plane, q0a, qpa);
-        add(fine_u + idx + plane + nx, q0b, qpb);
+        float4 na = va, nb = vb, nc = vc, nd = vd;
+        if (k + 2 < k1) {
+            const int n = idx + 2 * plane;
+            na = ld_f4(fine_u + n);
+            nb = ld_f4(fine_u + n + nx);
+            nc = ld_f4(fine_u + n + plane);
+            nd = ld_f4(fine_u + n + plane + nx);
+        }
+        put(fine_u + idx, va, q0a, qma);
+        put(fine_u + idx + nx, vb, q0b, qmb);
+        put(fine_u + idx + plane, vc, q0a, qpa);
+        put(fine_u + idx + plane + nx, vd, q0b, qpb);
         ++K;
         qma = q0a; qmb = q0b;
         q0a = qpa; q0b = qpb;
         if (k + 2 < k1) interp(K + 1, qpa, qpb);
+        va = na; vb = nb; vc = nc; vd = nd;
     }
 }
 
