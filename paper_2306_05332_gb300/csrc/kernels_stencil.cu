@@ -701,7 +701,7 @@ k_update_residual(const LevelGeom g, double* __restrict__ phi, const float* __re
 // unrolled by two so the next plane's loads overlap the current arithmetic.
 
 template <bool UNIFORM>
-__global__ void __launch_bounds__(BX * BY)
+__global__ void __launch_bounds__(BX * BY, 4)
 k_update_residual4(const LevelGeom g, double* __restrict__ phi, const float* __restrict__ e,
                    double* __restrict__ r64, float* __restrict__ r32, Partial* partials, int kchunk) {
     const int q = blockIdx.x * BX + threadIdx.x;        // strip: cells 4q .. 4q + 3
