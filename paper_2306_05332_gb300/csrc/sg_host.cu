@@ -481,6 +481,16 @@ bool use_fused(const sg_grid* g, bool faces, int l) {
            g->lv[l].n >= kFusedMinCells;
 }
 
+// The first super-step of a level's pre-smoothing starts from Y0 = 0: for
+// s = 2, 3 the fused kernel runs it as s - 1 stencil stages of f in one launch,
+// which beats s stage launches down to levels of kZeroFusedMinCells cells.
+constexpr long long kZeroFusedMinCells = 1LL << 17;
+
+bool use_fused_zero(const sg_grid* g, bool faces, int l) {
+    return g->precision == SG_MIXED && g->opt.fused && !faces && g->opt.s_smooth <= 3 &&
+           fused_supported(g->opt.rkl_order, g->opt.s_smooth) && g->lv[l].n >= kZeroFusedMinCells;
+}
+
 // The two coarsest levels B = L - 2 >= 1 and C = L - 1 of the FP32 V-cycle
 // in one cluster launch (kernels_cluster.cu): the cluster size, or 0 where the
 // level-by-level kernels run them.
@@ -569,6 +579,11 @@ sg_status vcycle(sg_grid* g, int L, W* u0, const W* rhs0, bool faces, bool zero0
                 }
                 if (zero_start && count == 0) SG_CK(cudaMemsetAsync(cur[l], 0, g->lv[l].n * sizeof(W), g->st));
                 return SG_OK;
+            }
+            if (zero_start && count > 0 && use_fused_zero(g, fc, l)) {
+                SG_TRY(superstep_fused(g, l, g->opt.rkl_order, g->opt.s_smooth, g->opt.tau_frac, nullptr, R(l),
+                                       cur[l]));
+                return relax<W>(g, l, count - 1, fc, cur[l], R(l));
             }
         }
         if (zero_start && count > 0) SG_CK(cudaMemsetAsync(cur[l], 0, g->lv[l].n * sizeof(W), g->st));
