@@ -98,6 +98,44 @@ __device__ __forceinline__ T lap_at(const T* u, const LevelGeom& g, int i, int j
     return lap7(c, xm, xp, ym, yp, zm, zp, ih2x<T>(g), ih2y<T>(g), ih2z<T>(g));
 }
 
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& err) {
+    s = a + b;
+    const float bb = s - a;
+    err = (a - (s - bb)) + (b - bb);
+}
+
+// float -> double from the IEEE fields (subnormal floats, below 1.2e-38, become 0).
+__device__ __forceinline__ double f2d_bits(float x) {
+    const unsigned u = __float_as_uint(x);
+    const unsigned sgn = u & 0x80000000u, ex = (u >> 23) & 0xffu, m = u & 0x7fffffu;
+    unsigned hi, lo;
+    if (ex == 0u) { hi = sgn; lo = 0u; }
+    else if (ex == 255u) { hi = sgn | 0x7ff00000u | (m >> 3); lo = m << 29; }
+    else { hi = sgn | ((ex + 896u) << 20) | (m >> 3); lo = m << 29; }
+    return __hiloint2double((int)hi, (int)lo);
+}
+
+// double -> float by truncating the significand (within one FP32 ulp; values
+// below 2^-126 become 0, beyond the FP32 range +-inf).
+__device__ __forceinline__ float d2f_bits(double x) {
+    const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+    const unsigned sgn = hi & 0x80000000u, ex = (hi >> 20) & 0x7ffu, mh = hi & 0xfffffu;
+    if (ex <= 896u) return __uint_as_float(sgn);
+    if (ex >= 1151u) return __uint_as_float(sgn | 0x7f800000u | ((ex == 2047u && (mh | lo)) ? 0x400000u : 0u));
+    return __uint_as_float(sgn | ((ex - 896u) << 23) | (mh << 3) | (lo >> 29));
+}
+
+// A residual in the output precision: FP64 -> FP32 by the bit-level
+// conversion (no FP64-pipe instruction), any other pair by the plain cast.
+template <typename TO, typename TI>
+__device__ __forceinline__ TO to_out(TI r) {
+    return TO(r);
+}
+template <>
+__device__ __forceinline__ float to_out<float, double>(double r) {
+    return d2f_bits(r);
+}
+
 template <typename T>
 struct CoefT {
     T tau, mut1, mu, nu, mut_tau, c0, gt;
@@ -228,7 +266,7 @@ k_residual(const LevelGeom g, const TI* __restrict__ u, const TI* __restrict__ r
             } else {
                 r = rhs[idx] - lap7(c, xm, xp, ym, yp, zm, zp, ihx2, ihy2, ihz2);
             }
-            const TO ro = TO(r);
+            const TO ro = to_out<TO>(r);
             if (r_out) r_out[idx] = ro;
             if (r_full) r_full[idx] = r;
             const A ra = A(ro);
@@ -263,7 +301,7 @@ k_residual_zero(const LevelGeom g, const double* __restrict__ rhs, TO* r_out, do
         const int plane = g.nx * g.ny;
         const bool dx = !g.per[0], dy = !g.per[1], dz = !g.per[2];
         auto emit = [&](int idx, double r) {
-            const TO ro = TO(r);
+            const TO ro = to_out<TO>(r);
             if (r_out) r_out[idx] = ro;
             if (r_full) r_full[idx] = r;
             const A ra = A(ro);
@@ -596,33 +634,6 @@ k_prolong_correct4(const LevelGeom g, const float* __restrict__ coarse, float* _
 // of the FP32 rate, and this kernel keeps three of them per cell (phi + e and
 // the two FMAs).
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void two_sum(float a, float b, float& s, float& err) {
-    s = a + b;
-    const float bb = s - a;
-    err = (a - (s - bb)) + (b - bb);
-}
-
-// float -> double from the IEEE fields (subnormal floats, below 1.2e-38, become 0).
-__device__ __forceinline__ double f2d_bits(float x) {
-    const unsigned u = __float_as_uint(x);
-    const unsigned sgn = u & 0x80000000u, ex = (u >> 23) & 0xffu, m = u & 0x7fffffu;
-    unsigned hi, lo;
-    if (ex == 0u) { hi = sgn; lo = 0u; }
-    else if (ex == 255u) { hi = sgn | 0x7ff00000u | (m >> 3); lo = m << 29; }
-    else { hi = sgn | ((ex + 896u) << 20) | (m >> 3); lo = m << 29; }
-    return __hiloint2double((int)hi, (int)lo);
-}
-
-// double -> float by truncating the significand (within one FP32 ulp; values
-// below 2^-126 become 0, beyond the FP32 range +-inf).
-__device__ __forceinline__ float d2f_bits(double x) {
-    const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
-    const unsigned sgn = hi & 0x80000000u, ex = (hi >> 20) & 0x7ffu, mh = hi & 0xfffffu;
-    if (ex <= 896u) return __uint_as_float(sgn);
-    if (ex >= 1151u) return __uint_as_float(sgn | 0x7f800000u | ((ex == 2047u && (mh | lo)) ? 0x400000u : 0u));
-    return __uint_as_float(sgn | ((ex - 896u) << 23) | (mh << 3) | (lo >> 29));
-}
-
 // r -= (A_0 e) for one cell, A_0 the homogeneous operator, formed without
 // rounding: the FP32 neighbour sum is split by TwoSum into a value and its
 // exact error (products by -6 and -2 are exact up to one FMA term), and both
