@@ -727,7 +727,7 @@ k_update_residual4(const LevelGeom g, double* __restrict__ phi, const float* __r
         int idx = k0 * plane + j * nx + i0;
         float4 c = ld_f4(e + idx);
         float4 zm = k0 > 0 ? ld_f4(e + idx - plane) : (pz ? ld_f4(e + idx + (nz - 1) * plane) : neg_f4(c));
-#pragma unroll 2
+#pragma unroll 1
         for (int k = k0; k < k1; ++k, idx += plane) {
             const float4 zp = k < nz - 1 ? ld_f4(e + idx + plane) : (pz ? ld_f4(e + idx - (nz - 1) * plane) : neg_f4(c));
             const float4 ym = j > 0 ? ld_f4(e + idx - nx) : (py ? ld_f4(e + idx + (ny - 1) * nx) : neg_f4(c));
