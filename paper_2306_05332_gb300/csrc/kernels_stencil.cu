@@ -9,6 +9,7 @@
 // These are HBM-bandwidth-bound kernels; no tensor cores are involved.
 #include "sg_internal.cuh"
 
+#include <algorithm>
 #include <cstdint>
 #include <type_traits>
 
@@ -278,6 +279,119 @@ k_residual(const LevelGeom g, const TI* __restrict__ u, const TI* __restrict__ r
     }
     const int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
     block_reduce_write<A>(sq, mx, A(0), partials, bid);
+}
+
+// The residual of phi = 0 (f minus the face terms) for an FP32 output, in two
+// launches so that no warp runs the FP64 face arithmetic for cells off the
+// walls: every cell's r = f by 4-cell strips (the norm over the cells without a
+// face term), then the cells next to a Dirichlet wall with face data, each
+// counted once, with their face terms and their share of the norm.
+__device__ __forceinline__ bool face_cell(const LevelGeom& g, int i, int j, int k) {
+    return (!g.per[0] && ((i == 0 && g.face[0]) || (i == g.nx - 1 && g.face[1]))) ||
+           (!g.per[1] && ((j == 0 && g.face[2]) || (j == g.ny - 1 && g.face[3]))) ||
+           (!g.per[2] && ((k == 0 && g.face[4]) || (k == g.nz - 1 && g.face[5])));
+}
+
+// f minus the face terms of cell (i, j, k) (the Laplacian of zero with the
+// Dirichlet ghosts 2 face - 0).
+template <bool UNIFORM>
+__device__ __forceinline__ double zero_face_residual(const LevelGeom& g, const double* rhs, int i, int j, int k) {
+    const int idx = (k * g.ny + j) * g.nx + i;
+    const bool dx = !g.per[0], dy = !g.per[1], dz = !g.per[2];
+    double xm = 0.0, xp = 0.0, ym = 0.0, yp = 0.0, zm = 0.0, zp = 0.0;
+    const int fx = k * g.ny + j, fy = k * g.nx + i, fz = j * g.nx + i;
+    if (dx && i == 0 && g.face[0]) xm = 2.0 * g.face[0][fx];
+    if (dx && i == g.nx - 1 && g.face[1]) xp = 2.0 * g.face[1][fx];
+    if (dy && j == 0 && g.face[2]) ym = 2.0 * g.face[2][fy];
+    if (dy && j == g.ny - 1 && g.face[3]) yp = 2.0 * g.face[3][fy];
+    if (dz && k == 0 && g.face[4]) zm = 2.0 * g.face[4][fz];
+    if (dz && k == g.nz - 1 && g.face[5]) zp = 2.0 * g.face[5][fz];
+    if (UNIFORM) {
+        const double s6 = ((xm + xp) + (ym + yp)) + (zm + zp);
+        return fma(-g.ihx2, fma(-6.0, 0.0, s6), rhs[idx]);
+    }
+    return rhs[idx] - lap7(0.0, xm, xp, ym, yp, zm, zp, g.ihx2, g.ihy2, g.ihz2);
+}
+
+constexpr int kWallBlocks = 256;
+
+__global__ void __launch_bounds__(BX * BY)
+k_residual_zero4(const LevelGeom g, const double* __restrict__ rhs, float* __restrict__ r_out,
+                 double* __restrict__ r_full, Partial* partials, int kchunk) {
+    const int q = blockIdx.x * BX + threadIdx.x;        // strip: cells 4q .. 4q + 3
+    const int j = blockIdx.y * BY + threadIdx.y;
+    float sq = 0.0f, mx = 0.0f;
+    if (4 * q < g.nx && j < g.ny) {
+        const int i0 = 4 * q, plane = g.nx * g.ny;
+        const int k0 = blockIdx.z * kchunk;
+        const int k1 = min(k0 + kchunk, g.nz);
+        int idx = k0 * plane + j * g.nx + i0;
+#pragma unroll 2
+        for (int k = k0; k < k1; ++k, idx += plane) {
+            const double2 a = ld_d2(rhs + idx), b = ld_d2(rhs + idx + 2);
+            if (r_full) {
+                *reinterpret_cast<double2*>(r_full + idx) = a;
+                *reinterpret_cast<double2*>(r_full + idx + 2) = b;
+            }
+            const float4 v = make_float4(d2f_bits(a.x), d2f_bits(a.y), d2f_bits(b.x), d2f_bits(b.y));
+            if (r_out) *reinterpret_cast<float4*>(r_out + idx) = v;
+            const float c[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const float x = face_cell(g, i0 + e, j, k) ? 0.0f : c[e];     // wall cells: the second pass
+                sq = fmaf(x, x, sq);
+                mx = fmaxf(mx, fabsf(x));
+            }
+        }
+    }
+    const int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+    block_reduce_write<float>(sq, mx, 0.0f, partials, bid);
+}
+
+// The cells next to a Dirichlet wall with face data, each once: the x faces
+// whole, the y faces without the x-face columns, the z faces without both.
+template <bool UNIFORM>
+__global__ void __launch_bounds__(BX * BY)
+k_residual_zero_walls(const LevelGeom g, const double* __restrict__ rhs, float* __restrict__ r_out,
+                      double* __restrict__ r_full, Partial* partials) {
+    const bool dx = !g.per[0], dy = !g.per[1], dz = !g.per[2];
+    const bool fx0 = dx && g.face[0], fx1 = dx && g.face[1] && g.nx > 1;
+    const bool fy0 = dy && g.face[2], fy1 = dy && g.face[3] && g.ny > 1;
+    const bool fz0 = dz && g.face[4], fz1 = dz && g.face[5] && g.nz > 1;
+    const int ilo = fx0 ? 1 : 0, ihi = fx1 ? g.nx - 2 : g.nx - 1, nxi = max(0, ihi - ilo + 1);
+    const int jlo = fy0 ? 1 : 0, jhi = fy1 ? g.ny - 2 : g.ny - 1, nyj = max(0, jhi - jlo + 1);
+    const long long sx = (long long)g.ny * g.nz, sy = (long long)nxi * g.nz, sz = (long long)nxi * nyj;
+    const long long seg[6] = {fx0 ? sx : 0, fx1 ? sx : 0, fy0 ? sy : 0, fy1 ? sy : 0, fz0 ? sz : 0, fz1 ? sz : 0};
+    const long long total = seg[0] + seg[1] + seg[2] + seg[3] + seg[4] + seg[5];
+    const int tid = threadIdx.x + threadIdx.y * BX;
+    float sq = 0.0f, mx = 0.0f;
+    for (long long t = (long long)blockIdx.x * (BX * BY) + tid; t < total; t += (long long)gridDim.x * (BX * BY)) {
+        long long u = t;
+        int s = 0;
+        while (u >= seg[s]) u -= seg[s++];
+        int i, j, k;
+        if (s < 2) {                                     // x face: (j, k)
+            i = s == 0 ? 0 : g.nx - 1;
+            j = (int)(u % g.ny);
+            k = (int)(u / g.ny);
+        } else if (s < 4) {                              // y face: (i, k)
+            j = s == 2 ? 0 : g.ny - 1;
+            i = ilo + (int)(u % nxi);
+            k = (int)(u / nxi);
+        } else {                                         // z face: (i, j)
+            k = s == 4 ? 0 : g.nz - 1;
+            i = ilo + (int)(u % nxi);
+            j = jlo + (int)(u / nxi);
+        }
+        const double r = zero_face_residual<UNIFORM>(g, rhs, i, j, k);
+        const int idx = (k * g.ny + j) * g.nx + i;
+        const float ro = d2f_bits(r);
+        if (r_out) r_out[idx] = ro;
+        if (r_full) r_full[idx] = r;
+        sq = fmaf(ro, ro, sq);
+        mx = fmaxf(mx, fabsf(ro));
+    }
+    block_reduce_write<float>(sq, mx, 0.0f, partials, blockIdx.x);
 }
 
 // The same residual for u = 0 (a solve that starts from a zero potential):
@@ -860,6 +974,12 @@ long long residual_blocks(const LevelGeom& g) {
     return (long long)((g.nx + BX - 1) / BX) * ((g.ny + BY - 1) / BY) * ((g.nz + kc - 1) / kc);
 }
 
+long long residual_zero_blocks(const LevelGeom& g) {
+    const int kc = kchunk_for(g, 4 * BX, BY);
+    const long long strips = (long long)((g.nx / 4 + BX - 1) / BX) * ((g.ny + BY - 1) / BY) * ((g.nz + kc - 1) / kc);
+    return std::max(residual_blocks(g), strips + kWallBlocks);
+}
+
 long long restrict_blocks(const LevelGeom& g) {
     const int kc = even_kchunk(g);
     return (long long)((g.nx + BX - 1) / BX) * ((g.ny + BY - 1) / BY) * ((g.nz + kc - 1) / kc);
@@ -901,7 +1021,30 @@ cudaError_t launch_stage(const LevelGeom& g, int order, bool first, const StageC
 
 template <typename TO>
 cudaError_t launch_residual_zero(const LevelGeom& g, const double* rhs, TO* r_out, Partial* partials,
-                                 int* nblocks_out, cudaStream_t st, double* r_full) {
+                                 int* nblocks_out, cudaStream_t st, double* r_full, int* nkernels) {
+    if (nkernels) *nkernels = 1;
+    if constexpr (std::is_same<TO, float>::value) {
+        const bool aligned = ((reinterpret_cast<uintptr_t>(rhs) | reinterpret_cast<uintptr_t>(r_out) |
+                               reinterpret_cast<uintptr_t>(r_full)) & 15) == 0;
+        if ((g.nx & 3) == 0 && aligned) {
+            const int kc = kchunk_for(g, 4 * BX, BY);
+            dim3 block(BX, BY, 1);
+            dim3 grid((unsigned)((g.nx / 4 + BX - 1) / BX), (unsigned)((g.ny + BY - 1) / BY),
+                      (unsigned)((g.nz + kc - 1) / kc));
+            const int nb = (int)(grid.x * grid.y * grid.z);
+            k_residual_zero4<<<grid, block, 0, st>>>(g, rhs, r_out, r_full, partials, kc);
+            int nw = 0;
+            if (has_faces(g)) {
+                nw = kWallBlocks;
+                const bool uniform = g.ihx2 == g.ihy2 && g.ihy2 == g.ihz2;
+                if (uniform) k_residual_zero_walls<true><<<nw, block, 0, st>>>(g, rhs, r_out, r_full, partials + nb);
+                else k_residual_zero_walls<false><<<nw, block, 0, st>>>(g, rhs, r_out, r_full, partials + nb);
+            }
+            if (nblocks_out) *nblocks_out = nb + nw;
+            if (nkernels) *nkernels = nw > 0 ? 2 : 1;
+            return cudaGetLastError();
+        }
+    }
     const int kc = kchunk_for(g, BX, BY);                        // the blocks of launch_residual
     dim3 block(BX, BY, 1);
     dim3 grid((g.nx + BX - 1) / BX, (g.ny + BY - 1) / BY, (g.nz + kc - 1) / kc);
@@ -1050,9 +1193,9 @@ template cudaError_t launch_stage<double>(const LevelGeom&, int, bool, const Sta
                                           const double*, const double*, const double*,
                                           const double*, double*, double*, cudaStream_t);
 template cudaError_t launch_residual_zero<double>(const LevelGeom&, const double*, double*, Partial*, int*,
-                                                  cudaStream_t, double*);
+                                                  cudaStream_t, double*, int*);
 template cudaError_t launch_residual_zero<float>(const LevelGeom&, const double*, float*, Partial*, int*,
-                                                 cudaStream_t, double*);
+                                                 cudaStream_t, double*, int*);
 template cudaError_t launch_residual<double, double>(const LevelGeom&, const double*, const double*,
                                                      double*, Partial*, int*, cudaStream_t, double*);
 template cudaError_t launch_residual<double, float>(const LevelGeom&, const double*, const double*,

@@ -654,17 +654,17 @@ sg_status level0_residual(sg_grid* g, const double* phi, const double* f, bool f
 
 // level0_residual for phi = 0 (no read of phi, no FP64 stencil).
 sg_status level0_residual_zero(sg_grid* g, const double* f, bool faces) {
-    int nb = 0;
+    int nb = 0, nk = 1;
     const LevelGeom G = geom(g, 0, faces);
     {
     ProfScope ps(g, K_RES0, double(g->lv[0].n) * (g->precision == SG_MIXED ? 20.0 : 8.0));
     if (g->precision == SG_MIXED)
-        SG_CK(launch_residual_zero<float>(G, f, (float*)g->lv[0].rhs, g->partials, &nb, g->st, g->r64));
+        SG_CK(launch_residual_zero<float>(G, f, (float*)g->lv[0].rhs, g->partials, &nb, g->st, g->r64, &nk));
     else
-        SG_CK(launch_residual_zero<double>(G, f, (double*)nullptr, g->partials, &nb, g->st));
+        SG_CK(launch_residual_zero<double>(G, f, (double*)nullptr, g->partials, &nb, g->st, nullptr, &nk));
     }
     SG_CK(launch_finalize(g->partials, nb, g->red, g->st));
-    g->launches += 2;
+    g->launches += nk + 1;
     return SG_OK;
 }
 
@@ -1066,6 +1066,7 @@ sg_status sg_create_grid(int nx, int ny, int nz, const double lo[3], const doubl
         g->lv.push_back(L);
         const LevelGeom G = geom(g, l, false);
         max_blocks = std::max(max_blocks, residual_blocks(G));
+        if (l == 0) max_blocks = std::max(max_blocks, residual_zero_blocks(geom(g, 0, true)));
         if (l + 1 < g->max_levels) max_blocks = std::max(max_blocks, restrict_blocks(G));
     }
     const long long n0 = (long long)nx * ny * nz;

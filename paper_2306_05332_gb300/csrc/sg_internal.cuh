@@ -64,6 +64,7 @@ constexpr int kRedThreads = 256;
 // ---- launchers (kernels_stencil.cu) ----------------------------------------
 // Number of blocks (= Partial slots) a residual / residual-restrict launch uses.
 long long residual_blocks(const LevelGeom& g);
+long long residual_zero_blocks(const LevelGeom& g);   // launch_residual_zero, both passes
 long long restrict_blocks(const LevelGeom& g);
 constexpr long long kSumBlocks = 152LL * 8;     // grid of the 1D reduction kernels
 
@@ -77,10 +78,12 @@ cudaError_t launch_stage(const LevelGeom& g, int order, bool first, const StageC
 template <typename TI, typename TO>
 cudaError_t launch_residual(const LevelGeom& g, const TI* u, const TI* rhs, TO* r_out,
                             Partial* partials, int* nblocks_out, cudaStream_t st, TI* r_full = nullptr);
-// The same for u = 0 (FP64 rhs): r = rhs - L 0, the face terms only.
+// The same for u = 0 (FP64 rhs): r = rhs - L 0, the face terms only
+// (*nkernels: the kernels it launched, one or two).
 template <typename TO>
 cudaError_t launch_residual_zero(const LevelGeom& g, const double* rhs, TO* r_out, Partial* partials,
-                                 int* nblocks_out, cudaStream_t st, double* r_full = nullptr);
+                                 int* nblocks_out, cudaStream_t st, double* r_full = nullptr,
+                                 int* nkernels = nullptr);
 
 // Fused residual + 8-cell restriction (+ norm partials, + coarse sum partials).
 template <typename T>
