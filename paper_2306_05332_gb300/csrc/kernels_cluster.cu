@@ -47,10 +47,12 @@ __device__ __forceinline__ float lap7f(float c, float xm, float xp, float ym, fl
     return ((xm - two_c) + xp) * hx + ((ym - two_c) + yp) * hy + ((zm - two_c) + zp) * hz;
 }
 
-// A field of one level: (pz + 2) planes of (ny + 2) rows of (nx + 2) floats.
+// A field of level B: (pz + 2) planes of (ny + 2) rows of nx + 8 floats, the
+// interior of a row at offset 4 (4-cell strips are 16-byte aligned) and its x
+// ghosts at offsets 3 and nx + 4.
 struct Slab {
     int nx, ny, pz, row, plane;
-    __device__ int at(int k, int j, int i) const { return (k + 1) * plane + (j + 1) * row + (i + 1); }
+    __device__ int at(int k, int j, int i) const { return (k + 1) * plane + (j + 1) * row + 4 + i; }
 };
 
 __device__ __forceinline__ Slab make_slab(int nx, int ny, int pz) {
@@ -58,8 +60,8 @@ __device__ __forceinline__ Slab make_slab(int nx, int ny, int pz) {
     s.nx = nx;
     s.ny = ny;
     s.pz = pz;
-    s.row = nx + 2;
-    s.plane = (nx + 2) * (ny + 2);
+    s.row = nx + 8;
+    s.plane = (nx + 8) * (ny + 2);
     return s;
 }
 
@@ -69,40 +71,47 @@ struct Ctx {
     bool px, py, pz;
 };
 
-// v at interior cell (k, j, i) of field `f` (offset in the CTA's shared
-// memory), with the x / y ghosts of this CTA and the z ghost plane of the
-// neighbouring CTA (or of this CTA at a wall).
-__device__ __forceinline__ void put(const Ctx& c, float* sm, int f, const Slab& s, int k, int j, int i, float v) {
+__device__ __forceinline__ float4 ld4b(const float* p) { return *reinterpret_cast<const float4*>(p); }
+__device__ __forceinline__ void st4b(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
+__device__ __forceinline__ float4 negb(float4 v) { return make_float4(-v.x, -v.y, -v.z, -v.w); }
+
+// The strip of cells 4q .. 4q + 3 of row j, plane k of field `f`, with its
+// ghosts as put() writes them for single cells.
+__device__ __forceinline__ void put4(const Ctx& c, float* sm, int f, const Slab& s, int k, int j, int q, float4 v) {
     float* fl = sm + f;
-    fl[s.at(k, j, i)] = v;
-    if (i == 0) fl[s.at(k, j, c.px ? s.nx : -1)] = c.px ? v : -v;
-    if (i == s.nx - 1) fl[s.at(k, j, c.px ? -1 : s.nx)] = c.px ? v : -v;
-    if (j == 0) fl[s.at(k, c.py ? s.ny : -1, i)] = c.py ? v : -v;
-    if (j == s.ny - 1) fl[s.at(k, c.py ? -1 : s.ny, i)] = c.py ? v : -v;
+    const int o = s.at(k, j, 4 * q);
+    st4b(fl + o, v);
+    if (q == 0) fl[c.px ? s.at(k, j, s.nx) : o - 1] = c.px ? v.x : -v.x;
+    if (4 * q + 4 == s.nx) fl[c.px ? s.at(k, j, -1) : o + 4] = c.px ? v.w : -v.w;
+    if (j == 0) st4b(fl + s.at(k, c.py ? s.ny : -1, 4 * q), c.py ? v : negb(v));
+    if (j == s.ny - 1) st4b(fl + s.at(k, c.py ? -1 : s.ny, 4 * q), c.py ? v : negb(v));
     if (k == 0) {
         if (c.rank > 0 || c.pz) {
             const int peer = c.rank > 0 ? c.rank - 1 : c.nc - 1;
-            float* r = c.cl.map_shared_rank(sm, peer) + f;
-            r[s.at(s.pz, j, i)] = v;
+            st4b(c.cl.map_shared_rank(sm, peer) + f + s.at(s.pz, j, 4 * q), v);
         } else {
-            fl[s.at(-1, j, i)] = -v;
+            st4b(fl + s.at(-1, j, 4 * q), negb(v));
         }
     }
     if (k == s.pz - 1) {
         if (c.rank < c.nc - 1 || c.pz) {
             const int peer = c.rank < c.nc - 1 ? c.rank + 1 : 0;
-            float* r = c.cl.map_shared_rank(sm, peer) + f;
-            r[s.at(-1, j, i)] = v;
+            st4b(c.cl.map_shared_rank(sm, peer) + f + s.at(-1, j, 4 * q), v);
         } else {
-            fl[s.at(s.pz, j, i)] = -v;
+            st4b(fl + s.at(s.pz, j, 4 * q), negb(v));
         }
     }
 }
 
-__device__ __forceinline__ float lap_at(const float* y, const Slab& s, int k, int j, int i, float hx, float hy,
-                                        float hz) {
-    const int o = s.at(k, j, i);
-    return lap7f(y[o], y[o - 1], y[o + 1], y[o - s.row], y[o + s.row], y[o - s.plane], y[o + s.plane], hx, hy, hz);
+// L of the strip at offset o of field y (cell by cell as lap_at).
+__device__ __forceinline__ float4 lap4b(const float* y, const Slab& s, int o, float hx, float hy, float hz) {
+    const float4 cc = ld4b(y + o), ym = ld4b(y + o - s.row), yp = ld4b(y + o + s.row);
+    const float4 zm = ld4b(y + o - s.plane), zp = ld4b(y + o + s.plane);
+    const float xl = y[o - 1], xr = y[o + 4];
+    return make_float4(lap7f(cc.x, xl, cc.y, ym.x, yp.x, zm.x, zp.x, hx, hy, hz),
+                       lap7f(cc.y, cc.x, cc.z, ym.y, yp.y, zm.y, zp.y, hx, hy, hz),
+                       lap7f(cc.z, cc.y, cc.w, ym.z, yp.z, zm.z, zp.z, hx, hy, hz),
+                       lap7f(cc.w, cc.z, xr, ym.w, yp.w, zm.w, zp.w, hx, hy, hz));
 }
 
 // Sum of v over the block, fixed order; every thread gets the result.
@@ -181,15 +190,30 @@ __global__ void __launch_bounds__(1024) k_bottom_levels(const __grid_constant__ 
     const int F = 0, E = fb, U = 2 * fb, FC = 6 * fb;
     const int nfl = FC + ncc;
     const int tid = threadIdx.x;
-    const bool act_b = tid < nx * ny, act_c = tid < cnx * cny;
-    const int i = act_b ? tid % nx : 0, j = act_b ? tid / nx : 0;
+    const bool act_c = tid < cnx * cny;
     const int I = act_c ? tid % cnx : 0, J = act_c ? tid / cnx : 0;
     const float hx = p.hx, hy = p.hy, hz = p.hz;
+    // level B by strips of four x cells: strip t is (q, j, k) = (t % nq, t / nq % ny,
+    // t / (nq ny)); a thread owns strips tid and tid + blockDim (the plan keeps
+    // nq ny pz <= 2 blockDim)
+    const int nqb = nx >> 2, nsb = nqb * ny * pz;
+    int sq_[2], sj_[2], sk_[2], so_[2];
+#pragma unroll
+    for (int a = 0; a < 2; ++a) {
+        const int t = min(tid + a * (int)blockDim.x, nsb - 1);
+        sq_[a] = t % nqb;
+        sj_[a] = (t / nqb) % ny;
+        sk_[a] = t / (nqb * ny);
+        so_[a] = sb.at(sk_[a], sj_[a], 4 * sq_[a]);
+    }
+    const int ns = tid < nsb ? (tid + (int)blockDim.x < nsb ? 2 : 1) : 0;
 
     for (int t = tid; t < nfl; t += blockDim.x) sm[t] = 0.0f;
     c.cl.sync();                                 // no peer writes a ghost before it is cleared
-    if (act_b)
-        for (int k = 0; k < pz; ++k) sm[F + sb.at(k, j, i)] = p.rhs[((size_t)(c.rank * pz + k) * ny + j) * nx + i];
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+        if (a < ns) st4b(sm + F + so_[a],
+             ld4b(p.rhs + ((size_t)(c.rank * pz + sk_[a]) * ny + sj_[a]) * nx + 4 * sq_[a]));
     __syncthreads();
 
     // ---- smoothing super-steps of level B (App. A, Eq. RKL_intermediate_source)
@@ -202,22 +226,42 @@ __global__ void __launch_bounds__(1024) k_bottom_levels(const __grid_constant__ 
             const int out = spare[(js - 1) % 3];
             const int ym1 = js == 1 ? y0 : spare[(js - 2) % 3];
             const int ym2 = js == 2 ? y0 : spare[js % 3];         // (js - 3) mod 3
-            if (act_b) {
-                for (int k = 0; k < pz; ++k) {
-                    const int o = sb.at(k, j, i);
-                    const float cc = sm[ym1 + o];
-                    const float Lf = lap_at(sm + ym1, sb, k, j, i, hx, hy, hz) - sm[F + o];
-                    float v;
-                    if (js == 1) {
-                        const float z = p.tau * Lf;
-                        v = cc + p.mut1 * z;
-                        if (p.order == 2) sm[Z + o] = z;
-                    } else {
-                        v = p.mu[js] * cc + p.nu[js] * sm[ym2 + o] + p.mut_tau[js] * Lf;
-                        if (p.order == 2) v = v + p.c0[js] * sm[y0 + o] + p.gt[js] * sm[Z + o];
+#pragma unroll
+        #pragma unroll
+    for (int a = 0; a < 2; ++a) {
+        if (a >= ns) break;
+                const int o = so_[a];
+                const float4 cc = ld4b(sm + ym1 + o), fv = ld4b(sm + F + o);
+                const float4 L = lap4b(sm + ym1, sb, o, hx, hy, hz);
+                const float cv[4] = {cc.x, cc.y, cc.z, cc.w}, lv[4] = {L.x, L.y, L.z, L.w};
+                const float fw[4] = {fv.x, fv.y, fv.z, fv.w};
+                float v[4];
+                if (js == 1) {
+                    float zz[4];
+#pragma unroll
+                    for (int e2 = 0; e2 < 4; ++e2) {
+                        const float Lf = lv[e2] - fw[e2];
+                        zz[e2] = p.tau * Lf;
+                        v[e2] = cv[e2] + p.mut1 * zz[e2];
                     }
-                    put(c, sm, out, sb, k, j, i, v);
+                    if (p.order == 2) st4b(sm + Z + o, make_float4(zz[0], zz[1], zz[2], zz[3]));
+                } else {
+                    const float4 pm = ld4b(sm + ym2 + o);
+                    const float pv[4] = {pm.x, pm.y, pm.z, pm.w};
+                    float yv[4] = {0.f, 0.f, 0.f, 0.f}, zv[4] = {0.f, 0.f, 0.f, 0.f};
+                    if (p.order == 2) {
+                        const float4 y4 = ld4b(sm + y0 + o), z4 = ld4b(sm + Z + o);
+                        yv[0] = y4.x; yv[1] = y4.y; yv[2] = y4.z; yv[3] = y4.w;
+                        zv[0] = z4.x; zv[1] = z4.y; zv[2] = z4.z; zv[3] = z4.w;
+                    }
+#pragma unroll
+                    for (int e2 = 0; e2 < 4; ++e2) {
+                        const float Lf = lv[e2] - fw[e2];
+                        v[e2] = p.mu[js] * cv[e2] + p.nu[js] * pv[e2] + p.mut_tau[js] * Lf;
+                        if (p.order == 2) v[e2] = v[e2] + p.c0[js] * yv[e2] + p.gt[js] * zv[e2];
+                    }
                 }
+                put4(c, sm, out, sb, sk_[a], sj_[a], sq_[a], make_float4(v[0], v[1], v[2], v[3]));
             }
             c.cl.sync();
         }
@@ -239,11 +283,13 @@ __global__ void __launch_bounds__(1024) k_bottom_levels(const __grid_constant__ 
 
     // ---- r_B = f_B - L e_B, restricted by the 8-child mean into f_C, which
     // every CTA receives whole
-    if (act_b)
-        for (int k = 0; k < pz; ++k) {
-            const int o = sb.at(k, j, i);
-            sm[Z + o] = sm[F + o] - lap_at(sm + e, sb, k, j, i, hx, hy, hz);
-        }
+#pragma unroll
+    for (int a = 0; a < 2; ++a) {
+        if (a >= ns) break;
+        const int o = so_[a];
+        const float4 fv = ld4b(sm + F + o), L = lap4b(sm + e, sb, o, hx, hy, hz);
+        st4b(sm + Z + o, make_float4(fv.x - L.x, fv.y - L.y, fv.z - L.z, fv.w - L.w));
+    }
     __syncthreads();
     if (act_c)
         for (int K = 0; K < cpz; ++K) {
@@ -373,43 +419,53 @@ __global__ void __launch_bounds__(1024) k_bottom_levels(const __grid_constant__ 
         sm[EC + t] = sg * sm[y_cur + (sk * cny + sj) * cnx + si];
     }
     __syncthreads();
-    if (act_b) {
-        const int Ia = i >> 1, Ja = j >> 1;
-        const int Ib = Ia + ((i & 1) ? 1 : -1), Jb = Ja + ((j & 1) ? 1 : -1);
+    {
         const float* ec = sm + EC;
-        auto q = [&](int K) {
-            return 9.0f * ec[sf.at(K, Ja, Ia)] + 3.0f * ec[sf.at(K, Ja, Ib)] + 3.0f * ec[sf.at(K, Jb, Ia)] +
-                   ec[sf.at(K, Jb, Ib)];
-        };
         const float w = 1.0f / 64.0f;
-        for (int k = 0; k < pz; k += 2) {
-            const int K = (c.rank * pz + k) >> 1;
-            const float qm = q(K - 1), q0 = q(K), qp = q(K + 1);
-            const int o0 = sb.at(k, j, i), o1 = sb.at(k + 1, j, i);
-            put(c, sm, e, sb, k, j, i, sm[e + o0] + (3.0f * q0 + qm) * w);
-            put(c, sm, e, sb, k + 1, j, i, sm[e + o1] + (3.0f * q0 + qp) * w);
+    #pragma unroll
+    for (int a = 0; a < 2; ++a) {
+        if (a >= ns) break;
+            const int j = sj_[a], kk = c.rank * pz + sk_[a];
+            const int Ja = j >> 1, Jb = Ja + ((j & 1) ? 1 : -1);
+            const int K = kk >> 1, Ko = (kk & 1) ? K + 1 : K - 1;     // parent plane, the other one
+            const float4 old = ld4b(sm + e + so_[a]);
+            const float ov[4] = {old.x, old.y, old.z, old.w};
+            float v[4];
+#pragma unroll
+            for (int e2 = 0; e2 < 4; ++e2) {
+                const int i = 4 * sq_[a] + e2;
+                const int Ia = i >> 1, Ib = Ia + ((i & 1) ? 1 : -1);
+                const float q0 = 9.0f * ec[sf.at(K, Ja, Ia)] + 3.0f * ec[sf.at(K, Ja, Ib)] +
+                                 3.0f * ec[sf.at(K, Jb, Ia)] + ec[sf.at(K, Jb, Ib)];
+                const float qo = 9.0f * ec[sf.at(Ko, Ja, Ia)] + 3.0f * ec[sf.at(Ko, Ja, Ib)] +
+                                 3.0f * ec[sf.at(Ko, Jb, Ia)] + ec[sf.at(Ko, Jb, Ib)];
+                v[e2] = ov[e2] + (3.0f * q0 + qo) * w;
+            }
+            put4(c, sm, e, sb, sk_[a], j, sq_[a], make_float4(v[0], v[1], v[2], v[3]));
         }
     }
     c.cl.sync();
 
     for (int n = 0; n < p.n_post; ++n) superstep();
 
-    if (act_b)
-        for (int k = 0; k < pz; ++k) p.u_out[((size_t)(c.rank * pz + k) * ny + j) * nx + i] = sm[e + sb.at(k, j, i)];
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+        if (a < ns) st4b(p.u_out + ((size_t)(c.rank * pz + sk_[a]) * ny + sj_[a]) * nx + 4 * sq_[a], ld4b(sm + e + so_[a]));
     c.cl.sync();                                  // peers may still write this CTA's ghosts until here
 }
 
 // Shared memory of one CTA, or 0 where level C does not split into 4-cell
-// strips, has more strips than the CTA has threads, or does not fit (two
-// dense iterates and a ghosted copy) in the region of four level-B slab
-// fields.
+// strips, has more strips than the CTA has threads, level B has more strips
+// than twice the threads, or level C does not fit (two dense iterates and a
+// ghosted copy) in the region of four level-B slab fields.
 size_t bottom_bytes(int nx, int ny, int nz, int nc) {
     const int pz = nz / nc;
-    const size_t fb = (size_t)(nx + 2) * (ny + 2) * (pz + 2);
+    const size_t fb = (size_t)(nx + 8) * (ny + 2) * (pz + 2);
     const size_t ncc = (size_t)(nx / 2) * (ny / 2) * (nz / 2);
     const size_t ff = (size_t)(nx / 2 + 2) * (ny / 2 + 2) * (nz / 2 + 2);
     const size_t threads = ((size_t)nx * ny + 31) / 32 * 32;
-    if ((nx / 2) % 4 != 0 || ncc / 4 > threads || 3 * ncc + ff > 4 * fb) return 0;
+    const size_t strips_b = (size_t)(nx / 4) * ny * pz;
+    if ((nx / 2) % 4 != 0 || ncc / 4 > threads || strips_b > 2 * threads || 3 * ncc + ff > 4 * fb) return 0;
     return (6 * fb + ncc) * sizeof(float);
 }
 
