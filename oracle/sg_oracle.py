@@ -426,6 +426,8 @@ class Options:
     single_s: int = 0          # levels == 1: fixed s (0 = accelerated schedule)
     single_tau_frac: float = 0.0   # levels == 1: 0 = coarse_tau_frac(N)
     smoother: str = "rkl"      # "rkl" (RKL super-steps) or "gsrb" (the paper's GS-RB)
+    omega: float = 1.0         # GS-RB relaxation factor: 1 = Gauss-Seidel, (1, 2) = SOR;
+                               # 0 = App. B's SOR omega of the level (``sor_omega``)
 
 
 @dataclass
@@ -474,7 +476,8 @@ def relax(u, rhs, h, bc, faces, opts, count):
     GS-RB sweeps (Sec. 2.2.4) when opts.smoother == "gsrb"."""
     for _ in range(count):
         if opts.smoother == "gsrb":
-            u = gs_rb_sweep(u, rhs, h, bc, faces)
+            om = opts.omega if opts.omega > 0 else sor_omega(u.shape, h)
+            u = gs_rb_sweep(u, rhs, h, bc, faces, om)
         else:
             u = rkl_superstep(u, rhs, h, bc, faces, opts.rkl_order, opts.s_smooth, opts.tau_frac)
     return u
@@ -519,8 +522,9 @@ def solve(rho, lo, hi, bc, faces=None, four_pi_G=1.0, tol=1e-10, levels=0,
     residual ||L phi - f|| / ||L 0 - f|| is above tol (Sec. 2.1, Sec. 4.1).
 
     ``cycles`` forces an exact cycle count (tolerance ignored).  levels = 1 is
-    the single-level RKL solver: each "cycle" is one super-step, with the
-    accelerated schedule (opts.single_s = 0) or a fixed s.
+    the single-level solver: each "cycle" is one RKL1 super-step, with the
+    accelerated schedule (opts.single_s = 0) or a fixed s, or, with
+    opts.smoother == "gsrb", one red-black Gauss-Seidel / SOR sweep (App. B).
     Returns (phi, SolveInfo).
     """
     opts = opts or Options()
@@ -537,7 +541,8 @@ def solve(rho, lo, hi, bc, faces=None, four_pi_G=1.0, tol=1e-10, levels=0,
     r0 = info.r0 if info.r0 > 0 else 1.0
     N = max(shape)
     single_c = opts.single_tau_frac if opts.single_tau_frac > 0 else coarse_tau_frac(N)
-    sched = accelerated_schedule(N, opts.max_cycles + 1) if L == 1 and opts.single_s == 0 else None
+    single_rkl = L == 1 and opts.smoother != "gsrb"
+    sched = accelerated_schedule(N, opts.max_cycles + 1) if single_rkl and opts.single_s == 0 else None
     limit = cycles if cycles is not None else opts.max_cycles
     m = 0
     while True:
@@ -548,7 +553,9 @@ def solve(rho, lo, hi, bc, faces=None, four_pi_G=1.0, tol=1e-10, levels=0,
             break
         if m >= limit:
             break
-        if L == 1:
+        if L == 1 and not single_rkl:
+            phi = relax(phi, f, h, bc, faces, opts, 1)
+        elif L == 1:
             s = opts.single_s if opts.single_s > 0 else sched[m]
             phi = rkl_superstep(phi, f, h, bc, faces, 1, s, single_c)
         else:

@@ -41,6 +41,8 @@ def _any_pin_fails():
         lambda: T.test_solve_matches_kronecker_direct((6, 4, 8), (0, 0, 0), (1, 2, 0.5)),
         lambda: T.test_vcycle_fixed_point(),
         lambda: T.test_accelerated_schedule_skips_repeats(),
+        lambda: T.test_gsrb_sweep_radius_follows_young((4, 4, 6), (0, 0, 0)),
+        lambda: T.test_gsrb_half_sweeps_solve_their_rows((0, 0, 0)),
     ]
     failed = 0
     for pin in pins:
@@ -123,6 +125,28 @@ def m_sk_opt_floor(k, N):
     return int(math.floor(S.BESSEL_J0_FIRST_ZERO / math.pi * (N / k) - 0.5))
 
 
+def m_diagonal_no_wall(shape, h, bc):
+    # the Dirichlet ghost's -1/h^2 left out of the row's diagonal
+    return np.full(shape, -2.0 * sum(1.0 / (hd * hd) for hd in h))
+
+
+def m_gsrb_colour_by_rows(u, rhs, h, bc, faces=None, omega=1.0):
+    # colours by (j + k) only: neighbours along x share a colour
+    nz, ny, nx = u.shape
+    diag = S.operator_diagonal(u.shape, h, bc)
+    K, J, _ = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    u = u.copy()
+    for colour in (0, 1):
+        mask = ((J + K) % 2) == colour
+        r = S.laplacian(u, h, bc, faces) - rhs
+        u[mask] = u[mask] - omega * r[mask] / diag[mask]
+    return u
+
+
+def m_gsrb_omega_dropped(u, rhs, h, bc, faces=None, omega=1.0):
+    return ORIG["gs_rb_sweep"](u, rhs, h, bc, faces, 1.0)
+
+
 MUTATIONS = [
     ("restrict", m_restrict_quarter),
     ("prolong", m_prolong_wrong_direction),
@@ -135,6 +159,9 @@ MUTATIONS = [
     ("source", m_source_no_mean),
     ("coarse_tau_frac", m_coarse_tau_one),
     ("s_k_opt", m_sk_opt_floor),
+    ("operator_diagonal", m_diagonal_no_wall),
+    ("gs_rb_sweep", m_gsrb_colour_by_rows),
+    ("gs_rb_sweep", m_gsrb_omega_dropped),
 ]
 
 

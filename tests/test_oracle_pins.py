@@ -535,6 +535,90 @@ def test_sor_omega_reduces_to_textbook_cube():
     assert abs(om - 2.0 / (1.0 + math.sqrt(1.0 - rj * rj))) < 1e-14
 
 
+def _colour(shape):
+    K, J, I = np.meshgrid(*(np.arange(n) for n in shape), indexing="ij")
+    return (I + J + K) % 2
+
+
+def _sweep_matrix(shape, h, bc, omega):
+    """Iteration matrix of one oracle GS-RB sweep (rhs = 0, homogeneous ghosts)."""
+    n = int(np.prod(shape))
+    M = np.zeros((n, n))
+    for i in range(n):
+        e = np.zeros(n)
+        e[i] = 1.0
+        M[:, i] = O.gs_rb_sweep(e.reshape(shape), np.zeros(shape), h, bc, None, omega).ravel()
+    return M
+
+
+@pytest.mark.parametrize("shape,bc", [((4, 4, 6), (0, 0, 0)), ((4, 6, 4), (1, 0, 1)),
+                                      ((6, 4, 4), (0, 1, 1))])
+def test_gsrb_sweep_radius_follows_young(shape, bc):
+    # The 7-point graph is bipartite under the red-black colouring (periodic
+    # extents even), so the ordering is consistent (Young): one Gauss-Seidel
+    # sweep has spectral radius rho(J)^2, and above the optimal omega every
+    # SOR eigenvalue has modulus omega - 1.  J from the Kronecker matrix.
+    h = (0.3, 0.5, 0.4)
+    A = kron_operator(shape, h, bc)
+    J = np.eye(A.shape[0]) - A / np.diag(A)[:, None]
+    rj = max(abs(np.linalg.eigvals(J)))
+    assert 0.5 < rj < 1.0
+    rgs = max(abs(np.linalg.eigvals(_sweep_matrix(shape, h, bc, 1.0))))
+    assert abs(rgs - rj ** 2) < 1e-10
+    w_opt = 2.0 / (1.0 + math.sqrt(1.0 - rj ** 2))
+    w = 0.5 * (w_opt + 2.0)
+    mods = abs(np.linalg.eigvals(_sweep_matrix(shape, h, bc, w)))
+    np.testing.assert_allclose(mods, w - 1.0, atol=1e-6, rtol=0)
+
+
+@pytest.mark.parametrize("bc", [(0, 0, 0), (1, 0, 1)])
+def test_gsrb_half_sweeps_solve_their_rows(bc):
+    # omega = 1: the first half-sweep makes the residual of every even cell
+    # zero with the odd cells as they came in; the second makes every odd
+    # cell's residual zero.  Residuals through the Kronecker matrix and the
+    # 2 g / h^2 face vector, with Dirichlet data on the walls.
+    shape, h = (6, 4, 8), (0.3, 0.2, 0.25)
+    faces = W.random_faces(shape, 11)
+    u, f = W.random_field(shape, 12), W.random_field(shape, 13)
+    out = O.gs_rb_sweep(u, f, h, bc, faces, 1.0)
+    A = kron_operator(shape, h, bc)
+    b = np.zeros(shape)
+    if bc[0] == 0:
+        b[:, :, 0] += 2 * faces[0] / h[0] ** 2
+        b[:, :, -1] += 2 * faces[1] / h[0] ** 2
+    if bc[1] == 0:
+        b[:, 0, :] += 2 * faces[2] / h[1] ** 2
+        b[:, -1, :] += 2 * faces[3] / h[1] ** 2
+    if bc[2] == 0:
+        b[0, :, :] += 2 * faces[4] / h[2] ** 2
+        b[-1, :, :] += 2 * faces[5] / h[2] ** 2
+    res = lambda v: (A @ v.ravel()).reshape(shape) + b - f
+    odd = _colour(shape) == 1
+    half = np.where(odd, u, out)
+    scale = np.abs(f).max() + np.abs(b).max()
+    assert np.abs(res(half)[~odd]).max() < 1e-12 * scale
+    assert np.abs(res(out)[odd]).max() < 1e-12 * scale
+    assert np.abs(res(out)[~odd]).max() > 1e-3 * scale
+
+
+@pytest.mark.parametrize("omega", [1.0, 0.0])
+def test_single_level_gsrb_solve_reaches_direct_solution(omega):
+    # levels = 1 with the GS-RB smoother: Gauss-Seidel (omega = 1) or App. B's
+    # SOR (omega = 0 picks its omega) converge to the Kronecker direct solution.
+    shape, lo, hi, bc = (8, 6, 10), (0, 0, 0), (1.0, 0.6, 0.8), (0, 1, 0)
+    rho = W.random_field(shape, 21)
+    faces = W.random_faces(shape, 22)
+    opts = O.Options(smoother="gsrb", omega=omega, max_cycles=2000)
+    phi, info = O.solve(rho, lo, hi, bc, faces, 1.0, tol=1e-11, levels=1, opts=opts)
+    ref = O.dense_solve(rho, lo, hi, bc, faces, 1.0)
+    assert info.rel_residual <= 1e-11
+    assert np.linalg.norm(phi - ref) / np.linalg.norm(ref) < 1e-8
+    if omega == 0.0:
+        gs = O.solve(rho, lo, hi, bc, faces, 1.0, tol=1e-11, levels=1,
+                     opts=O.Options(smoother="gsrb", max_cycles=2000))[1]
+        assert info.cycles < gs.cycles / 2
+
+
 # ---------------------------------------------------------------------------
 # Adjoint
 # ---------------------------------------------------------------------------
