@@ -277,6 +277,33 @@ def run_reference(a, world, rank):
 # ---------------------------------------------------------------------------
 # Our arm
 # ---------------------------------------------------------------------------
+def single_level_race(sg, W, torch, stream, n=128, bound=1e-10):
+    """App. B's comparison without multigrid: Gauss-Seidel, SOR (App. B's
+    omega) and the accelerated RKL1 schedule, each a single-level FP64 solve of
+    the smooth-sphere problem of Sec. 4.1 at n^3 until max |L phi - f| <= bound.
+    Wall time of each solve (host loop included: one residual read back per
+    sweep or super-step, as each method needs for its stopping test)."""
+    p = W.smooth_sphere(n)
+    gr = sg.Grid(p.shape, p.lo, p.hi, p.bc, precision="fp64", stream=stream.cuda_stream)
+    gr.set_boundary(p.faces)
+    rho = torch.tensor(p.rho, device="cuda")
+    out = {"n": n, "max_residual_bound": bound}
+    for name, opts in (("gs", dict(smoother="gsrb", omega=1.0)), ("sor", dict(smoother="gsrb", omega=0.0)),
+                       ("rkl", dict(smoother="rkl"))):
+        gr.set_options(max_residual_tol=bound, max_cycles=200000, **opts)
+        gr.set_density(rho, p.four_pi_G)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        info = gr.solve(tol=0.0, levels=1, check=False)
+        torch.cuda.synchronize()
+        out[name] = {"ms": (time.perf_counter() - t0) * 1e3, "iterations": info["cycles"],
+                     "max_residual": info["max_residual"], "status": info["status"]}
+    for name in ("gs", "sor"):
+        out[f"{name}_over_rkl"] = out[name]["ms"] / out["rkl"]["ms"]
+    del gr
+    return out
+
+
 def run_ours(a, world, rank, local):
     import numpy as np
     import torch
@@ -415,7 +442,16 @@ def run_ours(a, world, rank, local):
         i1 = step()
         t1 = (time.perf_counter() - t0) * 1e3
         extra["rkl1_s2_smoother"] = {"solves_per_s": 1000.0 / t1, "ms": t1, "cycles": i1["cycles"]}
+        # the paper's own smoother (GS-RB sweeps, N_pre = 2, N_post = 1) in the same V-cycle
+        g.set_options(**dict(SOLVER, smoother="gsrb"))
+        step()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ig = step()
+        tg = (time.perf_counter() - t0) * 1e3
+        extra["gsrb_smoother"] = {"solves_per_s": 1000.0 / tg, "ms": tg, "cycles": ig["cycles"]}
         g.set_options(**SOLVER)
+        extra["single_level_race_128"] = single_level_race(sg, W, torch, stream)
 
     if not a.no_extra:
         # autotuned smoother for this grid, keeping the configured RKL2 order

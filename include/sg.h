@@ -57,6 +57,11 @@ typedef enum sg_bc {
     SG_BC_PERIODIC = 1           /* Eq. periodic on every level */
 } sg_bc;
 
+typedef enum sg_smoother {
+    SG_SMOOTH_RKL = 0,           /* RKL super-steps of s_smooth stages (App. A) */
+    SG_SMOOTH_GSRB = 1           /* red-black Gauss-Seidel / SOR sweeps (Sec. 2.2.4, App. B) */
+} sg_smoother;
+
 typedef enum sg_precision {
     SG_FP64 = 0,                 /* every sweep in FP64 */
     SG_MIXED = 1                 /* FP32 V-cycle on the error equation inside an FP64
@@ -74,12 +79,29 @@ typedef struct sg_options {
                                0 runs exactly coarse_max_ss super-steps             [1e-2]*/
     int    coarse_max_ss;   /* coarsest solve: cap on super-steps                   [64] */
     double coarse_tau_frac; /* coarsest solve tau / tau_max; 0 = cos^2(pi / 2N)     [0]  */
-    int    max_cycles;      /* V-cycle (or single-level super-step) cap             [100]*/
+    int    max_cycles;      /* V-cycle (or single-level super-step / sweep) cap,
+                               1 .. 10^7                                        [100]*/
     int    single_s;        /* levels == 1: fixed s; 0 = Legendre-zero schedule     [0]  */
     double single_tau_frac; /* levels == 1: tau / tau_max; 0 = cos^2(pi / 2N)       [0]  */
-    int    fixed_cycles;    /* > 0: run exactly this many cycles, ignore tol        [0]  */
+    int    fixed_cycles;    /* > 0: run exactly this many cycles (<= 10^7), ignore tol [0] */
     int    use_graph;       /* replay each V-cycle as a captured CUDA graph         [1]  */
     int    fused;           /* fused multi-stage super-step kernels where possible  [1]  */
+    int    smoother;        /* sg_smoother.  With SG_SMOOTH_GSRB one relaxation
+                               (n_pre, n_post) is one red-black sweep, every cell
+                               solving its own row (Dirichlet ghost folded into the
+                               diagonal), the even cells (i + j + k) first; levels == 1
+                               runs one sweep per cycle (App. B's single-level GS /
+                               SOR); the coarsest level keeps the RKL1 schedule; the
+                               fused and cluster kernels are not used; periodic axes
+                               need even extents on the swept levels (SG_ERR_ARG
+                               from sg_solve otherwise)                        [RKL]*/
+    double omega;           /* GS-RB relaxation factor in [0, 2): 1 = Gauss-Seidel,
+                               (1, 2) SOR, 0 = App. B's SOR omega of each level:
+                               2 / (1 + sqrt(1 - rho_J^2)), rho_J = sum_d cos(pi/n_d)
+                               / h_d^2 over sum_d 1 / h_d^2                   [1.0]*/
+    double max_residual_tol;/* > 0: stop when max |L phi - f| <= this (App. B's
+                               test) instead of the relative L2 test; tol is then
+                               ignored                                          [0]  */
 } sg_options;
 
 #define SG_MAX_HISTORY 256
@@ -95,8 +117,9 @@ typedef struct sg_solve_info {
     double r0;                          /* ||L 0 - f||_2 (volume-weighted L2, Sec. 4.1) */
     double rel_residual;                /* final ||L phi - f||_2 / r0 */
     double max_residual;                /* final max |L phi - f| */
-    double history[SG_MAX_HISTORY];     /* rel. residual before cycle m (m = 0..cycles) */
-    int    coarse_ss[SG_MAX_HISTORY];   /* coarsest-level super-steps in cycle m */
+    double history[SG_MAX_HISTORY];     /* rel. residual before cycle m (m = 0..cycles;
+                                           the first SG_MAX_HISTORY are kept) */
+    int    coarse_ss[SG_MAX_HISTORY];   /* coarsest-level super-steps in cycle m (likewise) */
     double elapsed_ms;                  /* device time of the solve (CUDA events) */
     long long stage_cell_updates;       /* sum over levels of cells x RKL stages */
     long long kernel_launches;          /* kernels launched by the solve */
@@ -205,7 +228,7 @@ typedef struct sg_tune_entry {
  * of their CUDA-event times (so per-solve set-up drops out) and score the time
  * per decade of residual reduction over cycles 2..6, bounded below by the
  * smoother's damping of the checkerboard mode (sg_tune_entry.factor); the best
- * candidate is written into the grid's options.  The trial cycles overwrite the potential
+ * candidate is written into the grid's options (smoother = SG_SMOOTH_RKL).  The trial cycles overwrite the potential
  * (call before sg_solve).  table (may be NULL) receives up to cap entries,
  * *count the number tried.  The App. A.4 spectral analysis motivates the
  * search: the best s balances the cost of s stages against the reduction of
@@ -230,11 +253,12 @@ int sg_max_levels(const sg_grid* g);
  * the compulsory reads and writes of their input and output arrays, each cell
  * counted once, independent of caching.
  * ------------------------------------------------------------------------ */
-#define SG_KERNEL_CLASSES 9
+#define SG_KERNEL_CLASSES 10
 typedef struct sg_kernel_stat {
     char      name[24];       /* rkl_stage_l0, rkl_stage_coarse, residual_l0, residual_restrict,
                                  prolong_correct, coarse_solve, update, reduce_misc,
-                                 bottom_levels (the two coarsest levels in one launch) */
+                                 bottom_levels (the two coarsest levels in one launch),
+                                 gsrb_sweep (one colour of a GS-RB sweep) */
     long long launches;
     double    ms;             /* summed event time of the launches */
     double    bytes;          /* summed algorithmic bytes */
@@ -260,6 +284,15 @@ sg_status sg_kernel_stats(const sg_grid* g, sg_kernel_stat* out);
  * s < 2 (RKL2). */
 sg_status sg_op_superstep(sg_grid* g, int level, int dtype, int order, int s, double tau_frac,
                           int homogeneous, const void* u, const void* rhs, void* out);
+
+/* One red-black Gauss-Seidel / SOR sweep (Sec. 2.2.4, App. B) of L u = rhs at
+ * `level`, in place on u: the cells with (i + j + k) even, then the odd ones,
+ * each u <- u - omega (L u - rhs) / d with d the diagonal of its row (-2 sum
+ * 1/h^2, and -1/h_d^2 per Dirichlet wall it touches).  omega in [0, 2); 0 =
+ * App. B's SOR omega of the level.  SG_ERR_ARG when a periodic axis of the
+ * level has an odd extent (the colouring would not hold across the wrap). */
+sg_status sg_op_gsrb_sweep(sg_grid* g, int level, int dtype, int homogeneous, double omega,
+                           void* u, const void* rhs);
 
 /* Residual r = rhs - L u at `level` (the negative of Eq. residual), restricted
  * to level + 1 by the 8-cell mean (Eq. restriction_example_3D) into coarse_out

@@ -42,7 +42,8 @@ class Options(ctypes.Structure):
                 ("coarse_max_ss", ctypes.c_int), ("coarse_tau_frac", ctypes.c_double),
                 ("max_cycles", ctypes.c_int), ("single_s", ctypes.c_int),
                 ("single_tau_frac", ctypes.c_double), ("fixed_cycles", ctypes.c_int),
-                ("use_graph", ctypes.c_int), ("fused", ctypes.c_int)]
+                ("use_graph", ctypes.c_int), ("fused", ctypes.c_int), ("smoother", ctypes.c_int),
+                ("omega", ctypes.c_double), ("max_residual_tol", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -61,7 +62,8 @@ class SolveInfo(ctypes.Structure):
         return {"status": STATUS.get(self.status, self.status), "cycles": n, "levels": self.levels,
                 "s_smooth": self.s_smooth, "rkl_order": self.rkl_order, "precision": self.precision,
                 "r0": self.r0, "rel_residual": self.rel_residual, "max_residual": self.max_residual,
-                "history": list(self.history[:n + 1]), "coarse_ss": list(self.coarse_ss[:n]),
+                "history": list(self.history[:min(n + 1, SG_MAX_HISTORY)]),
+                "coarse_ss": list(self.coarse_ss[:min(n, SG_MAX_HISTORY)]),
                 "elapsed_ms": self.elapsed_ms, "stage_cell_updates": self.stage_cell_updates,
                 "kernel_launches": self.kernel_launches}
 
@@ -71,7 +73,8 @@ class KernelStat(ctypes.Structure):
                 ("bytes", ctypes.c_double)]
 
 
-SG_KERNEL_CLASSES = 9
+SG_KERNEL_CLASSES = 10
+SMOOTHERS = {"rkl": 0, "gsrb": 1}
 
 
 class TuneEntry(ctypes.Structure):
@@ -108,6 +111,7 @@ _SIGS = {
     "sg_last_error": ([], ctypes.c_char_p),
     "sg_max_levels": ([_P], _I),
     "sg_op_superstep": ([_P, _I, _I, _I, _I, _D, _I, _P, _P, _P], _I),
+    "sg_op_gsrb_sweep": ([_P, _I, _I, _I, _D, _P, _P], _I),
     "sg_op_residual_restrict": ([_P, _I, _I, _I, _P, _P, _P, ctypes.POINTER(_D)], _I),
     "sg_op_prolong_correct": ([_P, _I, _I, _P, _P], _I),
     "sg_op_coarse_solve": ([_P, _I, _I, _P, _P, ctypes.POINTER(_I)], _I),
@@ -230,6 +234,8 @@ class Grid:
         for k, v in kw.items():
             if not hasattr(o, k):
                 raise KeyError(k)
+            if k == "smoother" and isinstance(v, str):
+                v = SMOOTHERS[v]
             setattr(o, k, v)
         _check(lib().sg_set_options(self._h, ctypes.byref(o)))
         return o
@@ -313,6 +319,12 @@ class Grid:
         _check(lib().sg_op_superstep(self._h, level, dt, order, s, float(tau_frac), int(homogeneous),
                                      _dev_ptr(u, dt) if u is not None else None, _dev_ptr(rhs, dt),
                                      _dev_ptr(out, dt)))
+
+    def op_gsrb_sweep(self, level, u, rhs, omega=1.0, homogeneous=False):
+        """One red-black Gauss-Seidel / SOR sweep of L u = rhs, in place on u."""
+        dt = self.dtype_code
+        _check(lib().sg_op_gsrb_sweep(self._h, level, dt, int(homogeneous), float(omega), _dev_ptr(u, dt),
+                                      _dev_ptr(rhs, dt)))
 
     def op_residual_restrict(self, level, u, rhs, coarse_out=None, homogeneous=False):
         dt = self.dtype_code

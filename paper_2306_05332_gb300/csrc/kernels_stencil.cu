@@ -196,6 +196,60 @@ k_stage(const LevelGeom g, const CoefT<T> cf, const T* __restrict__ ym1, const T
 }
 
 // ---------------------------------------------------------------------------
+// One colour of a red-black Gauss-Seidel / SOR sweep (Sec. 2.2.4, App. B).
+// Every cell with (i + j + k) % 2 == colour solves its own row of L u = rhs,
+// u <- u - omega (L u - rhs) / d, where d is the row's diagonal: -2 sum 1/h^2,
+// and -1/h_d^2 more for each Dirichlet wall the cell touches (its ghost,
+// -u or 2 phi_face - u, holds -u).  A cell of one colour has neighbours of the
+// other colour only (periodic extents even), so the update runs in place: no
+// thread reads a value another thread of the launch writes.  Each thread walks
+// the cells of its colour in its column, two planes apart, carrying the plane
+// between them from one cell's zp to the next cell's zm.
+// ---------------------------------------------------------------------------
+template <typename T, bool FACES>
+__global__ void __launch_bounds__(BX * BY)
+k_gsrb(const LevelGeom g, int colour, T omega, T* u, const T* __restrict__ rhs, int kchunk) {
+    const int i = blockIdx.x * BX + threadIdx.x;
+    const int j = blockIdx.y * BY + threadIdx.y;
+    if (i >= g.nx || j >= g.ny) return;
+    const int k0 = blockIdx.z * kchunk;
+    const int k1 = min(k0 + kchunk, g.nz);
+    const int plane = g.nx * g.ny;
+    const T ihx2 = ih2x<T>(g), ihy2 = ih2y<T>(g), ihz2 = ih2z<T>(g);
+    T dxy = T(-2) * (ihx2 + ihy2 + ihz2);
+    if (!g.per[0]) {
+        if (i == 0) dxy -= ihx2;
+        if (i == g.nx - 1) dxy -= ihx2;
+    }
+    if (!g.per[1]) {
+        if (j == 0) dxy -= ihy2;
+        if (j == g.ny - 1) dxy -= ihy2;
+    }
+    const T inv_in = T(1) / dxy;
+    int k = k0 + ((i + j + k0 + colour) & 1);
+    int idx = k * plane + j * g.nx + i;
+    T zm = T(0);
+    bool carried = false;
+    for (; k < k1; k += 2, idx += 2 * plane) {
+        const T c = u[idx];
+        if (!carried) zm = (k > 0) ? u[idx - plane] : z_low<FACES>(u, g, i, j, idx, plane, c);
+        const T zp = (k < g.nz - 1) ? u[idx + plane] : z_high<FACES>(u, g, i, j, idx, plane, c);
+        T xm, xp, ym, yp;
+        xy_neighbours<FACES>(u, g, i, j, k, idx, c, xm, xp, ym, yp);
+        const T r = lap7(c, xm, xp, ym, yp, zm, zp, ihx2, ihy2, ihz2) - rhs[idx];
+        T inv = inv_in;
+        if (!g.per[2] && (k == 0 || k == g.nz - 1)) {
+            T d = dxy - ihz2;
+            if (k == 0 && k == g.nz - 1) d -= ihz2;
+            inv = T(1) / d;
+        }
+        u[idx] = c - omega * r * inv;
+        zm = zp;
+        carried = true;
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Block reduction helpers (fixed order: deterministic).
 // ---------------------------------------------------------------------------
 // Reduction in the kernel's accumulator precision A (FP32 kernels must not
@@ -1185,7 +1239,19 @@ cudaError_t launch_sum_partials_f64(const double* x, long long n, Partial* parti
     return cudaGetLastError();
 }
 
+template <typename T>
+cudaError_t launch_gsrb(const LevelGeom& g, int colour, double omega, T* u, const T* rhs, cudaStream_t st) {
+    const int kc = kchunk_for(g, BX, BY);
+    dim3 block(BX, BY, 1);
+    dim3 grid((g.nx + BX - 1) / BX, (g.ny + BY - 1) / BY, (g.nz + kc - 1) / kc);
+    if (has_faces(g)) k_gsrb<T, true><<<grid, block, 0, st>>>(g, colour & 1, T(omega), u, rhs, kc);
+    else k_gsrb<T, false><<<grid, block, 0, st>>>(g, colour & 1, T(omega), u, rhs, kc);
+    return cudaGetLastError();
+}
+
 // Explicit instantiations.
+template cudaError_t launch_gsrb<float>(const LevelGeom&, int, double, float*, const float*, cudaStream_t);
+template cudaError_t launch_gsrb<double>(const LevelGeom&, int, double, double*, const double*, cudaStream_t);
 template cudaError_t launch_stage<float>(const LevelGeom&, int, bool, const StageCoef&, const float*,
                                          const float*, const float*, const float*, const float*,
                                          float*, float*, cudaStream_t);

@@ -156,10 +156,12 @@ int rule_levels(int nx, int ny, int nz) {
 }
 
 // Kernel classes for the optional per-kernel CUDA-event profile.
-enum KClass { K_STAGE0 = 0, K_STAGE_C, K_RES0, K_RESTRICT, K_PROLONG, K_COARSE, K_UPDATE, K_MISC, K_BOTTOM, K_NCLASS };
+enum KClass { K_STAGE0 = 0, K_STAGE_C, K_RES0, K_RESTRICT, K_PROLONG, K_COARSE, K_UPDATE, K_MISC, K_BOTTOM,
+              K_GSRB, K_NCLASS };
 const char* const kClassName[K_NCLASS] = {"rkl_stage_l0", "rkl_stage_coarse", "residual_l0",
                                           "residual_restrict", "prolong_correct", "coarse_solve",
-                                          "update_residual", "reduce_misc", "bottom_levels"};
+                                          "update_residual", "reduce_misc", "bottom_levels",
+                                          "gsrb_sweep"};
 
 struct ProfRec {
     int cls;
@@ -202,7 +204,7 @@ struct sg_grid {
     int last_levels = 0;
     // graph cache
     cudaGraphExec_t gexec = nullptr;
-    long long gkey[8] = {0};
+    long long gkey[10] = {0};
     long long graph_launches = 0;
     long long launches = 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -310,6 +312,10 @@ void prof_sync_point(sg_grid* g, bool graph_replayed) {
     prof_accumulate(g, g->live, true);
 }
 
+// Cap on cycles (single-level sweeps run tens of thousands); the info keeps
+// the first SG_MAX_HISTORY residuals.
+constexpr int kMaxCycles = 10000000;
+
 sg_status check_opts(const sg_options* o) {
     if (o->rkl_order != 1 && o->rkl_order != 2) return fail(SG_ERR_ARG, "rkl_order must be 1 or 2");
     if (o->s_smooth < 1 || (o->rkl_order == 2 && o->s_smooth < 2) || o->s_smooth > 512)
@@ -320,10 +326,14 @@ sg_status check_opts(const sg_options* o) {
     if (!(o->coarse_tol >= 0.0 && o->coarse_tol < 1.0)) return fail(SG_ERR_ARG, "coarse_tol must be in [0, 1)");
     if (o->coarse_max_ss < 1 || o->coarse_max_ss > 100000) return fail(SG_ERR_ARG, "coarse_max_ss out of range");
     if (!(o->coarse_tau_frac >= 0.0 && o->coarse_tau_frac <= 1.0)) return fail(SG_ERR_ARG, "coarse_tau_frac out of range");
-    if (o->max_cycles < 1 || o->max_cycles > SG_MAX_HISTORY - 1) return fail(SG_ERR_ARG, "max_cycles out of range");
+    if (o->max_cycles < 1 || o->max_cycles > kMaxCycles) return fail(SG_ERR_ARG, "max_cycles out of range");
     if (o->single_s < 0 || o->single_s > 100000) return fail(SG_ERR_ARG, "single_s out of range");
     if (!(o->single_tau_frac >= 0.0 && o->single_tau_frac <= 1.0)) return fail(SG_ERR_ARG, "single_tau_frac out of range");
-    if (o->fixed_cycles < 0 || o->fixed_cycles > SG_MAX_HISTORY - 1) return fail(SG_ERR_ARG, "fixed_cycles out of range");
+    if (o->fixed_cycles < 0 || o->fixed_cycles > kMaxCycles) return fail(SG_ERR_ARG, "fixed_cycles out of range");
+    if (o->smoother != SG_SMOOTH_RKL && o->smoother != SG_SMOOTH_GSRB) return fail(SG_ERR_ARG, "unknown smoother");
+    if (!(o->omega >= 0.0 && o->omega < 2.0)) return fail(SG_ERR_ARG, "omega must be in [0, 2)");
+    if (!(o->max_residual_tol >= 0.0 && o->max_residual_tol < 1e300))
+        return fail(SG_ERR_ARG, "max_residual_tol must be finite and >= 0");
     return SG_OK;
 }
 
@@ -385,8 +395,48 @@ sg_status superstep(sg_grid* g, int l, int order, int s, double tau_frac, bool f
     return SG_OK;
 }
 
+// App. B: SOR omega = 2 / (1 + sqrt(1 - rho_J^2)) with the Jacobi radius
+// rho_J = 2 dt sum_d cos(pi / n_d) / h_d^2, dt = (2 sum_d 1 / h_d^2)^-1 (the
+// printed dt read as the inverse of the whole bracket, which gives the
+// textbook Jacobi radius of a uniform cube).
+double sor_omega(const Level& L) {
+    const int n3[3] = {L.nx, L.ny, L.nz};
+    double num = 0.0, den = 0.0;
+    for (int d = 0; d < 3; ++d) {
+        const double ih2 = 1.0 / (L.h[d] * L.h[d]);
+        num += std::cos(M_PI / n3[d]) * ih2;
+        den += ih2;
+    }
+    const double rj = num / den;
+    return 2.0 / (1.0 + std::sqrt(1.0 - rj * rj));
+}
+
+double gsrb_omega(const sg_grid* g, int l) {
+    return g->opt.omega > 0.0 ? g->opt.omega : sor_omega(g->lv[l]);
+}
+
+// One red-black Gauss-Seidel / SOR sweep at level l (Sec. 2.2.4): the even
+// cells, then the odd ones, each in place.
+template <typename W>
+sg_status gsrb_sweep(sg_grid* g, int l, bool faces, W* u, const W* rhs, double omega) {
+    const LevelGeom G = geom(g, l, faces && l == 0);
+    for (int colour = 0; colour < 2; ++colour) {
+        {
+            ProfScope ps(g, K_GSRB, 2.0 * g->lv[l].n * sizeof(W));
+            SG_CK(launch_gsrb<W>(G, colour, omega, u, rhs, g->st));
+        }
+        ++g->launches;
+    }
+    return SG_OK;
+}
+
 template <typename W>
 sg_status relax(sg_grid* g, int l, int count, bool faces, W* u, const W* rhs) {
+    if (g->opt.smoother == SG_SMOOTH_GSRB) {
+        const double om = gsrb_omega(g, l);
+        for (int c = 0; c < count; ++c) SG_TRY(gsrb_sweep<W>(g, l, faces, u, rhs, om));
+        return SG_OK;
+    }
     for (int c = 0; c < count; ++c)
         SG_TRY(superstep<W>(g, l, g->opt.rkl_order, g->opt.s_smooth, g->opt.tau_frac, faces, u, rhs));
     return SG_OK;
@@ -477,7 +527,7 @@ sg_status superstep_fused(sg_grid* g, int l, int order, int s, double tau_frac, 
 constexpr long long kFusedMinCells = 1LL << 21;
 
 bool use_fused(const sg_grid* g, bool faces, int l) {
-    return g->precision == SG_MIXED && g->opt.fused && !faces && fused_supported(g->opt.rkl_order, g->opt.s_smooth) &&
+    return g->precision == SG_MIXED && g->opt.fused && !faces && g->opt.smoother == SG_SMOOTH_RKL && fused_supported(g->opt.rkl_order, g->opt.s_smooth) &&
            g->lv[l].n >= kFusedMinCells;
 }
 
@@ -487,7 +537,8 @@ bool use_fused(const sg_grid* g, bool faces, int l) {
 constexpr long long kZeroFusedMinCells = 1LL << 17;
 
 bool use_fused_zero(const sg_grid* g, bool faces, int l) {
-    return g->precision == SG_MIXED && g->opt.fused && !faces && g->opt.s_smooth <= 3 &&
+    return g->precision == SG_MIXED && g->opt.fused && !faces && g->opt.smoother == SG_SMOOTH_RKL &&
+           g->opt.s_smooth <= 3 &&
            fused_supported(g->opt.rkl_order, g->opt.s_smooth) && g->lv[l].n >= kZeroFusedMinCells;
 }
 
@@ -496,7 +547,7 @@ bool use_fused_zero(const sg_grid* g, bool faces, int l) {
 // level-by-level kernels run them.
 int bottom_nc(const sg_grid* g, int L, int* threads, size_t* bytes) {
     const int B = L - 2;
-    if (g->precision != SG_MIXED || !g->opt.fused || B < 1) return 0;
+    if (g->precision != SG_MIXED || !g->opt.fused || g->opt.smoother != SG_SMOOTH_RKL || B < 1) return 0;
     const Level& lb = g->lv[B];
     return bottom_plan(lb.nx, lb.ny, lb.nz, g->opt.s_smooth, threads, bytes);
 }
@@ -586,7 +637,7 @@ sg_status vcycle(sg_grid* g, int L, W* u0, const W* rhs0, bool faces, bool zero0
                 return relax<W>(g, l, count - 1, fc, cur[l], R(l));
             }
         }
-        if (zero_start && count > 0) SG_CK(cudaMemsetAsync(cur[l], 0, g->lv[l].n * sizeof(W), g->st));
+        if (zero_start) SG_CK(cudaMemsetAsync(cur[l], 0, g->lv[l].n * sizeof(W), g->st));   // also for count = 0
         return relax<W>(g, l, count, fc, cur[l], R(l));
     };
     int bottom_threads = 0;
@@ -711,11 +762,12 @@ sg_status run_cycle(sg_grid* g, int L, double* phi, const double* f, bool faces,
                            (g->precision == SG_MIXED ? coarse_fits<float>(g->lv[L - 1].n)
                                                      : coarse_fits<double>(g->lv[L - 1].n));
     if (!graphable) return cycle_body(g, L, phi, f, faces);
-    long long key[8] = {L, (long long)(uintptr_t)phi, (long long)(uintptr_t)f, faces ? 1 : 0,
-                        g->opt.rkl_order * 1000 + g->opt.s_smooth,
-                        g->opt.n_pre * 1000 + g->opt.n_post,
-                        (long long)std::llround(g->opt.tau_frac * 1e12),
-                        (long long)std::llround(g->opt.coarse_tol * 1e15) * 100000 + g->opt.coarse_max_ss};
+    long long key[10] = {L, (long long)(uintptr_t)phi, (long long)(uintptr_t)f, faces ? 1 : 0,
+                         g->opt.rkl_order * 1000 + g->opt.s_smooth,
+                         g->opt.n_pre * 1000 + g->opt.n_post,
+                         (long long)std::llround(g->opt.tau_frac * 1e12),
+                         (long long)std::llround(g->opt.coarse_tol * 1e15) * 100000 + g->opt.coarse_max_ss,
+                         g->opt.smoother, (long long)std::llround(g->opt.omega * 1e15)};
     long long key2 = ((long long)std::llround(g->opt.coarse_tau_frac * 1e12) * 2 + (g->prof ? 1 : 0)) * 2 +
                      (g->opt.fused ? 1 : 0);
     key[7] ^= key2 * 1315423911LL;
@@ -756,8 +808,9 @@ sg_status run_cycle(sg_grid* g, int L, double* phi, const double* f, bool faces,
 
 long long stage_updates_per_cycle(const sg_grid* g, int L) {
     long long su = 0;
+    const int per_relax = g->opt.smoother == SG_SMOOTH_GSRB ? 1 : g->opt.s_smooth;   // a sweep updates a cell once
     for (int l = 0; l < L - 1; ++l)
-        su += (long long)g->lv[l].n * (g->opt.n_pre + g->opt.n_post) * g->opt.s_smooth;
+        su += (long long)g->lv[l].n * (g->opt.n_pre + g->opt.n_post) * per_relax;
     return su;
 }
 
@@ -786,6 +839,15 @@ struct SolveState {
 // residual, the coarse schedule; leaves the residual of the start in host_red[0].
 sg_status solve_begin(sg_grid* g, SolveState& S, double tol, int L, double* phi, const double* f, bool faces,
                       bool have_guess) {
+    if (g->opt.smoother == SG_SMOOTH_GSRB) {
+        // red-black colouring must hold across a periodic wrap on every swept level
+        for (int l = 0; l < std::max(1, L - 1); ++l) {
+            const int n3[3] = {g->lv[l].nx, g->lv[l].ny, g->lv[l].nz};
+            for (int d = 0; d < 3; ++d)
+                if (g->bc[d] == SG_BC_PERIODIC && (n3[d] & 1))
+                    return fail(SG_ERR_ARG, "GS-RB smoothing needs even extents on periodic axes");
+        }
+    }
     std::memset(&S.info, 0, sizeof(S.info));
     S.info.levels = L;
     S.info.s_smooth = g->opt.s_smooth;
@@ -817,7 +879,8 @@ sg_status solve_begin(sg_grid* g, SolveState& S, double tol, int L, double* phi,
     S.rden = r0 > 0.0 ? r0 : 1.0;
     const int N0 = std::max(L0.nx, std::max(L0.ny, L0.nz));
     if (L == 1) {
-        S.single_sched = accelerated_schedule(N0, g->opt.max_cycles + 1);
+        // every distinct entry: the schedule repeats its last value (k = 1) from there on
+        S.single_sched = accelerated_schedule(N0, N0 / 2 + 2);
     } else {
         const Level& Lc = g->lv[L - 1];
         const int Nc = std::max(Lc.nx, std::max(Lc.ny, Lc.nz));
@@ -840,21 +903,26 @@ sg_status solve_begin(sg_grid* g, SolveState& S, double tol, int L, double* phi,
 // it reaches the tolerance, the true FP64 residual f - A phi is computed once to
 // confirm (and, should it not confirm, the recurrence restarts from it).
 sg_status solve_check(sg_grid* g, SolveState& S) {
+    // the stopping test: relative L2 (Sec. 4.1) or, when max_residual_tol is
+    // set, the maximum residual (App. B)
+    const double mtol = g->opt.max_residual_tol;
+    auto met = [&](double rel, double maxabs) { return mtol > 0.0 ? maxabs <= mtol : rel <= S.tol; };
     double rel = std::sqrt(g->host_red[0].sumsq / S.nn) / S.rden;
-    if (g->opt.fixed_cycles == 0 && rel <= S.tol && std::isfinite(rel) && g->precision == SG_MIXED && S.L > 1) {
+    if (g->opt.fixed_cycles == 0 && met(rel, g->host_red[0].maxabs) && std::isfinite(rel) &&
+        g->precision == SG_MIXED && S.L > 1) {
         SG_TRY(level0_residual(g, S.phi, S.f, S.faces));
         SG_CK(cudaMemcpyAsync(g->host_red, g->red, sizeof(Reduced), cudaMemcpyDeviceToHost, g->st));
         SG_CK(cudaStreamSynchronize(g->st));
         prof_sync_point(g, false);
         rel = std::sqrt(g->host_red[0].sumsq / S.nn) / S.rden;
     }
-    S.info.history[S.m] = rel;
+    if (S.m < SG_MAX_HISTORY) S.info.history[S.m] = rel;
     S.info.rel_residual = rel;
     S.info.max_residual = g->host_red[0].maxabs;
     if (!std::isfinite(rel)) {
         S.status = fail(SG_ERR_NONFINITE, "residual norm is not finite");
         S.done = true;
-    } else if (g->opt.fixed_cycles == 0 && rel <= S.tol) {
+    } else if (g->opt.fixed_cycles == 0 && met(rel, g->host_red[0].maxabs)) {
         S.done = true;
     } else if (S.m >= S.limit) {
         if (g->opt.fixed_cycles == 0) S.status = fail(SG_ERR_NOT_CONVERGED, "max_cycles reached above the tolerance");
@@ -866,7 +934,30 @@ sg_status solve_check(sg_grid* g, SolveState& S) {
 // One single-level super-step (levels == 1), its residual and norm copy.
 sg_status solve_single_step(sg_grid* g, SolveState& S) {
     const Level& L0 = g->lv[0];
-    const int s = g->opt.single_s > 0 ? g->opt.single_s : S.single_sched[S.m];
+    if (g->opt.smoother == SG_SMOOTH_GSRB) {
+        // one red-black Gauss-Seidel / SOR sweep (App. B); mixed precision sweeps
+        // the error equation from e = 0, which gives the same correction
+        const double om = gsrb_omega(g, 0);
+        if (g->precision == SG_MIXED) {
+            float* e = (float*)L0.u;
+            SG_CK(cudaMemsetAsync(e, 0, L0.n * sizeof(float), g->st));
+            SG_TRY(gsrb_sweep<float>(g, 0, false, e, (const float*)L0.rhs, om));
+            {
+                ProfScope ps(g, K_UPDATE, 20.0 * L0.n);
+                SG_CK(launch_add_f32_to_f64(S.phi, e, L0.n, g->st));
+            }
+            ++g->launches;
+        } else {
+            SG_TRY(gsrb_sweep<double>(g, 0, S.faces, S.phi, S.f, om));
+        }
+        S.su += L0.n;
+        SG_TRY(level0_residual(g, S.phi, S.f, S.faces));
+        SG_CK(cudaMemcpyAsync(g->host_red, g->red, sizeof(Reduced), cudaMemcpyDeviceToHost, g->st));
+        *g->host_ss = 0;
+        return SG_OK;
+    }
+    const int s = g->opt.single_s > 0 ? g->opt.single_s
+                                       : S.single_sched[std::min<size_t>(S.m, S.single_sched.size() - 1)];
     if (g->precision == SG_MIXED) {
         // mixed precision: an FP32 super-step on the error equation L e = r
         float* e = (float*)L0.u;
@@ -891,7 +982,7 @@ sg_status solve_single_step(sg_grid* g, SolveState& S) {
 void solve_after_cycle(sg_grid* g, SolveState& S) {
     if (S.L > 1) {
         S.su += stage_updates_per_cycle(g, S.L);
-        S.info.coarse_ss[S.m] = *g->host_ss;
+        if (S.m < SG_MAX_HISTORY) S.info.coarse_ss[S.m] = *g->host_ss;
         const Level& Lc = g->lv[S.L - 1];
         const int Nc = std::max(Lc.nx, std::max(Lc.ny, Lc.nz));
         const std::vector<int> sc = accelerated_schedule(Nc, std::max(1, *g->host_ss));
@@ -1007,6 +1098,9 @@ sg_status sg_default_options(sg_options* o) {
     o->fixed_cycles = 0;
     o->use_graph = 1;
     o->fused = 1;
+    o->smoother = SG_SMOOTH_RKL;
+    o->omega = 1.0;
+    o->max_residual_tol = 0.0;
     return SG_OK;
 }
 
@@ -1377,6 +1471,7 @@ sg_status sg_autotune(sg_grid* g, int levels, int keep_order, sg_tune_entry* tab
         g->opt.s_smooth = c.s;
         g->opt.tau_frac = c.c;
         g->opt.fused = c.fused;
+        g->opt.smoother = SG_SMOOTH_RKL;
         // Time 2 and 6 cycles (after a capture / warm-up run) and take the
         // difference, so the per-solve set-up cost drops out of the score.
         sg_solve_info info2, info6;
@@ -1464,6 +1559,23 @@ sg_status sg_op_superstep(sg_grid* g, int level, int dtype, int order, int s, do
     SG_CK(cudaMemcpyAsync(out, u, bytes, cudaMemcpyDeviceToDevice, g->st));
     if (dtype == 0) return superstep<double>(g, level, order, s, tau_frac, faces, (double*)out, (const double*)rhs);
     return superstep<float>(g, level, order, s, tau_frac, faces, (float*)out, (const float*)rhs);
+}
+
+sg_status sg_op_gsrb_sweep(sg_grid* g, int level, int dtype, int homogeneous, double omega, void* u,
+                           const void* rhs) {
+    g_err.clear();
+    SG_TRY(op_check(g, level, dtype));
+    if (!u || !rhs || u == rhs) return fail(SG_ERR_ARG, "bad pointers");
+    if (!(omega >= 0.0 && omega < 2.0)) return fail(SG_ERR_ARG, "omega must be in [0, 2)");
+    const Level& Lv = g->lv[level];
+    const int n3[3] = {Lv.nx, Lv.ny, Lv.nz};
+    for (int d = 0; d < 3; ++d)
+        if (g->bc[d] == SG_BC_PERIODIC && (n3[d] & 1))
+            return fail(SG_ERR_ARG, "GS-RB needs even extents on periodic axes");
+    const bool faces = !homogeneous && level == 0 && g->have_faces;
+    const double om = omega > 0.0 ? omega : sor_omega(Lv);
+    if (dtype == 0) return gsrb_sweep<double>(g, level, faces, (double*)u, (const double*)rhs, om);
+    return gsrb_sweep<float>(g, level, faces, (float*)u, (const float*)rhs, om);
 }
 
 sg_status sg_op_residual_restrict(sg_grid* g, int level, int dtype, int homogeneous, const void* u,

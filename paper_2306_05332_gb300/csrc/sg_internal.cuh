@@ -73,6 +73,11 @@ cudaError_t launch_stage(const LevelGeom& g, int order, bool first, const StageC
                          const T* ym1, const T* ym2, const T* y0, const T* z0, const T* rhs,
                          T* out, T* z0_out, cudaStream_t st);
 
+// One colour (0: (i + j + k) even, 1: odd) of a red-black Gauss-Seidel / SOR
+// sweep of L u = rhs, in place (periodic extents must be even).
+template <typename T>
+cudaError_t launch_gsrb(const LevelGeom& g, int colour, double omega, T* u, const T* rhs, cudaStream_t st);
+
 // r = rhs - L u (TI), optionally stored as TO (r_out) and in full precision
 // (r_full), block partials of sum r^2 / max|r|.
 template <typename TI, typename TO>

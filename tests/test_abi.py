@@ -62,6 +62,7 @@ def test_default_options(sg):
     o = sg.default_options()
     assert (o.rkl_order, o.s_smooth, o.n_pre, o.n_post) == (2, 3, 2, 1)
     assert o.tau_frac == 1.0 and o.use_graph == 1 and o.coarse_tol == 1e-2
+    assert (o.smoother, o.omega, o.max_residual_tol) == (0, 1.0, 0.0)
 
 
 @pytest.mark.parametrize("shape,lo,hi,bc,prec", [
