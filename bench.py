@@ -58,6 +58,8 @@ def args_():
     ap.add_argument("--profile-solves", type=int, default=0,
                     help="only run this many solves of the sphere workload (for ncu captures; no JSON line)")
     ap.add_argument("--n", type=int, default=N, help="grid size of --profile-solves")
+    ap.add_argument("--smoother", choices=["rkl", "gsrb"], default="rkl",
+                    help="smoother of --profile-solves (rkl: the bench's RKL2 settings; gsrb: red-black GS)")
     return ap.parse_args()
 
 
@@ -532,7 +534,7 @@ def run_profile_solves(a):
     torch.cuda.set_stream(stream)
     g = sg.Grid(p.shape, p.lo, p.hi, p.bc, precision="mixed", stream=stream.cuda_stream)
     g.set_boundary(p.faces)
-    g.set_options(**SOLVER)
+    g.set_options(**SOLVER, smoother=a.smoother)
     rho = torch.tensor(p.rho, device="cuda")
     for k in range(a.profile_solves):
         g.set_density(rho, 1.0)
