@@ -453,7 +453,7 @@ def run_ours(a, world, rank, local):
         t64 = (time.perf_counter() - t0) * 1e3
         extra["fp64_gpu_solve"] = {"solves_per_s": 1000.0 / t64, "ms": t64, "cycles": i64["cycles"]}
         del g64
-        g.set_options(**dict(SOLVER, rkl_order=1, s_smooth=2, tau_frac=0.75))
+        g.set_options(**dict(SOLVER, rkl_order=1, s_smooth=2, tau_frac=0.75, n_pre=2, n_post=1))
         step()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -461,7 +461,7 @@ def run_ours(a, world, rank, local):
         t1 = (time.perf_counter() - t0) * 1e3
         extra["rkl1_s2_smoother"] = {"solves_per_s": 1000.0 / t1, "ms": t1, "cycles": i1["cycles"]}
         # the paper's own smoother (GS-RB sweeps, N_pre = 2, N_post = 1) in the same V-cycle
-        g.set_options(**dict(SOLVER, smoother="gsrb"))
+        g.set_options(**dict(SOLVER, smoother="gsrb", n_pre=2, n_post=1))
         step()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
