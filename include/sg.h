@@ -218,12 +218,14 @@ typedef struct sg_tune_entry {
                                   n_pre + n_post when larger (that mode bounds the asymptotic
                                   rate: the coarse grid does not see it) */
     double ms_per_decade;      /* ms_per_cycle / -log10(factor): the score (lower is better) */
+    int    n_pre, n_post;      /* smoothing super-steps per V-cycle tried */
 } sg_tune_entry;
 
 /*
  * Pick the smoother for this grid and its current density by measurement: for
  * every candidate (RKL order 1 and 2 -- or only the current order when
- * keep_order is 1 --, s = 2..6, a few tau fractions, fused on and off) run
+ * keep_order is 1 --, s = 2..6, a few tau fractions, fused on and off, and
+ * (N_pre, N_post) = (2, 1), (3, 2), (4, 3) or (5, 3)) run
  * two and six V-cycles at `levels` (0 = the level rule), take the difference
  * of their CUDA-event times (so per-solve set-up drops out) and score the time
  * per decade of residual reduction over cycles 2..6, bounded below by the

@@ -28,6 +28,7 @@ Passages followed
                                                -> ``spectral_radius``, ``s_opt_global``
 * App. A.5, Eq. sk_optimal and the accelerated schedule with skipped repeats
                                                -> ``s_k_opt``, ``accelerated_schedule``
+* Sec. 3, Eq. 4thorder_acceleration            -> ``gravity``
 * Sec. 4.1, L2 norm with cell volumes          -> ``l2norm``
 * Sec. 4.1, level-count rule                   -> ``level_count``
 * App. B, SOR omega and GS-RB (Sec. 2.2.4)      -> ``gs_rb_sweep``, ``sor_omega``
@@ -38,7 +39,8 @@ the level once per pass; prolongation fills coarse ghosts with the level's
 boundary rule; the coarsest-level and single-level solver uses
 tau = cos^2(pi / 2N) tau_max unless told otherwise; in the Legendre-zero schedule
 N is the level's largest extent and the bracket [N/k] is plain division;
-periodic potentials are returned with zero mean.
+periodic potentials are returned with zero mean; the second ghost layer of the
+fourth-order gradient reflects through the face value like the first.
 
 Every function here is pinned by ``tests/test_oracle_*.py`` against closed
 forms, FFT/DST direct solves, a dense direct solve, and Legendre identities.
@@ -125,6 +127,41 @@ def laplacian(u, h, bc, faces=None):
     return ((p[1:-1, 1:-1, :-2] - 2.0 * c + p[1:-1, 1:-1, 2:]) / (hx * hx)
             + (p[1:-1, :-2, 1:-1] - 2.0 * c + p[1:-1, 2:, 1:-1]) / (hy * hy)
             + (p[:-2, 1:-1, 1:-1] - 2.0 * c + p[2:, 1:-1, 1:-1]) / (hz * hz))
+
+
+def gravity(phi, h, bc, faces=None):
+    """g = -grad phi by the fourth-order central difference of Sec. 3, Eq.
+    4thorder_acceleration, along each axis d:
+
+        g_d = -(4/3) (phi_{+1} - phi_{-1}) / (2 h_d) + (1/3) (phi_{+2} - phi_{-2}) / (4 h_d).
+
+    The stencil reaches two cells past a wall; the paper fills only the first
+    ghost (Eq. solution_ghost).  Both ghost layers here continue that rule as a
+    reflection through the face value: the ghost m + 1 cells beyond the wall is
+    2 phi_face - (the m-th cell from the wall), m = 0, 1 (zero face values when
+    ``faces`` is None).  Periodic axes wrap (Eq. periodic).
+    Returns [3][nz][ny][nx], the x component first."""
+    phi = np.asarray(phi, dtype=np.float64)
+    out = np.empty((3,) + phi.shape)
+    for d in range(3):
+        ax = 2 - d
+        n = phi.shape[ax]
+        if bc[d] == PERIODIC:
+            p = np.take(phi, np.arange(-2, n + 2) % n, axis=ax)
+        else:
+            lo = np.expand_dims(faces[2 * d], ax) if faces is not None else 0.0
+            hi = np.expand_dims(faces[2 * d + 1], ax) if faces is not None else 0.0
+            below = 2.0 * lo - np.take(phi, [1, 0], axis=ax)          # ghosts -2, -1
+            above = 2.0 * hi - np.take(phi, [n - 1, n - 2], axis=ax)  # ghosts n, n + 1
+            p = np.concatenate([below, phi, above], axis=ax)
+
+        def at(off):                      # phi_{i + off} for every cell i along the axis
+            return np.take(p, np.arange(2 + off, n + 2 + off), axis=ax)
+
+        hd = h[d]
+        out[d] = (-(4.0 / 3.0) * (at(1) - at(-1)) / (2.0 * hd)
+                  + (1.0 / 3.0) * (at(2) - at(-2)) / (4.0 * hd))
+    return out
 
 
 def residual(u, rhs, h, bc, faces=None):

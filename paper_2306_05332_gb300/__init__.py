@@ -80,7 +80,7 @@ SMOOTHERS = {"rkl": 0, "gsrb": 1}
 class TuneEntry(ctypes.Structure):
     _fields_ = [("rkl_order", ctypes.c_int), ("s_smooth", ctypes.c_int), ("fused", ctypes.c_int),
                 ("tau_frac", ctypes.c_double), ("ms_per_cycle", ctypes.c_double), ("factor", ctypes.c_double),
-                ("ms_per_decade", ctypes.c_double)]
+                ("ms_per_decade", ctypes.c_double), ("n_pre", ctypes.c_int), ("n_post", ctypes.c_int)]
 
 
 class SGError(RuntimeError):
@@ -296,7 +296,7 @@ class Grid:
 
     def autotune(self, levels=0, keep_order=True):
         """Measure the smoother candidates and keep the fastest per residual decade."""
-        cap = 128
+        cap = 256
         arr = (TuneEntry * cap)()
         n = ctypes.c_int(0)
         _check(lib().sg_autotune(self._h, int(levels), int(bool(keep_order)), arr, cap, ctypes.byref(n)))

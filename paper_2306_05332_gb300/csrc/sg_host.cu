@@ -1449,17 +1449,20 @@ sg_status sg_autotune(sg_grid* g, int levels, int keep_order, sg_tune_entry* tab
     const int L = levels == 0 ? g->max_levels : levels;
     if (L < 2) return fail(SG_ERR_ARG, "autotuning needs a multigrid hierarchy (levels >= 2)");
     const sg_options saved = g->opt;
-    struct Cand { int order, s, fused; double c; };
+    struct Cand { int order, s, fused; double c; int pre, post; };
     std::vector<Cand> cands;
+    // more smoothing per cycle trades the cycle's fixed work (update,
+    // transfers, coarsest levels) against fewer cycles
+    const int counts[][2] = {{2, 1}, {3, 2}, {4, 3}, {5, 3}};
     for (int order = 1; order <= 2; ++order) {
         if (keep_order && order != saved.rkl_order) continue;
         for (int s = 2; s <= 6; ++s) {
             const double cs1[] = {0.6, 0.75, 0.9};
-            const double cs2[] = {0.8, 1.0};
+            const double cs2[] = {0.8, 0.9, 1.0};
             const double* cs = order == 1 ? cs1 : cs2;
-            const int ncs = order == 1 ? 3 : 2;
-            for (int ic = 0; ic < ncs; ++ic)
-                for (int fz = 0; fz <= (g->precision == SG_MIXED ? 1 : 0); ++fz) cands.push_back({order, s, fz, cs[ic]});
+            for (int ic = 0; ic < 3; ++ic)
+                for (int fz = 0; fz <= (g->precision == SG_MIXED ? 1 : 0); ++fz)
+                    for (const auto& pc : counts) cands.push_back({order, s, fz, cs[ic], pc[0], pc[1]});
         }
     }
     double best = 1e300;
@@ -1471,6 +1474,8 @@ sg_status sg_autotune(sg_grid* g, int levels, int keep_order, sg_tune_entry* tab
         g->opt.s_smooth = c.s;
         g->opt.tau_frac = c.c;
         g->opt.fused = c.fused;
+        g->opt.n_pre = c.pre;
+        g->opt.n_post = c.post;
         g->opt.smoother = SG_SMOOTH_RKL;
         // Time 2 and 6 cycles (after a capture / warm-up run) and take the
         // difference, so the per-solve set-up cost drops out of the score.
@@ -1495,7 +1500,7 @@ sg_status sg_autotune(sg_grid* g, int levels, int keep_order, sg_tune_entry* tab
         factor = std::max(factor, top);
         const double mpc = (info6.elapsed_ms - info2.elapsed_ms) / 4.0;
         const double score = (factor > 0 && factor < 1) ? mpc / -std::log10(factor) : 1e300;
-        if (table && tried < cap) table[tried] = {c.order, c.s, c.fused, c.c, mpc, factor, score};
+        if (table && tried < cap) table[tried] = {c.order, c.s, c.fused, c.c, mpc, factor, score, c.pre, c.post};
         (void)info2;
         ++tried;
         if (score < best) {

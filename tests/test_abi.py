@@ -41,8 +41,9 @@ def test_library_exports_every_header_function(sg):
 def test_struct_layouts_match_header(sg, tmp_path):
     src = tmp_path / "sizes.c"
     src.write_text('#include "sg.h"\n#include <stdio.h>\n#include <stddef.h>\n'
-                   'int main(void){printf("%zu %zu %zu %zu\\n", sizeof(sg_options), sizeof(sg_solve_info),'
-                   ' offsetof(sg_solve_info, history), offsetof(sg_solve_info, elapsed_ms));return 0;}\n')
+                   'int main(void){printf("%zu %zu %zu %zu %zu\\n", sizeof(sg_options), sizeof(sg_solve_info),'
+                   ' offsetof(sg_solve_info, history), offsetof(sg_solve_info, elapsed_ms),'
+                   ' sizeof(sg_tune_entry));return 0;}\n')
     exe = tmp_path / "sizes"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
     out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()
@@ -50,6 +51,7 @@ def test_struct_layouts_match_header(sg, tmp_path):
     assert int(out[1]) == ctypes.sizeof(sg.SolveInfo)
     assert int(out[2]) == sg.SolveInfo.history.offset
     assert int(out[3]) == sg.SolveInfo.elapsed_ms.offset
+    assert int(out[4]) == ctypes.sizeof(sg.TuneEntry)
 
 
 def test_status_codes_match_header(sg):

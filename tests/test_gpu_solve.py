@@ -282,6 +282,8 @@ def test_autotune_keeps_order_and_converges():
     assert len(table) > 0 and all(t["rkl_order"] == 2 for t in table)
     best = min(table, key=lambda t: t["ms_per_decade"])
     assert opts["s_smooth"] == best["s_smooth"] and opts["rkl_order"] == 2
+    assert (opts["n_pre"], opts["n_post"]) == (best["n_pre"], best["n_post"])
+    assert {(t["n_pre"], t["n_post"]) for t in table} == {(2, 1), (3, 2), (4, 3), (5, 3)}
     assert all(0 < t["factor"] <= 1 + 1e-9 for t in table)
     # RKL2 with even s at tau_max does not damp the checkerboard mode, which
     # the coarse grid cannot see: such candidates never converge and score last

@@ -43,6 +43,9 @@ def _any_pin_fails():
         lambda: T.test_accelerated_schedule_skips_repeats(),
         lambda: T.test_gsrb_sweep_radius_follows_young((4, 4, 6), (0, 0, 0)),
         lambda: T.test_gsrb_half_sweeps_solve_their_rows((0, 0, 0)),
+        lambda: T.test_gravity_exact_for_quartics_away_from_walls(),
+        lambda: T.test_gravity_of_linear_field_exact_at_the_walls(),
+        lambda: T.test_gravity_periodic_sinusoid_closed_form(),
     ]
     failed = 0
     for pin in pins:
@@ -147,6 +150,34 @@ def m_gsrb_omega_dropped(u, rhs, h, bc, faces=None, omega=1.0):
     return ORIG["gs_rb_sweep"](u, rhs, h, bc, faces, 1.0)
 
 
+def m_gravity_second_ghost_even(phi, h, bc, faces=None):
+    # the second ghost layer copied from the second cell (even) instead of
+    # reflected through the face value
+    phi = np.asarray(phi, dtype=np.float64)
+    out = np.empty((3,) + phi.shape)
+    for d in range(3):
+        ax = 2 - d
+        n = phi.shape[ax]
+        if bc[d] == S.PERIODIC:
+            p = np.take(phi, np.arange(-2, n + 2) % n, axis=ax)
+        else:
+            lo = np.expand_dims(faces[2 * d], ax) if faces is not None else 0.0
+            hi = np.expand_dims(faces[2 * d + 1], ax) if faces is not None else 0.0
+            below = np.concatenate([np.take(phi, [1], axis=ax), 2.0 * lo - np.take(phi, [0], axis=ax)], axis=ax)
+            above = np.concatenate([2.0 * hi - np.take(phi, [n - 1], axis=ax), np.take(phi, [n - 2], axis=ax)],
+                                   axis=ax)
+            p = np.concatenate([below, phi, above], axis=ax)
+        at = lambda off: np.take(p, np.arange(2 + off, n + 2 + off), axis=ax)
+        out[d] = -(4.0 / 3.0) * (at(1) - at(-1)) / (2.0 * h[d]) + (1.0 / 3.0) * (at(2) - at(-2)) / (4.0 * h[d])
+    return out
+
+
+def m_gravity_coefficient(phi, h, bc, faces=None):
+    # 4/3 read as 3/4
+    g = ORIG["gravity"](phi, h, bc, faces)
+    return g * 0.5625
+
+
 MUTATIONS = [
     ("restrict", m_restrict_quarter),
     ("prolong", m_prolong_wrong_direction),
@@ -162,6 +193,8 @@ MUTATIONS = [
     ("operator_diagonal", m_diagonal_no_wall),
     ("gs_rb_sweep", m_gsrb_colour_by_rows),
     ("gs_rb_sweep", m_gsrb_omega_dropped),
+    ("gravity", m_gravity_second_ghost_even),
+    ("gravity", m_gravity_coefficient),
 ]
 
 

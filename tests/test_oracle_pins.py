@@ -433,7 +433,7 @@ def test_gsrb_vcycle_reduces_residual_about_tenfold():
 def test_second_order_accuracy_smooth_model_problem():
     # Sec. 4.1, Fig. error: error of the potential scales as h^2.
     errs = []
-    for n in (16, 32):
+    for n in (32, 64):
         p = W.smooth_sphere(n)
         phi, _ = O.solve(p.rho, p.lo, p.hi, p.bc, p.faces, p.four_pi_G, tol=1e-12,
                          opts=O.Options(rkl_order=1, s_smooth=2, tau_frac=0.75))
@@ -617,6 +617,91 @@ def test_single_level_gsrb_solve_reaches_direct_solution(omega):
         gs = O.solve(rho, lo, hi, bc, faces, 1.0, tol=1e-11, levels=1,
                      opts=O.Options(smoother="gsrb", max_cycles=2000))[1]
         assert info.cycles < gs.cycles / 2
+
+
+# ---------------------------------------------------------------------------
+# Fourth-order acceleration (Sec. 3)
+# ---------------------------------------------------------------------------
+
+def _centres(shape, lo, hi):
+    nz, ny, nx = shape
+    ax = [lo[d] + (np.arange(n) + 0.5) * (hi[d] - lo[d]) / n for d, n in enumerate((nx, ny, nz))]
+    Z, Y, X = np.meshgrid(ax[2], ax[1], ax[0], indexing="ij")
+    return X, Y, Z
+
+
+def _faces_of(fn, shape, lo, hi):
+    """Face-centre values of fn(x, y, z) in the face layout of the oracle."""
+    X, Y, Z = _centres(shape, lo, hi)
+    return [fn(np.full_like(X[:, :, 0], lo[0]), Y[:, :, 0], Z[:, :, 0]),
+            fn(np.full_like(X[:, :, 0], hi[0]), Y[:, :, 0], Z[:, :, 0]),
+            fn(X[:, 0, :], np.full_like(Y[:, 0, :], lo[1]), Z[:, 0, :]),
+            fn(X[:, 0, :], np.full_like(Y[:, 0, :], hi[1]), Z[:, 0, :]),
+            fn(X[0, :, :], Y[0, :, :], np.full_like(Z[0, :, :], lo[2])),
+            fn(X[0, :, :], Y[0, :, :], np.full_like(Z[0, :, :], hi[2]))]
+
+
+def test_gravity_exact_for_quartics_away_from_walls():
+    # the five-point central difference is exact for polynomials of degree 4
+    shape, lo, hi = (9, 8, 10), (0.0, -0.5, 0.25), (1.3, 0.2, 1.35)
+    X, Y, Z = _centres(shape, lo, hi)
+    phi = 0.7 * X ** 4 - X ** 3 + 2 * Y ** 4 + Y * Z ** 2 - 3 * Z ** 4 + X * Y * Z + 0.5
+    gx = -(2.8 * X ** 3 - 3 * X ** 2 + Y * Z)
+    gy = -(8 * Y ** 3 + Z ** 2 + X * Z)
+    gz = -(2 * Y * Z - 12 * Z ** 3 + X * Y)
+    g = O.gravity(phi, O.spacing(shape, lo, hi), (0, 0, 0), None)
+    inner = (slice(2, -2),) * 3
+    for d, ref in enumerate((gx, gy, gz)):
+        np.testing.assert_allclose(g[d][inner], ref[inner], rtol=0, atol=1e-10 * np.abs(ref).max())
+
+
+def test_gravity_of_linear_field_exact_at_the_walls():
+    # with the face values of a linear field the reflected ghosts continue it
+    shape, lo, hi = (6, 7, 5), (-1.0, 0.0, 0.5), (1.0, 0.7, 1.3)
+    fn = lambda x, y, z: 0.3 - 1.5 * x + 2.5 * y + 0.75 * z
+    X, Y, Z = _centres(shape, lo, hi)
+    g = O.gravity(fn(X, Y, Z), O.spacing(shape, lo, hi), (0, 0, 0), _faces_of(fn, shape, lo, hi))
+    for d, v in enumerate((1.5, -2.5, -0.75)):
+        np.testing.assert_allclose(g[d], v, rtol=0, atol=1e-12)
+
+
+def test_gravity_periodic_sinusoid_closed_form():
+    # d/dx sin(kx) by the stencil: cos(kx) (8 sin(kh) - sin(2kh)) / (6h)
+    shape, lo, hi = (6, 4, 16), (0.0, 0.0, 0.0), (2.0, 1.0, 1.0)
+    X, Y, Z = _centres(shape, lo, hi)
+    k, h = 2 * np.pi * 3 / 2.0, 2.0 / 16
+    g = O.gravity(np.sin(k * X + 0.3), (h, 0.25, 1.0 / 6), (1, 1, 1))
+    np.testing.assert_allclose(g[0], -np.cos(k * X + 0.3) * (8 * np.sin(k * h) - np.sin(2 * k * h)) / (6 * h),
+                               rtol=0, atol=1e-12)
+    np.testing.assert_allclose(g[1], 0.0, atol=1e-12)
+    np.testing.assert_allclose(g[2], 0.0, atol=1e-12)
+
+
+def test_gravity_is_fourth_order_and_second_order_after_the_solve():
+    # smooth periodic field: error falls 16x per halving of h; Sec. 4.1 model
+    # problem: g of the discrete solution against Eq. acceleration_3D falls
+    # about 4x (the potential's h^2 error dominates, Fig. error_map)
+    errs = []
+    for n in (16, 32):
+        X, Y, Z = _centres((n, n, n), (0, 0, 0), (1, 1, 1))
+        phi = np.sin(2 * np.pi * X) * np.cos(2 * np.pi * Y)
+        g = O.gravity(phi, (1.0 / n,) * 3, (1, 1, 1))
+        errs.append(np.abs(g[0] + 2 * np.pi * np.cos(2 * np.pi * X) * np.cos(2 * np.pi * Y)).max())
+    assert 14.0 < errs[0] / errs[1] < 18.0
+    errs = []
+    for n in (32, 64):
+        p = W.smooth_sphere(n)
+        phi, _ = O.solve(p.rho, p.lo, p.hi, p.bc, p.faces, p.four_pi_G, tol=1e-12)
+        X, Y, Z = _centres(p.shape, p.lo, p.hi)
+        r = np.sqrt(X * X + Y * Y + Z * Z)
+        r0, rho0 = 0.25, 1.0
+        M = 32 * np.pi * rho0 * r0 ** 3 / 105
+        gr = np.where(r <= r0, -4 * np.pi * rho0 * (r / 3 - 0.4 * r ** 3 / r0 ** 2 + r ** 5 / (7 * r0 ** 4)),
+                      -M / r ** 2)
+        g = O.gravity(phi, O.spacing(p.shape, p.lo, p.hi), p.bc, p.faces)
+        err = np.sqrt(sum((g[d] - gr * c / r) ** 2 for d, c in enumerate((X, Y, Z))))
+        errs.append(O.l2norm(err) / O.l2norm(np.abs(gr)))
+    assert 3.3 < errs[0] / errs[1] < 5.0
 
 
 # ---------------------------------------------------------------------------
