@@ -482,7 +482,26 @@ def run_ours(a, world, rank, local):
         tt = (time.perf_counter() - t0) * 1e3
         extra["autotuned_rkl2"] = {"solves_per_s": 1000.0 / tt, "ms": tt, "cycles": itn["cycles"],
                                    "s_smooth": tuned["s_smooth"], "tau_frac": tuned["tau_frac"],
+                                   "n_pre": tuned["n_pre"], "n_post": tuned["n_post"],
                                    "fused": tuned["fused"], "candidates": len(table)}
+        # the acceleration of the solution (Sec. 3, fourth order), device buffers:
+        # reads phi (8 B/cell), writes three components (24 B/cell), 12 FP64
+        # operations per cell
+        gout = torch.empty((3,) + tuple(p.shape), dtype=torch.float64, device=dev)
+        g.gravity(out=gout)
+        g.set_profiling(True)
+        for _ in range(5):
+            torch.cuda.synchronize()
+            flush.fill_(1.0)
+            g.gravity(out=gout)
+        torch.cuda.synchronize()
+        sgv = g.kernel_stats()["gravity"]
+        g.set_profiling(False)
+        per_ms = sgv["ms"] / max(1, sgv["launches"])
+        extra["gravity_256"] = {"us_per_call": per_ms * 1e3,
+                                "GBps_algorithmic": 32.0 * n0 / (per_ms * 1e-3) / 1e9,
+                                "fp64_tflops": 12.0 * n0 / (per_ms * 1e-3) / 1e12}
+        del gout
         g.set_options(**SOLVER, fused=1)
         del g
         torch.cuda.empty_cache()

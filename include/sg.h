@@ -181,6 +181,23 @@ sg_status sg_solve(sg_grid* g, double tol, int s, int levels, sg_solve_info* inf
 sg_status sg_potential(sg_grid* g, double* phi_out, int on_device);
 
 /*
+ * Gravitational acceleration g = -grad phi by the fourth-order central
+ * difference of Sec. 3, Eq. 4thorder_acceleration, along each axis:
+ *   g_d = -(4/3) (phi_{+1} - phi_{-1}) / (2 h_d) + (1/3) (phi_{+2} - phi_{-2}) / (4 h_d).
+ * phi: NULL for the potential of the last solve (SG_ERR_STATE before one), or
+ * a caller potential [nz][ny][nx].  g_out: [3][nz][ny][nx] float64, the x
+ * component first.  on_device = 1: phi (when given) and g_out are device
+ * pointers and the call is stream-ordered on the grid's stream; 0: host
+ * memory, copied in and out (device staging allocated on first use).  The
+ * stencil reaches two cells past a wall: on Dirichlet axes both ghost layers
+ * reflect through the grid's face values (ghost m = 2 phi_face - the m-th cell
+ * from the wall, m = 1, 2; zero faces when none were set), periodic axes wrap.
+ * Errors: SG_ERR_ARG (NULL g or g_out), SG_ERR_STATE (phi NULL before any
+ * solve), SG_ERR_CUDA (a CUDA call failed, the staging allocation included).
+ */
+sg_status sg_gravity(sg_grid* g, const double* phi, double* g_out, int on_device);
+
+/*
  * Adjoint of the solve for a loss L(phi): given dL/dphi, return
  * dL/drho = four_pi_G * lambda with L_h lambda = dL/dphi under homogeneous
  * boundaries (the discrete operator is symmetric, so it is its own adjoint; the
@@ -255,12 +272,13 @@ int sg_max_levels(const sg_grid* g);
  * the compulsory reads and writes of their input and output arrays, each cell
  * counted once, independent of caching.
  * ------------------------------------------------------------------------ */
-#define SG_KERNEL_CLASSES 10
+#define SG_KERNEL_CLASSES 11
 typedef struct sg_kernel_stat {
     char      name[24];       /* rkl_stage_l0, rkl_stage_coarse, residual_l0, residual_restrict,
                                  prolong_correct, coarse_solve, update, reduce_misc,
                                  bottom_levels (the two coarsest levels in one launch),
-                                 gsrb_sweep (one colour of a GS-RB sweep) */
+                                 gsrb_sweep (one colour of a GS-RB sweep),
+                                 gravity (sg_gravity) */
     long long launches;
     double    ms;             /* summed event time of the launches */
     double    bytes;          /* summed algorithmic bytes */

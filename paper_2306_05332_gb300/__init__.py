@@ -73,7 +73,7 @@ class KernelStat(ctypes.Structure):
                 ("bytes", ctypes.c_double)]
 
 
-SG_KERNEL_CLASSES = 10
+SG_KERNEL_CLASSES = 11
 SMOOTHERS = {"rkl": 0, "gsrb": 1}
 
 
@@ -105,6 +105,7 @@ _SIGS = {
     "sg_set_potential_guess": ([_P, _P, _I], _I),
     "sg_solve": ([_P, _D, _I, _I, ctypes.POINTER(SolveInfo)], _I),
     "sg_potential": ([_P, _P, _I], _I),
+    "sg_gravity": ([_P, _P, _P, _I], _I),
     "sg_backward": ([_P, _P, _P, _I, _D, ctypes.POINTER(SolveInfo)], _I),
     "sg_solve_batch": ([ctypes.POINTER(_P), _I, _D, ctypes.POINTER(SolveInfo)], _I),
     "sg_destroy": ([_P], None),
@@ -268,6 +269,23 @@ class Grid:
         if check and st not in (0,):
             _check(st)
         return info.as_dict()
+
+    def gravity(self, out=None, phi=None):
+        """g = -grad phi to fourth order (Sec. 3) as an array (3, nz, ny, nx):
+        of the last solve's potential, or of `phi`.  `out` (numpy float64 or a
+        CUDA float64 tensor of that shape) receives it when given; with a CUDA
+        `out`, `phi` (if any) must be a CUDA tensor too."""
+        if out is None:
+            out = np.empty((3,) + tuple(self.shape), dtype=np.float64)
+        _require_writable(out)
+        po, do, keep_o = _ptr(out)
+        pp, keep_p = None, None
+        if phi is not None:
+            pp, dp, keep_p = _ptr(phi)
+            if dp != do:
+                raise TypeError("phi and out must both be host arrays or both CUDA tensors")
+        _check(lib().sg_gravity(self._h, pp, po, do))
+        return out
 
     def potential(self, out=None):
         if out is None:

@@ -7,6 +7,7 @@
 // the z-1 / z / z+1 values in registers, so each cell of the stencil input is
 // read from HBM once per sweep (x/y neighbours hit L1/L2), coalesced along x.
 // These are HBM-bandwidth-bound kernels; no tensor cores are involved.
+#include "sg_field_ops.cuh"
 #include "sg_internal.cuh"
 
 #include <algorithm>
@@ -246,6 +247,65 @@ k_gsrb(const LevelGeom g, int colour, T omega, T* u, const T* __restrict__ rhs, 
         u[idx] = c - omega * r * inv;
         zm = zp;
         carried = true;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Acceleration g = -grad phi by the fourth-order central difference of Sec. 3
+// (Eq. 4thorder_acceleration): along each axis,
+//   g_d = -(8 (phi_{+1} - phi_{-1}) - (phi_{+2} - phi_{-2})) / (12 h_d),
+// the paper's -(4/3)(.)/(2h) + (1/3)(.)/(4h) over a common denominator.  Past
+// a Dirichlet wall both ghost layers reflect through the face value (the
+// m-th ghost is 2 phi_face - the m-th cell from the wall; zero face values
+// without face data); periodic axes wrap.  FP64 throughout.
+// ---------------------------------------------------------------------------
+// phi at cell i + off (off in -2..2, not 0) along an axis of extent n >= 2 and
+// stride `stride`, from the cell at flat index idx; flo / fhi: that axis's
+// low / high face arrays (or nullptr), fi: this cell's index in them.
+__device__ __forceinline__ double axis_phi(const double* u, int idx, int i, int n, int stride, int off, bool per,
+                                           const double* flo, const double* fhi, int fi) {
+    const int q = i + off;
+    if (q >= 0 && q < n) return u[idx + off * stride];
+    if (per) return u[idx + (q < 0 ? off + n : off - n) * stride];
+    const int m = q < 0 ? -1 - q : 2 * n - 1 - q;           // the mirrored cell
+    const double* f = q < 0 ? flo : fhi;
+    const double fv = f ? f[fi] : 0.0;
+    return 2.0 * fv - u[idx + (m - i) * stride];
+}
+
+__device__ __forceinline__ double fourth_order(double m2, double m1, double p1, double p2, double c) {
+    return c * fma(8.0, p1 - m1, m2 - p2);
+}
+
+__global__ void __launch_bounds__(BX * BY)
+k_gravity(const LevelGeom g, const double* __restrict__ u, double* __restrict__ out, double cx, double cy,
+          double cz, int kchunk) {
+    const int i = blockIdx.x * BX + threadIdx.x;
+    const int j = blockIdx.y * BY + threadIdx.y;
+    if (i >= g.nx || j >= g.ny) return;
+    const int k0 = blockIdx.z * kchunk;
+    const int k1 = min(k0 + kchunk, g.nz);
+    const int plane = g.nx * g.ny;
+    const long long n = (long long)plane * g.nz;
+    for (int k = k0; k < k1; ++k) {
+        const int idx = k * plane + j * g.nx + i;
+        const int fx = k * g.ny + j, fy = k * g.nx + i, fz = j * g.nx + i;
+        const bool px = g.per[0], py = g.per[1], pz = g.per[2];
+        const double gx = fourth_order(axis_phi(u, idx, i, g.nx, 1, -2, px, g.face[0], g.face[1], fx),
+                                       axis_phi(u, idx, i, g.nx, 1, -1, px, g.face[0], g.face[1], fx),
+                                       axis_phi(u, idx, i, g.nx, 1, 1, px, g.face[0], g.face[1], fx),
+                                       axis_phi(u, idx, i, g.nx, 1, 2, px, g.face[0], g.face[1], fx), cx);
+        const double gy = fourth_order(axis_phi(u, idx, j, g.ny, g.nx, -2, py, g.face[2], g.face[3], fy),
+                                       axis_phi(u, idx, j, g.ny, g.nx, -1, py, g.face[2], g.face[3], fy),
+                                       axis_phi(u, idx, j, g.ny, g.nx, 1, py, g.face[2], g.face[3], fy),
+                                       axis_phi(u, idx, j, g.ny, g.nx, 2, py, g.face[2], g.face[3], fy), cy);
+        const double gz = fourth_order(axis_phi(u, idx, k, g.nz, plane, -2, pz, g.face[4], g.face[5], fz),
+                                       axis_phi(u, idx, k, g.nz, plane, -1, pz, g.face[4], g.face[5], fz),
+                                       axis_phi(u, idx, k, g.nz, plane, 1, pz, g.face[4], g.face[5], fz),
+                                       axis_phi(u, idx, k, g.nz, plane, 2, pz, g.face[4], g.face[5], fz), cz);
+        out[idx] = gx;
+        out[n + idx] = gy;
+        out[2 * n + idx] = gz;
     }
 }
 
@@ -1246,6 +1306,14 @@ cudaError_t launch_gsrb(const LevelGeom& g, int colour, double omega, T* u, cons
     dim3 grid((g.nx + BX - 1) / BX, (g.ny + BY - 1) / BY, (g.nz + kc - 1) / kc);
     if (has_faces(g)) k_gsrb<T, true><<<grid, block, 0, st>>>(g, colour & 1, T(omega), u, rhs, kc);
     else k_gsrb<T, false><<<grid, block, 0, st>>>(g, colour & 1, T(omega), u, rhs, kc);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gravity(const LevelGeom& g, const double* phi, double* out, const double c[3], cudaStream_t st) {
+    const int kc = kchunk_for(g, BX, BY);
+    dim3 block(BX, BY, 1);
+    dim3 grid((g.nx + BX - 1) / BX, (g.ny + BY - 1) / BY, (g.nz + kc - 1) / kc);
+    k_gravity<<<grid, block, 0, st>>>(g, phi, out, c[0], c[1], c[2], kc);
     return cudaGetLastError();
 }
 

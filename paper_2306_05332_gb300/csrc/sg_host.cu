@@ -8,6 +8,7 @@
 // an FP64 residual r = f - L phi and an FP64 update phi += e (defect
 // correction); in SG_FP64 it runs in FP64 on phi directly.
 #include "sg.h"
+#include "sg_field_ops.cuh"
 #include "sg_internal.cuh"
 
 #include <algorithm>
@@ -157,11 +158,11 @@ int rule_levels(int nx, int ny, int nz) {
 
 // Kernel classes for the optional per-kernel CUDA-event profile.
 enum KClass { K_STAGE0 = 0, K_STAGE_C, K_RES0, K_RESTRICT, K_PROLONG, K_COARSE, K_UPDATE, K_MISC, K_BOTTOM,
-              K_GSRB, K_NCLASS };
+              K_GSRB, K_GRAVITY, K_NCLASS };
 const char* const kClassName[K_NCLASS] = {"rkl_stage_l0", "rkl_stage_coarse", "residual_l0",
                                           "residual_restrict", "prolong_correct", "coarse_solve",
                                           "update_residual", "reduce_misc", "bottom_levels",
-                                          "gsrb_sweep"};
+                                          "gsrb_sweep", "gravity"};
 
 struct ProfRec {
     int cls;
@@ -185,6 +186,8 @@ struct sg_grid {
     double* f = nullptr;
     double* faces[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     bool have_faces = false;
+    double* gphi = nullptr;         // sg_gravity: a host potential, staged
+    double* gout = nullptr;         // sg_gravity: the three components, staged for the host
     double* lam = nullptr;          // adjoint solution
     double* w = nullptr;            // adjoint source
     double* r64 = nullptr;          // FP64 residual f - A phi carried by recurrence (mixed)
@@ -1059,6 +1062,8 @@ void free_grid(sg_grid* g) {
     for (int i = 0; i < 6; ++i) cudaFree(g->faces[i]);
     cudaFree(g->lam);
     cudaFree(g->w);
+    cudaFree(g->gphi);
+    cudaFree(g->gout);
     cudaFree(g->r64);
     cudaFree(g->partials);
     cudaFree(g->red);
@@ -1279,6 +1284,33 @@ sg_status sg_solve(sg_grid* g, double tol, int s, int levels, sg_solve_info* inf
         g->last_levels = L;
     }
     return st;
+}
+
+sg_status sg_gravity(sg_grid* g, const double* phi, double* g_out, int on_device) {
+    g_err.clear();
+    if (!g || !g_out) return fail(SG_ERR_ARG, "NULL argument");
+    if (!phi && !g->have_solution) return fail(SG_ERR_STATE, "no solution yet");
+    const long long n = g->lv[0].n;
+    const double* src = phi ? phi : g->phi;
+    if (phi && !on_device) {
+        if (!g->gphi) SG_CK(cudaMalloc(&g->gphi, n * sizeof(double)));
+        SG_TRY(copy_in(g->gphi, phi, n, 0, g->st));
+        src = g->gphi;
+    }
+    double* dst = g_out;
+    if (!on_device) {
+        if (!g->gout) SG_CK(cudaMalloc(&g->gout, 3 * n * sizeof(double)));
+        dst = g->gout;
+    }
+    const Level& L0 = g->lv[0];
+    const double c[3] = {-1.0 / (12.0 * L0.h[0]), -1.0 / (12.0 * L0.h[1]), -1.0 / (12.0 * L0.h[2])};
+    {
+        ProfScope ps(g, K_GRAVITY, 32.0 * n);
+        SG_CK(launch_gravity(geom(g, 0, g->have_faces), src, dst, c, g->st));
+    }
+    ++g->launches;
+    if (!on_device) SG_TRY(copy_out(g_out, dst, 3 * n, 0, g->st));
+    return SG_OK;
 }
 
 sg_status sg_potential(sg_grid* g, double* phi_out, int on_device) {
