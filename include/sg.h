@@ -287,8 +287,10 @@ typedef struct sg_kernel_stat {
 /* Enable (1) or disable (0) the profile and reset its totals. */
 sg_status sg_set_profiling(sg_grid* g, int on);
 
-/* Copy the SG_KERNEL_CLASSES totals into out[]. */
-sg_status sg_kernel_stats(const sg_grid* g, sg_kernel_stat* out);
+/* Copy the SG_KERNEL_CLASSES totals into out[].  Launches recorded since the
+ * last solve (single operators, sg_gravity) are timed first, which
+ * synchronises the grid's stream. */
+sg_status sg_kernel_stats(sg_grid* g, sg_kernel_stat* out);
 
 /* ------------------------------------------------------------------------
  * Single operators, for verification and for callers composing their own

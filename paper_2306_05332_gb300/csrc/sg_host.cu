@@ -1561,9 +1561,14 @@ sg_status sg_set_profiling(sg_grid* g, int on) {
     return SG_OK;
 }
 
-sg_status sg_kernel_stats(const sg_grid* g, sg_kernel_stat* out) {
+sg_status sg_kernel_stats(sg_grid* g, sg_kernel_stat* out) {
     g_err.clear();
     if (!g || !out) return fail(SG_ERR_ARG, "NULL argument");
+    if (g->prof && !g->live.empty() && !g->capturing) {
+        // launches recorded since the last solve's sync point (single operators, sg_gravity)
+        SG_CK(cudaStreamSynchronize(g->st));
+        prof_accumulate(g, g->live, true);
+    }
     for (int c = 0; c < K_NCLASS; ++c) {
         out[c] = g->stats[c];
         std::snprintf(out[c].name, sizeof(out[c].name), "%s", kClassName[c]);
