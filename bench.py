@@ -235,7 +235,7 @@ def ncu_traffic(cls, cells):
 # ---------------------------------------------------------------------------
 # CPU oracle timing (bounded sample)
 # ---------------------------------------------------------------------------
-def oracle_vcycle_seconds(p, reps=1):
+def oracle_vcycle_seconds(p, reps=1, levels=LEVELS):
     import numpy as np
     import oracle as O
     opts = O.Options(**SOLVER)
@@ -245,7 +245,7 @@ def oracle_vcycle_seconds(p, reps=1):
     t = []
     for _ in range(reps):
         t0 = time.perf_counter()
-        phi = O.vcycle(phi, f, h, p.bc, p.faces, LEVELS, opts)
+        phi = O.vcycle(phi, f, h, p.bc, p.faces, levels, opts)
         O.l2norm(O.residual(phi, f, h, p.bc, p.faces))
         t.append(time.perf_counter() - t0)
     return statistics.median(t)
@@ -270,14 +270,20 @@ def oracle_cycles_per_solve():
         return int(json.load(f)["cycles"])
 
 
+# The reference arm's per-step sample: the same sphere problem at N / 2 per
+# axis with one level fewer (the same 16^3 coarsest level), whose V-cycle does
+# an eighth of the finest-level work; the 256^3 cycle time is taken as 8x.
+REF_N, REF_LEVELS, REF_SCALE = N // 2, LEVELS - 1, 8.0
+
+
 def run_reference(a, world, rank):
     if rank != 0:
         return
     import workloads as W
-    p = W.sphere(N)
+    p = W.sphere(REF_N)
     for _ in range(a.warmup):
-        oracle_vcycle_seconds(p, 1)
-    ts = [oracle_vcycle_seconds(p, 1) for _ in range(a.steps)]
+        oracle_vcycle_seconds(p, 1, REF_LEVELS)
+    ts = [oracle_vcycle_seconds(p, 1, REF_LEVELS) * REF_SCALE for _ in range(a.steps)]
     cycles = oracle_cycles_per_solve()
     t = statistics.mean(ts) * cycles
     value = 1.0 / t
@@ -286,8 +292,10 @@ def run_reference(a, world, rank):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": config(world),
             "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle",
-                             "sample": f"each step: 1 V-cycle + residual of the numpy FP64 oracle at {N}^3, "
-                                       f"x {cycles} cycles per solve (the oracle's count on this workload)"},
+                             "sample": f"each step: 1 V-cycle + residual of the numpy FP64 oracle on the "
+                                       f"{REF_N}^3 instance of the sphere workload ({REF_LEVELS} levels, the "
+                                       f"same 16^3 coarsest level) x {REF_SCALE:g} for the {N}^3 cell count, "
+                                       f"x {cycles} cycles per solve (the oracle's count on the {N}^3 workload)"},
             "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
