@@ -250,77 +250,6 @@ k_gsrb(const LevelGeom g, int colour, T omega, T* u, const T* __restrict__ rhs, 
     }
 }
 
-// The same colour update for levels without face data and an even x extent:
-// each thread owns the x pair (2p, 2p + 1) of its row, of which exactly one
-// cell has the colour on every plane, so every thread works on every plane
-// and a warp's loads of a row are one contiguous pair vector per lane.  The
-// pairs of planes k - 1, k, k + 1 stay in registers (the z neighbours of the
-// updated cell are the same element of the pairs above and below; that
-// element has the other colour there, so the registers never go stale).
-template <typename T> struct Pair;
-template <> struct Pair<float> { using type = float2; };
-template <> struct Pair<double> { using type = double2; };
-
-template <typename T>
-__global__ void __launch_bounds__(BX * BY)
-k_gsrb_pairs(const LevelGeom g, int colour, T omega, T* u, const T* __restrict__ rhs, int kchunk) {
-    using P2 = typename Pair<T>::type;
-    const int p = blockIdx.x * BX + threadIdx.x;
-    const int j = blockIdx.y * BY + threadIdx.y;
-    const int npairs = g.nx >> 1;
-    if (p >= npairs || j >= g.ny) return;
-    const int k0 = blockIdx.z * kchunk;
-    const int k1 = min(k0 + kchunk, g.nz);
-    const int plane = g.nx * g.ny;
-    const T ihx2 = ih2x<T>(g), ihy2 = ih2y<T>(g), ihz2 = ih2z<T>(g);
-    const T d0 = T(-2) * (ihx2 + ihy2 + ihz2);
-    T dy = d0;
-    if (!g.per[1]) {
-        if (j == 0) dy -= ihy2;
-        if (j == g.ny - 1) dy -= ihy2;
-    }
-    const T inv0 = T(1) / d0;
-    const int row = j * g.nx + 2 * p;                 // flat index of the pair's first cell in plane 0
-    auto pair_at = [&](int k) -> P2 { return *reinterpret_cast<const P2*>(u + k * plane + row); };
-    auto neg = [](P2 v) -> P2 { v.x = -v.x; v.y = -v.y; return v; };
-    P2 pc = pair_at(k0);
-    P2 pm = (k0 > 0) ? pair_at(k0 - 1) : (g.per[2] ? pair_at(g.nz - 1) : neg(pc));
-    for (int k = k0; k < k1; ++k) {
-        const P2 pp = (k < g.nz - 1) ? pair_at(k + 1) : (g.per[2] ? pair_at(0) : neg(pc));
-        const int dlt = (colour + j + k) & 1;         // which element of the pair has the colour
-        const int i = 2 * p + dlt;
-        const int idx = k * plane + row + dlt;
-        const T c = dlt ? pc.y : pc.x;
-        const T zm = dlt ? pm.y : pm.x;
-        const T zp = dlt ? pp.y : pp.x;
-        T xm, xp;
-        if (dlt) {
-            xm = pc.x;
-            xp = (i < g.nx - 1) ? u[idx + 1] : (g.per[0] ? u[idx - (g.nx - 1)] : -c);
-        } else {
-            xp = pc.y;
-            xm = (i > 0) ? u[idx - 1] : (g.per[0] ? u[idx + (g.nx - 1)] : -c);
-        }
-        const T ym = (j > 0) ? u[idx - g.nx] : (g.per[1] ? u[idx + (g.ny - 1) * g.nx] : -c);
-        const T yp = (j < g.ny - 1) ? u[idx + g.nx] : (g.per[1] ? u[idx - (g.ny - 1) * g.nx] : -c);
-        const T r = lap7(c, xm, xp, ym, yp, zm, zp, ihx2, ihy2, ihz2) - rhs[idx];
-        T d = dy;
-        bool wall = dy != d0;
-        if (!g.per[0] && (i == 0 || i == g.nx - 1)) {
-            d -= ihx2;
-            wall = true;
-        }
-        if (!g.per[2]) {
-            if (k == 0) { d -= ihz2; wall = true; }
-            if (k == g.nz - 1) { d -= ihz2; wall = true; }
-        }
-        const T inv = wall ? T(1) / d : inv0;
-        u[idx] = c - omega * r * inv;
-        pm = pc;
-        pc = pp;
-    }
-}
-
 // ---------------------------------------------------------------------------
 // Acceleration g = -grad phi by the fourth-order central difference of Sec. 3
 // (Eq. 4thorder_acceleration): along each axis,
@@ -1375,16 +1304,8 @@ cudaError_t launch_gsrb(const LevelGeom& g, int colour, double omega, T* u, cons
     const int kc = kchunk_for(g, BX, BY);
     dim3 block(BX, BY, 1);
     dim3 grid((g.nx + BX - 1) / BX, (g.ny + BY - 1) / BY, (g.nz + kc - 1) / kc);
-    const bool aligned = ((reinterpret_cast<uintptr_t>(u) | reinterpret_cast<uintptr_t>(rhs)) % (2 * sizeof(T))) == 0;
-    if (!has_faces(g) && (g.nx & 1) == 0 && aligned) {
-        const int kp = kchunk_for(g, 2 * BX, BY);
-        dim3 gp((unsigned)((g.nx / 2 + BX - 1) / BX), (unsigned)((g.ny + BY - 1) / BY), (unsigned)((g.nz + kp - 1) / kp));
-        k_gsrb_pairs<T><<<gp, block, 0, st>>>(g, colour & 1, T(omega), u, rhs, kp);
-    } else if (has_faces(g)) {
-        k_gsrb<T, true><<<grid, block, 0, st>>>(g, colour & 1, T(omega), u, rhs, kc);
-    } else {
-        k_gsrb<T, false><<<grid, block, 0, st>>>(g, colour & 1, T(omega), u, rhs, kc);
-    }
+    if (has_faces(g)) k_gsrb<T, true><<<grid, block, 0, st>>>(g, colour & 1, T(omega), u, rhs, kc);
+    else k_gsrb<T, false><<<grid, block, 0, st>>>(g, colour & 1, T(omega), u, rhs, kc);
     return cudaGetLastError();
 }
 
