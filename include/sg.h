@@ -192,7 +192,8 @@ sg_status sg_potential(sg_grid* g, double* phi_out, int on_device);
  * stencil reaches two cells past a wall: on Dirichlet axes both ghost layers
  * reflect through the grid's face values (ghost m = 2 phi_face - the m-th cell
  * from the wall, m = 1, 2; zero faces when none were set), periodic axes wrap.
- * Errors: SG_ERR_ARG (NULL g or g_out), SG_ERR_STATE (phi NULL before any
+ * g_out must not overlap phi.
+ * Errors: SG_ERR_ARG (NULL g or g_out, overlap), SG_ERR_STATE (phi NULL before any
  * solve), SG_ERR_CUDA (a CUDA call failed, the staging allocation included).
  */
 sg_status sg_gravity(sg_grid* g, const double* phi, double* g_out, int on_device);

@@ -1291,6 +1291,11 @@ sg_status sg_gravity(sg_grid* g, const double* phi, double* g_out, int on_device
     if (!g || !g_out) return fail(SG_ERR_ARG, "NULL argument");
     if (!phi && !g->have_solution) return fail(SG_ERR_STATE, "no solution yet");
     const long long n = g->lv[0].n;
+    if (phi && on_device) {
+        const uintptr_t a0 = reinterpret_cast<uintptr_t>(phi), b0 = reinterpret_cast<uintptr_t>(g_out);
+        if (a0 < b0 + 3 * n * sizeof(double) && b0 < a0 + n * sizeof(double))
+            return fail(SG_ERR_ARG, "g_out overlaps phi");
+    }
     const double* src = phi ? phi : g->phi;
     if (phi && !on_device) {
         if (!g->gphi) SG_CK(cudaMalloc(&g->gphi, n * sizeof(double)));

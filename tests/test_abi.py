@@ -90,6 +90,8 @@ def test_null_arguments_rejected(sg):
     assert L.sg_default_options(None) == 1
     assert L.sg_solve(None, 1e-8, 0, 0, None) == 1
     assert L.sg_set_density(None, None, 0, 1.0) == 1
+    assert L.sg_gravity(None, None, None, 0) == 1
+    assert L.sg_op_gsrb_sweep(None, 0, 0, 0, 1.0, None, None) == 1
     L.sg_destroy(None)
 
 

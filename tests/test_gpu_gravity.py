@@ -98,3 +98,12 @@ def test_full_size_256_analytic_sphere_potential():
     torch.cuda.synchronize()
     ref = O.gravity(p.exact, O.spacing(p.shape, p.lo, p.hi), p.bc, fc)
     assert relerr(out, ref) < TOL
+
+
+def test_overlapping_output_is_rejected():
+    sg = _sg()
+    g, _, _ = make_grid((8, 6, 10), (0, 0, 0))
+    out = torch.zeros((3, 8, 6, 10), dtype=torch.float64, device="cuda")
+    with pytest.raises(sg.SGError) as e:
+        g.gravity(out=out, phi=out[1])
+    assert e.value.status == 1
