@@ -73,3 +73,13 @@ def test_reference_arm_prints_on_rank_zero_only():
         steps, warmup, gpus = 1, 0, 2
     # rank 1 of 2 returns at once without work or output
     assert bench.run_reference(A(), 2, 1) is None
+
+
+def test_unblocked_bytes_model():
+    # two levels of 8 and 1 cells, RKL2 s = 3, (2, 1) smoothing, 2 cycles,
+    # 10 coarse stage-cells: per cycle 8 (3 (16 + 2 24) + 8.5 + 8.5) + 40 8,
+    # twice, + 16 10 + (20 + 28) 8
+    sys.path.insert(0, ROOT)
+    import bench
+    solver = dict(bench.SOLVER, s_smooth=3, n_pre=2, n_post=1)
+    assert bench.unblocked_bytes_per_solve([8, 1], solver, 2, 10) == 4528.0
