@@ -266,6 +266,37 @@ const char* sg_last_error(void);
 int sg_max_levels(const sg_grid* g);
 
 /* ------------------------------------------------------------------------
+ * Host-side planning: the numbers the solver computes on the host before it
+ * launches anything.  No device work; callable without a GPU.
+ * ------------------------------------------------------------------------ */
+
+/* The first `count` entries of the Legendre-zero schedule of App. A.5 for a
+ * level whose largest extent is N: s_k = Round(2.4048 / pi * N / k - 1/2),
+ * halves rounded up, for k = N/2 .. 1, a k skipped when its s repeats the
+ * previous one, then s_1 repeated (at least 1 each).  The coarsest-level and
+ * single-level solves run it.  SG_ERR_ARG for N < 1, count < 0, or s_out NULL
+ * with count > 0. */
+sg_status sg_plan_schedule(int N, int count, int* s_out);
+
+/* The stage coefficients the kernels run for one s-stage super-step of order 1
+ * (RKL1) or 2 (RKL2) (App. A, Eq. RKL_intermediate_source): arrays of s + 1
+ * entries, entry j = 1..s (entry 0 unused): mu_j, nu_j, mu~_j (mut) and
+ * gamma~_j (gt, zero for RKL1); *tau_max_over_dtpar = tau_max / dt_par.  Any
+ * output may be NULL.  SG_ERR_ARG for order not 1 or 2, s < 1 (RKL1), s < 2
+ * (RKL2) or s > 100000. */
+sg_status sg_plan_stage_coefficients(int order, int s, double* mu, double* nu, double* mut, double* gt,
+                                     double* tau_max_over_dtpar);
+
+/* Largest level count of the level rule (Sec. 4.1: N / 2^(L-1) even on every
+ * axis) for nx x ny x nz cells; 0 for a size below 1. */
+int sg_plan_levels(int nx, int ny, int nz);
+
+/* App. B's SOR omega = 2 / (1 + sqrt(1 - rho_J^2)) for nx x ny x nz cells on the
+ * box [lo, hi], rho_J = sum_d cos(pi / n_d) / h_d^2 over sum_d 1 / h_d^2.
+ * SG_ERR_ARG for sizes below 2, lo >= hi on an axis or NULL pointers. */
+sg_status sg_plan_sor_omega(int nx, int ny, int nz, const double lo[3], const double hi[3], double* omega);
+
+/* ------------------------------------------------------------------------
  * Optional per-kernel profile.  When enabled, every kernel the grid launches
  * is bracketed by CUDA events on the grid's stream (this adds a few
  * microseconds per launch, so time solves with it disabled) and the totals are

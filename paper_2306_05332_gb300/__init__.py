@@ -119,6 +119,11 @@ _SIGS = {
     "sg_set_profiling": ([_P, _I], _I),
     "sg_kernel_stats": ([_P, ctypes.POINTER(KernelStat)], _I),
     "sg_autotune": ([_P, _I, _I, ctypes.POINTER(TuneEntry), _I, ctypes.POINTER(_I)], _I),
+    "sg_plan_schedule": ([_I, _I, ctypes.POINTER(_I)], _I),
+    "sg_plan_stage_coefficients": ([_I, _I, ctypes.POINTER(_D), ctypes.POINTER(_D), ctypes.POINTER(_D),
+                                    ctypes.POINTER(_D), ctypes.POINTER(_D)], _I),
+    "sg_plan_levels": ([_I, _I, _I], _I),
+    "sg_plan_sor_omega": ([_I, _I, _I, ctypes.POINTER(_D), ctypes.POINTER(_D), ctypes.POINTER(_D)], _I),
     "sg_residual_restrict_noalloc": ([_I, _I, _I, ctypes.POINTER(_D), ctypes.POINTER(_D), ctypes.POINTER(_I),
                                       ctypes.POINTER(_P), _I, _P, _P, _P, ctypes.POINTER(_D), _P], _I),
 }
@@ -389,6 +394,36 @@ def residual_restrict_noalloc(shape, lo, hi, bc, u, rhs, coarse_out=None, faces=
                                               _dev_ptr(coarse_out, dt) if coarse_out is not None else None,
                                               out, stream))
     return (out[0], out[1]) if norms else None
+
+
+def plan_schedule(N, count):
+    """The Legendre-zero schedule of App. A.5 the solver runs (host only)."""
+    out = (_I * max(1, count))()
+    _check(lib().sg_plan_schedule(int(N), int(count), out))
+    return list(out[:count])
+
+
+def plan_stage_coefficients(order, s):
+    """{mu, nu, mut, gt: lists of s + 1, tau_max_over_dtpar} of one super-step (host only)."""
+    arrs = [(_D * (s + 1))() for _ in range(4)]
+    t = _D(0.0)
+    _check(lib().sg_plan_stage_coefficients(int(order), int(s), *arrs, ctypes.byref(t)))
+    return {"mu": list(arrs[0]), "nu": list(arrs[1]), "mut": list(arrs[2]), "gt": list(arrs[3]),
+            "tau_max_over_dtpar": t.value}
+
+
+def plan_levels(shape):
+    """Level count of the level rule for shape (nz, ny, nx) (host only)."""
+    nz, ny, nx = (int(v) for v in shape)
+    return lib().sg_plan_levels(nx, ny, nz)
+
+
+def plan_sor_omega(shape, lo, hi):
+    """App. B's SOR omega for shape (nz, ny, nx) on [lo, hi] (x, y, z order; host only)."""
+    nz, ny, nx = (int(v) for v in shape)
+    om = _D(0.0)
+    _check(lib().sg_plan_sor_omega(nx, ny, nz, (_D * 3)(*lo), (_D * 3)(*hi), ctypes.byref(om)))
+    return om.value
 
 
 def solve_batch(grids, tol=1e-8):

@@ -1209,6 +1209,50 @@ sg_status sg_get_options(const sg_grid* g, sg_options* opt) {
 
 int sg_max_levels(const sg_grid* g) { return g ? g->max_levels : 0; }
 
+sg_status sg_plan_schedule(int N, int count, int* s_out) {
+    g_err.clear();
+    if (N < 1 || count < 0 || (count > 0 && !s_out)) return fail(SG_ERR_ARG, "bad schedule arguments");
+    const std::vector<int> sched = accelerated_schedule(N, count);
+    for (int q = 0; q < count; ++q) s_out[q] = sched[q];
+    return SG_OK;
+}
+
+sg_status sg_plan_stage_coefficients(int order, int s, double* mu, double* nu, double* mut, double* gt,
+                                     double* tau_max_over_dtpar) {
+    g_err.clear();
+    if ((order != 1 && order != 2) || s < order || s > 100000) return fail(SG_ERR_ARG, "bad order / s");
+    const Rkl r = make_rkl(order, s);
+    for (int j = 0; j <= s; ++j) {
+        if (mu) mu[j] = r.mu[j];
+        if (nu) nu[j] = r.nu[j];
+        if (mut) mut[j] = r.mut[j];
+        if (gt) gt[j] = r.gt[j];
+    }
+    if (tau_max_over_dtpar) *tau_max_over_dtpar = r.tau_over_dtpar;
+    return SG_OK;
+}
+
+int sg_plan_levels(int nx, int ny, int nz) {
+    if (nx < 1 || ny < 1 || nz < 1) return 0;
+    return rule_levels(nx, ny, nz);
+}
+
+sg_status sg_plan_sor_omega(int nx, int ny, int nz, const double lo[3], const double hi[3], double* omega) {
+    g_err.clear();
+    if (!lo || !hi || !omega || nx < 2 || ny < 2 || nz < 2) return fail(SG_ERR_ARG, "bad arguments");
+    Level L;
+    L.nx = nx;
+    L.ny = ny;
+    L.nz = nz;
+    const int n3[3] = {nx, ny, nz};
+    for (int d = 0; d < 3; ++d) {
+        if (!(hi[d] > lo[d])) return fail(SG_ERR_ARG, "lo must be below hi on every axis");
+        L.h[d] = (hi[d] - lo[d]) / n3[d];
+    }
+    *omega = sor_omega(L);
+    return SG_OK;
+}
+
 sg_status sg_set_boundary(sg_grid* g, const double* const faces[6], int on_device) {
     g_err.clear();
     if (!g || !faces) return fail(SG_ERR_ARG, "NULL argument");
