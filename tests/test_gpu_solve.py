@@ -138,12 +138,31 @@ def test_anisotropic_mixed_boundaries(precision):
     assert rel_l2(phi, ref) < (1e-10 if precision == "fp64" else 1e-8)
 
 
-def test_full_size_sphere_256_mixed_five_levels():
+def _bench_settings():
+    import json
+    import os
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    sys.path.insert(0, root)
+    import bench
+    with open(os.path.join(root, "tests", "golden", "oracle_cycles_sphere256.json")) as f:
+        return bench.SOLVER, json.load(f)["cycles"]
+
+
+@pytest.mark.parametrize("settings", ["defaults", "bench"])
+def test_full_size_sphere_256_mixed_five_levels(settings):
     p = W.sphere(256)
     g = grid_for(p, "mixed")
+    if settings == "bench":
+        # the configuration bench.py times; the oracle's own cycle count on this
+        # workload with the same settings is stored by tests/golden/make_oracle_cycles.py
+        solver, oracle_cycles = _bench_settings()
+        g.set_options(**solver)
     info = g.solve(tol=1e-8, levels=5)
     phi = g.potential()
     assert info["levels"] == 5 and info["rel_residual"] <= 1e-8
+    if settings == "bench":
+        assert info["cycles"] == oracle_cycles
     h = O.spacing(p.shape, p.lo, p.hi)
     f = O.source(p.rho, 1.0, p.bc)
     r = O.residual(phi, f, h, p.bc, p.faces)
