@@ -83,3 +83,19 @@ def test_unblocked_bytes_model():
     import bench
     solver = dict(bench.SOLVER, s_smooth=3, n_pre=2, n_post=1)
     assert bench.unblocked_bytes_per_solve([8, 1], solver, 2, 10) == 4528.0
+
+
+def test_oracle_cycle_count_matches_bench_settings():
+    # the stored oracle cycle count must have been taken with the settings the
+    # bench times (tests/golden/make_oracle_cycles.py writes them out)
+    sys.path.insert(0, ROOT)
+    import bench
+    with open(os.path.join(ROOT, "tests", "golden", "oracle_cycles_sphere256.json")) as f:
+        g = json.load(f)
+    fields = dict(kv.split("=") for kv in g["solver"].split()[1:])
+    S = bench.SOLVER
+    assert g["solver"].split()[0] == f"RKL{S['rkl_order']}"
+    assert int(fields["s"]) == S["s_smooth"] and float(fields["tau_frac"]) == S["tau_frac"]
+    assert int(fields["n_pre"]) == S["n_pre"] and int(fields["n_post"]) == S["n_post"]
+    assert float(fields["coarse_tol"]) == S["coarse_tol"] and int(fields["coarse_max_ss"]) == S["coarse_max_ss"]
+    assert g["levels"] == bench.LEVELS and g["tol"] == bench.TOL
