@@ -31,6 +31,9 @@ Passages followed
 * Sec. 3, Eq. 4thorder_acceleration            -> ``gravity``
 * Sec. 4.1, L2 norm with cell volumes          -> ``l2norm``
 * Sec. 4.1, level-count rule                   -> ``level_count``
+* Sec. 2.1-2.3, the discrete solution the V-cycle converges to (Kronecker
+  sum of 1D second differences, DST-II / DFT diagonalisation)
+                                               -> ``direct_solve``
 * App. B, SOR omega and GS-RB (Sec. 2.2.4)      -> ``gs_rb_sweep``, ``sor_omega``
 
 Readings where the paper is silent or ambiguous (all listed in the design
@@ -650,6 +653,75 @@ def dense_solve(rho, lo, hi, bc, faces=None, four_pi_G=1.0):
     else:
         x = np.linalg.solve(A, rhs)
     return x.reshape(shape)
+
+
+def _axis_eigenvalues(n, hd, periodic):
+    """Eigenvalues of the 1D cell-centred second difference on n cells.
+    Dirichlet (ghost = -active, Eqs. solution_ghost / error_ghost): modes
+    sin(pi m (i + 1/2) / n), m = 1..n (the DST-II basis), lambda_m =
+    -(4 / h^2) sin^2(pi m / (2 n)).  Periodic (Eq. periodic): modes
+    exp(2 pi i m j / n), m = 0..n-1 (the DFT basis), lambda_m =
+    -(4 / h^2) sin^2(pi m / n)."""
+    m = np.arange(n) if periodic else np.arange(1, n + 1)
+    arg = np.pi * m / n if periodic else np.pi * m / (2.0 * n)
+    return -(4.0 / (hd * hd)) * np.sin(arg) ** 2
+
+
+def direct_solve(rho, lo, hi, bc, faces=None, four_pi_G=1.0):
+    """The exact discrete solution of L_h phi = f at any size, the result the
+    V-cycle of Sec. 2.1 converges to (Eq. discrete_laplace_3D with the ghost
+    rules of Sec. 2.3): L_h is a Kronecker sum of 1D second differences, each
+    diagonalised by the DST-II (Dirichlet axis) or the DFT (periodic axis).
+
+        b   = 2 phi_face / h_d^2 in the cells next to each Dirichlet face
+              (the known part of the ghost 2 phi_face - phi_active)
+        phi = V diag(1 / (lx + ly + lz)) V^-1 (f - b)
+
+    With every axis periodic, f is mean-free (Eq. source_modification), the
+    zero mode is dropped and phi has zero mean."""
+    import scipy.fft as sfft
+    rho = np.asarray(rho, dtype=np.float64)
+    shape = rho.shape
+    h = spacing(shape, lo, hi)
+    f = source(rho, four_pi_G, bc)
+    b = np.zeros(shape)
+    if faces is not None:
+        for d in range(3):
+            if bc[d] == PERIODIC:
+                continue
+            ax = 2 - d
+            lo_cells = [slice(None)] * 3
+            hi_cells = [slice(None)] * 3
+            lo_cells[ax], hi_cells[ax] = 0, -1
+            b[tuple(lo_cells)] += 2.0 * np.asarray(faces[2 * d]) / (h[d] * h[d])
+            b[tuple(hi_cells)] += 2.0 * np.asarray(faces[2 * d + 1]) / (h[d] * h[d])
+    c = f - b
+    lam = np.zeros(shape)
+    for d in range(3):
+        ax = 2 - d
+        ev = _axis_eigenvalues(shape[ax], h[d], bc[d] == PERIODIC)
+        sh = [1, 1, 1]
+        sh[ax] = shape[ax]
+        lam = lam + ev.reshape(sh)
+    dirichlet_axes = [2 - d for d in range(3) if bc[d] != PERIODIC]
+    periodic_axes = [2 - d for d in range(3) if bc[d] == PERIODIC]
+    ck = c
+    for ax in dirichlet_axes:
+        ck = sfft.dst(ck, type=2, axis=ax)
+    if periodic_axes:
+        ck = sfft.fftn(ck, axes=periodic_axes)
+    if all_periodic(bc):
+        lam[0, 0, 0] = 1.0
+        ck[0, 0, 0] = 0.0
+    ck = ck / lam
+    if periodic_axes:
+        ck = np.real(sfft.ifftn(ck, axes=periodic_axes))
+    for ax in dirichlet_axes:
+        ck = sfft.idst(ck, type=2, axis=ax)
+    phi = np.asarray(ck, dtype=np.float64)
+    if all_periodic(bc):
+        phi = phi - phi.mean()
+    return phi
 
 
 def operator_diagonal(shape, h, bc):

@@ -185,13 +185,21 @@ def _require_writable(out):
         raise TypeError("out must be a C-contiguous float64 array")
 
 
-def _dev_ptr(t, dtype):
+def _dev_ptr(t, dtype, shape=None, device=None):
+    """Device pointer of a contiguous CUDA tensor of the given dtype code
+    (0: float64, 1: float32).  With `shape` / `device` the tensor must have
+    exactly that shape and sit on that device: the kernels take bare pointers
+    and would read or write past a smaller buffer."""
     torch = _torch()
     if torch is None or not isinstance(t, torch.Tensor) or not t.is_cuda:
         raise TypeError("operator entry points take CUDA tensors")
     want = torch.float64 if dtype == 0 else torch.float32
     if t.dtype != want or not t.is_contiguous():
         raise TypeError(f"tensor must be contiguous {want}")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"tensor has shape {tuple(t.shape)}, expected {tuple(shape)}")
+    if device is not None and t.device != device:
+        raise ValueError(f"tensor is on {t.device}, expected {device}")
     return ctypes.c_void_p(t.data_ptr())
 
 
@@ -208,6 +216,9 @@ class Grid:
             torch = _torch()
             stream = torch.cuda.current_stream().cuda_stream if (torch and torch.cuda.is_available()) else 0
         self.stream = int(stream)
+        torch = _torch()
+        self.device = (torch.device("cuda", torch.cuda.current_device())
+                       if (torch and torch.cuda.is_available()) else None)
         h = ctypes.c_void_p()
         _check(lib().sg_create_grid(nx, ny, nz, (_D * 3)(*self.lo), (_D * 3)(*self.hi), (_I * 3)(*self.bc),
                                     self.precision, ctypes.c_void_p(self.stream), ctypes.byref(h)))
@@ -336,38 +347,72 @@ class Grid:
     def dtype_code(self):
         return 0 if self.precision == FP64 else 1
 
+    def level_shape(self, level):
+        """(nz, ny, nx) of multigrid level `level` (each axis halved per level)."""
+        if not 0 <= int(level) < self.max_levels:
+            raise ValueError(f"level {level} out of range [0, {self.max_levels})")
+        return tuple(n >> int(level) for n in self.shape)
+
+    def _op(self, t, level):
+        """Pointer of an operator argument: the level's shape, the grid's dtype and device."""
+        return _dev_ptr(t, self.dtype_code, self.level_shape(level), self.device)
+
     def op_superstep(self, level, order, s, tau_frac, u, rhs, out, homogeneous=False):
         """out = one RKL super-step from u (None: u = 0, fused FP32 path only)."""
         dt = self.dtype_code
-        _check(lib().sg_op_superstep(self._h, level, dt, order, s, float(tau_frac), int(homogeneous),
-                                     _dev_ptr(u, dt) if u is not None else None, _dev_ptr(rhs, dt),
-                                     _dev_ptr(out, dt)))
+        with _device_of(self.device):
+            _check(lib().sg_op_superstep(self._h, level, dt, order, s, float(tau_frac), int(homogeneous),
+                                         self._op(u, level) if u is not None else None, self._op(rhs, level),
+                                         self._op(out, level)))
 
     def op_gsrb_sweep(self, level, u, rhs, omega=1.0, homogeneous=False):
         """One red-black Gauss-Seidel / SOR sweep of L u = rhs, in place on u."""
         dt = self.dtype_code
-        _check(lib().sg_op_gsrb_sweep(self._h, level, dt, int(homogeneous), float(omega), _dev_ptr(u, dt),
-                                      _dev_ptr(rhs, dt)))
+        with _device_of(self.device):
+            _check(lib().sg_op_gsrb_sweep(self._h, level, dt, int(homogeneous), float(omega),
+                                          self._op(u, level), self._op(rhs, level)))
 
     def op_residual_restrict(self, level, u, rhs, coarse_out=None, homogeneous=False):
         dt = self.dtype_code
         norms = (_D * 2)()
-        _check(lib().sg_op_residual_restrict(self._h, level, dt, int(homogeneous), _dev_ptr(u, dt),
-                                             _dev_ptr(rhs, dt),
-                                             _dev_ptr(coarse_out, dt) if coarse_out is not None else None,
-                                             norms))
+        cp = None
+        if coarse_out is not None:
+            cshape = tuple(n // 2 for n in self.level_shape(level))
+            cp = _dev_ptr(coarse_out, dt, cshape, self.device)
+        with _device_of(self.device):
+            _check(lib().sg_op_residual_restrict(self._h, level, dt, int(homogeneous), self._op(u, level),
+                                                 self._op(rhs, level), cp, norms))
         return norms[0], norms[1]
 
     def op_prolong_correct(self, level, coarse, fine):
         dt = self.dtype_code
-        _check(lib().sg_op_prolong_correct(self._h, level, dt, _dev_ptr(coarse, dt), _dev_ptr(fine, dt)))
+        with _device_of(self.device):
+            _check(lib().sg_op_prolong_correct(self._h, level, dt, self._op(coarse, level + 1),
+                                               self._op(fine, level)))
 
     def op_coarse_solve(self, level, rhs, out):
         dt = self.dtype_code
         done = ctypes.c_int(0)
-        _check(lib().sg_op_coarse_solve(self._h, level, dt, _dev_ptr(rhs, dt), _dev_ptr(out, dt),
-                                        ctypes.byref(done)))
+        with _device_of(self.device):
+            _check(lib().sg_op_coarse_solve(self._h, level, dt, self._op(rhs, level), self._op(out, level),
+                                            ctypes.byref(done)))
         return done.value
+
+
+class _NoDevice:
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        return False
+
+
+def _device_of(device):
+    """Context that makes `device` current for the duration of a call."""
+    torch = _torch()
+    if device is None or torch is None:
+        return _NoDevice()
+    return torch.cuda.device(device)
 
 
 def residual_restrict_noalloc(shape, lo, hi, bc, u, rhs, coarse_out=None, faces=None, norms=True,
@@ -381,18 +426,30 @@ def residual_restrict_noalloc(shape, lo, hi, bc, u, rhs, coarse_out=None, faces=
     current stream).  Calls on one device must not overlap: they share one
     scratch array."""
     torch = _torch()
+    if torch is None or not isinstance(u, torch.Tensor) or not u.is_cuda:
+        raise TypeError("u must be a CUDA tensor")
     dt = 0 if u.dtype == torch.float64 else 1
     nz, ny, nx = (int(v) for v in shape)
+    dev = u.device
+    # the kernels take bare pointers: every array must have the stated shape and
+    # sit on u's device, whose scratch array the call uses
+    up = _dev_ptr(u, dt, (nz, ny, nx), dev)
+    rp = _dev_ptr(rhs, dt, (nz, ny, nx), dev)
+    cp = None
+    if coarse_out is not None:
+        cp = _dev_ptr(coarse_out, dt, (nz // 2, ny // 2, nx // 2), dev)
     fp = None
     if faces is not None:
-        fp = (_P * 6)(*[None if f is None else _dev_ptr(f, 0).value for f in faces])
+        if len(faces) != 6:
+            raise ValueError("faces: six entries (-x, +x, -y, +y, -z, +z)")
+        fshape = [(nz, ny)] * 2 + [(nz, nx)] * 2 + [(ny, nx)] * 2
+        fp = (_P * 6)(*[None if f is None else _dev_ptr(f, 0, fs, dev).value for f, fs in zip(faces, fshape)])
     out = (_D * 2)() if norms else None
     if stream is None:
-        stream = torch.cuda.current_stream(u.device).cuda_stream
-    _check(lib().sg_residual_restrict_noalloc(nx, ny, nz, (_D * 3)(*lo), (_D * 3)(*hi), (_I * 3)(*bc), fp, dt,
-                                              _dev_ptr(u, dt), _dev_ptr(rhs, dt),
-                                              _dev_ptr(coarse_out, dt) if coarse_out is not None else None,
-                                              out, stream))
+        stream = torch.cuda.current_stream(dev).cuda_stream
+    with torch.cuda.device(dev):
+        _check(lib().sg_residual_restrict_noalloc(nx, ny, nz, (_D * 3)(*lo), (_D * 3)(*hi), (_I * 3)(*bc), fp, dt,
+                                                  up, rp, cp, out, stream))
     return (out[0], out[1]) if norms else None
 
 

@@ -172,6 +172,8 @@ struct ProfRec {
 
 }  // namespace
 
+constexpr int kGraphKeySlots = 17;   // items the cached cycle graph is keyed on (run_cycle)
+
 struct sg_grid {
     int n[3];
     double lo[3], hi[3];
@@ -207,7 +209,7 @@ struct sg_grid {
     int last_levels = 0;
     // graph cache
     cudaGraphExec_t gexec = nullptr;
-    long long gkey[10] = {0};
+    uint64_t gkey[kGraphKeySlots] = {0};
     long long graph_launches = 0;
     long long launches = 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -765,15 +767,20 @@ sg_status run_cycle(sg_grid* g, int L, double* phi, const double* f, bool faces,
                            (g->precision == SG_MIXED ? coarse_fits<float>(g->lv[L - 1].n)
                                                      : coarse_fits<double>(g->lv[L - 1].n));
     if (!graphable) return cycle_body(g, L, phi, f, faces);
-    long long key[10] = {L, (long long)(uintptr_t)phi, (long long)(uintptr_t)f, faces ? 1 : 0,
-                         g->opt.rkl_order * 1000 + g->opt.s_smooth,
-                         g->opt.n_pre * 1000 + g->opt.n_post,
-                         (long long)std::llround(g->opt.tau_frac * 1e12),
-                         (long long)std::llround(g->opt.coarse_tol * 1e15) * 100000 + g->opt.coarse_max_ss,
-                         g->opt.smoother, (long long)std::llround(g->opt.omega * 1e15)};
-    long long key2 = ((long long)std::llround(g->opt.coarse_tau_frac * 1e12) * 2 + (g->prof ? 1 : 0)) * 2 +
-                     (g->opt.fused ? 1 : 0);
-    key[7] ^= key2 * 1315423911LL;
+    // Everything the captured cycle depends on, one slot per item (doubles by
+    // their bit pattern), compared slot by slot: no scaling, no folding.
+    auto bits = [](double v) {
+        uint64_t u;
+        std::memcpy(&u, &v, sizeof(u));
+        return u;
+    };
+    const uint64_t key[kGraphKeySlots] = {(uint64_t)L, (uint64_t)(uintptr_t)phi, (uint64_t)(uintptr_t)f,
+                                          faces ? 1u : 0u, (uint64_t)g->opt.rkl_order, (uint64_t)g->opt.s_smooth,
+                                          bits(g->opt.tau_frac), (uint64_t)g->opt.n_pre, (uint64_t)g->opt.n_post,
+                                          bits(g->opt.coarse_tol), (uint64_t)g->opt.coarse_max_ss,
+                                          bits(g->opt.coarse_tau_frac), (uint64_t)g->opt.smoother,
+                                          bits(g->opt.omega), (uint64_t)(g->opt.fused ? 1 : 0),
+                                          (uint64_t)(g->prof ? 1 : 0), (uint64_t)(uintptr_t)g->d_sched};
     if (!g->gexec || std::memcmp(key, g->gkey, sizeof(key)) != 0) {
         drop_graph(g);
         cudaGraph_t graph = nullptr;
