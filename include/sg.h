@@ -81,7 +81,9 @@ typedef struct sg_options {
     double coarse_tau_frac; /* coarsest solve tau / tau_max; 0 = cos^2(pi / 2N)     [0]  */
     int    max_cycles;      /* V-cycle (or single-level super-step / sweep) cap,
                                1 .. 10^7                                        [100]*/
-    int    single_s;        /* levels == 1: fixed s; 0 = Legendre-zero schedule     [0]  */
+    int    single_s;        /* levels == 1: fixed s; 0 = Legendre-zero schedule
+                               (App. A.5); -1 = App. A.4's global s_opt of the
+                               grid's largest extent (sg_plan_s_opt)             [0]  */
     double single_tau_frac; /* levels == 1: tau / tau_max; 0 = cos^2(pi / 2N)       [0]  */
     int    fixed_cycles;    /* > 0: run exactly this many cycles (<= 10^7), ignore tol [0] */
     int    use_graph;       /* replay each V-cycle as a captured CUDA graph         [1]  */
@@ -286,6 +288,14 @@ sg_status sg_plan_schedule(int N, int count, int* s_out);
  * (RKL2) or s > 100000. */
 sg_status sg_plan_stage_coefficients(int order, int s, double* mu, double* nu, double* mut, double* gt,
                                      double* tau_max_over_dtpar);
+
+/* App. A.4's single fixed stage count s_opt for a level whose largest extent is
+ * N (Eqs. eigenvalue_RKL, spectral_rad_RKL, sopt_theory and the two-step search
+ * that follows them): the s in [first zero of P_s(cos(pi / N)), N] with the
+ * smallest spectral radius max_{1 <= k <= min(6, N/2)} |P_s(cos(k pi / N))|, the
+ * first such s on ties.  levels == 1 with single_s = -1 runs it.  SG_ERR_ARG
+ * for N < 2, N > 10^6 or s_out NULL. */
+sg_status sg_plan_s_opt(int N, int* s_out);
 
 /* Largest level count of the level rule (Sec. 4.1: N / 2^(L-1) even on every
  * axis) for nx x ny x nz cells; 0 for a size below 1. */

@@ -463,7 +463,8 @@ class Options:
     coarse_max_ss: int = 64    # cap on coarsest-level super-steps
     coarse_tau_frac: float = 0.0   # 0 = coarse_tau_frac(N)
     max_cycles: int = 100
-    single_s: int = 0          # levels == 1: fixed s (0 = accelerated schedule)
+    single_s: int = 0          # levels == 1: fixed s (0 = accelerated schedule,
+                               # -1 = App. A.4's global s_opt of the largest extent)
     single_tau_frac: float = 0.0   # levels == 1: 0 = coarse_tau_frac(N)
     smoother: str = "rkl"      # "rkl" (RKL super-steps) or "gsrb" (the paper's GS-RB)
     omega: float = 1.0         # GS-RB relaxation factor: 1 = Gauss-Seidel, (1, 2) = SOR;
@@ -596,7 +597,12 @@ def solve(rho, lo, hi, bc, faces=None, four_pi_G=1.0, tol=1e-10, levels=0,
         if L == 1 and not single_rkl:
             phi = relax(phi, f, h, bc, faces, opts, 1)
         elif L == 1:
-            s = opts.single_s if opts.single_s > 0 else sched[m]
+            if opts.single_s > 0:
+                s = opts.single_s
+            elif opts.single_s < 0:
+                s = s_opt_global(N)
+            else:
+                s = sched[m]
             phi = rkl_superstep(phi, f, h, bc, faces, 1, s, single_c)
         else:
             phi = vcycle(phi, f, h, bc, faces, L, opts, record=info.coarse_ss)

@@ -123,6 +123,7 @@ _SIGS = {
     "sg_plan_stage_coefficients": ([_I, _I, ctypes.POINTER(_D), ctypes.POINTER(_D), ctypes.POINTER(_D),
                                     ctypes.POINTER(_D), ctypes.POINTER(_D)], _I),
     "sg_plan_levels": ([_I, _I, _I], _I),
+    "sg_plan_s_opt": ([_I, ctypes.POINTER(_I)], _I),
     "sg_plan_sor_omega": ([_I, _I, _I, ctypes.POINTER(_D), ctypes.POINTER(_D), ctypes.POINTER(_D)], _I),
     "sg_residual_restrict_noalloc": ([_I, _I, _I, ctypes.POINTER(_D), ctypes.POINTER(_D), ctypes.POINTER(_I),
                                       ctypes.POINTER(_P), _I, _P, _P, _P, ctypes.POINTER(_D), _P], _I),
@@ -467,6 +468,13 @@ def plan_stage_coefficients(order, s):
     _check(lib().sg_plan_stage_coefficients(int(order), int(s), *arrs, ctypes.byref(t)))
     return {"mu": list(arrs[0]), "nu": list(arrs[1]), "mut": list(arrs[2]), "gt": list(arrs[3]),
             "tau_max_over_dtpar": t.value}
+
+
+def plan_s_opt(N):
+    """App. A.4's global s_opt for a level of largest extent N (host only)."""
+    out = _I(0)
+    _check(lib().sg_plan_s_opt(int(N), ctypes.byref(out)))
+    return out.value
 
 
 def plan_levels(shape):

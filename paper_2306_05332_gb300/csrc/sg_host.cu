@@ -141,6 +141,55 @@ std::vector<int> accelerated_schedule(int N, int count) {
     return out;
 }
 
+// P_s(x) by the three-term recursion of the Legendre polynomials.
+double legendre_p(int s, double x) {
+    if (s == 0) return 1.0;
+    double pm = 1.0, p = x;
+    for (int j = 2; j <= s; ++j) {
+        const double pn = ((2.0 * j - 1.0) * x * p - (j - 1.0) * pm) / j;
+        pm = p;
+        p = pn;
+    }
+    return p;
+}
+
+// App. A.4: the first s at which lambda_k,RKL(s) = P_s(cos(k pi / N)) (Eq.
+// eigenvalue_RKL) reaches zero or changes sign.
+int first_zero_s(int k, int N) {
+    const double x = std::cos(k * M_PI / N);
+    double prev = 1.0;
+    for (int s = 1;; ++s) {
+        const double cur = legendre_p(s, x);
+        if (cur == 0.0 || (cur > 0.0) != (prev > 0.0)) return s;
+        prev = cur;
+    }
+}
+
+// Eq. spectral_rad_RKL with k restricted to 1 .. min(6, N/2) (App. A.4, step 1).
+double spectral_radius6(int s, int N) {
+    const int kmax = std::min(6, std::max(1, N / 2));
+    double r = 0.0;
+    for (int k = 1; k <= kmax; ++k) r = std::max(r, std::fabs(legendre_p(s, std::cos(k * M_PI / N))));
+    return r;
+}
+
+// App. A.4's two-step search for the single fixed s: the s in [first zero of
+// lambda_1,RKL(s), N] with the smallest six-mode spectral radius (the first
+// one on ties).
+int s_opt_global(int N) {
+    const int s0 = first_zero_s(1, N);
+    int best = s0;
+    double best_r = INFINITY;
+    for (int s = s0; s <= std::max(s0, N); ++s) {
+        const double r = spectral_radius6(s, N);
+        if (r < best_r) {
+            best_r = r;
+            best = s;
+        }
+    }
+    return best;
+}
+
 double cell_tau_frac(int N) {
     const double c = std::cos(M_PI / (2.0 * N));
     return c * c;
@@ -332,7 +381,7 @@ sg_status check_opts(const sg_options* o) {
     if (o->coarse_max_ss < 1 || o->coarse_max_ss > 100000) return fail(SG_ERR_ARG, "coarse_max_ss out of range");
     if (!(o->coarse_tau_frac >= 0.0 && o->coarse_tau_frac <= 1.0)) return fail(SG_ERR_ARG, "coarse_tau_frac out of range");
     if (o->max_cycles < 1 || o->max_cycles > kMaxCycles) return fail(SG_ERR_ARG, "max_cycles out of range");
-    if (o->single_s < 0 || o->single_s > 100000) return fail(SG_ERR_ARG, "single_s out of range");
+    if (o->single_s < -1 || o->single_s > 100000) return fail(SG_ERR_ARG, "single_s out of range");
     if (!(o->single_tau_frac >= 0.0 && o->single_tau_frac <= 1.0)) return fail(SG_ERR_ARG, "single_tau_frac out of range");
     if (o->fixed_cycles < 0 || o->fixed_cycles > kMaxCycles) return fail(SG_ERR_ARG, "fixed_cycles out of range");
     if (o->smoother != SG_SMOOTH_RKL && o->smoother != SG_SMOOTH_GSRB) return fail(SG_ERR_ARG, "unknown smoother");
@@ -839,6 +888,7 @@ struct SolveState {
     int limit = 0;
     double single_c = 1.0;
     std::vector<int> single_sched;
+    int single_s_opt = 0;           // single_s = -1: App. A.4's global s_opt of the level
     long long su = 0;
     int m = 0;
     bool done = false;
@@ -891,6 +941,7 @@ sg_status solve_begin(sg_grid* g, SolveState& S, double tol, int L, double* phi,
     if (L == 1) {
         // every distinct entry: the schedule repeats its last value (k = 1) from there on
         S.single_sched = accelerated_schedule(N0, N0 / 2 + 2);
+        S.single_s_opt = g->opt.single_s < 0 ? s_opt_global(N0) : 0;
     } else {
         const Level& Lc = g->lv[L - 1];
         const int Nc = std::max(Lc.nx, std::max(Lc.ny, Lc.nz));
@@ -966,8 +1017,9 @@ sg_status solve_single_step(sg_grid* g, SolveState& S) {
         *g->host_ss = 0;
         return SG_OK;
     }
-    const int s = g->opt.single_s > 0 ? g->opt.single_s
-                                       : S.single_sched[std::min<size_t>(S.m, S.single_sched.size() - 1)];
+    const int s = g->opt.single_s > 0   ? g->opt.single_s
+                  : g->opt.single_s < 0 ? S.single_s_opt
+                                        : S.single_sched[std::min<size_t>(S.m, S.single_sched.size() - 1)];
     if (g->precision == SG_MIXED) {
         // mixed precision: an FP32 super-step on the error equation L e = r
         float* e = (float*)L0.u;
@@ -1236,6 +1288,13 @@ sg_status sg_plan_stage_coefficients(int order, int s, double* mu, double* nu, d
         if (gt) gt[j] = r.gt[j];
     }
     if (tau_max_over_dtpar) *tau_max_over_dtpar = r.tau_over_dtpar;
+    return SG_OK;
+}
+
+sg_status sg_plan_s_opt(int N, int* s_out) {
+    g_err.clear();
+    if (N < 2 || N > 1000000 || !s_out) return fail(SG_ERR_ARG, "need 2 <= N <= 10^6 and an output pointer");
+    *s_out = s_opt_global(N);
     return SG_OK;
 }
 

@@ -264,3 +264,27 @@ def test_fused_option_change_takes_effect_on_the_same_grid():
     # fused: one launch per super-step (3 per cycle); unfused: one per stage
     assert counts[1] == [2 * 3, 2 * 3]
     assert counts[0] == [2 * 3 * 3]
+
+
+def test_operator_wrappers_check_shapes():
+    # every operator argument must have its level's shape (coarse arrays the
+    # next level's); a mismatch raises before anything is launched
+    g, _, _ = make_grid((16, 24, 8), (1, 1, 1), "fp64")
+    u = torch.zeros((16, 24, 8), dtype=torch.float64, device="cuda")
+    rhs = torch.zeros_like(u)
+    out = torch.zeros_like(u)
+    bad = torch.zeros((16, 24, 4), dtype=torch.float64, device="cuda")
+    with pytest.raises(ValueError):
+        g.op_superstep(0, 2, 3, 1.0, u, bad, out)
+    with pytest.raises(ValueError):
+        g.op_superstep(1, 2, 3, 1.0, u, rhs, out)            # level-0 arrays at level 1
+    with pytest.raises(ValueError):
+        g.op_residual_restrict(0, u, rhs, torch.zeros((8, 12, 2), dtype=torch.float64, device="cuda"))
+    with pytest.raises(ValueError):
+        g.op_prolong_correct(0, bad, out)
+    with pytest.raises(ValueError):
+        g.op_gsrb_sweep(0, bad, rhs)
+    with pytest.raises(ValueError):
+        g.op_coarse_solve(0, bad, out)
+    with pytest.raises(TypeError):
+        g.op_superstep(0, 2, 3, 1.0, u.float(), rhs, out)

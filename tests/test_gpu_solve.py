@@ -62,6 +62,46 @@ def test_sinusoid_single_level_rkl1_closed_form():
     np.testing.assert_allclose(info["history"], rinfo.history, rtol=1e-9, atol=1e-14)
 
 
+@pytest.mark.parametrize("single_s", [0, -1])
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_single_level_accelerated_rkl_matches_oracle(single_s, precision):
+    # App. A.5 (single_s = 0: the Legendre-zero schedule, k = N/2 .. 1 with
+    # repeats skipped, then s_1,opt) and App. A.4 (single_s = -1: the global
+    # s_opt every super-step), single-level, a fixed count of super-steps
+    p = W.smooth_sphere(32)
+    steps = 24
+    g = grid_for(p, precision, single_s=single_s, fixed_cycles=steps)
+    info = g.solve(tol=0.0, levels=1)
+    phi = g.potential()
+    opts = O.Options(single_s=single_s)
+    ref, rinfo = O.solve(p.rho, p.lo, p.hi, p.bc, p.faces, p.four_pi_G, levels=1, opts=opts, cycles=steps)
+    assert info["cycles"] == rinfo.cycles == steps
+    if precision == "fp64":
+        assert rel_l2(phi, ref) < 1e-12
+        np.testing.assert_allclose(info["history"], rinfo.history, rtol=1e-9, atol=1e-14)
+    else:
+        # FP32 super-steps on the error equation, FP64 update: FP32 rounding of
+        # each correction, relative to the potential
+        assert rel_l2(phi, ref) < 1e-5
+    if single_s == -1:
+        sg = _sg()
+        assert sg.plan_s_opt(32) == O.s_opt_global(32)
+
+
+def test_single_level_accelerated_rkl_anisotropic_to_tolerance():
+    # the schedule of the largest extent on a 24 x 40 x 32 box with mixed walls
+    shape, lo, hi, bc = (24, 40, 32), (0.0, 0.0, 0.0), (1.0, 1.25, 0.75), (0, 1, 0)
+    rho = W.random_field(shape, 81)
+    faces = W.random_faces(shape, 82)
+    p = W.Problem(rho=rho, lo=lo, hi=hi, bc=bc, faces=faces, four_pi_G=1.0)
+    g = grid_for(p, "fp64")
+    info = g.solve(tol=1e-9, levels=1)
+    phi = g.potential()
+    ref, rinfo = O.solve(rho, lo, hi, bc, faces, 1.0, tol=1e-9, levels=1)
+    assert info["cycles"] == rinfo.cycles
+    assert rel_l2(phi, ref) < 1e-12
+
+
 @pytest.mark.parametrize("order,s,c", [(2, 3, 1.0), (1, 2, 0.75)])
 def test_sphere_fp64_fixed_cycles_match_oracle(order, s, c):
     p = W.sphere(64)

@@ -1,7 +1,7 @@
 """The host-side numbers of the CUDA path against the oracle, on the CPU
 (no device work): the Legendre-zero schedule of App. A.5, the RKL stage
 coefficients the kernels run (App. A; RKL2 of the a_s + b_s P_s family), the
-level rule of Sec. 4.1 and App. B's SOR omega.  The C++ and the oracle are
+level rule of Sec. 4.1, App. B's SOR omega and App. A.4's global s_opt.  The C++ and the oracle are
 written separately; schedules and level counts must agree exactly, the
 coefficients to a few ulps."""
 
@@ -51,6 +51,11 @@ def test_sor_omega_matches_oracle(sg, shape, lo, hi):
     assert abs(om - O.sor_omega(shape, O.spacing(shape, lo, hi))) < 1e-14
 
 
+@pytest.mark.parametrize("N", [2, 3, 4, 8, 16, 24, 32, 48, 64, 96, 100, 128, 200, 256, 512, 1024])
+def test_global_s_opt_matches_oracle(sg, N):
+    assert sg.plan_s_opt(N) == O.s_opt_global(N)
+
+
 def test_planning_rejects_bad_arguments(sg):
     L = sg.lib()
     assert L.sg_plan_schedule(0, 3, None) == 1
@@ -58,5 +63,6 @@ def test_planning_rejects_bad_arguments(sg):
     assert L.sg_plan_stage_coefficients(2, 1, None, None, None, None, None) == 1
     assert L.sg_plan_stage_coefficients(3, 5, None, None, None, None, None) == 1
     assert L.sg_plan_levels(0, 4, 4) == 0
+    assert L.sg_plan_s_opt(1, None) == 1
     with pytest.raises(sg.SGError):
         sg.plan_sor_omega((8, 8, 8), (0, 0, 0), (1, 0, 1))

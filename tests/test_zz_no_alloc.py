@@ -143,3 +143,22 @@ def test_rejects_bad_arguments():
     assert _raw((8, 8, 8), dtype=2) == 1
     assert _raw((8, 8, 1)) == 1
     assert _raw((8, 8, 8), bc=(0, 3, 0)) == 1
+
+
+@pytest.mark.gpu
+def test_binding_rejects_arrays_of_the_wrong_shape():
+    # the kernels take bare pointers: the binding checks every array against the
+    # stated shape before the call, so a short buffer is never written past
+    sg = _sg()
+    shape, bc = (8, 8, 8), (0, 0, 0)
+    u = torch.zeros(shape, dtype=torch.float64, device="cuda")
+    rhs = torch.zeros(shape, dtype=torch.float64, device="cuda")
+    with pytest.raises(ValueError):
+        sg.residual_restrict_noalloc((8, 8, 16), LO, HI, bc, u, rhs, None)
+    with pytest.raises(ValueError):
+        sg.residual_restrict_noalloc(shape, LO, HI, bc, u, rhs, torch.zeros((4, 4, 2), dtype=torch.float64,
+                                                                            device="cuda"))
+    faces = [torch.zeros((8, 8), dtype=torch.float64, device="cuda") for _ in range(6)]
+    faces[4] = torch.zeros((8, 4), dtype=torch.float64, device="cuda")
+    with pytest.raises(ValueError):
+        sg.residual_restrict_noalloc(shape, LO, HI, bc, u, rhs, None, faces=faces)
