@@ -62,6 +62,11 @@ typedef enum sg_smoother {
     SG_SMOOTH_GSRB = 1           /* red-black Gauss-Seidel / SOR sweeps (Sec. 2.2.4, App. B) */
 } sg_smoother;
 
+typedef enum sg_staging {
+    SG_STAGE_CP_ASYNC = 0,       /* fused super-step planes staged by per-strip asynchronous copies */
+    SG_STAGE_TMA = 1             /* ... by tensor-map box copies completing on an mbarrier */
+} sg_staging;
+
 typedef enum sg_precision {
     SG_FP64 = 0,                 /* every sweep in FP64 */
     SG_MIXED = 1                 /* FP32 V-cycle on the error equation inside an FP64
@@ -104,6 +109,17 @@ typedef struct sg_options {
     double max_residual_tol;/* > 0: stop when max |L phi - f| <= this (App. B's
                                test) instead of the relative L2 test; tol is then
                                ignored                                          [0]  */
+    int    tile_rows;       /* rows of the tile of the fused s = 2, 3 super-step:
+                               14 or 16; 0 = the launcher's cost model (the plan
+                               whose busiest SM has the least work)           [0]  */
+    int    staging;         /* sg_staging: how the fused s = 2, 3 super-step stages
+                               its planes in shared memory.  SG_STAGE_TMA: two
+                               tensor-map box copies per field and plane, issued
+                               by one thread, completing on an mbarrier (waits
+                               bounded), halo cells past a wall rebuilt from
+                               their mirrors; it needs no wrap in x and y,
+                               nx % 4 == 0 and an even ny (other levels stage by
+                               per-strip copies)                  [SG_STAGE_CP_ASYNC]*/
 } sg_options;
 
 #define SG_MAX_HISTORY 256
@@ -143,6 +159,22 @@ sg_status sg_default_options(sg_options* opt);
  */
 sg_status sg_create_grid(int nx, int ny, int nz, const double lo[3], const double hi[3],
                          const int bc[3], int precision, void* cuda_stream, sg_grid** out);
+
+/*
+ * Create a two-dimensional solver grid of nx x ny cells on the rectangle
+ * [lo, hi] (order x, y), boundary kinds bc[2], for the 2D variants of Sec. 2.2:
+ * the five-point Laplacian (Eq. discrete_laplace_2D), the 4-cell restriction
+ * (Eqs. restriction_equation_2D, restriction_example_2D) and the 9/3/3/1
+ * prolongation (Eq. prolongation_example_2D), with the same V-cycle, RKL
+ * stages, coarsest solve and ghost rules (Sec. 2.3) as the 3D grid.  Every
+ * other call takes the grid as a 3D grid with nz = 1: arrays are [1][ny][nx]
+ * = [ny][nx]; faces -x, +x are [ny], -y, +y are [nx]; the z faces are unused
+ * (pass NULL).  Level rule of Sec. 4.1 on x and y.  The fused super-step and
+ * cluster kernels are 3D-only; a 2D grid runs the per-stage kernels.  Sizes:
+ * 2 <= n_d <= 65536, nx * ny <= 2^31 - 1.  Errors as sg_create_grid.
+ */
+sg_status sg_create_grid_2d(int nx, int ny, const double lo[2], const double hi[2], const int bc[2], int precision,
+                            void* cuda_stream, sg_grid** out);
 
 /* Replace the grid's options (copied).  SG_ERR_ARG if a field is out of range. */
 sg_status sg_set_options(sg_grid* g, const sg_options* opt);
@@ -239,13 +271,15 @@ typedef struct sg_tune_entry {
                                   rate: the coarse grid does not see it) */
     double ms_per_decade;      /* ms_per_cycle / -log10(factor): the score (lower is better) */
     int    n_pre, n_post;      /* smoothing super-steps per V-cycle tried */
+    int    tile_rows;          /* tile rows of the fused super-step tried (0: cost model) */
 } sg_tune_entry;
 
 /*
  * Pick the smoother for this grid and its current density by measurement: for
  * every candidate (RKL order 1 and 2 -- or only the current order when
  * keep_order is 1 --, s = 2..6, a few tau fractions, fused on and off, and
- * (N_pre, N_post) = (2, 1), (3, 2), (4, 3) or (5, 3)) run
+ * (N_pre, N_post) = (2, 1), (3, 2), (4, 3) or (5, 3), and for the fused
+ * s = 2, 3 super-step both tile shapes, 32 x 14 and 32 x 16) run
  * two and six V-cycles at `levels` (0 = the level rule), take the difference
  * of their CUDA-event times (so per-solve set-up drops out) and score the time
  * per decade of residual reduction over cycles 2..6, bounded below by the
@@ -359,7 +393,8 @@ sg_status sg_op_gsrb_sweep(sg_grid* g, int level, int dtype, int homogeneous, do
                            void* u, const void* rhs);
 
 /* Residual r = rhs - L u at `level` (the negative of Eq. residual), restricted
- * to level + 1 by the 8-cell mean (Eq. restriction_example_3D) into coarse_out
+ * to level + 1 by the 8-cell mean (Eq. restriction_example_3D; the 4-cell mean of Eq.
+ * restriction_example_2D on a 2D grid) into coarse_out
  * when it is not NULL.  norms (host, may be NULL) receives
  * {sum r^2 (volume-weighted L2 squared), max |r|}; passing norms synchronises
  * the stream. */
@@ -367,8 +402,9 @@ sg_status sg_op_residual_restrict(sg_grid* g, int level, int dtype, int homogene
                                   const void* u, const void* rhs, void* coarse_out,
                                   double norms[2]);
 
-/* fine += P(coarse) (Eq. prolongation_example_3D) with coarse ghosts by the
- * boundary rule; `level` is the fine level, coarse is level + 1. */
+/* fine += P(coarse) (Eq. prolongation_example_3D; on a 2D grid Eq.
+ * prolongation_example_2D) with coarse ghosts by the boundary rule; `level` is
+ * the fine level, coarse is level + 1. */
 sg_status sg_op_prolong_correct(sg_grid* g, int level, int dtype, const void* coarse, void* fine);
 
 /* Coarsest-grid style solve of L u = rhs at `level` from u = 0 by the

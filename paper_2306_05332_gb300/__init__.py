@@ -25,7 +25,7 @@ import numpy as np
 
 from .build import LIB as LIB_PATH
 
-__all__ = ["Grid", "SGError", "Options", "SolveInfo", "lib", "solve", "PoissonSolve",
+__all__ = ["Grid", "Grid2D", "SGError", "Options", "SolveInfo", "lib", "solve", "PoissonSolve",
            "DIRICHLET", "PERIODIC", "FP64", "MIXED", "default_options", "exported_symbols"]
 
 DIRICHLET, PERIODIC = 0, 1
@@ -43,7 +43,8 @@ class Options(ctypes.Structure):
                 ("max_cycles", ctypes.c_int), ("single_s", ctypes.c_int),
                 ("single_tau_frac", ctypes.c_double), ("fixed_cycles", ctypes.c_int),
                 ("use_graph", ctypes.c_int), ("fused", ctypes.c_int), ("smoother", ctypes.c_int),
-                ("omega", ctypes.c_double), ("max_residual_tol", ctypes.c_double)]
+                ("omega", ctypes.c_double), ("max_residual_tol", ctypes.c_double), ("tile_rows", ctypes.c_int),
+                ("staging", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -75,12 +76,14 @@ class KernelStat(ctypes.Structure):
 
 SG_KERNEL_CLASSES = 11
 SMOOTHERS = {"rkl": 0, "gsrb": 1}
+STAGINGS = {"cp_async": 0, "tma": 1}
 
 
 class TuneEntry(ctypes.Structure):
     _fields_ = [("rkl_order", ctypes.c_int), ("s_smooth", ctypes.c_int), ("fused", ctypes.c_int),
                 ("tau_frac", ctypes.c_double), ("ms_per_cycle", ctypes.c_double), ("factor", ctypes.c_double),
-                ("ms_per_decade", ctypes.c_double), ("n_pre", ctypes.c_int), ("n_post", ctypes.c_int)]
+                ("ms_per_decade", ctypes.c_double), ("n_pre", ctypes.c_int), ("n_post", ctypes.c_int),
+                ("tile_rows", ctypes.c_int)]
 
 
 class SGError(RuntimeError):
@@ -98,6 +101,8 @@ _SIGS = {
     "sg_default_options": ([ctypes.POINTER(Options)], _I),
     "sg_create_grid": ([_I, _I, _I, ctypes.POINTER(_D), ctypes.POINTER(_D), ctypes.POINTER(_I), _I, _P,
                         ctypes.POINTER(_P)], _I),
+    "sg_create_grid_2d": ([_I, _I, ctypes.POINTER(_D), ctypes.POINTER(_D), ctypes.POINTER(_I), _I, _P,
+                           ctypes.POINTER(_P)], _I),
     "sg_set_options": ([_P, ctypes.POINTER(Options)], _I),
     "sg_get_options": ([_P, ctypes.POINTER(Options)], _I),
     "sg_set_boundary": ([_P, ctypes.POINTER(_P), _I], _I),
@@ -254,6 +259,8 @@ class Grid:
                 raise KeyError(k)
             if k == "smoother" and isinstance(v, str):
                 v = SMOOTHERS[v]
+            if k == "staging" and isinstance(v, str):
+                v = STAGINGS[v]
             setattr(o, k, v)
         _check(lib().sg_set_options(self._h, ctypes.byref(o)))
         return o
@@ -398,6 +405,47 @@ class Grid:
             _check(lib().sg_op_coarse_solve(self._h, level, dt, self._op(rhs, level), self._op(out, level),
                                             ctypes.byref(done)))
         return done.value
+
+
+class Grid2D(Grid):
+    """A two-dimensional grid (Sec. 2.2's 2D variants: five-point operator,
+    4-cell restriction, 9/3/3/1 prolongation): shape (ny, nx) on the rectangle
+    [lo, hi] (x, y order), bc = (x, y).  Arrays are (ny, nx); set_boundary takes
+    the four faces -x, +x (length ny) and -y, +y (length nx); gravity returns
+    (3, ny, nx) with a zero z component."""
+
+    def __init__(self, shape, lo=(0.0, 0.0), hi=(1.0, 1.0), bc=(DIRICHLET, DIRICHLET), precision="mixed",
+                 stream=None):
+        ny, nx = (int(v) for v in shape)
+        self.shape = (ny, nx)
+        self.lo, self.hi, self.bc = tuple(lo), tuple(hi), tuple(int(b) for b in bc)
+        self.precision = {"fp64": FP64, "mixed": MIXED, FP64: FP64, MIXED: MIXED}[precision]
+        torch = _torch()
+        if stream is None:
+            stream = torch.cuda.current_stream().cuda_stream if (torch and torch.cuda.is_available()) else 0
+        self.stream = int(stream)
+        self.device = (torch.device("cuda", torch.cuda.current_device())
+                       if (torch and torch.cuda.is_available()) else None)
+        h = ctypes.c_void_p()
+        _check(lib().sg_create_grid_2d(nx, ny, (_D * 2)(*self.lo), (_D * 2)(*self.hi), (_I * 2)(*self.bc),
+                                       self.precision, ctypes.c_void_p(self.stream), ctypes.byref(h)))
+        self._h = h
+        self.four_pi_G = 1.0
+
+    def set_boundary(self, faces):
+        faces = list(faces)
+        if len(faces) != 4:
+            raise ValueError("a 2D grid takes four faces: -x, +x, -y, +y")
+        ny, nx = self.shape
+        for f, n in zip(faces, (ny, ny, nx, nx)):
+            if f is not None and np.asarray(f).size != n:
+                raise ValueError(f"face of {np.asarray(f).size} values, expected {n}")
+        super().set_boundary(faces + [None, None])
+
+    def level_shape(self, level):
+        if not 0 <= int(level) < self.max_levels:
+            raise ValueError(f"level {level} out of range [0, {self.max_levels})")
+        return tuple(n >> int(level) for n in self.shape)
 
 
 class _NoDevice:

@@ -407,10 +407,11 @@ cudaError_t fused_configure() {
 }
 
 cudaError_t launch_superstep_fused(const LevelGeom& g, int order, int s, bool zero_y0, const FusedCoef& cf,
-                                   const float* y0, const float* f, float* out, cudaStream_t st) {
+                                   const float* y0, const float* f, float* out, cudaStream_t st, int tile_rows,
+                                   bool tma) {
     switch (s) {
         case 2:
-        case 3: return launch_superstep_lean(g, order, s, zero_y0, cf, y0, f, out, st);
+        case 3: return launch_superstep_lean(g, order, s, zero_y0, cf, y0, f, out, st, tile_rows, tma);
         case 4: return dispatch<4>(order, zero_y0, g, cf, y0, f, out, st);
         case 5: return dispatch<5>(order, zero_y0, g, cf, y0, f, out, st);
         case 6: return dispatch<6>(order, zero_y0, g, cf, y0, f, out, st);

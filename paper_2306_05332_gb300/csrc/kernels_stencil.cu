@@ -259,53 +259,117 @@ k_gsrb(const LevelGeom g, int colour, T omega, T* u, const T* __restrict__ rhs, 
 // m-th ghost is 2 phi_face - the m-th cell from the wall; zero face values
 // without face data); periodic axes wrap.  FP64 throughout.
 // ---------------------------------------------------------------------------
-// phi at cell i + off (off in -2..2, not 0) along an axis of extent n >= 2 and
-// stride `stride`, from the cell at flat index idx; flo / fhi: that axis's
-// low / high face arrays (or nullptr), fi: this cell's index in them.
-__device__ __forceinline__ double axis_phi(const double* u, int idx, int i, int n, int stride, int off, bool per,
-                                           const double* flo, const double* fhi, int fi) {
-    const int q = i + off;
-    if (q >= 0 && q < n) return u[idx + off * stride];
-    if (per) return u[idx + (q < 0 ? off + n : off - n) * stride];
-    const int m = q < 0 ? -1 - q : 2 * n - 1 - q;           // the mirrored cell
-    const double* f = q < 0 ? flo : fhi;
-    const double fv = f ? f[fi] : 0.0;
-    return 2.0 * fv - u[idx + (m - i) * stride];
+// The kernel: a 32 x 8 column tile walks its z chunk, the z neighbours in a
+// five-plane register window (one load per cell), the x and y neighbours from
+// the plane's tile with a two-cell halo in shared memory (double-buffered: one
+// barrier per plane).  160 threads fetch the halo of each plane by the wall /
+// periodic rule above; every other access is a fixed offset.
+constexpr int kGravHalo = 2;
+constexpr int kGravTX = BX + 2 * kGravHalo, kGravTY = BY + 2 * kGravHalo;
+
+// phi at (x, y, z) of a level with possibly out-of-range x or y (one axis at a
+// time: the halo of the star stencil has no corners): the periodic image, or
+// the reflection 2 phi_face - phi(mirror) past a Dirichlet wall (x, y >= 2 cells).
+__device__ __forceinline__ double halo_phi(const double* u, const LevelGeom& g, int x, int y, int z) {
+    const int plane = g.nx * g.ny;
+    if (x < 0 || x >= g.nx) {
+        if (g.per[0]) return u[z * plane + y * g.nx + (x < 0 ? x + g.nx : x - g.nx)];
+        const int m = x < 0 ? -1 - x : 2 * g.nx - 1 - x;
+        const double* f = x < 0 ? g.face[0] : g.face[1];
+        return 2.0 * (f ? f[z * g.ny + y] : 0.0) - u[z * plane + y * g.nx + m];
+    }
+    if (y < 0 || y >= g.ny) {
+        if (g.per[1]) return u[z * plane + (y < 0 ? y + g.ny : y - g.ny) * g.nx + x];
+        const int m = y < 0 ? -1 - y : 2 * g.ny - 1 - y;
+        const double* f = y < 0 ? g.face[2] : g.face[3];
+        return 2.0 * (f ? f[z * g.nx + x] : 0.0) - u[z * plane + m * g.nx + x];
+    }
+    return u[z * plane + y * g.nx + x];
 }
 
-__device__ __forceinline__ double fourth_order(double m2, double m1, double p1, double p2, double c) {
-    return c * fma(8.0, p1 - m1, m2 - p2);
+// phi of column (x, y) at plane q, possibly past a z wall.
+__device__ __forceinline__ double zcol_phi(const double* u, const LevelGeom& g, int col, int fz, int q) {
+    const int plane = g.nx * g.ny;
+    if (q >= 0 && q < g.nz) return u[q * plane + col];
+    if (g.per[2]) {                 // nz may be 1 (a 2D grid): wrap by the remainder
+        int m = q % g.nz;
+        if (m < 0) m += g.nz;
+        return u[m * plane + col];
+    }
+    const int m = q < 0 ? -1 - q : 2 * g.nz - 1 - q;
+    const double* f = q < 0 ? g.face[4] : g.face[5];
+    return 2.0 * (f ? f[fz] : 0.0) - u[m * plane + col];
 }
 
 __global__ void __launch_bounds__(BX * BY)
-k_gravity(const LevelGeom g, const double* __restrict__ u, double* __restrict__ out, double cx, double cy,
-          double cz, int kchunk) {
-    const int i = blockIdx.x * BX + threadIdx.x;
-    const int j = blockIdx.y * BY + threadIdx.y;
-    if (i >= g.nx || j >= g.ny) return;
-    const int k0 = blockIdx.z * kchunk;
-    const int k1 = min(k0 + kchunk, g.nz);
+k_gravity_stream(const LevelGeom g, const double* __restrict__ u, double* __restrict__ out, double cx, double cy,
+                 double cz, int kchunk) {
+    __shared__ double tile[2][kGravTY][kGravTX];
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * BX + tx;
+    const int i0 = blockIdx.x * BX, j0 = blockIdx.y * BY;
+    const int i = i0 + tx, j = j0 + ty;
+    const bool active = i < g.nx && j < g.ny;
     const int plane = g.nx * g.ny;
     const long long n = (long long)plane * g.nz;
+    const int k0 = blockIdx.z * kchunk, k1 = min(k0 + kchunk, g.nz);
+    // halo cell of this thread (tid < 160): 32 of the x halo (2 columns each
+    // side, 8 rows), 128 of the y halo (2 rows each side, 32 columns)
+    int hx = 0, hy = 0, sx = 0, sy = 0;
+    bool halo = false;
+    if (tid < 4 * BY) {
+        const int r = tid % BY, c = tid / BY;                 // c: 0, 1 left; 2, 3 right
+        sx = c < 2 ? c : BX + c;                              // tile columns 0, 1, BX + 2, BX + 3
+        sy = r + kGravHalo;
+        hx = i0 + sx - kGravHalo;
+        hy = j0 + r;
+        halo = hy < g.ny && (hx < g.nx + kGravHalo);
+    } else if (tid < 4 * BY + 4 * BX) {
+        const int t = tid - 4 * BY, c = t % BX, r = t / BX;  // r: 0, 1 below; 2, 3 above
+        sx = c + kGravHalo;
+        sy = r < 2 ? r : BY + r;
+        hx = i0 + c;
+        hy = j0 + sy - kGravHalo;
+        halo = hx < g.nx && (hy < g.ny + kGravHalo);
+    }
+    // keep halo cells of ragged tiles inside what the stencil can reach
+    if (halo) {
+        const int last_x = min(g.nx, i0 + BX) - 1, last_y = min(g.ny, j0 + BY) - 1;
+        if (hx > last_x + kGravHalo || hy > last_y + kGravHalo) halo = false;
+    }
+    const int col = active ? j * g.nx + i : 0;
+    const int fz = col;
+    double zm2 = 0.0, zm1 = 0.0, c = 0.0, zp1 = 0.0, zp2 = 0.0;
+    if (active) {
+        zm2 = zcol_phi(u, g, col, fz, k0 - 2);
+        zm1 = zcol_phi(u, g, col, fz, k0 - 1);
+        c = zcol_phi(u, g, col, fz, k0);
+        zp1 = zcol_phi(u, g, col, fz, k0 + 1);
+    }
     for (int k = k0; k < k1; ++k) {
-        const int idx = k * plane + j * g.nx + i;
-        const int fx = k * g.ny + j, fy = k * g.nx + i, fz = j * g.nx + i;
-        const bool px = g.per[0], py = g.per[1], pz = g.per[2];
-        const double gx = fourth_order(axis_phi(u, idx, i, g.nx, 1, -2, px, g.face[0], g.face[1], fx),
-                                       axis_phi(u, idx, i, g.nx, 1, -1, px, g.face[0], g.face[1], fx),
-                                       axis_phi(u, idx, i, g.nx, 1, 1, px, g.face[0], g.face[1], fx),
-                                       axis_phi(u, idx, i, g.nx, 1, 2, px, g.face[0], g.face[1], fx), cx);
-        const double gy = fourth_order(axis_phi(u, idx, j, g.ny, g.nx, -2, py, g.face[2], g.face[3], fy),
-                                       axis_phi(u, idx, j, g.ny, g.nx, -1, py, g.face[2], g.face[3], fy),
-                                       axis_phi(u, idx, j, g.ny, g.nx, 1, py, g.face[2], g.face[3], fy),
-                                       axis_phi(u, idx, j, g.ny, g.nx, 2, py, g.face[2], g.face[3], fy), cy);
-        const double gz = fourth_order(axis_phi(u, idx, k, g.nz, plane, -2, pz, g.face[4], g.face[5], fz),
-                                       axis_phi(u, idx, k, g.nz, plane, -1, pz, g.face[4], g.face[5], fz),
-                                       axis_phi(u, idx, k, g.nz, plane, 1, pz, g.face[4], g.face[5], fz),
-                                       axis_phi(u, idx, k, g.nz, plane, 2, pz, g.face[4], g.face[5], fz), cz);
-        out[idx] = gx;
-        out[n + idx] = gy;
-        out[2 * n + idx] = gz;
+        double(*t)[kGravTX] = tile[k & 1];
+        if (active) {
+            zp2 = zcol_phi(u, g, col, fz, k + 2);
+            t[ty + kGravHalo][tx + kGravHalo] = c;
+        } else if (i < g.nx + kGravHalo && j < g.ny + kGravHalo && (i < g.nx || j < g.ny)) {
+            // a ragged tile: this position is the halo just past the level's last column or row
+            t[ty + kGravHalo][tx + kGravHalo] = halo_phi(u, g, i, j, k);
+        }
+        if (halo) t[sy][sx] = halo_phi(u, g, hx, hy, k);
+        __syncthreads();
+        if (active) {
+            const int a = ty + kGravHalo, b = tx + kGravHalo;
+            const double gx = cx * fma(8.0, t[a][b + 1] - t[a][b - 1], t[a][b - 2] - t[a][b + 2]);
+            const double gy = cy * fma(8.0, t[a + 1][b] - t[a - 1][b], t[a - 2][b] - t[a + 2][b]);
+            const double gz = cz * fma(8.0, zp1 - zm1, zm2 - zp2);
+            const long long idx = (long long)k * plane + col;
+            out[idx] = gx;
+            out[n + idx] = gy;
+            out[2 * n + idx] = gz;
+            zm2 = zm1;
+            zm1 = c;
+            c = zp1;
+            zp1 = zp2;
+        }
     }
 }
 
@@ -760,6 +824,73 @@ k_prolong_correct(const LevelGeom g, const T* __restrict__ coarse, T* fine_u, in
     }
 }
 
+// ---- two-dimensional levels (Sec. 2.2: nz = 1, no z term) -------------------
+// Residual + 4-cell restriction (Eq. restriction_example_2D): r = rhs - L u by
+// the five-point operator (Eq. discrete_laplace_2D; on a 2D level the z
+// neighbours are the cell itself and 1 / h_z^2 is zero, so the seven-point
+// form reduces to it exactly), the coarse value the mean of a 2 x 2 block: the
+// x pair by a shuffle, the y pair through shared memory.
+template <typename T, bool FACES>
+__global__ void __launch_bounds__(BX * BY)
+k_residual_restrict2d(const LevelGeom g, const T* __restrict__ u, const T* __restrict__ rhs, T* coarse,
+                      Partial* partials) {
+    using A = typename Acc<T>::type;
+    __shared__ T s_acc[BY][BX];
+    const int i = blockIdx.x * BX + threadIdx.x;
+    const int j = blockIdx.y * BY + threadIdx.y;
+    const bool active = i < g.nx && j < g.ny;
+    A sq = A(0), mx = A(0), csum = A(0);
+    T r = T(0);
+    if (active) {
+        const int idx = j * g.nx + i;
+        const T c = u[idx];
+        T xm, xp, ym, yp;
+        xy_neighbours<FACES>(u, g, i, j, 0, idx, c, xm, xp, ym, yp);
+        const T two_c = T(2) * c;
+        r = rhs[idx] - (((xm - two_c) + xp) * ih2x<T>(g) + ((ym - two_c) + yp) * ih2y<T>(g));
+        const A ra = A(r);
+        sq = ra * ra;
+        mx = acc_abs(ra);
+    }
+    const T rx = r + __shfl_xor_sync(0xffffffffu, r, 1);          // x pair
+    s_acc[threadIdx.y][threadIdx.x] = rx;
+    __syncthreads();
+    if (((threadIdx.x | threadIdx.y) & 1) == 0 && active) {
+        const T cval = (s_acc[threadIdx.y][threadIdx.x] + s_acc[threadIdx.y + 1][threadIdx.x]) * T(0.25);
+        if (coarse) coarse[(j >> 1) * (g.nx >> 1) + (i >> 1)] = cval;
+        csum = A(cval);
+    }
+    block_reduce_write<A>(sq, mx, csum, partials, blockIdx.x + gridDim.x * blockIdx.y);
+}
+
+// Prolongation + correction of a 2D level (Eq. prolongation_example_2D): each
+// fine cell adds (9 A + 3 B + 3 C + D) / 16, A its parent, B and C the parent's
+// neighbours towards the cell along x and y, D the one between them; coarse
+// ghosts follow the level's rule (-e at a Dirichlet wall, the periodic image).
+template <typename T>
+__global__ void __launch_bounds__(BX * BY)
+k_prolong_correct2d(const LevelGeom g, const T* __restrict__ coarse, T* fine_u) {
+    const int i = blockIdx.x * BX + threadIdx.x;
+    const int j = blockIdx.y * BY + threadIdx.y;
+    if (i >= g.nx || j >= g.ny) return;
+    const int cnx = g.nx >> 1, cny = g.ny >> 1;
+    const int Ia = i >> 1, Ja = j >> 1;
+    int Ib = Ia + ((i & 1) ? 1 : -1), Jb = Ja + ((j & 1) ? 1 : -1);
+    T sx = T(1), sy = T(1);
+    if (Ib < 0 || Ib >= cnx) {
+        if (g.per[0]) Ib = (Ib + cnx) % cnx;
+        else { Ib = Ia; sx = T(-1); }
+    }
+    if (Jb < 0 || Jb >= cny) {
+        if (g.per[1]) Jb = (Jb + cny) % cny;
+        else { Jb = Ja; sy = T(-1); }
+    }
+    const T v = T(9) * coarse[Ja * cnx + Ia] + T(3) * sx * coarse[Ja * cnx + Ib] +
+                T(3) * sy * coarse[Jb * cnx + Ia] + sx * sy * coarse[Jb * cnx + Ib];
+    const int idx = j * g.nx + i;
+    fine_u[idx] = fine_u[idx] + v * T(1.0 / 16.0);
+}
+
 // The same prolongation + correction for FP32, nx % 4 == 0 and aligned
 // arrays: a thread owns a strip of four fine x cells on a pair of fine rows
 // (2J, 2J + 1).  Per coarse plane it reads coarse x = 2q - 1 .. 2q + 2 on rows
@@ -1095,6 +1226,7 @@ long long residual_zero_blocks(const LevelGeom& g) {
 }
 
 long long restrict_blocks(const LevelGeom& g) {
+    if (g.twod) return (long long)((g.nx + BX - 1) / BX) * ((g.ny + BY - 1) / BY);
     const int kc = even_kchunk(g);
     return (long long)((g.nx + BX - 1) / BX) * ((g.ny + BY - 1) / BY) * ((g.nz + kc - 1) / kc);
 }
@@ -1191,6 +1323,14 @@ cudaError_t launch_residual(const LevelGeom& g, const TI* u, const TI* rhs, TO* 
 template <typename T>
 cudaError_t launch_residual_restrict(const LevelGeom& g, const T* u, const T* rhs, T* coarse_out,
                                      Partial* partials, int* nblocks_out, cudaStream_t st) {
+    if (g.twod) {
+        dim3 block(BX, BY, 1);
+        dim3 grid((g.nx + BX - 1) / BX, (g.ny + BY - 1) / BY, 1);
+        if (has_faces(g)) k_residual_restrict2d<T, true><<<grid, block, 0, st>>>(g, u, rhs, coarse_out, partials);
+        else k_residual_restrict2d<T, false><<<grid, block, 0, st>>>(g, u, rhs, coarse_out, partials);
+        if (nblocks_out) *nblocks_out = (int)(grid.x * grid.y);
+        return cudaGetLastError();
+    }
     if constexpr (std::is_same<T, float>::value) {
         const bool aligned = ((reinterpret_cast<uintptr_t>(u) | reinterpret_cast<uintptr_t>(rhs) |
                                reinterpret_cast<uintptr_t>(coarse_out)) & 15) == 0;
@@ -1218,6 +1358,12 @@ cudaError_t launch_residual_restrict(const LevelGeom& g, const T* u, const T* rh
 
 template <typename T>
 cudaError_t launch_prolong_correct(const LevelGeom& g, const T* coarse, T* fine_u, cudaStream_t st) {
+    if (g.twod) {
+        dim3 block(BX, BY, 1);
+        dim3 grid((g.nx + BX - 1) / BX, (g.ny + BY - 1) / BY, 1);
+        k_prolong_correct2d<T><<<grid, block, 0, st>>>(g, coarse, fine_u);
+        return cudaGetLastError();
+    }
     if constexpr (std::is_same<T, float>::value) {
         const bool aligned = ((reinterpret_cast<uintptr_t>(coarse) | reinterpret_cast<uintptr_t>(fine_u)) & 15) == 0;
         if ((g.nx & 3) == 0 && (g.ny & 1) == 0 && (g.nz & 1) == 0 && aligned) {
@@ -1313,7 +1459,7 @@ cudaError_t launch_gravity(const LevelGeom& g, const double* phi, double* out, c
     const int kc = kchunk_for(g, BX, BY);
     dim3 block(BX, BY, 1);
     dim3 grid((g.nx + BX - 1) / BX, (g.ny + BY - 1) / BY, (g.nz + kc - 1) / kc);
-    k_gravity<<<grid, block, 0, st>>>(g, phi, out, c[0], c[1], c[2], kc);
+    k_gravity_stream<<<grid, block, 0, st>>>(g, phi, out, c[0], c[1], c[2], kc);
     return cudaGetLastError();
 }
 

@@ -45,8 +45,11 @@
 // when Y0 = 0).  Halo cells are re-read from L2 by neighbouring tiles.
 #include "sg_internal.cuh"
 
+#include <cuda.h>          // CUtensorMap and its encoder's signature (called through the runtime's entry point)
+
 #include <algorithm>
 #include <cstdint>
+#include <cstring>
 #include <type_traits>
 
 namespace sg {
@@ -65,6 +68,54 @@ __device__ __forceinline__ void cpa_commit() { asm volatile("cp.async.commit_gro
 __device__ __forceinline__ void cpa_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 __device__ __forceinline__ void cpa_wait_prev() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 __device__ __forceinline__ void prefetch_l2(const float* p) { asm volatile("prefetch.global.L2 [%0];\n" ::"l"(p)); }
+
+// ---- TMA staging: box copies completing on an mbarrier ---------------------
+__device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_init_fence() { asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory"); }
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
+    unsigned done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+// Every wait is bounded: a phase that does not complete within kWaitTries
+// hardware-suspended tries (seconds) is reported instead of hanging the GPU.
+constexpr int kWaitTries = 1 << 22;
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity) {
+    for (int i = 0; i < kWaitTries; ++i)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+// Generic-proxy accesses of a ring slot before the barrier that ends a phase,
+// async-proxy (TMA) writes of the same slot after it.
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+__device__ __forceinline__ void tma_load(float* dst, const CUtensorMap* map, int x, int y, int z,
+                                         unsigned long long* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+        "[%5];\n" ::"r"(smem_addr(dst)),
+        "l"(map), "r"(x), "r"(y), "r"(z), "r"(smem_addr(bar))
+        : "memory");
+}
+__device__ __forceinline__ void tma_prefetch(const CUtensorMap* map, int x, int y, int z) {
+    asm volatile("cp.async.bulk.prefetch.tensor.3d.L2.global.tile [%0, {%1, %2, %3}];\n" ::"l"(map), "r"(x), "r"(y),
+                 "r"(z)
+                 : "memory");
+}
+
+// Bounded waits that gave up (a device counter the host reads when a solve
+// turns non-finite; the kernel that gave up writes a NaN into its output).
+__device__ unsigned int g_lean_wait_timeouts = 0;
 
 // Index of cell v of an axis of n cells in the stored array and its sign:
 // periodic image, or odd reflection about both walls (period 2n).
@@ -98,11 +149,13 @@ struct Lean {
     static constexpr int W = TX + 2 * HX;            // plane row (floats)
     static constexpr int H = TY + 2 * NS;            // plane rows
     static constexpr int Q = W / 4;                  // strips per row
-    static constexpr int P = W * H;                  // floats per plane
-    static constexpr int HQ = H * Q;                 // strips per plane
     // planes store the even rows, then the odd rows, so that the first rows of
-    // consecutive row pairs are contiguous (conflict-free quarter-warp accesses)
-    __host__ __device__ static constexpr int rowoff(int r) { return (r & 1) * (H / 2) * W + (r >> 1) * W; }
+    // consecutive row pairs are contiguous (conflict-free quarter-warp accesses);
+    // each half starts on a 128-byte boundary, the alignment of a TMA box copy
+    static constexpr int HO = ((H / 2) * W + 31) / 32 * 32;   // offset of the odd rows (floats)
+    static constexpr int P = 2 * HO;                 // floats per plane
+    static constexpr int HQ = H * Q;                 // strips per plane
+    __host__ __device__ static constexpr int rowoff(int r) { return (r & 1) * HO + (r >> 1) * W; }
     // pipeline stage j covers rows [j, H - j) (an even count) and strips
     // [qlo(j), qhi(j)); one item = the strips of rows r and r + 1 at one q
     __host__ __device__ static constexpr int qlo(int j) { return (HX - (NS - j)) / 4; }
@@ -136,7 +189,8 @@ struct Lean {
     static constexpr int OW2 = OY + (NS - 1) * RY * P;
     static constexpr int OW3 = OW2 + RW2 * P;
     static constexpr int NFLOATS = OW3 + RW3 * P;
-    static constexpr size_t BYTES = size_t(NFLOATS) * sizeof(float);
+    static constexpr int NBAR = 4;                   // TMA path: one mbarrier per plane in flight
+    static constexpr size_t BYTES = size_t(NFLOATS) * sizeof(float) + NBAR * sizeof(unsigned long long);
     static_assert(S == 2 || S == 3, "lean super-step covers s = 2, 3");
     static_assert(HX >= NS - 1 && HX % 4 == 0, "x halo");
     static_assert(TY % 2 == 0 && H % 2 == 0, "row pairs");
@@ -165,11 +219,11 @@ struct LoadDesc {
     int flags;      // bit 4: one 16-byte copy; bits 0-3: cells negated by the x/y reflection
 };
 
-__device__ __forceinline__ LoadDesc make_desc(int k, int X0, int Yt, const LevelGeom& g, bool vec_ok, int W, int Q,
-                                              int H) {
+__device__ __forceinline__ LoadDesc make_desc(int k, int X0, int Yt, const LevelGeom& g, bool vec_ok, int Q,
+                                              int HO, int W) {
     LoadDesc d;
     const int r = k / Q, q = k % Q;
-    d.dst = (r & 1) * (H / 2) * W + (r >> 1) * W + 4 * q;
+    d.dst = (r & 1) * HO + (r >> 1) * W + 4 * q;
     int sy;
     const int yy = map_axis(Yt + r, g.ny, g.per[1] != 0, &sy);
     d.row = yy * g.nx;
@@ -216,6 +270,71 @@ __device__ __forceinline__ void fixup(const LoadDesc& d, float* plane_dst, int z
     *p = v;
 }
 
+// TMA path, tiles that reach past a Dirichlet x or y wall: the box copy fills
+// cells outside the level with zeros; each halo strip rebuilds its
+// out-of-level cells as the odd reflection of in-level cells of the same
+// staged plane (Eq. error_ghost, repeated: the mirror of cell -1-k is -cell k).
+struct FixDesc {
+    int dst;        // strip offset in the plane; -1: this thread owns no strip
+    int srow;       // offset of the mirrored row in the plane (-1: outside the tile)
+    int cols;       // mirrored local column of each cell, 8 bits each
+    int masks;      // bits 0-3: cell outside the level; 4-7: mirror inside the tile; 8-11: negated
+};
+
+template <int Q, int HO, int W, int H>
+__device__ __forceinline__ FixDesc make_fix(int k, int X0, int Yt, const LevelGeom& g) {
+    FixDesc d;
+    d.dst = -1;
+    d.srow = -1;
+    d.cols = 0;
+    d.masks = 0;
+    const int r = k / Q, q = k % Q;
+    const int gy = Yt + r;
+    int sy;
+    const int yy = map_axis(gy, g.ny, false, &sy);
+    const int rr = yy - Yt;
+    const bool row_in = rr >= 0 && rr < H;
+    const bool y_out = gy < 0 || gy >= g.ny;
+    int masks = 0, cols = 0;
+    for (int e = 0; e < 4; ++e) {
+        const int gx = X0 + 4 * q + e;
+        int sx;
+        const int xx = map_axis(gx, g.nx, false, &sx);
+        const int cc = xx - X0;
+        if (y_out || gx < 0 || gx >= g.nx) {
+            masks |= 1 << e;
+            if (row_in && cc >= 0 && cc < W) {
+                masks |= 16 << e;
+                cols |= cc << (8 * e);
+            }
+            if (sx * sy < 0) masks |= 256 << e;
+        }
+    }
+    d.dst = (r & 1) * HO + (r >> 1) * W + 4 * q;
+    if (masks) {
+        d.srow = row_in ? (rr & 1) * HO + (rr >> 1) * W : -1;
+        d.cols = cols;
+        d.masks = masks;
+    }
+    return d;
+}
+
+// The cells of one strip after a plane has landed: out-of-level cells from
+// their mirrors, every cell negated when the plane is the z reflection.
+__device__ __forceinline__ float4 fixed_strip(const FixDesc& d, const float* plane, float4 own, int zsign) {
+    float v[4] = {own.x, own.y, own.z, own.w};
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        if (d.masks & (1 << e)) {
+            float m = 0.f;
+            if (d.masks & (16 << e)) m = plane[d.srow + ((d.cols >> (8 * e)) & 255)];
+            v[e] = (d.masks & (256 << e)) ? -m : m;
+        }
+        if (zsign < 0) v[e] = -v[e];
+    }
+    return make_float4(v[0], v[1], v[2], v[3]);
+}
+
 __device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
 __device__ __forceinline__ void st4(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
 
@@ -257,29 +376,41 @@ __device__ __forceinline__ float4 later_strip(float4 c, float4 n, float4 s, floa
     return cat4(v01, v23);
 }
 
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+    unsigned long long d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(pk(a)), "l"(pk(b)));
+    return upk(d);
+}
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) {
+    unsigned long long d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(pk(a)), "l"(pk(b)));
+    return upk(d);
+}
+
 // One strip of stage 1: Lf = L Y0 - f, Y1 = c + mu~_1 tau Lf and the combined
-// fields W_2 (and W_3 for s = 3).  Scalar FP32: the chain Lf -> Y1 -> W_3 is
-// long, and four independent cells per strip hide its latency better than
-// two packed pairs.
+// fields W_2 (and W_3 for s = 3), in packed FP32 pairs (cells 0, 1 and 2, 3 of
+// the strip): a thread runs two strips of a row pair, so four independent
+// pairs hide the latency of the chain Lf -> Y1 -> W_j.
 template <int S>
 __device__ __forceinline__ void first_strip(const LeanCoef& k, float4 c, float4 n, float4 s, float4 d, float4 u,
                                             float l, float r, float4 f, float4& y1, float4& w2, float4& w3) {
-    const float sx[4] = {l + c.y, c.x + c.z, c.y + c.w, c.z + r};
-    const float sy[4] = {n.x + s.x, n.y + s.y, n.z + s.z, n.w + s.w};
-    const float sz[4] = {d.x + u.x, d.y + u.y, d.z + u.z, d.w + u.w};
-    const float cc[4] = {c.x, c.y, c.z, c.w};
-    const float ff[4] = {f.x, f.y, f.z, f.w};
-    float a[4], b[4], e3[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-        const float lf = fmaf(k.ihx2, sx[e], fmaf(k.ihy2, sy[e], fmaf(k.ihz2, sz[e], fmaf(k.m2s, cc[e], -ff[e]))));
-        a[e] = fmaf(k.m1t, lf, cc[e]);
-        b[e] = fmaf(k.k2y0, cc[e], fmaf(k.k2z, lf, k.k2f * ff[e]));
-        if (S == 3) e3[e] = fmaf(k.k3c, cc[e], fmaf(k.k3l, lf, k.k3f * ff[e]));
+    const float2 ihx = dup2(k.ihx2), ihy = dup2(k.ihy2), ihz = dup2(k.ihz2), m2s = dup2(k.m2s);
+    const float2 m1t = dup2(k.m1t), k2y0 = dup2(k.k2y0), k2z = dup2(k.k2z), k2f = dup2(k.k2f);
+    const float2 sx01 = make_float2(l + c.y, c.x + c.z), sx23 = make_float2(c.y + c.w, c.z + r);
+    const float2 lf01 = sub2(fma2(ihx, sx01, fma2(ihy, add2(lo2(n), lo2(s)), fma2(ihz, add2(lo2(d), lo2(u)),
+                                                                                    mul2(m2s, lo2(c))))), lo2(f));
+    const float2 lf23 = sub2(fma2(ihx, sx23, fma2(ihy, add2(hi2(n), hi2(s)), fma2(ihz, add2(hi2(d), hi2(u)),
+                                                                                    mul2(m2s, hi2(c))))), hi2(f));
+    y1 = cat4(fma2(m1t, lf01, lo2(c)), fma2(m1t, lf23, hi2(c)));
+    w2 = cat4(fma2(k2y0, lo2(c), fma2(k2z, lf01, mul2(k2f, lo2(f)))),
+              fma2(k2y0, hi2(c), fma2(k2z, lf23, mul2(k2f, hi2(f)))));
+    if (S == 3) {
+        const float2 k3c = dup2(k.k3c), k3l = dup2(k.k3l), k3f = dup2(k.k3f);
+        w3 = cat4(fma2(k3c, lo2(c), fma2(k3l, lf01, mul2(k3f, lo2(f)))),
+                  fma2(k3c, hi2(c), fma2(k3l, lf23, mul2(k3f, hi2(f)))));
+    } else {
+        w3 = make_float4(0.f, 0.f, 0.f, 0.f);
     }
-    y1 = make_float4(a[0], a[1], a[2], a[3]);
-    w2 = make_float4(b[0], b[1], b[2], b[3]);
-    w3 = make_float4(e3[0], e3[1], e3[2], e3[3]);
 }
 
 __device__ __forceinline__ float4 scale4(float k, float4 v) { return make_float4(k * v.x, k * v.y, k * v.z, k * v.w); }
@@ -295,17 +426,42 @@ __device__ __forceinline__ void store_out(float* dst, float4 v, bool vec, int n)
     }
 }
 
-template <int S, int ORDER, bool ZERO, int TY>
+// Tensor maps of the TMA path: Y0 and f as [nz][ny/2][nx] views of their even
+// (index 0) and odd (index 1) rows (row stride 2 nx), so that one box copy
+// fills the even-row half or the odd-row half of a staged plane.
+struct LeanMaps {
+    CUtensorMap y0[2];
+    CUtensorMap f[2];
+};
+
+template <int S, int ORDER, bool ZERO, int TY, bool TMA>
 __global__ void __launch_bounds__(Lean<S, ZERO, TY>::NT, Lean<S, ZERO, TY>::CTAS)
 k_superstep_lean(const __grid_constant__ LevelGeom g, const __grid_constant__ LeanCoef k,
-                 const float* __restrict__ y0g, const float* __restrict__ fg, float* __restrict__ outg,
-                 int tiles_x, int kchunk, int vec_ok) {
+                 const __grid_constant__ LeanMaps maps, const float* __restrict__ y0g,
+                 const float* __restrict__ fg, float* __restrict__ outg, int tiles_x, int kchunk, int vec_ok) {
     using C = Lean<S, ZERO, TY>;
     constexpr int W = C::W, P = C::P, Q = C::Q, HQ = C::HQ, NS = C::NS;
-    extern __shared__ __align__(16) float sm[];
+    extern __shared__ __align__(128) float sm[];
     const int tid = threadIdx.x, lane = tid & 31;
     const int nx = g.nx, ny = g.ny, nz = g.nz, plane = nx * ny;
     const bool pz = g.per[2] != 0;
+    unsigned long long* mbar = reinterpret_cast<unsigned long long*>(sm + C::NFLOATS);
+    const bool producer = TMA && tid == C::NT - 1;      // issues every box copy of the CTA
+    if (TMA) {
+        // box copies land on 128-byte boundaries: refuse a misaligned window
+        if ((smem_addr(sm) & 127u) != 0) {
+            if (tid == 0) {
+                atomicAdd(&g_lean_wait_timeouts, 1u);
+                outg[0] = __int_as_float(0x7fc00000);
+            }
+            return;
+        }
+        if (producer) {
+            for (int b = 0; b < C::NBAR; ++b) mbar_init(mbar + b, 1);
+            mbar_init_fence();
+        }
+        __syncthreads();
+    }
 
     // ---- one segment of the stream: tile (bx, by), planes [kz0, kz1)
     auto segment = [&](int bx, int by, int kz0, int kz1) {
@@ -384,15 +540,29 @@ k_superstep_lean(const __grid_constant__ LevelGeom g, const __grid_constant__ Le
             st_vec = vec_ok && st_n == 4;
         }
     }
-    // staged-plane loads: thread k < HQ stages strip k of Y0 and of f
+    // staged-plane loads.  cp.async path: thread k < HQ stages strip k of Y0 and
+    // of f.  TMA path: the producer copies two boxes per field (even rows, odd
+    // rows); threads k < HQ of tiles that reach past a wall rebuild the
+    // out-of-level cells of strip k.
     LoadDesc ld;
     ld.dst = -1;
-    if (tid < HQ) ld = make_desc(tid, X0, Yt, g, vec_ok != 0, W, Q, C::H);
+    FixDesc fx;
+    fx.dst = -1;
+    fx.masks = 0;
+    const bool wall = X0 < 0 || X0 + W > nx || Yt < 0 || Yt + C::H > ny;
+    if (TMA) {
+        if (tid < HQ) fx = make_fix<Q, C::HO, W, C::H>(tid, X0, Yt, g);
+    } else {
+        if (tid < HQ) ld = make_desc(tid, X0, Yt, g, vec_ok != 0, Q, C::HO, W);
+    }
+    // box coordinates: local even rows are the global rows of Yt's parity
+    const int ypar = Yt & 1;
+    const int ybox_e = (Yt - ypar) / 2, ybox_o = (Yt + ypar) / 2;
     // L2 prefetch: three points of each staged row (first, middle and last cell of
     // the row's part inside the box), per field
     int pf = -1;
     const float* pf_src = fg;
-    {
+    if (!TMA) {
         constexpr int NPF = 3 * C::H;
         const int fld = tid / NPF, rem = tid % NPF;
         if (fld < (ZERO ? 1 : 2)) {
@@ -410,15 +580,83 @@ k_superstep_lean(const __grid_constant__ LevelGeom g, const __grid_constant__ Le
     const int nload = kz1 + NS - t_first;               // planes t_first + v, v < nload, are staged
     const int u_store0 = kz0 - t_first + 2 * NS - 1;    // phases whose last-stage plane lies in [kz0, kz1)
     const int u_store1 = kz1 - t_first + 2 * NS - 1;
-    // plane t_first + v of a ring with R slots sits in slot (v & (R - 1))
+    // plane t_first + v of a ring with R slots sits in slot (v & (R - 1)); on the
+    // TMA path its copies complete on mbarrier (v + 2) & 3, phase ((v + 2) >> 2) & 1
     auto stage_plane = [&](int v, int* zsign) {
-        const int src = map_axis(t_first + v, nz, pz, zsign) * plane;
-        if constexpr (!ZERO) issue(ld, sm + C::OY0 + (v & 3) * P, y0g + src);
-        issue(ld, sm + C::OF + (v & (C::RF - 1)) * P, fg + src);
+        const int zz = map_axis(t_first + v, nz, pz, zsign);
+        if constexpr (TMA) {
+            if (producer) {
+                unsigned long long* bar = mbar + ((v + 2) & 3);
+                fence_proxy_async();
+                mbar_expect_tx(bar, (ZERO ? 1u : 2u) * unsigned(C::H * W * sizeof(float)));
+                if constexpr (!ZERO) {
+                    float* d = sm + C::OY0 + (v & 3) * P;
+                    tma_load(d, &maps.y0[ypar], X0, ybox_e, zz, bar);
+                    tma_load(d + C::HO, &maps.y0[ypar ^ 1], X0, ybox_o, zz, bar);
+                }
+                float* d = sm + C::OF + (v & (C::RF - 1)) * P;
+                tma_load(d, &maps.f[ypar], X0, ybox_e, zz, bar);
+                tma_load(d + C::HO, &maps.f[ypar ^ 1], X0, ybox_o, zz, bar);
+            }
+        } else {
+            const int src = zz * plane;
+            if constexpr (!ZERO) issue(ld, sm + C::OY0 + (v & 3) * P, y0g + src);
+            issue(ld, sm + C::OF + (v & (C::RF - 1)) * P, fg + src);
+        }
     };
+    auto prefetch_plane = [&](int v) {
+        int zsg;
+        const int zz = map_axis(t_first + v, nz, pz, &zsg);
+        if constexpr (TMA) {
+            if (producer) {
+                if constexpr (!ZERO) {
+                    tma_prefetch(&maps.y0[ypar], X0, ybox_e, zz);
+                    tma_prefetch(&maps.y0[ypar ^ 1], X0, ybox_o, zz);
+                }
+                tma_prefetch(&maps.f[ypar], X0, ybox_e, zz);
+                tma_prefetch(&maps.f[ypar ^ 1], X0, ybox_o, zz);
+            }
+        } else if (pf >= 0) {
+            prefetch_l2(pf_src + zz * plane + pf);
+        }
+    };
+    // cp.async path: the thread's own copies have landed; negate reflected cells
     auto fix_plane = [&](int v, int zsign) {
         if constexpr (!ZERO) fixup(ld, sm + C::OY0 + (v & 3) * P, zsign);
         fixup(ld, sm + C::OF + (v & (C::RF - 1)) * P, zsign);
+    };
+    // TMA path: wait (bounded) for plane v, then rebuild its out-of-level cells
+    // (wall tiles) and negate it (z reflection).  Every thread takes the same
+    // branches, so the barrier between the reads and the writes of a negated
+    // plane is reached by all.  Returns false if the wait gave up.
+    auto land_plane = [&](int v, int zsign) -> bool {
+        const bool ok = mbar_wait(mbar + ((v + 2) & 3), ((v + 2) >> 2) & 1);
+        float* pfp = sm + C::OF + (v & (C::RF - 1)) * P;
+        float* pyp = sm + C::OY0 + (v & 3) * P;
+        if (zsign < 0) {
+            float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a;
+            if (ok && fx.dst >= 0) {
+                a = fixed_strip(fx, pfp, ld4(pfp + fx.dst), -1);
+                if constexpr (!ZERO) b = fixed_strip(fx, pyp, ld4(pyp + fx.dst), -1);
+            }
+            __syncthreads();
+            if (ok && fx.dst >= 0) {
+                st4(pfp + fx.dst, a);
+                if constexpr (!ZERO) st4(pyp + fx.dst, b);
+            }
+        } else if (ok && wall && fx.masks) {
+            st4(pfp + fx.dst, fixed_strip(fx, pfp, ld4(pfp + fx.dst), 1));
+            if constexpr (!ZERO) st4(pyp + fx.dst, fixed_strip(fx, pyp, ld4(pyp + fx.dst), 1));
+        }
+        return ok;
+    };
+    // a bounded wait gave up: count it, poison the output so that the solve
+    // reports a non-finite residual, and leave (every thread of the CTA agrees)
+    auto give_up = [&]() {
+        if (tid == 0) {
+            atomicAdd(&g_lean_wait_timeouts, 1u);
+            outg[0] = __int_as_float(0x7fc00000);
+        }
     };
 
     // ---- prologue: planes t_first - 2 .. t_first; t_first + 1 stays in flight
@@ -426,19 +664,27 @@ k_superstep_lean(const __grid_constant__ LevelGeom g, const __grid_constant__ Le
     stage_plane(-2, &zs0);
     stage_plane(-1, &zs1);
     stage_plane(0, &zs2);
-    cpa_commit();
-    cpa_wait_all();
-    fix_plane(-2, zs0);
-    fix_plane(-1, zs1);
-    fix_plane(0, zs2);
-    if (1 < nload) stage_plane(1, &zs_next);
-    cpa_commit();
-    if (pf >= 0)
-        for (int v = 2; v < kPrefetch && v < nload; ++v) {
-            int zsg;
-            prefetch_l2(pf_src + map_axis(t_first + v, nz, pz, &zsg) * plane + pf);
+    if constexpr (TMA) {
+        if (1 < nload) stage_plane(1, &zs_next);
+        bool ok = land_plane(-2, zs0);
+        ok = land_plane(-1, zs1) && ok;
+        ok = land_plane(0, zs2) && ok;
+        for (int v = 2; v < kPrefetch && v < nload; ++v) prefetch_plane(v);
+        if (__syncthreads_or(!ok)) {
+            give_up();
+            return;
         }
-    __syncthreads();
+    } else {
+        cpa_commit();
+        cpa_wait_all();
+        fix_plane(-2, zs0);
+        fix_plane(-1, zs1);
+        fix_plane(0, zs2);
+        if (1 < nload) stage_plane(1, &zs_next);
+        cpa_commit();
+        for (int v = 2; v < kPrefetch && v < nload; ++v) prefetch_plane(v);
+        __syncthreads();
+    }
 
     // z window of the thread's two strips: planes p - 1 (dn) and p (cen)
     float4 dn0 = make_float4(0.f, 0.f, 0.f, 0.f), cen0 = dn0, dn1 = dn0, cen1 = dn0;
@@ -454,15 +700,12 @@ k_superstep_lean(const __grid_constant__ LevelGeom g, const __grid_constant__ Le
     // One phase.  (dn, cen) hold the thread's strips of planes p - 1 and p of its
     // input stage; the strips of plane p + 1 are loaded into `nxt`.  The loop
     // below rotates the three register sets by renaming (unrolled by three).
-    auto phase = [&](int u, float4& dn0, float4& cen0, float4& nxt0, float4& dn1, float4& cen1, float4& nxt1) {
+    auto phase = [&](int u, float4& dn0, float4& cen0, float4& nxt0, float4& dn1, float4& cen1, float4& nxt1) -> bool {
         // stage plane t + 2 into shared memory, prefetch plane t + kPrefetch into L2
         const int zs_cur = zs_next;
         if (u + 2 < nload) stage_plane(u + 2, &zs_next);
-        cpa_commit();
-        if (pf >= 0 && u + kPrefetch < nload) {
-            int zsg;
-            prefetch_l2(pf_src + map_axis(t_first + u + kPrefetch, nz, pz, &zsg) * plane + pf);
-        }
+        if constexpr (!TMA) cpa_commit();
+        if (u + kPrefetch < nload) prefetch_plane(u + kPrefetch);
 
         if (!ZERO && J == 1) {
             // ---- stage 1 on plane t - 1
@@ -538,19 +781,29 @@ k_superstep_lean(const __grid_constant__ LevelGeom g, const __grid_constant__ Le
         }
 
         // plane t + 1 (staged in the previous phase) has landed: fix its reflected cells
-        cpa_wait_prev();
-        if (u + 1 < nload) fix_plane(u + 1, zs_cur);
-        __syncthreads();
+        if constexpr (TMA) {
+            bool ok = true;
+            if (u + 1 < nload) ok = land_plane(u + 1, zs_cur);
+            return !__syncthreads_or(!ok);
+        } else {
+            cpa_wait_prev();
+            if (u + 1 < nload) fix_plane(u + 1, zs_cur);
+            __syncthreads();
+            return true;
+        }
     };
 
     float4 nx0 = make_float4(0.f, 0.f, 0.f, 0.f), nx1 = nx0;
+    bool ok = true;                                 // false: a bounded wait gave up (the whole CTA agrees)
     for (int u = 0; u < nph; u += 3) {              // nph is uniform: every thread takes the same exits
-        phase(u, dn0, cen0, nx0, dn1, cen1, nx1);
-        if (u + 1 >= nph) break;
-        phase(u + 1, cen0, nx0, dn0, cen1, nx1, dn1);
-        if (u + 2 >= nph) break;
-        phase(u + 2, nx0, dn0, cen0, nx1, dn1, cen1);
+        ok = phase(u, dn0, cen0, nx0, dn1, cen1, nx1);
+        if (!ok || u + 1 >= nph) break;
+        ok = phase(u + 1, cen0, nx0, dn0, cen1, nx1, dn1);
+        if (!ok || u + 2 >= nph) break;
+        ok = phase(u + 2, nx0, dn0, cen0, nx1, dn1, cen1);
+        if (!ok) break;
     }
+    if (!ok) give_up();
     };
 
     // CTA b streams planes [c kchunk, (c + 1) kchunk) of one tile: all tiles
@@ -642,12 +895,70 @@ LeanPlan lean_plan(const LevelGeom& g) {
     return p;
 }
 
-template <int S, int ORDER, bool ZERO, int TY>
-cudaError_t lean_launch(const LeanPlan& p, const LevelGeom& g, const LeanCoef& k, const float* y0, const float* f,
-                        float* out, int vec_ok, cudaStream_t st) {
+// ---- tensor maps (TMA path) --------------------------------------------------
+using TensorMapEncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                          const cuuint64_t*, const cuuint32_t*, const cuuint32_t*,
+                                          CUtensorMapInterleave, CUtensorMapSwizzle, CUtensorMapL2promotion,
+                                          CUtensorMapFloatOOBfill);
+
+// The driver's tensor-map encoder, looked up once through the runtime (no link
+// against the driver library); nullptr where the driver lacks it.
+TensorMapEncodeTiled tensor_map_encoder() {
+    static TensorMapEncodeTiled fn = []() -> TensorMapEncodeTiled {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            return nullptr;
+        return reinterpret_cast<TensorMapEncodeTiled>(p);
+    }();
+    return fn;
+}
+
+// [nz][ny/2][nx] view of the rows of parity `par` of a level array: row stride
+// 2 nx, box of w x h rows x 1 plane, zeros outside the level.
+bool encode_rows(CUtensorMap* m, const float* base, int par, const LevelGeom& g, int w, int h) {
+    TensorMapEncodeTiled enc = tensor_map_encoder();
+    if (!enc) return false;
+    const cuuint64_t dims[3] = {cuuint64_t(g.nx), cuuint64_t(g.ny / 2), cuuint64_t(g.nz)};
+    const cuuint64_t strides[2] = {cuuint64_t(g.nx) * 2 * sizeof(float), cuuint64_t(g.nx) * g.ny * sizeof(float)};
+    const cuuint32_t box[3] = {cuuint32_t(w), cuuint32_t(h), 1};
+    const cuuint32_t es[3] = {1, 1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(base + par * g.nx), dims, strides, box, es,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int S, int ORDER, bool ZERO, int TY, bool TMA>
+cudaError_t lean_launch(const LeanPlan& p, const LevelGeom& g, const LeanCoef& k, const LeanMaps& maps,
+                        const float* y0, const float* f, float* out, int vec_ok, cudaStream_t st) {
     using C = Lean<S, ZERO, TY>;
-    k_superstep_lean<S, ORDER, ZERO, TY><<<(unsigned)p.ncta, C::NT, C::BYTES, st>>>(g, k, y0, f, out, (int)p.tiles_x, p.kchunk, vec_ok);
+    k_superstep_lean<S, ORDER, ZERO, TY, TMA><<<(unsigned)p.ncta, C::NT, C::BYTES, st>>>(g, k, maps, y0, f, out,
+                                                                                          (int)p.tiles_x, p.kchunk,
+                                                                                          vec_ok);
     return cudaGetLastError();
+}
+
+// The TMA path stages planes by box copies; it needs x and y walls without
+// wrap-around (a box cannot wrap a periodic axis), 16-byte aligned rows
+// (nx % 4 == 0, aligned arrays: the odd-row view starts nx floats in) and an
+// even ny.  Other levels keep the per-strip cp.async path.
+template <int S, int ORDER, bool ZERO, int TY>
+cudaError_t lean_run(const LeanPlan& p, const LevelGeom& g, const LeanCoef& k, const float* y0, const float* f,
+                     float* out, int vec_ok, cudaStream_t st, bool want_tma) {
+    using C = Lean<S, ZERO, TY>;
+    LeanMaps maps;
+    std::memset(&maps, 0, sizeof(maps));
+    bool tma = want_tma && vec_ok && !g.per[0] && !g.per[1] && (g.ny % 2) == 0;
+    if (tma) {
+        for (int par = 0; par < 2 && tma; ++par) {
+            tma = encode_rows(&maps.f[par], f, par, g, C::W, C::H / 2);
+            if (!ZERO && tma) tma = encode_rows(&maps.y0[par], y0, par, g, C::W, C::H / 2);
+        }
+    }
+    if (tma) return lean_launch<S, ORDER, ZERO, TY, true>(p, g, k, maps, y0, f, out, vec_ok, st);
+    return lean_launch<S, ORDER, ZERO, TY, false>(p, g, k, maps, y0, f, out, vec_ok, st);
 }
 
 // Tiles 16 or 14 rows high: the shorter tile costs more halo per cell but can
@@ -655,25 +966,37 @@ cudaError_t lean_launch(const LeanPlan& p, const LevelGeom& g, const LeanCoef& k
 // SMs); the plan with the cheaper longest SM is launched.
 template <int S, int ORDER, bool ZERO>
 cudaError_t lean_one(const LevelGeom& g, const LeanCoef& k, const float* y0, const float* f, float* out,
-                     cudaStream_t st) {
+                     cudaStream_t st, int tile_rows, bool tma) {
     const bool aligned = ((reinterpret_cast<uintptr_t>(y0) | reinterpret_cast<uintptr_t>(f) |
                            reinterpret_cast<uintptr_t>(out)) & 15) == 0;
     const int vec_ok = ((g.nx & 3) == 0 && aligned) ? 1 : 0;
     const LeanPlan a = lean_plan<S, ORDER, ZERO, 16>(g), b = lean_plan<S, ORDER, ZERO, 14>(g);
-    if (b.cost < a.cost) return lean_launch<S, ORDER, ZERO, 14>(b, g, k, y0, f, out, vec_ok, st);
-    return lean_launch<S, ORDER, ZERO, 16>(a, g, k, y0, f, out, vec_ok, st);
+    const bool use14 = tile_rows == 14 || (tile_rows != 16 && b.cost < a.cost);
+    if (use14) return lean_run<S, ORDER, ZERO, 14>(b, g, k, y0, f, out, vec_ok, st, tma);
+    return lean_run<S, ORDER, ZERO, 16>(a, g, k, y0, f, out, vec_ok, st, tma);
 }
 
-template <int S, int ORDER, bool ZERO, int TY>
-cudaError_t lean_configure_one() {
+template <int S, int ORDER, bool ZERO, int TY, bool TMA>
+cudaError_t lean_configure_kernel(int* per_sm) {
     using C = Lean<S, ZERO, TY>;
-    auto kern = k_superstep_lean<S, ORDER, ZERO, TY>;
+    auto kern = k_superstep_lean<S, ORDER, ZERO, TY, TMA>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::BYTES);
     if (e != cudaSuccess) return e;
     int n = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, C::NT, C::BYTES);
     if (e != cudaSuccess) return e;
-    LeanResident<S, ORDER, ZERO, TY>::per_sm = n > 0 ? n : 1;
+    *per_sm = n > 0 ? n : 1;
+    return cudaSuccess;
+}
+
+// Both load paths of a tile shape; the plan uses the smaller residency.
+template <int S, int ORDER, bool ZERO, int TY>
+cudaError_t lean_configure_one() {
+    int a = 1, b = 1;
+    cudaError_t e = lean_configure_kernel<S, ORDER, ZERO, TY, false>(&a);
+    if (e != cudaSuccess) return e;
+    if ((e = lean_configure_kernel<S, ORDER, ZERO, TY, true>(&b)) != cudaSuccess) return e;
+    LeanResident<S, ORDER, ZERO, TY>::per_sm = std::min(a, b);
     return cudaSuccess;
 }
 
@@ -685,9 +1008,12 @@ cudaError_t lean_configure_ty() {
 
 template <int S>
 cudaError_t lean_dispatch(int order, bool zero, const LevelGeom& g, const LeanCoef& k, const float* y0,
-                          const float* f, float* out, cudaStream_t st) {
-    if (order == 1) return zero ? lean_one<S, 1, true>(g, k, y0, f, out, st) : lean_one<S, 1, false>(g, k, y0, f, out, st);
-    return zero ? lean_one<S, 2, true>(g, k, y0, f, out, st) : lean_one<S, 2, false>(g, k, y0, f, out, st);
+                          const float* f, float* out, cudaStream_t st, int rows, bool tma) {
+    if (order == 1)
+        return zero ? lean_one<S, 1, true>(g, k, y0, f, out, st, rows, tma)
+                    : lean_one<S, 1, false>(g, k, y0, f, out, st, rows, tma);
+    return zero ? lean_one<S, 2, true>(g, k, y0, f, out, st, rows, tma)
+                : lean_one<S, 2, false>(g, k, y0, f, out, st, rows, tma);
 }
 
 }  // namespace
@@ -707,11 +1033,18 @@ cudaError_t lean_configure() {
     return lean_configure_ty<3, 2, true>();
 }
 
+unsigned lean_wait_failures() {
+    unsigned n = 0;
+    if (cudaMemcpyFromSymbol(&n, g_lean_wait_timeouts, sizeof(n)) != cudaSuccess) return 0;
+    return n;
+}
+
 cudaError_t launch_superstep_lean(const LevelGeom& g, int order, int s, bool zero_y0, const FusedCoef& cf,
-                                  const float* y0, const float* f, float* out, cudaStream_t st) {
+                                  const float* y0, const float* f, float* out, cudaStream_t st, int tile_rows,
+                                  bool tma) {
     const LeanCoef k = make_lean_coef(g, order, s, cf);
-    if (s == 2) return lean_dispatch<2>(order, zero_y0, g, k, y0, f, out, st);
-    if (s == 3) return lean_dispatch<3>(order, zero_y0, g, k, y0, f, out, st);
+    if (s == 2) return lean_dispatch<2>(order, zero_y0, g, k, y0, f, out, st, tile_rows, tma);
+    if (s == 3) return lean_dispatch<3>(order, zero_y0, g, k, y0, f, out, st, tile_rows, tma);
     return cudaErrorInvalidValue;
 }
 

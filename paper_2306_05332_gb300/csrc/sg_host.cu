@@ -16,6 +16,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <atomic>
 #include <mutex>
 #include <string>
 #include <type_traits>
@@ -195,6 +196,17 @@ double cell_tau_frac(int N) {
     return c * c;
 }
 
+// Sec. 4.1's level rule on the x and y axes of a two-dimensional grid.
+int rule_levels_2d(int nx, int ny) {
+    int L = 1;
+    auto ok = [](int n, int L) {
+        const long long p = 1LL << L;
+        return (n % p == 0) && ((n / p) % 2 == 0);
+    };
+    while (L < 30 && ok(nx, L) && ok(ny, L)) ++L;
+    return L;
+}
+
 int rule_levels(int nx, int ny, int nz) {
     int L = 1;
     auto ok = [](int n, int L) {
@@ -221,16 +233,16 @@ struct ProfRec {
 
 }  // namespace
 
-constexpr int kGraphKeySlots = 17;   // items the cached cycle graph is keyed on (run_cycle)
+constexpr int kGraphKeySlots = 19;   // items the cached cycle graph is keyed on (run_cycle)
 
 struct sg_grid {
     int n[3];
+    bool twod = false;              // a two-dimensional grid (sg_create_grid_2d): nz = 1, no z term
     double lo[3], hi[3];
     int bc[3];
     int precision;
     cudaStream_t st;
     cudaStream_t own_stream = nullptr;
-    cudaStream_t batch_stream = nullptr;    // private stream of this grid's branch in a batch graph
     int max_levels;
     std::vector<Level> lv;
     double* phi = nullptr;
@@ -256,6 +268,15 @@ struct sg_grid {
     bool have_solution = false;
     bool guess_set = false;
     int last_levels = 0;
+    // the cycle loop on the device: state (device and pinned mirror), the whole
+    // solve as one graph (WHILE nodes), its key, and a serial number that
+    // distinguishes grids created at a reused address
+    DeviceLoop* dloop = nullptr;
+    DeviceLoop* host_loop = nullptr;
+    cudaGraphExec_t sexec = nullptr;
+    uint64_t skey[kGraphKeySlots] = {0};
+    long long s_per_cycle = 0, s_per_confirm = 0;   // kernels of one cycle / one confirmation in it
+    unsigned long long serial = 0;
     // graph cache
     cudaGraphExec_t gexec = nullptr;
     uint64_t gkey[kGraphKeySlots] = {0};
@@ -294,6 +315,7 @@ LevelGeom geom(const sg_grid* g, int l, bool with_faces) {
         const int d = f / 2;
         G.face[f] = (with_faces && l == 0 && g->bc[d] == SG_BC_DIRICHLET) ? g->faces[f] : nullptr;
     }
+    G.twod = g->twod ? 1 : 0;
     return G;
 }
 
@@ -388,6 +410,9 @@ sg_status check_opts(const sg_options* o) {
     if (!(o->omega >= 0.0 && o->omega < 2.0)) return fail(SG_ERR_ARG, "omega must be in [0, 2)");
     if (!(o->max_residual_tol >= 0.0 && o->max_residual_tol < 1e300))
         return fail(SG_ERR_ARG, "max_residual_tol must be finite and >= 0");
+    if (o->tile_rows != 0 && o->tile_rows != 14 && o->tile_rows != 16)
+        return fail(SG_ERR_ARG, "tile_rows must be 0, 14 or 16");
+    if (o->staging != SG_STAGE_CP_ASYNC && o->staging != SG_STAGE_TMA) return fail(SG_ERR_ARG, "unknown staging");
     return SG_OK;
 }
 
@@ -568,7 +593,8 @@ sg_status superstep_fused(sg_grid* g, int l, int order, int s, double tau_frac, 
     }
     {
         ProfScope ps(g, l == 0 ? K_STAGE0 : K_STAGE_C, double(L.n) * sizeof(float) * (y0 ? 3 : 2));
-        SG_CK(launch_superstep_fused(geom(g, l, false), order, s, y0 == nullptr, cf, y0, rhs, out, g->st));
+        SG_CK(launch_superstep_fused(geom(g, l, false), order, s, y0 == nullptr, cf, y0, rhs, out, g->st,
+                                     g->opt.tile_rows, g->opt.staging == SG_STAGE_TMA));
     }
     ++g->launches;
     return SG_OK;
@@ -581,7 +607,8 @@ sg_status superstep_fused(sg_grid* g, int l, int order, int s, double tau_frac, 
 constexpr long long kFusedMinCells = 1LL << 21;
 
 bool use_fused(const sg_grid* g, bool faces, int l) {
-    return g->precision == SG_MIXED && g->opt.fused && !faces && g->opt.smoother == SG_SMOOTH_RKL && fused_supported(g->opt.rkl_order, g->opt.s_smooth) &&
+    return !g->twod && g->precision == SG_MIXED && g->opt.fused && !faces && g->opt.smoother == SG_SMOOTH_RKL &&
+           fused_supported(g->opt.rkl_order, g->opt.s_smooth) &&
            g->lv[l].n >= kFusedMinCells;
 }
 
@@ -591,7 +618,7 @@ bool use_fused(const sg_grid* g, bool faces, int l) {
 constexpr long long kZeroFusedMinCells = 1LL << 17;
 
 bool use_fused_zero(const sg_grid* g, bool faces, int l) {
-    return g->precision == SG_MIXED && g->opt.fused && !faces && g->opt.smoother == SG_SMOOTH_RKL &&
+    return !g->twod && g->precision == SG_MIXED && g->opt.fused && !faces && g->opt.smoother == SG_SMOOTH_RKL &&
            g->opt.s_smooth <= 3 &&
            fused_supported(g->opt.rkl_order, g->opt.s_smooth) && g->lv[l].n >= kZeroFusedMinCells;
 }
@@ -601,7 +628,7 @@ bool use_fused_zero(const sg_grid* g, bool faces, int l) {
 // level-by-level kernels run them.
 int bottom_nc(const sg_grid* g, int L, int* threads, size_t* bytes) {
     const int B = L - 2;
-    if (g->precision != SG_MIXED || !g->opt.fused || g->opt.smoother != SG_SMOOTH_RKL || B < 1) return 0;
+    if (g->twod || g->precision != SG_MIXED || !g->opt.fused || g->opt.smoother != SG_SMOOTH_RKL || B < 1) return 0;
     const Level& lb = g->lv[B];
     return bottom_plan(lb.nx, lb.ny, lb.nz, g->opt.s_smooth, threads, bytes);
 }
@@ -775,7 +802,8 @@ sg_status level0_residual_zero(sg_grid* g, const double* f, bool faces) {
 
 // Everything one cycle enqueues after the first residual: V-cycle, update,
 // residual + norm, and the copies of the norm / coarse count to pinned memory.
-sg_status cycle_body(sg_grid* g, int L, double* phi, const double* f, bool faces) {
+// One V-cycle and the residual norm after it (into red[0]); no host copies.
+sg_status cycle_core(sg_grid* g, int L, double* phi, const double* f, bool faces) {
     if (g->precision == SG_MIXED) {
         // the inner cycle starts from e = 0: its first super-step takes Y0 = 0
         float* e = (float*)g->lv[0].u;
@@ -794,6 +822,11 @@ sg_status cycle_body(sg_grid* g, int L, double* phi, const double* f, bool faces
         SG_TRY(vcycle<double>(g, L, phi, f, faces, false, nullptr));
         SG_TRY(level0_residual(g, phi, f, faces));
     }
+    return SG_OK;
+}
+
+sg_status cycle_body(sg_grid* g, int L, double* phi, const double* f, bool faces) {
+    SG_TRY(cycle_core(g, L, phi, f, faces));
     SG_CK(cudaMemcpyAsync(g->host_red, g->red, sizeof(Reduced), cudaMemcpyDeviceToHost, g->st));
     SG_CK(cudaMemcpyAsync(g->host_ss, g->d_ss, sizeof(int), cudaMemcpyDeviceToHost, g->st));
     return SG_OK;
@@ -802,6 +835,9 @@ sg_status cycle_body(sg_grid* g, int L, double* phi, const double* f, bool faces
 void drop_graph(sg_grid* g) {
     if (g->gexec) cudaGraphExecDestroy(g->gexec);
     g->gexec = nullptr;
+    if (g->sexec) cudaGraphExecDestroy(g->sexec);
+    g->sexec = nullptr;
+    std::memset(g->skey, 0, sizeof(g->skey));
     std::memset(g->gkey, 0, sizeof(g->gkey));
     for (const ProfRec& r : g->graph_recs) {
         g->ev_pool.push_back(r.a);
@@ -810,26 +846,37 @@ void drop_graph(sg_grid* g) {
     g->graph_recs.clear();
 }
 
-sg_status run_cycle(sg_grid* g, int L, double* phi, const double* f, bool faces, bool* replayed) {
-    *replayed = false;
-    const bool graphable = g->opt.use_graph &&
-                           (g->precision == SG_MIXED ? coarse_fits<float>(g->lv[L - 1].n)
-                                                     : coarse_fits<double>(g->lv[L - 1].n));
-    if (!graphable) return cycle_body(g, L, phi, f, faces);
-    // Everything the captured cycle depends on, one slot per item (doubles by
-    // their bit pattern), compared slot by slot: no scaling, no folding.
+// Whether the V-cycle can be captured into a CUDA graph (the coarsest level
+// fits one CTA: the larger coarse solve reads its norm on the host).
+bool cycle_graphable(const sg_grid* g, int L) {
+    return g->opt.use_graph && L > 1 &&
+           (g->precision == SG_MIXED ? coarse_fits<float>(g->lv[L - 1].n) : coarse_fits<double>(g->lv[L - 1].n));
+}
+
+// Everything a captured cycle depends on, one slot per item (doubles by their
+// bit pattern), compared slot by slot: no scaling, no folding.
+void graph_key(const sg_grid* g, int L, const double* phi, const double* f, bool faces, uint64_t key[kGraphKeySlots]) {
     auto bits = [](double v) {
         uint64_t u;
         std::memcpy(&u, &v, sizeof(u));
         return u;
     };
-    const uint64_t key[kGraphKeySlots] = {(uint64_t)L, (uint64_t)(uintptr_t)phi, (uint64_t)(uintptr_t)f,
-                                          faces ? 1u : 0u, (uint64_t)g->opt.rkl_order, (uint64_t)g->opt.s_smooth,
-                                          bits(g->opt.tau_frac), (uint64_t)g->opt.n_pre, (uint64_t)g->opt.n_post,
-                                          bits(g->opt.coarse_tol), (uint64_t)g->opt.coarse_max_ss,
-                                          bits(g->opt.coarse_tau_frac), (uint64_t)g->opt.smoother,
-                                          bits(g->opt.omega), (uint64_t)(g->opt.fused ? 1 : 0),
-                                          (uint64_t)(g->prof ? 1 : 0), (uint64_t)(uintptr_t)g->d_sched};
+    const uint64_t k[kGraphKeySlots] = {(uint64_t)L, (uint64_t)(uintptr_t)phi, (uint64_t)(uintptr_t)f,
+                                        faces ? 1u : 0u, (uint64_t)g->opt.rkl_order, (uint64_t)g->opt.s_smooth,
+                                        bits(g->opt.tau_frac), (uint64_t)g->opt.n_pre, (uint64_t)g->opt.n_post,
+                                        bits(g->opt.coarse_tol), (uint64_t)g->opt.coarse_max_ss,
+                                        bits(g->opt.coarse_tau_frac), (uint64_t)g->opt.smoother,
+                                        bits(g->opt.omega), (uint64_t)(g->opt.fused ? 1 : 0),
+                                        (uint64_t)(g->prof ? 1 : 0), (uint64_t)(uintptr_t)g->d_sched,
+                                        (uint64_t)g->opt.tile_rows, (uint64_t)g->opt.staging};
+    std::memcpy(key, k, sizeof(k));
+}
+
+sg_status run_cycle(sg_grid* g, int L, double* phi, const double* f, bool faces, bool* replayed) {
+    *replayed = false;
+    if (!cycle_graphable(g, L)) return cycle_body(g, L, phi, f, faces);
+    uint64_t key[kGraphKeySlots];
+    graph_key(g, L, phi, f, faces, key);
     if (!g->gexec || std::memcmp(key, g->gkey, sizeof(key)) != 0) {
         drop_graph(g);
         cudaGraph_t graph = nullptr;
@@ -903,7 +950,7 @@ sg_status solve_begin(sg_grid* g, SolveState& S, double tol, int L, double* phi,
         // red-black colouring must hold across a periodic wrap on every swept level
         for (int l = 0; l < std::max(1, L - 1); ++l) {
             const int n3[3] = {g->lv[l].nx, g->lv[l].ny, g->lv[l].nz};
-            for (int d = 0; d < 3; ++d)
+            for (int d = 0; d < (g->twod ? 2 : 3); ++d)
                 if (g->bc[d] == SG_BC_PERIODIC && (n3[d] & 1))
                     return fail(SG_ERR_ARG, "GS-RB smoothing needs even extents on periodic axes");
         }
@@ -981,7 +1028,10 @@ sg_status solve_check(sg_grid* g, SolveState& S) {
     S.info.rel_residual = rel;
     S.info.max_residual = g->host_red[0].maxabs;
     if (!std::isfinite(rel)) {
-        S.status = fail(SG_ERR_NONFINITE, "residual norm is not finite");
+        const unsigned waits = g->precision == SG_MIXED ? lean_wait_failures() : 0u;
+        S.status = fail(SG_ERR_NONFINITE, waits ? "residual norm is not finite: " + std::to_string(waits) +
+                                                      " fused super-step launch(es) gave up a bounded wait"
+                                                : std::string("residual norm is not finite"));
         S.done = true;
     } else if (g->opt.fixed_cycles == 0 && met(rel, g->host_red[0].maxabs)) {
         S.done = true;
@@ -1075,14 +1125,177 @@ sg_status solve_end(sg_grid* g, SolveState& S, sg_solve_info* info) {
     return S.status;
 }
 
+// ---- the whole solve as one graph ------------------------------------------------
+// Appends the cycle loop of grid g to `graph`, as a branch with no incoming
+// edge (a batch adds one branch per grid):
+//   init -> WHILE(outer) { WHILE(inner) { V-cycle, residual norm, step }
+//                          [mixed: the true FP64 residual]  confirm }
+// The one-thread init / step / confirm kernels (kernels_loop.cu) take the host
+// loop's decisions on the device and set the two conditions.  *per_cycle and
+// *per_confirm receive the kernels of one inner and one outer iteration.
+sg_status add_solve_loop(sg_grid* g, cudaGraph_t graph, int L, double* phi, const double* f, bool faces,
+                         long long* per_cycle, long long* per_confirm) {
+    cudaStream_t st = g->st;
+    cudaGraphConditionalHandle ho = 0, hi = 0;
+    SG_CK(cudaGraphConditionalHandleCreate(&ho, graph, 0, cudaGraphCondAssignDefault));
+    SG_CK(cudaGraphConditionalHandleCreate(&hi, graph, 0, cudaGraphCondAssignDefault));
+    // appends a WHILE node after the work captured so far on st; returns its body
+    auto add_while = [&](cudaGraphConditionalHandle h, cudaGraph_t* body) -> sg_status {
+        cudaStreamCaptureStatus cs;
+        cudaGraph_t cg = nullptr;
+        const cudaGraphNode_t* deps = nullptr;
+        size_t nd = 0;
+        SG_CK(cudaStreamGetCaptureInfo(st, &cs, nullptr, &cg, &deps, nullptr, &nd));
+        // zero-initialised storage: the parameter union has no default constructor
+        alignas(cudaGraphNodeParams) unsigned char raw[sizeof(cudaGraphNodeParams)] = {};
+        cudaGraphNodeParams& cp = *reinterpret_cast<cudaGraphNodeParams*>(raw);
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = h;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        cudaGraphNode_t node = nullptr;
+        SG_CK(cudaGraphAddNode(&node, cg, deps, nullptr, nd, &cp));
+        *body = cp.conditional.phGraph_out[0];
+        SG_CK(cudaStreamUpdateCaptureDependencies(st, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+        return SG_OK;
+    };
+    // a capture into `target` that always ends, even on an error
+    auto capture = [&](cudaGraph_t target, auto&& fill) -> sg_status {
+        SG_CK(cudaStreamBeginCaptureToGraph(st, target, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+        const sg_status s = fill();
+        cudaGraph_t out = nullptr;
+        const cudaError_t e = cudaStreamEndCapture(st, &out);
+        if (s != SG_OK) return s;
+        if (e != cudaSuccess) return fail(SG_ERR_CUDA, std::string("solve graph capture: ") + cudaGetErrorString(e));
+        return SG_OK;
+    };
+    cudaGraph_t outer_body = nullptr, inner_body = nullptr;
+    SG_TRY(capture(graph, [&]() -> sg_status {
+        SG_CK(launch_loop_init(g->dloop, ho, hi, st));
+        return add_while(ho, &outer_body);
+    }));
+    const long long before = g->launches;
+    SG_TRY(capture(outer_body, [&]() -> sg_status {
+        SG_TRY(add_while(hi, &inner_body));
+        const long long b0 = g->launches;
+        if (g->precision == SG_MIXED) SG_TRY(level0_residual(g, phi, f, faces));
+        SG_CK(launch_loop_confirm(g->dloop, g->red, ho, hi, st));
+        *per_confirm = g->launches - b0 + 1;
+        return SG_OK;
+    }));
+    SG_TRY(capture(inner_body, [&]() -> sg_status {
+        const long long b0 = g->launches;
+        SG_TRY(cycle_core(g, L, phi, f, faces));
+        SG_CK(launch_loop_step(g->dloop, g->red, g->d_ss, g->d_sched, hi, st));
+        *per_cycle = g->launches - b0 + 1;
+        return SG_OK;
+    }));
+    g->launches = before;
+    return SG_OK;
+}
+
+// State of the device loop for the solve S (after the host's first check).
+void fill_device_loop(sg_grid* g, const SolveState& S, DeviceLoop* d) {
+    std::memset(d, 0, sizeof(*d));
+    d->rden = S.rden;
+    d->nn = S.nn;
+    d->tol = S.tol;
+    d->mtol = g->opt.max_residual_tol;
+    d->limit = S.limit;
+    d->fixed = g->opt.fixed_cycles > 0 ? 1 : 0;
+    d->confirm = (g->precision == SG_MIXED && S.L > 1) ? 1 : 0;
+    d->m = S.m;
+    d->status = S.done ? kLoopDone : kLoopRunning;
+    d->sched_len = g->opt.coarse_max_ss;
+    const Level& Lc = g->lv[S.L - 1];
+    d->coarse_cells = Lc.n;
+    d->rel = S.info.rel_residual;
+    d->maxabs = S.info.max_residual;
+    d->history[0] = S.info.history[0];
+}
+
+// Results of a finished device loop into S.
+void read_device_loop(sg_grid* g, SolveState& S, const DeviceLoop& d, long long per_cycle, long long per_confirm) {
+    const int m0 = S.m;
+    S.m = d.m;
+    for (int q = m0 + 1; q <= d.m && q < SG_MAX_HISTORY; ++q) S.info.history[q] = d.history[q];
+    for (int q = m0; q < d.m && q < SG_MAX_HISTORY; ++q) S.info.coarse_ss[q] = d.coarse_ss[q];
+    S.info.rel_residual = d.rel;
+    S.info.max_residual = d.maxabs;
+    S.su += (long long)(d.m - m0) * stage_updates_per_cycle(g, S.L) + d.coarse_stage_cells;
+    g->launches += 1 + (long long)(d.m - m0) * per_cycle + (long long)d.confirms * per_confirm;
+    if (d.status == kLoopNonFinite) {
+        const unsigned waits = g->precision == SG_MIXED ? lean_wait_failures() : 0u;
+        S.status = fail(SG_ERR_NONFINITE, waits ? "residual norm is not finite: " + std::to_string(waits) +
+                                                      " fused super-step launch(es) gave up a bounded wait"
+                                                : std::string("residual norm is not finite"));
+    } else if (d.status == kLoopNotConverged) {
+        S.status = fail(SG_ERR_NOT_CONVERGED, "max_cycles reached above the tolerance");
+    }
+    S.done = true;
+}
+
+// Whether a solve runs as one graph with its cycle loop on the device: the
+// cycle can be captured and no per-kernel profile is being taken (the
+// profile's event records cannot sit inside a conditional body).
+bool use_device_loop(const sg_grid* g, int L) {
+    return cycle_graphable(g, L) && !g->prof && g->dloop != nullptr;
+}
+
+void drop_solve_graph(sg_grid* g) {
+    if (g->sexec) cudaGraphExecDestroy(g->sexec);
+    g->sexec = nullptr;
+    std::memset(g->skey, 0, sizeof(g->skey));
+}
+
+// The cycles of solve S as one graph launch (captured once per key), the
+// loop state written before and read back after it: one host round trip.
+sg_status run_device_loop(sg_grid* g, SolveState& S) {
+    uint64_t key[kGraphKeySlots];
+    graph_key(g, S.L, S.phi, S.f, S.faces, key);
+    if (!g->sexec || std::memcmp(key, g->skey, sizeof(key)) != 0) {
+        drop_solve_graph(g);
+        cudaGraph_t graph = nullptr;
+        SG_CK(cudaGraphCreate(&graph, 0));
+        long long pc = 0, pf = 0;
+        const sg_status st = add_solve_loop(g, graph, S.L, S.phi, S.f, S.faces, &pc, &pf);
+        if (st != SG_OK) {
+            cudaGraphDestroy(graph);
+            return st;
+        }
+        const cudaError_t ei = cudaGraphInstantiate(&g->sexec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ei != cudaSuccess) {
+            g->sexec = nullptr;
+            return fail(SG_ERR_CUDA, std::string("solve graph instantiate: ") + cudaGetErrorString(ei));
+        }
+        g->s_per_cycle = pc;
+        g->s_per_confirm = pf;
+        std::memcpy(g->skey, key, sizeof(key));
+    }
+    fill_device_loop(g, S, g->host_loop);
+    SG_CK(cudaMemcpyAsync(g->dloop, g->host_loop, sizeof(DeviceLoop), cudaMemcpyHostToDevice, g->st));
+    SG_CK(cudaGraphLaunch(g->sexec, g->st));
+    SG_CK(cudaMemcpyAsync(g->host_loop, g->dloop, sizeof(DeviceLoop), cudaMemcpyDeviceToHost, g->st));
+    SG_CK(cudaStreamSynchronize(g->st));
+    read_device_loop(g, S, *g->host_loop, g->s_per_cycle, g->s_per_confirm);
+    return SG_OK;
+}
+
 // The solve loop of sg_solve (phi, f, faces) and sg_backward (lam, w, none).
 sg_status solve_impl(sg_grid* g, double tol, int L, double* phi, const double* f, bool faces,
                      bool have_guess, sg_solve_info* info) {
     SolveState S;
     SG_TRY(solve_begin(g, S, tol, L, phi, f, faces, have_guess));
+    bool first = true;
     while (true) {
         SG_TRY(solve_check(g, S));
         if (S.done) break;
+        if (first && use_device_loop(g, L)) {
+            SG_TRY(run_device_loop(g, S));
+            break;
+        }
+        first = false;
         bool replayed = false;
         if (L == 1) SG_TRY(solve_single_step(g, S));
         else SG_TRY(run_cycle(g, L, phi, f, faces, &replayed));
@@ -1128,6 +1341,8 @@ void free_grid(sg_grid* g) {
     cudaFree(g->red);
     cudaFree(g->d_sched);
     cudaFree(g->d_ss);
+    cudaFree(g->dloop);
+    if (g->host_loop) cudaFreeHost(g->host_loop);
     if (g->host_red) cudaFreeHost(g->host_red);
     if (g->host_ss) cudaFreeHost(g->host_ss);
     if (g->ev0) cudaEventDestroy(g->ev0);
@@ -1135,11 +1350,21 @@ void free_grid(sg_grid* g) {
     for (const ProfRec& r : g->live) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
     for (cudaEvent_t e : g->ev_pool) cudaEventDestroy(e);
     if (g->own_stream) cudaStreamDestroy(g->own_stream);
-    if (g->batch_stream) cudaStreamDestroy(g->batch_stream);
     delete g;
 }
 
 }  // namespace
+
+// The last batch graph (sg_solve_batch): its key (serial number and graph key
+// of every grid, in order), the executable graph and the kernels of one cycle
+// and one confirmation per branch.
+struct BatchGraph {
+    std::vector<uint64_t> key;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<long long> per_cycle, per_confirm;
+};
+static BatchGraph g_batch;
+static std::mutex g_batch_mu;
 
 // ============================================================================
 // C ABI
@@ -1165,28 +1390,29 @@ sg_status sg_default_options(sg_options* o) {
     o->smoother = SG_SMOOTH_RKL;
     o->omega = 1.0;
     o->max_residual_tol = 0.0;
+    o->tile_rows = 0;
+    o->staging = SG_STAGE_CP_ASYNC;
     return SG_OK;
 }
 
 const char* sg_last_error(void) { return g_err.c_str(); }
 
-sg_status sg_create_grid(int nx, int ny, int nz, const double lo[3], const double hi[3],
-                         const int bc[3], int precision, void* cuda_stream, sg_grid** out) {
-    g_err.clear();
-    if (!out || !lo || !hi || !bc) return fail(SG_ERR_ARG, "NULL argument");
+}  // extern "C"
+
+namespace {
+
+// Grid of nx x ny x nz cells; twod: a two-dimensional grid (nz = 1, the z axis
+// periodic with h_z = infinity, so 1 / h_z^2 = 0 and the z term vanishes).
+sg_status create_grid(int nx, int ny, int nz, const double lo[3], const double hi[3], const int bc[3],
+                      int precision, void* cuda_stream, sg_grid** out, bool twod) {
     const int n[3] = {nx, ny, nz};
-    for (int d = 0; d < 3; ++d) {
-        if (n[d] < 2 || n[d] > 4096) return fail(SG_ERR_ARG, "grid size must be in [2, 4096] per axis");
-        if (!(hi[d] > lo[d]) || !std::isfinite(lo[d]) || !std::isfinite(hi[d]))
-            return fail(SG_ERR_ARG, "need finite lo < hi on every axis");
-        if (bc[d] != SG_BC_DIRICHLET && bc[d] != SG_BC_PERIODIC) return fail(SG_ERR_ARG, "bad boundary kind");
-    }
-    if ((long long)nx * ny * nz > 2147483647LL) return fail(SG_ERR_ARG, "too many cells");
-    if (precision != SG_FP64 && precision != SG_MIXED) return fail(SG_ERR_ARG, "bad precision");
     SG_CK(coarse_configure());
     SG_CK(fused_configure());
     SG_CK(bottom_configure());
     sg_grid* g = new sg_grid();
+    static std::atomic<unsigned long long> serials{0};
+    g->serial = ++serials;
+    g->twod = twod;
     for (int d = 0; d < 3; ++d) {
         g->n[d] = n[d];
         g->lo[d] = lo[d];
@@ -1205,7 +1431,7 @@ sg_status sg_create_grid(int nx, int ny, int nz, const double lo[3], const doubl
         g->st = g->own_stream;
     }
     sg_default_options(&g->opt);
-    g->max_levels = rule_levels(nx, ny, nz);
+    g->max_levels = twod ? rule_levels_2d(nx, ny) : rule_levels(nx, ny, nz);
     const size_t ws = wsize(g);
     auto alloc = [&](void** p, size_t bytes) -> bool { return cudaMalloc(p, bytes) == cudaSuccess; };
     bool ok = true;
@@ -1214,9 +1440,10 @@ sg_status sg_create_grid(int nx, int ny, int nz, const double lo[3], const doubl
         Level L;
         L.nx = nx >> l;
         L.ny = ny >> l;
-        L.nz = nz >> l;
+        L.nz = twod ? 1 : nz >> l;
         L.n = (long long)L.nx * L.ny * L.nz;
         for (int d = 0; d < 3; ++d) L.h[d] = (hi[d] - lo[d]) / n[d] * double(1 << l);
+        if (twod) L.h[2] = INFINITY;
         const bool own_u = !(l == 0 && precision == SG_FP64);
         if (own_u) ok = ok && alloc(&L.u, L.n * ws) && alloc(&L.rhs, L.n * ws);
         ok = ok && alloc(&L.z0, L.n * ws);
@@ -1233,6 +1460,8 @@ sg_status sg_create_grid(int nx, int ny, int nz, const double lo[3], const doubl
     ok = ok && alloc((void**)&g->partials, max_blocks * sizeof(Partial));
     ok = ok && alloc((void**)&g->red, 8 * sizeof(Reduced));
     ok = ok && alloc((void**)&g->d_ss, sizeof(int));
+    ok = ok && alloc((void**)&g->dloop, sizeof(DeviceLoop));
+    ok = ok && cudaMallocHost((void**)&g->host_loop, sizeof(DeviceLoop)) == cudaSuccess;
     ok = ok && cudaMallocHost((void**)&g->host_red, 8 * sizeof(Reduced)) == cudaSuccess;
     ok = ok && cudaMallocHost((void**)&g->host_ss, sizeof(int)) == cudaSuccess;
     ok = ok && cudaEventCreate(&g->ev0) == cudaSuccess && cudaEventCreate(&g->ev1) == cudaSuccess;
@@ -1250,6 +1479,44 @@ sg_status sg_create_grid(int nx, int ny, int nz, const double lo[3], const doubl
     }
     *out = g;
     return SG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+sg_status sg_create_grid(int nx, int ny, int nz, const double lo[3], const double hi[3],
+                         const int bc[3], int precision, void* cuda_stream, sg_grid** out) {
+    g_err.clear();
+    if (!out || !lo || !hi || !bc) return fail(SG_ERR_ARG, "NULL argument");
+    const int n[3] = {nx, ny, nz};
+    for (int d = 0; d < 3; ++d) {
+        if (n[d] < 2 || n[d] > 4096) return fail(SG_ERR_ARG, "grid size must be in [2, 4096] per axis");
+        if (!(hi[d] > lo[d]) || !std::isfinite(lo[d]) || !std::isfinite(hi[d]))
+            return fail(SG_ERR_ARG, "need finite lo < hi on every axis");
+        if (bc[d] != SG_BC_DIRICHLET && bc[d] != SG_BC_PERIODIC) return fail(SG_ERR_ARG, "bad boundary kind");
+    }
+    if ((long long)nx * ny * nz > 2147483647LL) return fail(SG_ERR_ARG, "too many cells");
+    if (precision != SG_FP64 && precision != SG_MIXED) return fail(SG_ERR_ARG, "bad precision");
+    return create_grid(nx, ny, nz, lo, hi, bc, precision, cuda_stream, out, false);
+}
+
+sg_status sg_create_grid_2d(int nx, int ny, const double lo[2], const double hi[2], const int bc[2], int precision,
+                            void* cuda_stream, sg_grid** out) {
+    g_err.clear();
+    if (!out || !lo || !hi || !bc) return fail(SG_ERR_ARG, "NULL argument");
+    const int n[2] = {nx, ny};
+    for (int d = 0; d < 2; ++d) {
+        if (n[d] < 2 || n[d] > 65536) return fail(SG_ERR_ARG, "grid size must be in [2, 65536] per axis");
+        if (!(hi[d] > lo[d]) || !std::isfinite(lo[d]) || !std::isfinite(hi[d]))
+            return fail(SG_ERR_ARG, "need finite lo < hi on both axes");
+        if (bc[d] != SG_BC_DIRICHLET && bc[d] != SG_BC_PERIODIC) return fail(SG_ERR_ARG, "bad boundary kind");
+    }
+    if ((long long)nx * ny > 2147483647LL) return fail(SG_ERR_ARG, "too many cells");
+    if (precision != SG_FP64 && precision != SG_MIXED) return fail(SG_ERR_ARG, "bad precision");
+    const double lo3[3] = {lo[0], lo[1], 0.0}, hi3[3] = {hi[0], hi[1], 1.0};
+    const int bc3[3] = {bc[0], bc[1], SG_BC_PERIODIC};
+    return create_grid(nx, ny, 1, lo3, hi3, bc3, precision, cuda_stream, out, true);
 }
 
 sg_status sg_set_options(sg_grid* g, const sg_options* opt) {
@@ -1325,7 +1592,7 @@ sg_status sg_set_boundary(sg_grid* g, const double* const faces[6], int on_devic
     const long long fsz[6] = {(long long)g->n[2] * g->n[1], (long long)g->n[2] * g->n[1],
                               (long long)g->n[2] * g->n[0], (long long)g->n[2] * g->n[0],
                               (long long)g->n[1] * g->n[0], (long long)g->n[1] * g->n[0]};
-    for (int f = 0; f < 6; ++f) {
+    for (int f = 0; f < (g->twod ? 4 : 6); ++f) {
         if (!g->faces[f]) SG_CK(cudaMalloc(&g->faces[f], fsz[f] * sizeof(double)));
         if (faces[f]) SG_TRY(copy_in(g->faces[f], faces[f], fsz[f], on_device, g->st));
         else SG_CK(cudaMemsetAsync(g->faces[f], 0, fsz[f] * sizeof(double), g->st));
@@ -1469,17 +1736,14 @@ sg_status sg_solve_batch(sg_grid* const* grids, int n, double tol, sg_solve_info
             if (grids[k] == grids[i]) return fail(SG_ERR_ARG, "a grid appears twice in the batch");
     }
     sg_status first = SG_OK;
-    // Grids whose V-cycle can be captured go into one multi-branch CUDA graph per
-    // cycle; the rest (single level, coarsest level too large for one CTA, graph
-    // replay disabled) are solved one after the other.
+    // Grids whose cycle loop can run on the device become one branch each of a
+    // single graph (sg_solve's loop: WHILE nodes decided on the device); the
+    // rest (single level, coarsest level too large for one CTA, graph replay
+    // disabled, profiling on) are solved one after the other.
     std::vector<int> par;
     for (int i = 0; i < n; ++i) {
         sg_grid* g = grids[i];
-        const int L = g->max_levels;
-        const bool ok = L > 1 && g->opt.use_graph &&
-                        (g->precision == SG_MIXED ? coarse_fits<float>(g->lv[L - 1].n)
-                                                  : coarse_fits<double>(g->lv[L - 1].n));
-        if (ok) {
+        if (use_device_loop(g, g->max_levels)) {
             par.push_back(i);
         } else {
             const sg_status st = sg_solve(g, tol, 0, 0, infos ? &infos[i] : nullptr);
@@ -1489,94 +1753,63 @@ sg_status sg_solve_batch(sg_grid* const* grids, int n, double tol, sg_solve_info
     if (par.empty()) return first;
     const size_t P = par.size();
     std::vector<SolveState> S(P);
-    std::vector<cudaEvent_t> join(P, nullptr);
-    cudaEvent_t fork = nullptr;
-    cudaGraphExec_t exec = nullptr;
-    sg_status err = SG_OK;
-    auto cleanup = [&]() {
-        if (exec) cudaGraphExecDestroy(exec);
-        if (fork) cudaEventDestroy(fork);
-        for (auto e : join)
-            if (e) cudaEventDestroy(e);
-    };
-    auto bail = [&](sg_status st) {
-        cleanup();
-        return st;
-    };
-    if (cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) != cudaSuccess) return bail(fail(SG_ERR_CUDA, "event"));
     for (size_t k = 0; k < P; ++k) {
         sg_grid* g = grids[par[k]];
-        if (!g->batch_stream && cudaStreamCreateWithFlags(&g->batch_stream, cudaStreamNonBlocking) != cudaSuccess)
-            return bail(fail(SG_ERR_CUDA, "cudaStreamCreate (batch)"));
-        if (cudaEventCreateWithFlags(&join[k], cudaEventDisableTiming) != cudaSuccess)
-            return bail(fail(SG_ERR_CUDA, "event"));
-        err = solve_begin(g, S[k], tol, g->max_levels, g->phi, g->f, g->have_faces, g->guess_set);
-        if (err != SG_OK) return bail(err);
+        SG_TRY(solve_begin(g, S[k], tol, g->max_levels, g->phi, g->f, g->have_faces, g->guess_set));
         g->guess_set = false;
+        SG_TRY(solve_check(g, S[k]));
     }
+    // the batch graph, kept while the same grids (by serial number) with the
+    // same keys come back
+    std::vector<uint64_t> key;
+    for (size_t k = 0; k < P; ++k) {
+        sg_grid* g = grids[par[k]];
+        uint64_t gk[kGraphKeySlots];
+        graph_key(g, S[k].L, S[k].phi, S[k].f, S[k].faces, gk);
+        key.push_back(g->serial);
+        key.insert(key.end(), gk, gk + kGraphKeySlots);
+    }
+    std::lock_guard<std::mutex> lock(g_batch_mu);
     cudaStream_t origin = grids[par[0]]->st;
-    std::vector<size_t> active_prev;
-    long long graph_kernels = 0;
-    while (true) {
-        std::vector<size_t> active;
+    if (!g_batch.exec || g_batch.key != key) {
+        if (g_batch.exec) cudaGraphExecDestroy(g_batch.exec);
+        g_batch.exec = nullptr;
+        g_batch.key.clear();
+        cudaGraph_t graph = nullptr;
+        SG_CK(cudaGraphCreate(&graph, 0));
+        g_batch.per_cycle.assign(P, 0);
+        g_batch.per_confirm.assign(P, 0);
         for (size_t k = 0; k < P; ++k) {
-            if (S[k].done) continue;
-            err = solve_check(grids[par[k]], S[k]);
-            if (err != SG_OK) return bail(err);
-            if (!S[k].done) active.push_back(k);
-        }
-        if (active.empty()) break;
-        if (active != active_prev) {
-            // (Re)capture: fork one branch per unconverged grid off the origin stream.
-            if (exec) cudaGraphExecDestroy(exec);
-            exec = nullptr;
-            cudaGraph_t graph = nullptr;
-            if (cudaStreamBeginCapture(origin, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
-                return bail(fail(SG_ERR_CUDA, "batch capture"));
-            sg_status cst = SG_OK;
-            cudaEventRecord(fork, origin);
-            graph_kernels = 0;
-            for (size_t k : active) {
-                sg_grid* g = grids[par[k]];
-                cudaStreamWaitEvent(g->batch_stream, fork, 0);
-                cudaStream_t saved = g->st;
-                const bool prof = g->prof;
-                g->st = g->batch_stream;
-                g->prof = false;
-                const long long before = g->launches;
-                cst = cycle_body(g, S[k].L, S[k].phi, S[k].f, S[k].faces);
-                graph_kernels += g->launches - before;
-                g->launches = before;
-                g->st = saved;
-                g->prof = prof;
-                if (cst != SG_OK) break;
-                cudaEventRecord(join[k], g->batch_stream);
-                cudaStreamWaitEvent(origin, join[k], 0);
-            }
-            const cudaError_t ec = cudaStreamEndCapture(origin, &graph);
-            if (cst != SG_OK) {
-                if (graph) cudaGraphDestroy(graph);
-                return bail(cst);
-            }
-            if (ec != cudaSuccess) return bail(fail(SG_ERR_CUDA, std::string("batch capture: ") + cudaGetErrorString(ec)));
-            const cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
-            cudaGraphDestroy(graph);
-            if (ei != cudaSuccess) {
-                exec = nullptr;
-                return bail(fail(SG_ERR_CUDA, std::string("batch instantiate: ") + cudaGetErrorString(ei)));
-            }
-            active_prev = active;
-        }
-        if (cudaGraphLaunch(exec, origin) != cudaSuccess || cudaStreamSynchronize(origin) != cudaSuccess)
-            return bail(fail(SG_ERR_CUDA, "batch graph launch"));
-        for (size_t k : active) {
             sg_grid* g = grids[par[k]];
-            g->launches += graph_kernels / (long long)active.size();
-            solve_after_cycle(g, S[k]);
+            const sg_status st = add_solve_loop(g, graph, S[k].L, S[k].phi, S[k].f, S[k].faces,
+                                                &g_batch.per_cycle[k], &g_batch.per_confirm[k]);
+            if (st != SG_OK) {
+                cudaGraphDestroy(graph);
+                return st;
+            }
         }
+        const cudaError_t ei = cudaGraphInstantiate(&g_batch.exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ei != cudaSuccess) {
+            g_batch.exec = nullptr;
+            return fail(SG_ERR_CUDA, std::string("batch graph instantiate: ") + cudaGetErrorString(ei));
+        }
+        g_batch.key = key;
     }
     for (size_t k = 0; k < P; ++k) {
         sg_grid* g = grids[par[k]];
+        fill_device_loop(g, S[k], g->host_loop);
+        SG_CK(cudaMemcpyAsync(g->dloop, g->host_loop, sizeof(DeviceLoop), cudaMemcpyHostToDevice, origin));
+    }
+    SG_CK(cudaGraphLaunch(g_batch.exec, origin));
+    for (size_t k = 0; k < P; ++k) {
+        sg_grid* g = grids[par[k]];
+        SG_CK(cudaMemcpyAsync(g->host_loop, g->dloop, sizeof(DeviceLoop), cudaMemcpyDeviceToHost, origin));
+    }
+    SG_CK(cudaStreamSynchronize(origin));
+    for (size_t k = 0; k < P; ++k) {
+        sg_grid* g = grids[par[k]];
+        read_device_loop(g, S[k], *g->host_loop, g_batch.per_cycle[k], g_batch.per_confirm[k]);
         const sg_status st = solve_end(g, S[k], infos ? &infos[par[k]] : nullptr);
         if (st == SG_OK || st == SG_ERR_NOT_CONVERGED) {
             g->have_solution = true;
@@ -1584,7 +1817,6 @@ sg_status sg_solve_batch(sg_grid* const* grids, int n, double tol, sg_solve_info
         }
         if (st != SG_OK && first == SG_OK) first = st;
     }
-    cleanup();
     return first;
 }
 
@@ -1596,7 +1828,7 @@ sg_status sg_autotune(sg_grid* g, int levels, int keep_order, sg_tune_entry* tab
     const int L = levels == 0 ? g->max_levels : levels;
     if (L < 2) return fail(SG_ERR_ARG, "autotuning needs a multigrid hierarchy (levels >= 2)");
     const sg_options saved = g->opt;
-    struct Cand { int order, s, fused; double c; int pre, post; };
+    struct Cand { int order, s, fused; double c; int pre, post, rows; };
     std::vector<Cand> cands;
     // more smoothing per cycle trades the cycle's fixed work (update,
     // transfers, coarsest levels) against fewer cycles
@@ -1609,7 +1841,14 @@ sg_status sg_autotune(sg_grid* g, int levels, int keep_order, sg_tune_entry* tab
             const double* cs = order == 1 ? cs1 : cs2;
             for (int ic = 0; ic < 3; ++ic)
                 for (int fz = 0; fz <= (g->precision == SG_MIXED ? 1 : 0); ++fz)
-                    for (const auto& pc : counts) cands.push_back({order, s, fz, cs[ic], pc[0], pc[1]});
+                    for (const auto& pc : counts) {
+                        if (fz && s <= 3 && !g->twod) {          // the tile shapes of the fused s = 2, 3 kernel
+                            cands.push_back({order, s, fz, cs[ic], pc[0], pc[1], 14});
+                            cands.push_back({order, s, fz, cs[ic], pc[0], pc[1], 16});
+                        } else {
+                            cands.push_back({order, s, fz, cs[ic], pc[0], pc[1], 0});
+                        }
+                    }
         }
     }
     double best = 1e300;
@@ -1623,6 +1862,7 @@ sg_status sg_autotune(sg_grid* g, int levels, int keep_order, sg_tune_entry* tab
         g->opt.fused = c.fused;
         g->opt.n_pre = c.pre;
         g->opt.n_post = c.post;
+        g->opt.tile_rows = c.rows;
         g->opt.smoother = SG_SMOOTH_RKL;
         // Time 2 and 6 cycles (after a capture / warm-up run) and take the
         // difference, so the per-solve set-up cost drops out of the score.
@@ -1647,7 +1887,7 @@ sg_status sg_autotune(sg_grid* g, int levels, int keep_order, sg_tune_entry* tab
         factor = std::max(factor, top);
         const double mpc = (info6.elapsed_ms - info2.elapsed_ms) / 4.0;
         const double score = (factor > 0 && factor < 1) ? mpc / -std::log10(factor) : 1e300;
-        if (table && tried < cap) table[tried] = {c.order, c.s, c.fused, c.c, mpc, factor, score, c.pre, c.post};
+        if (table && tried < cap) table[tried] = {c.order, c.s, c.fused, c.c, mpc, factor, score, c.pre, c.post, c.rows};
         (void)info2;
         ++tried;
         if (score < best) {
@@ -1709,7 +1949,7 @@ sg_status sg_op_superstep(sg_grid* g, int level, int dtype, int order, int s, do
     if ((order != 1 && order != 2) || s < 1 || (order == 2 && s < 2) || !(tau_frac > 0 && tau_frac <= 1))
         return fail(SG_ERR_ARG, "bad order / s / tau_frac");
     const bool faces = !homogeneous && level == 0 && g->have_faces;
-    if (dtype == 1 && g->opt.fused && !faces && fused_supported(order, s))
+    if (dtype == 1 && g->opt.fused && !faces && !g->twod && fused_supported(order, s))
         return superstep_fused(g, level, order, s, tau_frac, (const float*)u, (const float*)rhs, (float*)out);
     if (!u) return fail(SG_ERR_ARG, "u == NULL (zero initial guess) needs the fused FP32 super-step");
     const size_t bytes = g->lv[level].n * (dtype == 0 ? 8 : 4);
@@ -1885,6 +2125,7 @@ extern "C" sg_status sg_residual_restrict_noalloc(int nx, int ny, int nz, const 
     G.ihy2f = float(G.ihy2);
     G.ihz2f = float(G.ihz2);
     for (int f = 0; f < 6; ++f) G.face[f] = (faces && bc[f / 2] == SG_BC_DIRICHLET) ? faces[f] : nullptr;
+    G.twod = 0;
 
     const long long need = coarse_out ? restrict_blocks(G) : residual_blocks(G);
     if (need > kStaticSlots)

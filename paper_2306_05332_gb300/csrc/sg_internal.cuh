@@ -21,6 +21,9 @@ struct LevelGeom {
                                       // (GB300 issues FP64 and its conversions at 1/64 of the FP32 rate)
     int per[3];                       // periodic flag per axis (x, y, z)
     const double* face[6];            // -x,+x,-y,+y,-z,+z or all nullptr (homogeneous)
+    int twod;                         // a two-dimensional level (Sec. 2.2): nz = 1, z periodic, 1 / h_z^2 = 0,
+                                      // so the seven-point kernels compute the five-point operator exactly;
+                                      // restriction averages 4 cells, prolongation weighs 9/3/3/1
 };
 
 // 1 / h^2 per axis in the kernel's precision.
@@ -118,6 +121,37 @@ cudaError_t launch_sub_mean_f64(double* x, long long n, const Reduced* red, cuda
 cudaError_t launch_sum_partials_f64(const double* x, long long n, Partial* partials,
                                     int* nblocks_out, cudaStream_t st);
 
+// ---- the convergence loop on the device (kernels_loop.cu) -------------------
+constexpr int kLoopHistory = 256;          // entries of the residual history kept (SG_MAX_HISTORY)
+constexpr int kLoopRunning = 0, kLoopDone = 1, kLoopNotConverged = 2, kLoopNonFinite = 3;
+// State of one solve's cycle loop in device memory: set by the host before
+// the solve graph is launched, read back once when it has finished.
+struct DeviceLoop {
+    double rden;            // ||L 0 - f|| (1 if zero)
+    double nn;              // cells of level 0
+    double tol;             // relative L2 tolerance
+    double mtol;            // > 0: stop on max |r| <= mtol instead
+    int limit;              // cycle cap (or the fixed count)
+    int fixed;              // run exactly `limit` cycles
+    int confirm;            // mixed precision: confirm a met recurrence residual in FP64
+    int m;                  // cycles run
+    int status;             // kLoop*
+    int pending;            // the inner loop ended for a confirmation
+    int sched_len;          // entries of the coarse schedule
+    int confirms;           // times the inner loop ended (the confirmation step ran)
+    long long coarse_cells; // cells of the coarsest level
+    long long coarse_stage_cells;   // sum over cycles of coarse cells x stages
+    double rel, maxabs;     // the last recorded residual
+    double history[kLoopHistory];
+    int coarse_ss[kLoopHistory];
+};
+cudaError_t launch_loop_init(const DeviceLoop* d, cudaGraphConditionalHandle outer, cudaGraphConditionalHandle inner,
+                             cudaStream_t st);
+cudaError_t launch_loop_step(DeviceLoop* d, const Reduced* red, const int* ss_done, const int* sched,
+                             cudaGraphConditionalHandle inner, cudaStream_t st);
+cudaError_t launch_loop_confirm(DeviceLoop* d, const Reduced* red, cudaGraphConditionalHandle outer,
+                                cudaGraphConditionalHandle inner, cudaStream_t st);
+
 // ---- fused super-step, FP32 (kernels_fused.cu) -----------------------------
 constexpr int kFusedMaxS = 6;
 struct FusedCoef {
@@ -130,12 +164,21 @@ bool fused_supported(int order, int s);
 cudaError_t fused_configure();
 // out = Y_s of one super-step from y0 (nullptr: Y0 = 0) with homogeneous or
 // periodic ghosts; out must not alias y0.
+// tile_rows: 14 or 16 fixes the tile of the s = 2, 3 kernel; 0 lets its cost
+// model choose.  tma: that kernel stages planes by tensor-map box copies where
+// the level allows it (otherwise by per-strip copies).
 cudaError_t launch_superstep_fused(const LevelGeom& g, int order, int s, bool zero_y0, const FusedCoef& cf,
-                                   const float* y0, const float* f, float* out, cudaStream_t st);
+                                   const float* y0, const float* f, float* out, cudaStream_t st,
+                                   int tile_rows = 0, bool tma = false);
 // s = 2, 3: stage-balanced variant with reflected halos (kernels_superstep.cu).
 cudaError_t lean_configure();
 cudaError_t launch_superstep_lean(const LevelGeom& g, int order, int s, bool zero_y0, const FusedCoef& cf,
-                                  const float* y0, const float* f, float* out, cudaStream_t st);
+                                  const float* y0, const float* f, float* out, cudaStream_t st, int tile_rows,
+                                  bool tma);
+// Launches of the TMA path that gave up a bounded wait (or found their shared
+// memory misaligned) since the library was loaded; each wrote a NaN into its
+// output, so the solve that ran it reports a non-finite residual.
+unsigned lean_wait_failures();
 
 // ---- coarsest-level solver (kernels_coarse.cu) -----------------------------
 struct CoarseParams {

@@ -23,7 +23,8 @@ TOL = 1e-12
 LO, HI = (0.0, -0.5, 0.25), (1.3, 0.2, 1.35)
 
 SHAPES_BC = [((20, 12, 36), (0, 0, 0)), ((16, 24, 8), (1, 1, 1)), ((12, 20, 40), (1, 0, 1)),
-             ((9, 37, 13), (0, 1, 0)), ((2, 6, 5), (0, 0, 1)), ((7, 2, 3), (1, 1, 0))]
+             ((9, 37, 13), (0, 1, 0)), ((2, 6, 5), (0, 0, 1)), ((7, 2, 3), (1, 1, 0)),
+             ((40, 19, 70), (0, 0, 0)), ((33, 17, 66), (1, 0, 1))]
 
 
 def _sg():

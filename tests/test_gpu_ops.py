@@ -166,7 +166,54 @@ def test_coarse_solve_tolerance_stop():
 # both orders, Y0 = 0 and general Y0, every boundary mix, ragged and tiny shapes.
 # ---------------------------------------------------------------------------
 FUSED_SHAPES = [((20, 12, 36), (0, 0, 0)), ((16, 24, 8), (1, 1, 1)), ((12, 20, 40), (1, 0, 1)),
-                ((37, 19, 70), (0, 1, 0)), ((6, 4, 2), (1, 1, 1)), ((4, 6, 10), (0, 0, 0))]
+                ((37, 19, 70), (0, 1, 0)), ((6, 4, 2), (1, 1, 1)), ((4, 6, 10), (0, 0, 0)),
+                ((20, 30, 44), (0, 0, 0)), ((18, 4, 4), (0, 0, 1)), ((9, 26, 100), (0, 0, 1))]
+
+# Shapes with nx % 4 == 0, even ny and no wrap in x and y, where the s = 2, 3
+# kernel can stage planes by tensor-map box copies (staging = "tma"): ragged x
+# and y tiles, a level narrower than the x halo, a periodic z axis (z
+# reflections and wraps), several z chunks per tile column.
+TMA_SHAPES = [((20, 12, 36), (0, 0, 0)), ((20, 30, 44), (0, 0, 0)), ((18, 4, 4), (0, 0, 1)),
+              ((9, 26, 100), (0, 0, 1)), ((168, 160, 160), (0, 0, 0)), ((160, 162, 164), (0, 0, 1))]
+
+
+@pytest.mark.parametrize("shape,bc", TMA_SHAPES)
+@pytest.mark.parametrize("order,s", [(2, 3), (1, 2)])
+@pytest.mark.parametrize("zero", [False, True])
+def test_tma_staging_matches_oracle_and_copy_staging(shape, bc, order, s, zero):
+    g, h, _ = make_grid(shape, bc, "mixed")
+    u = np.zeros(shape) if zero else W.random_field(shape, 40)
+    rhs = 50.0 * W.random_field(shape, 41)
+    outs = {}
+    for staging in ("cp_async", "tma"):
+        g.set_options(staging=staging)
+        out = torch.full(shape, float("nan"), dtype=torch.float32, device="cuda")
+        g.op_superstep(0, order, s, 0.9, None if zero else dev(u, torch.float32), dev(rhs, torch.float32), out,
+                       homogeneous=True)
+        torch.cuda.synchronize()
+        outs[staging] = out
+    u32 = u.astype(np.float32).astype(np.float64)
+    r32 = rhs.astype(np.float32).astype(np.float64)
+    ref = O.rkl_superstep(u32, r32, h, bc, None, order, s, 0.9)
+    assert torch.isfinite(outs["tma"]).all()
+    assert relerr(outs["tma"].double(), ref) < 5e-5
+    # the same arithmetic on the same staged values: identical to the last bit
+    assert torch.equal(outs["tma"], outs["cp_async"])
+
+
+def test_tma_staging_solve_equals_copy_staging():
+    p = W.sphere(128)
+    sg = pytest.importorskip("paper_2306_05332_gb300")
+    phis = {}
+    for staging in ("cp_async", "tma"):
+        g = sg.Grid(p.shape, p.lo, p.hi, p.bc, precision="mixed")
+        g.set_boundary(p.faces)
+        g.set_density(p.rho, 1.0)
+        g.set_options(rkl_order=2, s_smooth=3, tau_frac=0.9, n_pre=5, n_post=3, staging=staging)
+        info = g.solve(tol=1e-8, levels=4)
+        assert info["rel_residual"] <= 1e-8
+        phis[staging] = g.potential()
+    np.testing.assert_array_equal(phis["tma"], phis["cp_async"])
 
 
 @pytest.mark.parametrize("shape,bc", FUSED_SHAPES)
