@@ -47,6 +47,10 @@ TOL = 1e-8
 SOLVER = dict(rkl_order=2, s_smooth=3, tau_frac=0.9, n_pre=5, n_post=3, coarse_tol=1e-2, coarse_max_ss=64)
 METRIC = "Poisson solves/s to rel. residual 1e-8 at 256^3"
 FALLBACK_HBM_GBS = 6800.0
+# FP64 instructions per cell and stage of the FP64 stage kernel, averaged over
+# an s = 3 RKL2 super-step (one first stage, 13.5; two later ones, 16.5), as
+# counted by ncu (smsp__inst_executed_pipe_fp64) on 256^3 launches
+FP64_INSTR_PER_STAGE_CELL = 15.5
 
 
 def args_():
@@ -63,6 +67,10 @@ def args_():
     ap.add_argument("--n", type=int, default=N, help="grid size of --profile-solves")
     ap.add_argument("--smoother", choices=["rkl", "gsrb"], default="rkl",
                     help="smoother of --profile-solves (rkl: the bench's RKL2 settings; gsrb: red-black GS)")
+    ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed",
+                    help="precision of --profile-solves")
+    ap.add_argument("--gravity", action="store_true",
+                    help="with --profile-solves: after each solve, one acceleration pass (sg_gravity)")
     return ap.parse_args()
 
 
@@ -514,7 +522,30 @@ def run_ours(a, world, rank, local):
         t0 = time.perf_counter()
         i64 = g64.solve(tol=TOL, levels=LEVELS)
         t64 = (time.perf_counter() - t0) * 1e3
-        extra["fp64_gpu_solve"] = {"solves_per_s": 1000.0 / t64, "ms": t64, "cycles": i64["cycles"]}
+        # its roofline: the level-0 stage kernels are bound by the FP64 pipe, not
+        # HBM; FP64 instructions per cell counted by ncu on these kernels
+        # (13.5 in a first stage, 16.5 in a later one: 15.5 on average over an
+        # s = 3 super-step), against this GPU's measured FP64 FMA rate
+        fp64_tflops, _ = sg.measure_fp64_rate()
+        g64.set_density(rho_dev, 1.0)
+        g64.set_profiling(True)
+        g64.solve(tol=TOL, levels=LEVELS)
+        torch.cuda.synchronize()
+        st64 = g64.kernel_stats()["rkl_stage_l0"]
+        g64.set_profiling(False)
+        n0c = N ** 3
+        instr = FP64_INSTR_PER_STAGE_CELL * n0c * st64["launches"]
+        achieved = instr / (st64["ms"] * 1e-3)
+        peak_instr = fp64_tflops * 1e12 / 2.0
+        peak_hbm, _src = hbm_peak()
+        extra["fp64_gpu_solve"] = {"solves_per_s": 1000.0 / t64, "ms": t64, "cycles": i64["cycles"],
+                                   "roofline_level0_stages": {
+                                       "bound": "fp64", "achieved_fp64_instr_per_s": achieved,
+                                       "peak_fp64_instr_per_s": peak_instr, "frac": achieved / peak_instr,
+                                       "fp64_tflops_measured": fp64_tflops,
+                                       "hbm_frac": st64["bytes"] / (st64["ms"] * 1e-3) / 1e9 / peak_hbm,
+                                       "fp64_instr_per_stage_cell": FP64_INSTR_PER_STAGE_CELL,
+                                       "launches": st64["launches"], "ms": st64["ms"]}}
         del g64
         g.set_options(**dict(SOLVER, rkl_order=1, s_smooth=2, tau_frac=0.75, n_pre=2, n_post=1))
         step()
@@ -677,13 +708,19 @@ def run_profile_solves(a):
     p = W.sphere(a.n)
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
-    g = sg.Grid(p.shape, p.lo, p.hi, p.bc, precision="mixed", stream=stream.cuda_stream)
+    g = sg.Grid(p.shape, p.lo, p.hi, p.bc, precision=a.precision, stream=stream.cuda_stream)
     g.set_boundary(p.faces)
-    g.set_options(**SOLVER, smoother=a.smoother)
+    # use_graph = 2: each V-cycle a captured graph and the loop on the host, so
+    # that a profiler sees every kernel (it cannot see into the kernel nodes of
+    # the default solve graph, whose loop runs in conditional nodes)
+    g.set_options(**SOLVER, smoother=a.smoother, use_graph=2)
     rho = torch.tensor(p.rho, device="cuda")
+    gout = torch.empty((3,) + tuple(p.shape), dtype=torch.float64, device="cuda") if a.gravity else None
     for k in range(a.profile_solves):
         g.set_density(rho, 1.0)
         info = g.solve(tol=TOL, levels=LEVELS)
+        if gout is not None:
+            g.gravity(out=gout)
         print(k, info["cycles"], round(info["elapsed_ms"], 3), info["coarse_ss"][:5], flush=True)
 
 

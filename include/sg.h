@@ -91,7 +91,12 @@ typedef struct sg_options {
                                grid's largest extent (sg_plan_s_opt)             [0]  */
     double single_tau_frac; /* levels == 1: tau / tau_max; 0 = cos^2(pi / 2N)       [0]  */
     int    fixed_cycles;    /* > 0: run exactly this many cycles (<= 10^7), ignore tol [0] */
-    int    use_graph;       /* replay each V-cycle as a captured CUDA graph         [1]  */
+    int    use_graph;       /* 1: the whole solve as one CUDA graph, the cycle loop
+                               on the device (WHILE nodes); 2: each V-cycle
+                               replayed as a captured graph, the loop on the host
+                               (a profiler that cannot see into graphs with
+                               conditional nodes sees every kernel); 0: kernels
+                               launched one by one                               [1]  */
     int    fused;           /* fused multi-stage super-step kernels where possible  [1]  */
     int    smoother;        /* sg_smoother.  With SG_SMOOTH_GSRB one relaxation
                                (n_pre, n_post) is one red-black sweep, every cell
@@ -112,6 +117,10 @@ typedef struct sg_options {
     int    tile_rows;       /* rows of the tile of the fused s = 2, 3 super-step:
                                14 or 16; 0 = the launcher's cost model (the plan
                                whose busiest SM has the least work)           [0]  */
+    int    inner_n_pre;     /* smoothing super-steps on the way down on levels
+                               1 .. L-2; -1 = n_pre (the paper's N_pre on every
+                               level)                                           [-1] */
+    int    inner_n_post;    /* the same on the way up; -1 = n_post             [-1] */
     int    staging;         /* sg_staging: how the fused s = 2, 3 super-step stages
                                its planes in shared memory.  SG_STAGE_TMA: two
                                tensor-map box copies per field and plane, issued
@@ -207,7 +216,10 @@ sg_status sg_set_potential_guess(sg_grid* g, const double* phi, int on_device);
  * (SG_ERR_ARG beyond it).  tol must be >= 0.  Returns SG_ERR_NOT_CONVERGED
  * (potential kept) when max_cycles is reached above tol, SG_ERR_NONFINITE on a
  * NaN/Inf residual.  With periodic axes on every side the potential is
- * returned with zero mean.
+ * returned with zero mean.  With use_graph = 1 (the default) and a coarsest
+ * level that fits one CTA, the cycles run as one CUDA graph with the loop on
+ * the device (the graph is captured once per option set and kept); the host
+ * reads the loop's state once when it has finished.
  */
 sg_status sg_solve(sg_grid* g, double tol, int s, int levels, sg_solve_info* info);
 
@@ -247,11 +259,15 @@ sg_status sg_backward(sg_grid* g, const double* dL_dphi, double* dL_drho, int on
 /*
  * Solve n independent grids (each with its density, boundary and options set;
  * sizes may differ) to tolerance tol, with the levels of each grid's rule.
- * Every V-cycle of the whole batch is one CUDA graph launch: one branch per
- * unconverged grid, forked from the first grid's stream, so the kernels of
- * small grids run concurrently; the graph is re-captured when a grid
- * converges and leaves.  Grids that cannot be captured (one level, a coarsest
- * level too large for one CTA, use_graph = 0) are solved one after the other.
+ * The whole batch is one CUDA graph launch on the first grid's stream: one
+ * branch per grid, each its cycle loop on the device (a WHILE node repeating
+ * the V-cycle while a one-thread kernel finds the residual above tol), so the
+ * kernels of small grids run concurrently, a grid that converges leaves its
+ * loop without a host round trip, and the host reads the loop states once at
+ * the end.  The graph is kept and launched again while the same grids (with
+ * the same options) come back.  Grids whose loop cannot run on the device
+ * (one level, a coarsest level too large for one CTA, use_graph != 1,
+ * profiling on) are solved one after the other first.
  * Each grid keeps its own stopping rule and info.  infos may be NULL or an
  * array of n entries.  A grid may appear only once.  Returns the first
  * non-OK status.
@@ -272,14 +288,16 @@ typedef struct sg_tune_entry {
     double ms_per_decade;      /* ms_per_cycle / -log10(factor): the score (lower is better) */
     int    n_pre, n_post;      /* smoothing super-steps per V-cycle tried */
     int    tile_rows;          /* tile rows of the fused super-step tried (0: cost model) */
+    int    inner_n_pre, inner_n_post;   /* smoothing counts of levels 1 .. L-2 tried (-1: n_pre, n_post) */
 } sg_tune_entry;
 
 /*
  * Pick the smoother for this grid and its current density by measurement: for
  * every candidate (RKL order 1 and 2 -- or only the current order when
  * keep_order is 1 --, s = 2..6, a few tau fractions, fused on and off, and
- * (N_pre, N_post) = (2, 1), (3, 2), (4, 3) or (5, 3), and for the fused
- * s = 2, 3 super-step both tile shapes, 32 x 14 and 32 x 16) run
+ * (N_pre, N_post) = (2, 1), (3, 2), (4, 3) or (5, 3), on levels 1 .. L-2 the
+ * same or (2, 1), and for the fused s = 2, 3 super-step both tile shapes,
+ * 32 x 14 and 32 x 16) run
  * two and six V-cycles at `levels` (0 = the level rule), take the difference
  * of their CUDA-event times (so per-solve set-up drops out) and score the time
  * per decade of residual reduction over cycles 2..6, bounded below by the
@@ -322,6 +340,16 @@ sg_status sg_plan_schedule(int N, int count, int* s_out);
  * (RKL2) or s > 100000. */
 sg_status sg_plan_stage_coefficients(int order, int s, double* mu, double* nu, double* mut, double* gt,
                                      double* tau_max_over_dtpar);
+
+/* Measurement aid (no counterpart in the paper): the FP64 FMA throughput of
+ * the current device in TFLOP/s (2 flops per FMA), from eight independent FMA
+ * chains per thread on every SM, timed by CUDA events after a warm-up launch;
+ * *ms (may be NULL) receives the timed launch's duration.  It is the ceiling of
+ * the FP64 kernels (the FP64 solve's stages, the acceleration), whose
+ * roofline is min(HBM, this rate).  Allocates and frees a small buffer;
+ * synchronises the device's legacy stream.  SG_ERR_ARG for NULL tflops,
+ * SG_ERR_CUDA on a CUDA error. */
+sg_status sg_measure_fp64_rate(double* tflops, double* ms);
 
 /* App. A.4's single fixed stage count s_opt for a level whose largest extent is
  * N (Eqs. eigenvalue_RKL, spectral_rad_RKL, sopt_theory and the two-step search

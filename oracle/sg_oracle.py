@@ -459,6 +459,8 @@ class Options:
     tau_frac: float = 1.0      # smoother tau / tau_max
     n_pre: int = 2             # Sec. 4.1: N_pre = 2, N_post = 1
     n_post: int = 1
+    inner_n_pre: int = -1      # smoothing counts on levels 1 .. L-2 (-1: n_pre / n_post)
+    inner_n_post: int = -1
     coarse_tol: float = 1e-2   # coarsest-level relative residual target (0 = fixed count)
     coarse_max_ss: int = 64    # cap on coarsest-level super-steps
     coarse_tau_frac: float = 0.0   # 0 = coarse_tau_frac(N)
@@ -526,8 +528,12 @@ def relax(u, rhs, h, bc, faces, opts, count):
 
 def vcycle(phi, f, h, bc, faces, L, opts, record=None):
     """One correction-scheme V-cycle (Sec. 2.1), levels 0..L-1, one increment
-    of l per pass (step 2), upstroke l = L-2..1 (step 3), then step 4 on l = 0."""
+    of l per pass (step 2), upstroke l = L-2..1 (step 3), then step 4 on l = 0.
+    Levels 1..L-2 smooth opts.inner_n_pre / inner_n_post times when those are
+    set (the paper uses N_pre / N_post on every level)."""
     hs = level_spacings(h, L)
+    pre_in = opts.inner_n_pre if opts.inner_n_pre >= 0 else opts.n_pre
+    post_in = opts.inner_n_post if opts.inner_n_post >= 0 else opts.n_post
     per = all_periodic(bc)
     u = [None] * L
     rhs = [None] * L
@@ -543,13 +549,13 @@ def vcycle(phi, f, h, bc, faces, L, opts, record=None):
         rhs[l] = -fl                       # relax L dphi = -f^l
         u[l] = np.zeros_like(fl)           # 2c
         if l < L - 1:
-            u[l] = relax(u[l], rhs[l], hs[l], bc, None, opts, opts.n_pre)                  # 2d-i
+            u[l] = relax(u[l], rhs[l], hs[l], bc, None, opts, pre_in)                      # 2d-i
         else:
             u[l] = coarse_solve(rhs[l], hs[l], bc, None, opts, record=record)               # 2e
     # step 3
     for l in range(L - 2, 0, -1):
         u[l] = u[l] + prolong(u[l + 1], bc)                                                  # 3a
-        u[l] = relax(u[l], rhs[l], hs[l], bc, None, opts, opts.n_post)                      # 3b
+        u[l] = relax(u[l], rhs[l], hs[l], bc, None, opts, post_in)                          # 3b
     # step 4
     if L > 1:
         u[0] = u[0] + prolong(u[1], bc)                                                      # 4a

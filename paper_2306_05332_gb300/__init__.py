@@ -44,7 +44,7 @@ class Options(ctypes.Structure):
                 ("single_tau_frac", ctypes.c_double), ("fixed_cycles", ctypes.c_int),
                 ("use_graph", ctypes.c_int), ("fused", ctypes.c_int), ("smoother", ctypes.c_int),
                 ("omega", ctypes.c_double), ("max_residual_tol", ctypes.c_double), ("tile_rows", ctypes.c_int),
-                ("staging", ctypes.c_int)]
+                ("inner_n_pre", ctypes.c_int), ("inner_n_post", ctypes.c_int), ("staging", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -83,7 +83,7 @@ class TuneEntry(ctypes.Structure):
     _fields_ = [("rkl_order", ctypes.c_int), ("s_smooth", ctypes.c_int), ("fused", ctypes.c_int),
                 ("tau_frac", ctypes.c_double), ("ms_per_cycle", ctypes.c_double), ("factor", ctypes.c_double),
                 ("ms_per_decade", ctypes.c_double), ("n_pre", ctypes.c_int), ("n_post", ctypes.c_int),
-                ("tile_rows", ctypes.c_int)]
+                ("tile_rows", ctypes.c_int), ("inner_n_pre", ctypes.c_int), ("inner_n_post", ctypes.c_int)]
 
 
 class SGError(RuntimeError):
@@ -129,6 +129,7 @@ _SIGS = {
                                     ctypes.POINTER(_D), ctypes.POINTER(_D)], _I),
     "sg_plan_levels": ([_I, _I, _I], _I),
     "sg_plan_s_opt": ([_I, ctypes.POINTER(_I)], _I),
+    "sg_measure_fp64_rate": ([ctypes.POINTER(_D), ctypes.POINTER(_D)], _I),
     "sg_plan_sor_omega": ([_I, _I, _I, ctypes.POINTER(_D), ctypes.POINTER(_D), ctypes.POINTER(_D)], _I),
     "sg_residual_restrict_noalloc": ([_I, _I, _I, ctypes.POINTER(_D), ctypes.POINTER(_D), ctypes.POINTER(_I),
                                       ctypes.POINTER(_P), _I, _P, _P, _P, ctypes.POINTER(_D), _P], _I),
@@ -338,11 +339,11 @@ class Grid:
 
     def autotune(self, levels=0, keep_order=True):
         """Measure the smoother candidates and keep the fastest per residual decade."""
-        cap = 256
+        cap = 1024
         arr = (TuneEntry * cap)()
         n = ctypes.c_int(0)
         _check(lib().sg_autotune(self._h, int(levels), int(bool(keep_order)), arr, cap, ctypes.byref(n)))
-        table = [{k: getattr(arr[i], k) for k, _ in TuneEntry._fields_} for i in range(n.value)]
+        table = [{k: getattr(arr[i], k) for k, _ in TuneEntry._fields_} for i in range(min(n.value, cap))]
         return self.options().as_dict(), table
 
     def kernel_stats(self):
@@ -523,6 +524,13 @@ def plan_s_opt(N):
     out = _I(0)
     _check(lib().sg_plan_s_opt(int(N), ctypes.byref(out)))
     return out.value
+
+
+def measure_fp64_rate():
+    """(TFLOP/s, ms) of FP64 FMA chains on the current device (roofline aid)."""
+    t, ms = _D(0.0), _D(0.0)
+    _check(lib().sg_measure_fp64_rate(ctypes.byref(t), ctypes.byref(ms)))
+    return t.value, ms.value
 
 
 def plan_levels(shape):

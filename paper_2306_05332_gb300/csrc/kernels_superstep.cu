@@ -38,8 +38,7 @@
 // tiles stream the same planes at about the same time and share halos in L2.
 //
 // Latency.  Planes are staged into shared memory two phases before their
-// first use, and prefetched into L2 kPrefetch planes ahead, so a phase waits
-// on an L2 hit rather than on HBM.
+// first use (staging four phases ahead measured no faster).
 //
 // HBM traffic per super-step: read Y0 + read f + write Y_s (12 B/cell; 8 B/cell
 // when Y0 = 0).  Halo cells are re-read from L2 by neighbouring tiles.
@@ -67,7 +66,6 @@ __device__ __forceinline__ void cpa16(float* smem, const float* gmem) {
 __device__ __forceinline__ void cpa_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cpa_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 __device__ __forceinline__ void cpa_wait_prev() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
-__device__ __forceinline__ void prefetch_l2(const float* p) { asm volatile("prefetch.global.L2 [%0];\n" ::"l"(p)); }
 
 // ---- TMA staging: box copies completing on an mbarrier ---------------------
 __device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
@@ -338,7 +336,7 @@ __device__ __forceinline__ float4 fixed_strip(const FixDesc& d, const float* pla
 __device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
 __device__ __forceinline__ void st4(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
 
-constexpr int kPrefetch = 8;      // planes between the L2 prefetch and the first use
+constexpr int kPrefetch = 8;      // TMA path: planes between the box prefetch into L2 and the first use
 
 // Packed FP32 pairs (Blackwell f32x2 instructions): each call is two
 // independent FP32 operations with the rounding of the scalar ones.
@@ -558,23 +556,6 @@ k_superstep_lean(const __grid_constant__ LevelGeom g, const __grid_constant__ Le
     // box coordinates: local even rows are the global rows of Yt's parity
     const int ypar = Yt & 1;
     const int ybox_e = (Yt - ypar) / 2, ybox_o = (Yt + ypar) / 2;
-    // L2 prefetch: three points of each staged row (first, middle and last cell of
-    // the row's part inside the box), per field
-    int pf = -1;
-    const float* pf_src = fg;
-    if (!TMA) {
-        constexpr int NPF = 3 * C::H;
-        const int fld = tid / NPF, rem = tid % NPF;
-        if (fld < (ZERO ? 1 : 2)) {
-            int sy;
-            const int yy = map_axis(Yt + rem / 3, ny, g.per[1] != 0, &sy);
-            const int xlo = max(X0, 0), xhi = min(X0 + W, nx) - 1;
-            const int kq = rem % 3;
-            pf = yy * nx + (kq == 0 ? xlo : (kq == 1 ? (xlo + xhi) / 2 : xhi));
-            pf_src = (ZERO || fld == 1) ? fg : y0g;
-        }
-    }
-
     const int t_first = kz0 - NS + 2;                   // stage 1 computes plane t - 1
     const int nph = (kz1 - kz0) + 3 * NS - 3;           // phases
     const int nload = kz1 + NS - t_first;               // planes t_first + v, v < nload, are staged
@@ -604,6 +585,9 @@ k_superstep_lean(const __grid_constant__ LevelGeom g, const __grid_constant__ Le
             issue(ld, sm + C::OF + (v & (C::RF - 1)) * P, fg + src);
         }
     };
+    // TMA path: whole boxes into L2 kPrefetch planes ahead (the per-strip copies
+    // run without: a per-thread L2 prefetch there measured slower, 138.9
+    // against 132.8 us per general 256^3 launch)
     auto prefetch_plane = [&](int v) {
         int zsg;
         const int zz = map_axis(t_first + v, nz, pz, &zsg);
@@ -616,8 +600,6 @@ k_superstep_lean(const __grid_constant__ LevelGeom g, const __grid_constant__ Le
                 tma_prefetch(&maps.f[ypar], X0, ybox_e, zz);
                 tma_prefetch(&maps.f[ypar ^ 1], X0, ybox_o, zz);
             }
-        } else if (pf >= 0) {
-            prefetch_l2(pf_src + zz * plane + pf);
         }
     };
     // cp.async path: the thread's own copies have landed; negate reflected cells
@@ -682,7 +664,6 @@ k_superstep_lean(const __grid_constant__ LevelGeom g, const __grid_constant__ Le
         fix_plane(0, zs2);
         if (1 < nload) stage_plane(1, &zs_next);
         cpa_commit();
-        for (int v = 2; v < kPrefetch && v < nload; ++v) prefetch_plane(v);
         __syncthreads();
     }
 
@@ -701,11 +682,11 @@ k_superstep_lean(const __grid_constant__ LevelGeom g, const __grid_constant__ Le
     // input stage; the strips of plane p + 1 are loaded into `nxt`.  The loop
     // below rotates the three register sets by renaming (unrolled by three).
     auto phase = [&](int u, float4& dn0, float4& cen0, float4& nxt0, float4& dn1, float4& cen1, float4& nxt1) -> bool {
-        // stage plane t + 2 into shared memory, prefetch plane t + kPrefetch into L2
+        // stage plane t + 2 into shared memory (TMA path: prefetch plane t + kPrefetch into L2)
         const int zs_cur = zs_next;
         if (u + 2 < nload) stage_plane(u + 2, &zs_next);
         if constexpr (!TMA) cpa_commit();
-        if (u + kPrefetch < nload) prefetch_plane(u + kPrefetch);
+        if (TMA && u + kPrefetch < nload) prefetch_plane(u + kPrefetch);
 
         if (!ZERO && J == 1) {
             // ---- stage 1 on plane t - 1

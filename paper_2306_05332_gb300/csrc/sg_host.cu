@@ -233,7 +233,7 @@ struct ProfRec {
 
 }  // namespace
 
-constexpr int kGraphKeySlots = 19;   // items the cached cycle graph is keyed on (run_cycle)
+constexpr int kGraphKeySlots = 21;   // items the cached cycle graph is keyed on (run_cycle)
 
 struct sg_grid {
     int n[3];
@@ -293,6 +293,15 @@ struct sg_grid {
 };
 
 namespace {
+
+// Smoothing super-steps of level l on the way down / up: N_pre / N_post on
+// level 0, the inner counts (when set) on levels 1 .. L-2.
+int pre_count(const sg_grid* g, int l) {
+    return (l > 0 && g->opt.inner_n_pre >= 0) ? g->opt.inner_n_pre : g->opt.n_pre;
+}
+int post_count(const sg_grid* g, int l) {
+    return (l > 0 && g->opt.inner_n_post >= 0) ? g->opt.inner_n_post : g->opt.n_post;
+}
 
 bool all_periodic(const sg_grid* g) {
     return g->bc[0] == SG_BC_PERIODIC && g->bc[1] == SG_BC_PERIODIC && g->bc[2] == SG_BC_PERIODIC;
@@ -413,6 +422,9 @@ sg_status check_opts(const sg_options* o) {
     if (o->tile_rows != 0 && o->tile_rows != 14 && o->tile_rows != 16)
         return fail(SG_ERR_ARG, "tile_rows must be 0, 14 or 16");
     if (o->staging != SG_STAGE_CP_ASYNC && o->staging != SG_STAGE_TMA) return fail(SG_ERR_ARG, "unknown staging");
+    if (o->use_graph < 0 || o->use_graph > 2) return fail(SG_ERR_ARG, "use_graph must be 0, 1 or 2");
+    if (o->inner_n_pre < -1 || o->inner_n_pre > 64 || o->inner_n_post < -1 || o->inner_n_post > 64)
+        return fail(SG_ERR_ARG, "inner_n_pre / inner_n_post out of range (-1 .. 64)");
     return SG_OK;
 }
 
@@ -656,8 +668,8 @@ sg_status bottom_levels(sg_grid* g, int B, const float* rhs, float* u, int nc, i
     p.chz = gc.ihz2f;
     p.order = order;
     p.s = s;
-    p.n_pre = g->opt.n_pre;
-    p.n_post = g->opt.n_post;
+    p.n_pre = pre_count(g, B);
+    p.n_post = post_count(g, B);
     p.tau = float(tau);
     p.mut1 = float(r.mut[1]);
     for (int j = 2; j <= s; ++j) {
@@ -746,7 +758,7 @@ sg_status vcycle(sg_grid* g, int L, W* u0, const W* rhs0, bool faces, bool zero0
                 continue;
             }
         }
-        if (l < L - 1) SG_TRY(smooth(l, g->opt.n_pre, true, false));            // 2c + 2d-i
+        if (l < L - 1) SG_TRY(smooth(l, pre_count(g, l), true, false));         // 2c + 2d-i
         else SG_TRY(coarse_solve<W>(g, l, R(l), cur[l], g->d_ss));              // 2c + 2e
     }
     for (int l = L - 2; l >= 1; --l) {                                          // step 3
@@ -756,7 +768,7 @@ sg_status vcycle(sg_grid* g, int L, W* u0, const W* rhs0, bool faces, bool zero0
             SG_CK(launch_prolong_correct<W>(geom(g, l, false), cur[l + 1], cur[l], g->st));
         }
         ++g->launches;
-        SG_TRY(smooth(l, g->opt.n_post, false, false));
+        SG_TRY(smooth(l, post_count(g, l), false, false));
     }
     {
         ProfScope ps(g, K_PROLONG, (2.0 + 0.125) * g->lv[0].n * sizeof(W));
@@ -868,7 +880,8 @@ void graph_key(const sg_grid* g, int L, const double* phi, const double* f, bool
                                         bits(g->opt.coarse_tau_frac), (uint64_t)g->opt.smoother,
                                         bits(g->opt.omega), (uint64_t)(g->opt.fused ? 1 : 0),
                                         (uint64_t)(g->prof ? 1 : 0), (uint64_t)(uintptr_t)g->d_sched,
-                                        (uint64_t)g->opt.tile_rows, (uint64_t)g->opt.staging};
+                                        (uint64_t)g->opt.tile_rows, (uint64_t)g->opt.staging,
+                                        (uint64_t)(int64_t)g->opt.inner_n_pre, (uint64_t)(int64_t)g->opt.inner_n_post};
     std::memcpy(key, k, sizeof(k));
 }
 
@@ -916,7 +929,7 @@ long long stage_updates_per_cycle(const sg_grid* g, int L) {
     long long su = 0;
     const int per_relax = g->opt.smoother == SG_SMOOTH_GSRB ? 1 : g->opt.s_smooth;   // a sweep updates a cell once
     for (int l = 0; l < L - 1; ++l)
-        su += (long long)g->lv[l].n * (g->opt.n_pre + g->opt.n_post) * per_relax;
+        su += (long long)g->lv[l].n * (pre_count(g, l) + post_count(g, l)) * per_relax;
     return su;
 }
 
@@ -1239,7 +1252,7 @@ void read_device_loop(sg_grid* g, SolveState& S, const DeviceLoop& d, long long 
 // cycle can be captured and no per-kernel profile is being taken (the
 // profile's event records cannot sit inside a conditional body).
 bool use_device_loop(const sg_grid* g, int L) {
-    return cycle_graphable(g, L) && !g->prof && g->dloop != nullptr;
+    return g->opt.use_graph == 1 && cycle_graphable(g, L) && !g->prof && g->dloop != nullptr;
 }
 
 void drop_solve_graph(sg_grid* g) {
@@ -1391,6 +1404,8 @@ sg_status sg_default_options(sg_options* o) {
     o->omega = 1.0;
     o->max_residual_tol = 0.0;
     o->tile_rows = 0;
+    o->inner_n_pre = -1;
+    o->inner_n_post = -1;
     o->staging = SG_STAGE_CP_ASYNC;
     return SG_OK;
 }
@@ -1555,6 +1570,13 @@ sg_status sg_plan_stage_coefficients(int order, int s, double* mu, double* nu, d
         if (gt) gt[j] = r.gt[j];
     }
     if (tau_max_over_dtpar) *tau_max_over_dtpar = r.tau_over_dtpar;
+    return SG_OK;
+}
+
+sg_status sg_measure_fp64_rate(double* tflops, double* ms) {
+    g_err.clear();
+    if (!tflops) return fail(SG_ERR_ARG, "NULL tflops");
+    SG_CK(probe_fp64_rate(tflops, ms));
     return SG_OK;
 }
 
@@ -1828,7 +1850,7 @@ sg_status sg_autotune(sg_grid* g, int levels, int keep_order, sg_tune_entry* tab
     const int L = levels == 0 ? g->max_levels : levels;
     if (L < 2) return fail(SG_ERR_ARG, "autotuning needs a multigrid hierarchy (levels >= 2)");
     const sg_options saved = g->opt;
-    struct Cand { int order, s, fused; double c; int pre, post, rows; };
+    struct Cand { int order, s, fused; double c; int pre, post, rows, ipre, ipost; };
     std::vector<Cand> cands;
     // more smoothing per cycle trades the cycle's fixed work (update,
     // transfers, coarsest levels) against fewer cycles
@@ -1841,14 +1863,17 @@ sg_status sg_autotune(sg_grid* g, int levels, int keep_order, sg_tune_entry* tab
             const double* cs = order == 1 ? cs1 : cs2;
             for (int ic = 0; ic < 3; ++ic)
                 for (int fz = 0; fz <= (g->precision == SG_MIXED ? 1 : 0); ++fz)
-                    for (const auto& pc : counts) {
-                        if (fz && s <= 3 && !g->twod) {          // the tile shapes of the fused s = 2, 3 kernel
-                            cands.push_back({order, s, fz, cs[ic], pc[0], pc[1], 14});
-                            cands.push_back({order, s, fz, cs[ic], pc[0], pc[1], 16});
-                        } else {
-                            cands.push_back({order, s, fz, cs[ic], pc[0], pc[1], 0});
+                    for (const auto& pc : counts)
+                        for (int in = 0; in < 2; ++in) {      // inner levels: the same counts, or (2, 1)
+                            const int ip = in ? 2 : -1, iq = in ? 1 : -1;
+                            if (in && pc[0] == 2 && pc[1] == 1) continue;
+                            if (fz && s <= 3 && !g->twod) {      // the tile shapes of the fused s = 2, 3 kernel
+                                cands.push_back({order, s, fz, cs[ic], pc[0], pc[1], 14, ip, iq});
+                                cands.push_back({order, s, fz, cs[ic], pc[0], pc[1], 16, ip, iq});
+                            } else {
+                                cands.push_back({order, s, fz, cs[ic], pc[0], pc[1], 0, ip, iq});
+                            }
                         }
-                    }
         }
     }
     double best = 1e300;
@@ -1863,6 +1888,8 @@ sg_status sg_autotune(sg_grid* g, int levels, int keep_order, sg_tune_entry* tab
         g->opt.n_pre = c.pre;
         g->opt.n_post = c.post;
         g->opt.tile_rows = c.rows;
+        g->opt.inner_n_pre = c.ipre;
+        g->opt.inner_n_post = c.ipost;
         g->opt.smoother = SG_SMOOTH_RKL;
         // Time 2 and 6 cycles (after a capture / warm-up run) and take the
         // difference, so the per-solve set-up cost drops out of the score.
@@ -1887,7 +1914,8 @@ sg_status sg_autotune(sg_grid* g, int levels, int keep_order, sg_tune_entry* tab
         factor = std::max(factor, top);
         const double mpc = (info6.elapsed_ms - info2.elapsed_ms) / 4.0;
         const double score = (factor > 0 && factor < 1) ? mpc / -std::log10(factor) : 1e300;
-        if (table && tried < cap) table[tried] = {c.order, c.s, c.fused, c.c, mpc, factor, score, c.pre, c.post, c.rows};
+        if (table && tried < cap)
+            table[tried] = {c.order, c.s, c.fused, c.c, mpc, factor, score, c.pre, c.post, c.rows, c.ipre, c.ipost};
         (void)info2;
         ++tried;
         if (score < best) {

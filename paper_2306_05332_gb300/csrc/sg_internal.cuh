@@ -121,6 +121,10 @@ cudaError_t launch_sub_mean_f64(double* x, long long n, const Reduced* red, cuda
 cudaError_t launch_sum_partials_f64(const double* x, long long n, Partial* partials,
                                     int* nblocks_out, cudaStream_t st);
 
+// ---- FP64 throughput probe (kernels_probe.cu) -------------------------------
+// TFLOP/s of FP64 FMA chains on every SM of the current device (2 flops per FMA).
+cudaError_t probe_fp64_rate(double* tflops, double* ms);
+
 // ---- the convergence loop on the device (kernels_loop.cu) -------------------
 constexpr int kLoopHistory = 256;          // entries of the residual history kept (SG_MAX_HISTORY)
 constexpr int kLoopRunning = 0, kLoopDone = 1, kLoopNotConverged = 2, kLoopNonFinite = 3;

@@ -355,3 +355,58 @@ def test_autotune_keeps_order_and_converges():
     ref, _ = O.solve(p.rho, p.lo, p.hi, p.bc, p.faces, 1.0, tol=1e-12, levels=4)
     assert rel_l2(g.potential(), ref) < 1e-7
     assert info["rel_residual"] <= 1e-9
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_device_loop_host_loop_and_direct_launches_agree(precision):
+    # use_graph = 1: the cycle loop in the solve graph's WHILE nodes; 2: one graph
+    # per cycle, the loop on the host; 0: no graph.  Same kernels, same order:
+    # identical potentials, cycle counts, histories and coarse super-step counts.
+    p = W.sphere(64)
+    out = {}
+    for mode in (1, 2, 0):
+        g = grid_for(p, precision, use_graph=mode)
+        info = g.solve(tol=1e-9, levels=4)
+        out[mode] = (g.potential(), info)
+    for mode in (2, 0):
+        np.testing.assert_array_equal(out[mode][0], out[1][0])
+        for k in ("cycles", "history", "coarse_ss", "rel_residual", "stage_cell_updates"):
+            assert out[mode][1][k] == out[1][1][k], (mode, k)
+    assert out[1][1]["rel_residual"] <= 1e-9
+
+
+def test_device_loop_reports_the_cycle_cap_and_fixed_counts():
+    p = W.sphere(32)
+    g = grid_for(p, "mixed", max_cycles=3)
+    info = g.solve(tol=1e-14, levels=4, check=False)
+    assert info["status"] == "SG_ERR_NOT_CONVERGED" and info["cycles"] == 3
+    g.set_options(max_cycles=100, fixed_cycles=5)
+    g.set_density(p.rho, 1.0)
+    info = g.solve(tol=0.0, levels=4)
+    assert info["status"] == "SG_OK" and info["cycles"] == 5 and len(info["history"]) == 6
+
+
+@pytest.mark.parametrize("inner", [(2, 1), (0, 1)])
+def test_inner_level_smoothing_counts_match_oracle(inner):
+    # levels 1 .. L-2 smooth inner_n_pre / inner_n_post times (level 0 keeps
+    # N_pre / N_post): the FP64 solve against the oracle for the same cycles
+    p = W.sphere(64)
+    kw = dict(rkl_order=2, s_smooth=3, tau_frac=0.9, n_pre=5, n_post=3, coarse_tol=0.0, coarse_max_ss=12,
+              fixed_cycles=4, inner_n_pre=inner[0], inner_n_post=inner[1])
+    g = grid_for(p, "fp64", **kw)
+    info = g.solve(tol=0.0, levels=4)
+    opts = O.Options(rkl_order=2, s_smooth=3, tau_frac=0.9, n_pre=5, n_post=3, coarse_tol=0.0, coarse_max_ss=12,
+                     inner_n_pre=inner[0], inner_n_post=inner[1])
+    ref, rinfo = O.solve(p.rho, p.lo, p.hi, p.bc, p.faces, 1.0, levels=4, opts=opts, cycles=4)
+    assert info["cycles"] == 4
+    assert rel_l2(g.potential(), ref) < 1e-12
+    np.testing.assert_allclose(info["history"], rinfo.history, rtol=1e-9, atol=1e-14)
+    # mixed precision with the cluster launch of the two coarsest levels (level
+    # B smooths with the inner counts there too): the oracle's cycle count
+    gm = grid_for(p, "mixed", rkl_order=2, s_smooth=3, tau_frac=0.9, n_pre=5, n_post=3,
+                  inner_n_pre=inner[0], inner_n_post=inner[1])
+    im = gm.solve(tol=1e-9, levels=4)
+    opts_m = O.Options(rkl_order=2, s_smooth=3, tau_frac=0.9, n_pre=5, n_post=3, inner_n_pre=inner[0],
+                       inner_n_post=inner[1])
+    _, rm = O.solve(p.rho, p.lo, p.hi, p.bc, p.faces, 1.0, tol=1e-9, levels=4, opts=opts_m)
+    assert abs(im["cycles"] - rm.cycles) <= 1
