@@ -42,9 +42,11 @@ N = 256
 LEVELS = 5
 TOL = 1e-8
 # RKL2 smoother, s = 3 (odd: the checkerboard mode keeps a factor of 0.55 per
-# super-step), tau = 0.9 tau_max, N_pre = 5, N_post = 3: the fastest measured
-# RKL2 setting on this workload whose s is odd (6 V-cycles).
-SOLVER = dict(rkl_order=2, s_smooth=3, tau_frac=0.9, n_pre=5, n_post=3, coarse_tol=1e-2, coarse_max_ss=64)
+# super-step), tau = 0.9 tau_max, N_pre = 5, N_post = 3 on the finest level and
+# 3, 2 on the levels between it and the two coarsest: the fastest measured RKL2
+# setting on this workload whose s is odd (6 V-cycles).
+SOLVER = dict(rkl_order=2, s_smooth=3, tau_frac=0.9, n_pre=5, n_post=3, inner_n_pre=3, inner_n_post=2,
+              coarse_tol=1e-2, coarse_max_ss=64)
 METRIC = "Poisson solves/s to rel. residual 1e-8 at 256^3"
 FALLBACK_HBM_GBS = 6800.0
 # FP64 instructions per cell and stage of the FP64 stage kernel, averaged over
@@ -108,20 +110,32 @@ class Ranks:
         return self._reduce(x, None if self.dist is None else self.dist.ReduceOp.SUM)
 
 
+def smoothing_count(solver, level):
+    """Super-steps per cycle on a level: N_pre + N_post on the finest, the inner
+    counts (when set, else the same) on the levels below it."""
+    pre, post = solver["n_pre"], solver["n_post"]
+    if level > 0:
+        pre = solver.get("inner_n_pre", -1) if solver.get("inner_n_pre", -1) >= 0 else pre
+        post = solver.get("inner_n_post", -1) if solver.get("inner_n_post", -1) >= 0 else post
+    return pre + post
+
+
 def unblocked_bytes_per_solve(level_cells, solver, cycles, coarse_stage_cells):
     """HBM bytes one solve would move if every kernel ran unfused, each array
     read or written once per sweep (the per-cell figures of the kernels'
     algorithmic-byte table): per cycle, on every level but the coarsest,
-    (N_pre + N_post) RKL2 super-steps of s FP32 stages (16 B/cell for the
+    N_pre + N_post RKL2 super-steps (levels below the finest: the inner
+    counts) of s FP32 stages (16 B/cell for the
     first stage, 24 for the others), the residual + restriction and the
     prolongation + correction (8.5 B/cell each), the FP64 update of the
     finest level (40 B/cell); the coarsest level's stages (16 B/cell each);
     and once per solve the start and confirmation residuals (20 + 28 B/cell).
     The fused kernels move less, so the effective rate below may pass the
     copy bandwidth; that is the point of the temporal blocking."""
-    s, n_relax = solver["s_smooth"], solver["n_pre"] + solver["n_post"]
+    s = solver["s_smooth"]
     per_cycle = 0.0
-    for n in level_cells[:-1]:
+    for l, n in enumerate(level_cells[:-1]):
+        n_relax = smoothing_count(solver, l)
         per_cycle += n * (n_relax * (16.0 + 24.0 * (s - 1)) + 8.5 + 8.5)
     per_cycle += 40.0 * level_cells[0]
     return cycles * per_cycle + 16.0 * coarse_stage_cells + 48.0 * level_cells[0]
@@ -136,7 +150,7 @@ def throughput(world, steps, max_total_ms):
 def config(world):
     return {"workload": f"sphere{N}", "grid": [N, N, N], "levels": LEVELS, "tol": TOL,
             "precision": "mixed (FP32 V-cycle; FP64 residual carried by exact recurrence, confirmed in FP64 at the end; FP64 defect correction)",
-            "smoother": "RKL2 s=3 tau=0.9 tau_max, N_pre=5, N_post=3",
+            "smoother": "RKL2 s=3 tau=0.9 tau_max, N_pre=5, N_post=3 (levels 1-2: 3, 2)",
             "coarse": "accelerated RKL1 on 16^3, coarse_tol=1e-2",
             "boundary": "Dirichlet from analytic sphere potential",
             "per_gpu_instances": 1, "instances_total": world,
@@ -547,7 +561,8 @@ def run_ours(a, world, rank, local):
                                        "fp64_instr_per_stage_cell": FP64_INSTR_PER_STAGE_CELL,
                                        "launches": st64["launches"], "ms": st64["ms"]}}
         del g64
-        g.set_options(**dict(SOLVER, rkl_order=1, s_smooth=2, tau_frac=0.75, n_pre=2, n_post=1))
+        g.set_options(**dict(SOLVER, rkl_order=1, s_smooth=2, tau_frac=0.75, n_pre=2, n_post=1, inner_n_pre=-1,
+                             inner_n_post=-1))
         step()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -555,7 +570,7 @@ def run_ours(a, world, rank, local):
         t1 = (time.perf_counter() - t0) * 1e3
         extra["rkl1_s2_smoother"] = {"solves_per_s": 1000.0 / t1, "ms": t1, "cycles": i1["cycles"]}
         # the paper's own smoother (GS-RB sweeps, N_pre = 2, N_post = 1) in the same V-cycle
-        g.set_options(**dict(SOLVER, smoother="gsrb", n_pre=2, n_post=1))
+        g.set_options(**dict(SOLVER, smoother="gsrb", n_pre=2, n_post=1, inner_n_pre=-1, inner_n_post=-1))
         step()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -667,7 +682,7 @@ def run_ours(a, world, rank, local):
     effective = None
     try:
         cells = [(N >> l) ** 3 for l in range(LEVELS)]
-        smoothing = cycles * SOLVER["s_smooth"] * (SOLVER["n_pre"] + SOLVER["n_post"]) * sum(cells[:-1])
+        smoothing = cycles * SOLVER["s_smooth"] * sum(smoothing_count(SOLVER, l) * c for l, c in enumerate(cells[:-1]))
         coarse_stage_cells = max(0.0, su - smoothing)     # the solve's count minus the smoothing stages
         ub = unblocked_bytes_per_solve(cells, SOLVER, cycles, coarse_stage_cells)
         gbps = ub / (ms_per_step * 1e-3) / 1e9

@@ -81,8 +81,13 @@ def test_unblocked_bytes_model():
     # twice, + 16 10 + (20 + 28) 8
     sys.path.insert(0, ROOT)
     import bench
-    solver = dict(bench.SOLVER, s_smooth=3, n_pre=2, n_post=1)
+    solver = dict(bench.SOLVER, s_smooth=3, n_pre=2, n_post=1, inner_n_pre=-1, inner_n_post=-1)
     assert bench.unblocked_bytes_per_solve([8, 1], solver, 2, 10) == 4528.0
+    # inner levels with their own counts: level 1 of [64, 8, 1] smooths 2 + 1 = 3
+    # times where the finest smooths 5 + 3 = 8: per cycle 64 (8 64 + 17) + 8 (3 64 + 17) + 40 64
+    solver = dict(bench.SOLVER, s_smooth=3, n_pre=5, n_post=3, inner_n_pre=2, inner_n_post=1)
+    assert bench.unblocked_bytes_per_solve([64, 8, 1], solver, 1, 0) == (64 * (8 * 64 + 17) + 8 * (3 * 64 + 17)
+                                                                          + 40 * 64 + 48 * 64)
 
 
 def test_oracle_cycle_count_matches_bench_settings():
@@ -97,5 +102,7 @@ def test_oracle_cycle_count_matches_bench_settings():
     assert g["solver"].split()[0] == f"RKL{S['rkl_order']}"
     assert int(fields["s"]) == S["s_smooth"] and float(fields["tau_frac"]) == S["tau_frac"]
     assert int(fields["n_pre"]) == S["n_pre"] and int(fields["n_post"]) == S["n_post"]
+    assert int(fields.get("inner_n_pre", -1)) == S.get("inner_n_pre", -1)
+    assert int(fields.get("inner_n_post", -1)) == S.get("inner_n_post", -1)
     assert float(fields["coarse_tol"]) == S["coarse_tol"] and int(fields["coarse_max_ss"]) == S["coarse_max_ss"]
     assert g["levels"] == bench.LEVELS and g["tol"] == bench.TOL

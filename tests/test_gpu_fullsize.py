@@ -96,7 +96,8 @@ def test_c2_fp64_two_cycles_match_oracle_vcycles(sphere256):
     phi = g.potential()
     del g
     opts = O.Options(rkl_order=solver["rkl_order"], s_smooth=solver["s_smooth"], tau_frac=solver["tau_frac"],
-                     n_pre=solver["n_pre"], n_post=solver["n_post"], coarse_tol=0.0, coarse_max_ss=12)
+                     n_pre=solver["n_pre"], n_post=solver["n_post"], inner_n_pre=solver.get("inner_n_pre", -1),
+                     inner_n_post=solver.get("inner_n_post", -1), coarse_tol=0.0, coarse_max_ss=12)
     ref, rinfo = O.solve(p.rho, p.lo, p.hi, p.bc, p.faces, 1.0, levels=5, opts=opts, cycles=2)
     assert info["cycles"] == rinfo.cycles == 2
     assert rel_l2(phi, ref) < 1e-12
