@@ -592,6 +592,8 @@ def run_ours(a, world, rank, local):
         extra["autotuned_rkl2"] = {"solves_per_s": 1000.0 / tt, "ms": tt, "cycles": itn["cycles"],
                                    "s_smooth": tuned["s_smooth"], "tau_frac": tuned["tau_frac"],
                                    "n_pre": tuned["n_pre"], "n_post": tuned["n_post"],
+                                   "inner_n_pre": tuned["inner_n_pre"], "inner_n_post": tuned["inner_n_post"],
+                                   "tile_rows": tuned["tile_rows"],
                                    "fused": tuned["fused"], "candidates": len(table)}
         # the acceleration of the solution (Sec. 3, fourth order), device buffers:
         # reads phi (8 B/cell), writes three components (24 B/cell), 12 FP64
@@ -650,8 +652,8 @@ def run_ours(a, world, rank, local):
             if n not in tuned:
                 gb.set_density(rb, 1.0)
                 opts, _table = gb.autotune(keep_order=True)
-                tuned[n] = {k: opts[k] for k in ("rkl_order", "s_smooth", "tau_frac", "n_pre", "n_post", "fused",
-                                                 "tile_rows")}
+                tuned[n] = {k: opts[k] for k in ("rkl_order", "s_smooth", "tau_frac", "n_pre", "n_post",
+                                                 "inner_n_pre", "inner_n_post", "fused", "tile_rows")}
         for gb, pb in zip(grids, probs):
             gb.set_options(**tuned[pb.shape[0]])
         for gb, rb in zip(grids, rhos):
