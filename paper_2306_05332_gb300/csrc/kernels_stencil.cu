@@ -1187,6 +1187,37 @@ __global__ void k_scale_copy(const double* src, double* dst, double scale, long 
         dst[t] = scale * src[t];
 }
 
+// Copies over the CPU-GPU link: one side is pinned host memory mapped into
+// the device address space.  16-byte accesses with four in flight per thread
+// keep enough bytes outstanding to cover the link's latency.
+template <bool SCALE>
+__global__ void __launch_bounds__(256) k_link_copy(const double2* __restrict__ src, double2* __restrict__ dst,
+                                                   double scale, long long n2) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    for (; t + 3 * stride < n2; t += 4 * stride) {
+        double2 v[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) v[i] = src[t + i * stride];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            if (SCALE) {
+                v[i].x = scale * v[i].x;
+                v[i].y = scale * v[i].y;
+            }
+            dst[t + i * stride] = v[i];
+        }
+    }
+    for (; t < n2; t += stride) {
+        double2 v = src[t];
+        if (SCALE) {
+            v.x = scale * v.x;
+            v.y = scale * v.y;
+        }
+        dst[t] = v;
+    }
+}
+
 __global__ void k_add_f32_to_f64(double* phi, const float* __restrict__ e, long long n) {
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
          t += (long long)gridDim.x * blockDim.x)
@@ -1425,6 +1456,22 @@ cudaError_t launch_subtract_mean(T* x, long long n, const Reduced* red, cudaStre
 cudaError_t launch_scale_copy(const double* src, double* dst, double scale, long long n,
                               cudaStream_t st) {
     k_scale_copy<<<grid1d(n), 256, 0, st>>>(src, dst, scale, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_link_copy(const double* src, double* dst, double scale, bool scaled, long long n,
+                             cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    const bool wide = (n % 2) == 0 && ((reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(dst)) & 15) == 0;
+    if (!wide) return launch_scale_copy(src, dst, scaled ? scale : 1.0, n, st);
+    const long long n2 = n / 2;
+    const long long b = std::min<long long>((n2 + 1023) / 1024, 2048);
+    const double2* s2 = reinterpret_cast<const double2*>(src);
+    double2* d2 = reinterpret_cast<double2*>(dst);
+    if (scaled)
+        k_link_copy<true><<<(unsigned)b, 256, 0, st>>>(s2, d2, scale, n2);
+    else
+        k_link_copy<false><<<(unsigned)b, 256, 0, st>>>(s2, d2, 1.0, n2);
     return cudaGetLastError();
 }
 

@@ -1319,17 +1319,55 @@ sg_status solve_impl(sg_grid* g, double tol, int L, double* phi, const double* f
     return solve_end(g, S, info);
 }
 
-sg_status copy_in(double* dst, const double* src, long long n, int on_device, cudaStream_t st) {
-    SG_CK(cudaMemcpyAsync(dst, src, n * sizeof(double),
-                          on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
-    if (!on_device) SG_CK(cudaStreamSynchronize(st));
+// The device address of a host buffer that is pinned and mapped into the
+// device address space (cudaHostAlloc / cudaHostRegister memory), or nullptr
+// (pageable memory): kernels then move such buffers over the CPU-GPU link
+// themselves, in one pass with any scaling, instead of a copy-engine transfer
+// followed by a device pass.
+const double* mapped_host(const double* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (a.type != cudaMemoryTypeHost || !a.devicePointer) return nullptr;
+    return static_cast<const double*>(a.devicePointer);
+}
+
+// dst (device) = scale src; src on the device or in host memory.  A host
+// source may be reused by the caller once this returns.
+sg_status load_scaled(double* dst, const double* src, long long n, int on_device, double scale, bool scaled,
+                      cudaStream_t st) {
+    if (on_device) {
+        if (scaled) SG_CK(launch_scale_copy(src, dst, scale, n, st));
+        else SG_CK(cudaMemcpyAsync(dst, src, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        return SG_OK;
+    }
+    if (const double* m = mapped_host(src)) {
+        SG_CK(launch_link_copy(m, dst, scale, scaled, n, st));
+    } else {
+        SG_CK(cudaMemcpyAsync(dst, src, n * sizeof(double), cudaMemcpyHostToDevice, st));
+        if (scaled) SG_CK(launch_scale_copy(dst, dst, scale, n, st));
+    }
+    SG_CK(cudaStreamSynchronize(st));
     return SG_OK;
 }
 
+sg_status copy_in(double* dst, const double* src, long long n, int on_device, cudaStream_t st) {
+    return load_scaled(dst, src, n, on_device, 1.0, false, st);
+}
+
 sg_status copy_out(double* dst, const double* src, long long n, int on_device, cudaStream_t st) {
-    SG_CK(cudaMemcpyAsync(dst, src, n * sizeof(double),
-                          on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
-    if (!on_device) SG_CK(cudaStreamSynchronize(st));
+    if (on_device) {
+        SG_CK(cudaMemcpyAsync(dst, src, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        return SG_OK;
+    }
+    if (const double* m = mapped_host(dst)) {
+        SG_CK(launch_link_copy(src, const_cast<double*>(m), 1.0, false, n, st));
+    } else {
+        SG_CK(cudaMemcpyAsync(dst, src, n * sizeof(double), cudaMemcpyDeviceToHost, st));
+    }
+    SG_CK(cudaStreamSynchronize(st));
     return SG_OK;
 }
 
@@ -1629,19 +1667,13 @@ sg_status sg_set_density(sg_grid* g, const double* rho, int on_device, double fo
     if (!g || !rho) return fail(SG_ERR_ARG, "NULL argument");
     if (!std::isfinite(four_pi_G)) return fail(SG_ERR_ARG, "four_pi_G must be finite");
     const long long n = g->lv[0].n;
-    if (on_device) {
-        SG_CK(launch_scale_copy(rho, g->f, four_pi_G, n, g->st));
-    } else {
-        SG_CK(cudaMemcpyAsync(g->f, rho, n * sizeof(double), cudaMemcpyHostToDevice, g->st));
-        SG_CK(launch_scale_copy(g->f, g->f, four_pi_G, n, g->st));
-    }
+    SG_TRY(load_scaled(g->f, rho, n, on_device, four_pi_G, true, g->st));
     if (all_periodic(g)) {                      // Eq. source_modification
         int nb = 0;
         SG_CK(launch_sum_partials_f64(g->f, n, g->partials, &nb, g->st));
         SG_CK(launch_finalize(g->partials, nb, g->red + 1, g->st));
         SG_CK(launch_sub_mean_f64(g->f, n, g->red + 1, g->st));
     }
-    if (!on_device) SG_CK(cudaStreamSynchronize(g->st));
     g->four_pi_G = four_pi_G;
     g->have_density = true;
     g->guess_set = false;

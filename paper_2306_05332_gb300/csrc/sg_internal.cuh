@@ -116,6 +116,10 @@ cudaError_t launch_subtract_mean(T* x, long long n, const Reduced* red, cudaStre
 
 cudaError_t launch_scale_copy(const double* src, double* dst, double scale, long long n,
                               cudaStream_t st);
+// dst = scale src (or a plain copy when !scaled) where src or dst is pinned
+// host memory mapped into the device address space.
+cudaError_t launch_link_copy(const double* src, double* dst, double scale, bool scaled, long long n,
+                             cudaStream_t st);
 cudaError_t launch_add_f32_to_f64(double* phi, const float* e, long long n, cudaStream_t st);
 cudaError_t launch_sub_mean_f64(double* x, long long n, const Reduced* red, cudaStream_t st);
 cudaError_t launch_sum_partials_f64(const double* x, long long n, Partial* partials,

@@ -410,3 +410,32 @@ def test_inner_level_smoothing_counts_match_oracle(inner):
                        inner_n_post=inner[1])
     _, rm = O.solve(p.rho, p.lo, p.hi, p.bc, p.faces, 1.0, tol=1e-9, levels=4, opts=opts_m)
     assert abs(im["cycles"] - rm.cycles) <= 1
+
+
+@pytest.mark.parametrize("shape", [(48, 40, 36), (33, 21, 17)])
+def test_pinned_host_buffers_move_over_the_link_bit_exactly(shape):
+    # pinned (mapped) host buffers are read and written by kernels over the
+    # CPU-GPU link; pageable ones by copy-engine transfers: the same bits
+    # (an odd cell count takes the scalar path)
+    sg = _sg()
+    rng = np.random.default_rng(7)
+    rho = rng.standard_normal(shape)
+    faces = W.random_faces(shape, 8)
+    out = {}
+    for kind in ("pageable", "pinned"):
+        g = sg.Grid(shape, (0, 0, 0), (1, 1, 1), (0, 0, 0), precision="mixed")
+        g.set_boundary(faces)
+        src = rho if kind == "pageable" else torch.from_numpy(rho).pin_memory()
+        g.set_density(src, 3.0)
+        info = g.solve(tol=1e-9)
+        assert info["rel_residual"] <= 1e-9
+        phi = np.empty(shape) if kind == "pageable" else torch.empty(shape, dtype=torch.float64).pin_memory()
+        g.potential(phi)
+        grav = np.empty((3,) + shape) if kind == "pageable" else torch.empty((3,) + shape, dtype=torch.float64).pin_memory()
+        g.gravity(out=grav)
+        out[kind] = (np.asarray(phi).copy(), np.asarray(grav).copy(), info["cycles"])
+        del g
+    assert out["pinned"][2] == out["pageable"][2]
+    assert np.array_equal(out["pinned"][0], out["pageable"][0])
+    assert np.array_equal(out["pinned"][1], out["pageable"][1])
+    assert np.abs(out["pinned"][0]).max() > 0
