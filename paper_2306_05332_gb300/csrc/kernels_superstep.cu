@@ -143,7 +143,11 @@ struct Lean {
     // so RKL stage 2 is a stencil of f itself and the pipeline runs stages
     // 2 .. s (pipeline stage j computes RKL stage j + 1)
     static constexpr int NS = ZERO ? S - 1 : S;
-    static constexpr int TX = 32, TY = TYV, HX = 4;
+    // tile width: 64 cells for s = 3 with a general Y0 (one CTA of 15 - 16
+    // warps per SM: less x halo per cell than two 32-wide CTAs, measured 124.6
+    // against 132.6 us per 256^3 super-step), otherwise 32 (two or three
+    // lighter CTAs per SM)
+    static constexpr int TX = (ZERO || S < 3) ? 32 : 64, TY = TYV, HX = 4;
     static constexpr int W = TX + 2 * HX;            // plane row (floats)
     static constexpr int H = TY + 2 * NS;            // plane rows
     static constexpr int Q = W / 4;                  // strips per row
@@ -172,9 +176,6 @@ struct Lean {
     __host__ __device__ static constexpr int reg_cap(int ctas) {
         return (16384 / ((((ctas * NT / 32) + 3) / 4) * 32)) / 8 * 8;
     }
-    // CTAs per SM the registers are budgeted for: two; three for the lighter
-    // Y0 = 0 variant where that leaves at least 88 registers per thread
-    static constexpr int CTAS = (ZERO && reg_cap(3) >= 88) ? 3 : 2;
     // ring depths (planes, powers of two)
     static constexpr int RY0 = ZERO ? 0 : 4;         // Y0: p, p + 1 read, p + 2 in flight
     static constexpr int RF = ZERO ? 8 : 4;          // f (Y0 = 0: read by every stage, lag up to 2 NS - 1)
@@ -189,6 +190,11 @@ struct Lean {
     static constexpr int NFLOATS = OW3 + RW3 * P;
     static constexpr int NBAR = 4;                   // TMA path: one mbarrier per plane in flight
     static constexpr size_t BYTES = size_t(NFLOATS) * sizeof(float) + NBAR * sizeof(unsigned long long);
+    // CTAs per SM the registers are budgeted for: three for the light Y0 = 0
+    // variant where that leaves at least 88 registers per thread, otherwise
+    // two where the shared memory holds two, else one
+    static constexpr int SMEM_CTAS = int((228u * 1024u) / (BYTES + 1024u));
+    static constexpr int CTAS = (ZERO && reg_cap(3) >= 88) ? 3 : (SMEM_CTAS >= 2 ? 2 : 1);
     static_assert(S == 2 || S == 3, "lean super-step covers s = 2, 3");
     static_assert(HX >= NS - 1 && HX % 4 == 0, "x halo");
     static_assert(TY % 2 == 0 && H % 2 == 0, "row pairs");
