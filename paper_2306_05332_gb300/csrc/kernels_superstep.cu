@@ -3,13 +3,14 @@
 // error equation of the mixed-precision V-cycle (homogeneous Dirichlet or
 // periodic ghosts).
 //
-// Work split.  A CTA owns a 32 x 16 (or 32 x 14) column of the level, widened by a halo
-// (4 cells in x, s cells in y), and streams it along z.  Stage j is computed
-// on the tile widened by s - j cells in strips of four x cells; every thread
-// owns ONE strip of ONE stage for the whole stream, and each stage's strips
-// fill whole warps, so every warp does one strip per phase.  In phase t,
-// stage j works on plane t - (2j - 1): it reads only planes finished in
-// earlier phases, so one barrier per phase suffices.
+// Work split.  A CTA owns a TX x TY column of the level (TX = 64 for s = 3
+// with a general Y0, 32 otherwise; TY = 16 or 14), widened by a halo (4 cells
+// in x, s cells in y), and streams it along z.  Stage j is computed on the
+// tile widened by s - j cells in strips of four x cells; every thread owns the
+// two strips of one row pair of ONE stage for the whole stream, and each
+// stage's row pairs fill whole warps.  In phase t, stage j works on plane
+// t - (2j - 1): it reads only planes finished in earlier phases, so one
+// barrier per phase suffices.
 //
 // Boundaries without branches.  For a Dirichlet axis the halo outside the box
 // is loaded as the odd reflection of the interior (cell -1-k holds -cell k,
