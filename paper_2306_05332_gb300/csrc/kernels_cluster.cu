@@ -38,7 +38,7 @@ namespace sg {
 
 namespace {
 
-constexpr int kBottomMaxNC = 8;          // CTAs per cluster (portable size)
+constexpr int kBottomMaxNC = 16;         // CTAs per cluster (16: a non-portable size, where the device allows it)
 constexpr size_t kSmemLimit = 227u * 1024u - 1024u;   // dynamic shared memory per CTA
 
 __device__ __forceinline__ float lap7f(float c, float xm, float xp, float ym, float yp, float zm, float zp, float hx,
@@ -487,11 +487,15 @@ cudaError_t bottom_configure() {
     cudaError_t e = cudaFuncSetAttribute(k_bottom_levels, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)kSmemLimit);
     if (e != cudaSuccess) return e;
+    // clusters of 16 CTAs are opt-in; where the device refuses, the plan below
+    // finds no schedulable cluster of 16 and takes 8
+    if (cudaFuncSetAttribute(k_bottom_levels, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
+        cudaGetLastError();
     g_bottom_configured = true;
     return cudaSuccess;
 }
 
-// Cluster size for level B (nx, ny, nz): the largest power of two <= 8 that
+// Cluster size for level B (nx, ny, nz): the largest power of two <= 16 that
 // cuts nz into slabs of an even number of planes, with the fields in shared
 // memory and one cluster of that size schedulable; 0 if none.
 int bottom_plan(int nx, int ny, int nz, int s, int* threads, size_t* bytes) {

@@ -1,7 +1,8 @@
 """The two coarsest levels of the FP32 V-cycle in one cluster launch against
 the level-by-level kernels (the `fused` option switches between them), on
-every boundary mix and on the cluster sizes the planner picks (8, 4 and 2
-CTAs; level B of 32^3, 16^3, 8^3, 24^3 and 24 x 16 x 12 cells; a valid
+every boundary mix and on the cluster sizes the planner picks (16 where the
+device schedules clusters of 16, else 8; 8, 4 and 2 CTAs; level B of 32^3,
+32 x 16 x 16, 16^3, 8^3, 24^3 and 24 x 16 x 12 cells; a valid
 hierarchy has an even coarsest level, so level B always splits in two), and
 the fallback to the level-by-level kernels where the coarsest level's x extent
 is not a multiple of four.
@@ -33,8 +34,9 @@ LO, HI = (0.0, -0.5, 0.25), (1.3, 0.2, 1.35)
 
 # (shape (nz, ny, nx), bc, levels): level B = levels - 2
 CASES = [
-    ((128, 128, 128), (0, 0, 0), 4),   # B 32^3, 8 CTAs of 4 planes (the benchmark's level B)
-    ((64, 64, 64), (0, 0, 0), 4),      # B 16^3, 8 CTAs
+    ((128, 128, 128), (0, 0, 0), 4),   # B 32^3, 16 CTAs of 2 planes (the benchmark's level B)
+    ((128, 64, 64), (1, 1, 1), 4),     # B 32 x 16 x 16, 16 CTAs, the z wrap between the end CTAs
+    ((64, 64, 64), (0, 0, 0), 4),      # B 16^3, 8 CTAs of 2 planes
     ((32, 32, 32), (1, 1, 1), 4),      # B 8^3, 4 CTAs, coarse mean removed
     ((48, 48, 48), (1, 0, 1), 3),      # B 24^3, 4 CTAs, 3 strips per coarse row
     ((24, 32, 48), (0, 1, 0), 3),      # B 12 x 16 x 24 (z, y, x), 2 CTAs of 6 planes
