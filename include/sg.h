@@ -18,7 +18,11 @@
  *           [nz][ny], the y faces [nz][nx], the z faces [ny][nx], sampled at the
  *           centres of the boundary faces.  Unset faces are zero.
  * Memory.   `on_device = 1`: the pointer is CUDA device memory on the grid's
- *           device; `on_device = 0`: host memory (pageable or pinned).  Caller
+ *           device; `on_device = 0`: host memory (pageable or pinned).  Pinned
+ *           host memory mapped into the device address space (cudaHostAlloc,
+ *           cudaHostRegister) is read or written by the library's kernels over
+ *           the CPU-GPU link, pageable memory by copy-engine transfers; a host
+ *           buffer must hold the whole array.  Caller
  *           buffers are borrowed for the duration of the call only.  All work is
  *           ordered on the CUDA stream given to sg_create_grid; calls that
  *           return data to a host pointer synchronise that stream, calls that
