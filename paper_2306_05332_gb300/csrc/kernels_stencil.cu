@@ -196,6 +196,60 @@ k_stage(const LevelGeom g, const CoefT<T> cf, const T* __restrict__ ym1, const T
     }
 }
 
+// The same stage in FP32 on strips of four x cells (homogeneous or periodic
+// ghosts, nx % 4 == 0, 16-byte aligned arrays): one 16-byte load per
+// neighbour row and per operand, the z neighbours carried in registers, the
+// arithmetic of k_stage cell by cell.  The block is blockDim.x strips wide, so
+// that levels 64 cells across fill whole warps.
+template <int ORDER, bool FIRST>
+__global__ void __launch_bounds__(BX * BY)
+k_stage4(const LevelGeom g, const CoefT<float> cf, const float* __restrict__ ym1, const float* ym2,
+         const float* y0, const float* z0, const float* __restrict__ rhs, float* out, float* z0_out, int kchunk) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;     // cells 4q .. 4q + 3
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int nx = g.nx, ny = g.ny, nz = g.nz;
+    if (4 * q >= nx || j >= ny) return;
+    const int i0 = 4 * q, plane = nx * ny;
+    const bool px = g.per[0] != 0, py = g.per[1] != 0, pz = g.per[2] != 0;
+    const float hx = g.ihx2f, hy = g.ihy2f, hz = g.ihz2f;
+    const int k0 = blockIdx.z * kchunk;
+    const int k1 = min(k0 + kchunk, nz);
+    int idx = k0 * plane + j * nx + i0;
+    float4 c = ld_f4(ym1 + idx);
+    float4 zm = k0 > 0 ? ld_f4(ym1 + idx - plane) : (pz ? ld_f4(ym1 + idx + (nz - 1) * plane) : neg_f4(c));
+    for (int k = k0; k < k1; ++k, idx += plane) {
+        const float4 zp = k < nz - 1 ? ld_f4(ym1 + idx + plane) : (pz ? ld_f4(ym1 + idx - (nz - 1) * plane) : neg_f4(c));
+        const float4 ym = j > 0 ? ld_f4(ym1 + idx - nx) : (py ? ld_f4(ym1 + idx + (ny - 1) * nx) : neg_f4(c));
+        const float4 yp = j < ny - 1 ? ld_f4(ym1 + idx + nx) : (py ? ld_f4(ym1 + idx - (ny - 1) * nx) : neg_f4(c));
+        const float xl = i0 > 0 ? ym1[idx - 1] : (px ? ym1[idx + nx - 1] : -c.x);
+        const float xr = i0 + 4 < nx ? ym1[idx + 4] : (px ? ym1[idx + 4 - nx] : -c.w);
+        const float4 f = ld_f4(rhs + idx);
+        float4 lf;
+        lf.x = lap7(c.x, xl, c.y, ym.x, yp.x, zm.x, zp.x, hx, hy, hz) - f.x;
+        lf.y = lap7(c.y, c.x, c.z, ym.y, yp.y, zm.y, zp.y, hx, hy, hz) - f.y;
+        lf.z = lap7(c.z, c.y, c.w, ym.z, yp.z, zm.z, zp.z, hx, hy, hz) - f.z;
+        lf.w = lap7(c.w, c.z, xr, ym.w, yp.w, zm.w, zp.w, hx, hy, hz) - f.w;
+        if (FIRST) {
+            const float4 z = make_float4(cf.tau * lf.x, cf.tau * lf.y, cf.tau * lf.z, cf.tau * lf.w);
+            *reinterpret_cast<float4*>(out + idx) =
+                make_float4(c.x + cf.mut1 * z.x, c.y + cf.mut1 * z.y, c.z + cf.mut1 * z.z, c.w + cf.mut1 * z.w);
+            if (ORDER == 2) *reinterpret_cast<float4*>(z0_out + idx) = z;
+        } else {
+            const float4 a = ld_f4(ym2 + idx);
+            float4 v = make_float4(cf.mu * c.x + cf.nu * a.x + cf.mut_tau * lf.x, cf.mu * c.y + cf.nu * a.y + cf.mut_tau * lf.y,
+                                   cf.mu * c.z + cf.nu * a.z + cf.mut_tau * lf.z, cf.mu * c.w + cf.nu * a.w + cf.mut_tau * lf.w);
+            if (ORDER == 2) {
+                const float4 b = ld_f4(y0 + idx), d = ld_f4(z0 + idx);
+                v = make_float4(v.x + cf.c0 * b.x + cf.gt * d.x, v.y + cf.c0 * b.y + cf.gt * d.y,
+                                v.z + cf.c0 * b.z + cf.gt * d.z, v.w + cf.c0 * b.w + cf.gt * d.w);
+            }
+            *reinterpret_cast<float4*>(out + idx) = v;
+        }
+        zm = c;
+        c = zp;
+    }
+}
+
 // ---------------------------------------------------------------------------
 // One colour of a red-black Gauss-Seidel / SOR sweep (Sec. 2.2.4, App. B).
 // Every cell with (i + j + k) % 2 == colour solves its own row of L u = rhs,
@@ -1296,10 +1350,31 @@ cudaError_t launch_stage(const LevelGeom& g, int order, bool first, const StageC
     CoefT<T> cf;
     cf.tau = T(c.tau); cf.mut1 = T(c.mut1); cf.mu = T(c.mu); cf.nu = T(c.nu);
     cf.mut_tau = T(c.mut_tau); cf.c0 = T(c.c0); cf.gt = T(c.gt);
+    const bool faces = has_faces(g);
+    if constexpr (std::is_same<T, float>::value) {
+        const uintptr_t al = reinterpret_cast<uintptr_t>(ym1) | reinterpret_cast<uintptr_t>(ym2) |
+                             reinterpret_cast<uintptr_t>(y0) | reinterpret_cast<uintptr_t>(z0) |
+                             reinterpret_cast<uintptr_t>(rhs) | reinterpret_cast<uintptr_t>(out) |
+                             reinterpret_cast<uintptr_t>(z0_out);
+        if (!faces && (g.nx & 3) == 0 && (al & 15) == 0) {
+            // strips: a block of 32 x 8 strips, or 16 x 16 where a row holds 16 strips or fewer
+            const int bx = g.nx / 4 <= 16 ? 16 : BX, by = BX * BY / bx;
+            const int kc = kchunk_for(g, 4 * bx, by);
+            dim3 block(bx, by, 1);
+            dim3 grid((g.nx / 4 + bx - 1) / bx, (g.ny + by - 1) / by, (g.nz + kc - 1) / kc);
+            if (order == 1) {
+                if (first) k_stage4<1, true><<<grid, block, 0, st>>>(g, cf, ym1, ym2, y0, z0, rhs, out, z0_out, kc);
+                else k_stage4<1, false><<<grid, block, 0, st>>>(g, cf, ym1, ym2, y0, z0, rhs, out, z0_out, kc);
+            } else {
+                if (first) k_stage4<2, true><<<grid, block, 0, st>>>(g, cf, ym1, ym2, y0, z0, rhs, out, z0_out, kc);
+                else k_stage4<2, false><<<grid, block, 0, st>>>(g, cf, ym1, ym2, y0, z0, rhs, out, z0_out, kc);
+            }
+            return cudaGetLastError();
+        }
+    }
     const int kc = kchunk_for(g, BX, BY);
     dim3 block(BX, BY, 1);
     dim3 grid((g.nx + BX - 1) / BX, (g.ny + BY - 1) / BY, (g.nz + kc - 1) / kc);
-    const bool faces = has_faces(g);
     if (order == 1) {
         if (first) launch_stage_f<T, 1, true>(faces, grid, block, st, g, cf, ym1, ym2, y0, z0, rhs, out, z0_out, kc);
         else launch_stage_f<T, 1, false>(faces, grid, block, st, g, cf, ym1, ym2, y0, z0, rhs, out, z0_out, kc);
