@@ -613,10 +613,12 @@ sg_status superstep_fused(sg_grid* g, int l, int order, int s, double tau_frac, 
 }
 
 // The fused super-step streams each tile through all s stages one plane at a
-// time; on small levels that serial chain of planes costs more than it saves
-// in HBM traffic (the level is L2-resident anyway), so only levels with at
-// least kFusedMinCells cells use it.
-constexpr long long kFusedMinCells = 1LL << 21;
+// time; on small levels that serial chain of planes (its pipeline fill on
+// short z chunks) costs more than it saves in HBM traffic (the level is
+// L2-resident anyway), so only levels with at least kFusedMinCells cells use
+// it: with the strip stage kernel, 128^3 runs faster as one launch per stage
+// (7.72 against 7.85 ms per 256^3 solve).
+constexpr long long kFusedMinCells = 1LL << 22;
 
 bool use_fused(const sg_grid* g, bool faces, int l) {
     return !g->twod && g->precision == SG_MIXED && g->opt.fused && !faces && g->opt.smoother == SG_SMOOTH_RKL &&

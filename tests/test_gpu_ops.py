@@ -202,7 +202,8 @@ def test_tma_staging_matches_oracle_and_copy_staging(shape, bc, order, s, zero):
 
 
 def test_tma_staging_solve_equals_copy_staging():
-    p = W.sphere(128)
+    # 176^3: level 0 (5.5 M cells) runs the fused super-step (levels of 2^22 cells and more)
+    p = W.sphere(176)
     sg = pytest.importorskip("paper_2306_05332_gb300")
     phis = {}
     for staging in ("cp_async", "tma"):
@@ -294,8 +295,9 @@ def test_mixed_solve_fused_and_unfused_agree(fused):
 
 def test_fused_option_change_takes_effect_on_the_same_grid():
     # the cycle graph is cached per option set: switching the fused super-step
-    # off and on must re-capture (level 0 of 128^3 has 2^21 cells, the fused size)
-    p = W.sphere(128)
+    # off and on must re-capture (level 0 of 176^3 has 5.5 M cells, above the
+    # fused size of 2^22 cells; the levels below run one launch per stage)
+    p = W.sphere(176)
     sg = pytest.importorskip("paper_2306_05332_gb300")
     g = sg.Grid(p.shape, p.lo, p.hi, p.bc, precision="mixed")
     g.set_boundary(p.faces)
