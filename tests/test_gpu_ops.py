@@ -78,6 +78,30 @@ def test_superstep_fp32_homogeneous(shape, bc, order, s, c, fused):
     assert relerr(out.double(), ref) < TOL32
 
 
+# The FP32 per-stage kernel on 4-cell strips (nx % 4 == 0): an odd ny with a
+# periodic x axis, a row of 33 strips (two blocks in x, the second ragged), a
+# row of 16 strips (16 x 16 blocks), a level a single strip wide; every
+# boundary kind on some axis.
+STRIP_STAGE_SHAPES = [((24, 37, 44), (1, 0, 1)), ((9, 20, 132), (0, 1, 0)), ((12, 18, 64), (1, 1, 1)),
+                      ((6, 5, 4), (0, 0, 0))]
+
+
+@pytest.mark.parametrize("shape,bc", STRIP_STAGE_SHAPES)
+@pytest.mark.parametrize("order,s,c", [(1, 3, 0.75), (2, 3, 0.9), (2, 4, 1.0)])
+def test_strip_stage_kernel_matches_oracle(shape, bc, order, s, c):
+    g, h, _ = make_grid(shape, bc, "mixed")
+    g.set_options(fused=0)
+    u, rhs = W.random_field(shape, 50), 50.0 * W.random_field(shape, 51)
+    out = torch.full(shape, float("nan"), dtype=torch.float32, device="cuda")
+    g.op_superstep(0, order, s, c, dev(u, torch.float32), dev(rhs, torch.float32), out, homogeneous=True)
+    torch.cuda.synchronize()
+    u32 = u.astype(np.float32).astype(np.float64)
+    r32 = rhs.astype(np.float32).astype(np.float64)
+    ref = O.rkl_superstep(u32, r32, h, bc, None, order, s, c)
+    assert torch.isfinite(out).all()
+    assert relerr(out.double(), ref) < TOL32
+
+
 @pytest.mark.parametrize("shape,bc", SHAPES_BC)
 def test_residual_restrict_fp64(shape, bc):
     g, h, faces = make_grid(shape, bc, "fp64")
