@@ -5,7 +5,8 @@ Workload (one "step" = one complete solve through the library's public API):
   uniform-density sphere (R = 0.25, rho = 1) centred in [-1, 1]^3 on a 256^3
   cell-centred grid, Dirichlet faces from the analytic sphere potential,
   4 pi G = 1; RKL2-smoothed V-cycle (s = 3, tau = 0.9 tau_max, N_pre = 5,
-  N_post = 3), five levels down to 16^3, accelerated-RKL coarsest solve;
+  N_post = 3 on the finest level, 3 and 2 on the levels below it), five
+  levels down to 16^3, accelerated-RKL coarsest solve;
   FP32 V-cycle inside an FP64 residual / defect-correction loop; solved to
   relative residual 1e-8.  Each step resets the density (device copy) and
   solves from phi = 0.
