@@ -434,6 +434,19 @@ sg_status sg_op_residual_restrict(sg_grid* g, int level, int dtype, int homogene
                                   const void* u, const void* rhs, void* coarse_out,
                                   double norms[2]);
 
+/* The FP64 residual r = rhs - L u of level 0 that confirms a mixed solve
+ * (Sec. 2.1; the negative of Eq. residual), with the neighbour sum formed
+ * exactly in 64-bit fixed point on a scale common to the level (u and the
+ * Dirichlet face data set its largest exponent) and rounded to FP64 once:
+ * r into r_out, its FP32 copy (significand truncated) into r32_out.  u, rhs,
+ * r_out are device FP64 arrays of level 0 and r32_out a device FP32 one
+ * (any grid precision); norms as in sg_op_residual_restrict, of the FP32 copy.
+ * Levels whose values lie beyond 2^-900 .. 2^900, or are not finite, and
+ * levels that are not strips of four cells (nx % 4 != 0, arrays not 16-byte
+ * aligned) take the FP64 stencil. */
+sg_status sg_op_residual_exact(sg_grid* g, int homogeneous, const double* u, const double* rhs,
+                               double* r_out, float* r32_out, double norms[2]);
+
 /* fine += P(coarse) (Eq. prolongation_example_3D; on a 2D grid Eq.
  * prolongation_example_2D) with coarse ghosts by the boundary rule; `level` is
  * the fine level, coarse is level + 1. */

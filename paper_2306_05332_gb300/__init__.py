@@ -119,6 +119,7 @@ _SIGS = {
     "sg_op_superstep": ([_P, _I, _I, _I, _I, _D, _I, _P, _P, _P], _I),
     "sg_op_gsrb_sweep": ([_P, _I, _I, _I, _D, _P, _P], _I),
     "sg_op_residual_restrict": ([_P, _I, _I, _I, _P, _P, _P, ctypes.POINTER(_D)], _I),
+    "sg_op_residual_exact": ([_P, _I, _P, _P, _P, _P, ctypes.POINTER(_D)], _I),
     "sg_op_prolong_correct": ([_P, _I, _I, _P, _P], _I),
     "sg_op_coarse_solve": ([_P, _I, _I, _P, _P, ctypes.POINTER(_I)], _I),
     "sg_set_profiling": ([_P, _I], _I),
@@ -391,6 +392,17 @@ class Grid:
         with _device_of(self.device):
             _check(lib().sg_op_residual_restrict(self._h, level, dt, int(homogeneous), self._op(u, level),
                                                  self._op(rhs, level), cp, norms))
+        return norms[0], norms[1]
+
+    def op_residual_exact(self, u, rhs, r_out, r32_out, homogeneous=False):
+        """FP64 residual of level 0 with the neighbour sum in exact fixed point (FP64 u, rhs, r_out; FP32 r32_out)."""
+        shape = self.level_shape(0)
+        norms = (_D * 2)()
+        with _device_of(self.device):
+            _check(lib().sg_op_residual_exact(self._h, int(homogeneous), _dev_ptr(u, 0, shape, self.device),
+                                              _dev_ptr(rhs, 0, shape, self.device),
+                                              _dev_ptr(r_out, 0, shape, self.device),
+                                              _dev_ptr(r32_out, 1, shape, self.device), norms))
         return norms[0], norms[1]
 
     def op_prolong_correct(self, level, coarse, fine):

@@ -1174,6 +1174,338 @@ k_update_residual4(const LevelGeom g, double* __restrict__ phi, const float* __r
 }
 
 // ---------------------------------------------------------------------------
+// The FP64 residual r = f - A phi that confirms a mixed solve (Sec. 2.1; the
+// standard sign), its stencil sum in exact 64-bit fixed point.
+//
+// In FP64 the seven-point sum costs about seven FP64-pipe instructions per
+// cell, which GB300 issues at 1/64 of the FP32 rate.  Here every operand of
+// the sum (phi, and the Dirichlet ghost 2 phi_face - phi) becomes an integer
+// on one scale common to the level, V = trunc(v 2^(1079 - M)), where M is the
+// largest biased exponent among the phi values and, one above their own, the
+// face values (a pre-pass finds it).  The conversion works on the IEEE fields
+// with integer operations: |V| < 2^57, ghosts stay below 2^58 and the
+// neighbour sum below 9 * 2^58, so the sum is exact in 64 bits.  Truncation
+// moves an operand by less than 2^(M - 1079), 1/16 of an FP64 ulp of the
+// largest operand: the integer sum is at least as close to the exact
+// Laplacian as an FP64 evaluation of it.  The sum is rounded to FP64 once (to
+// nearest, ties to even; integer operations again) and enters r through one
+// FP64 FMA per axis, one in all when h is the same on every axis.  A level
+// whose M lies outside [kFxMinExp, kFxMaxExp] (values beyond 2^-900 .. 2^900,
+// or not finite) takes the FP64 stencil instead.
+// ---------------------------------------------------------------------------
+constexpr unsigned kFxMinExp = 1023u - 900u;
+constexpr unsigned kFxMaxExp = 1023u + 900u;
+
+// v 2^(1079 - M), truncated toward zero, for |v| < 2^(M - 1022).
+__device__ __forceinline__ long long fx_from(double v, unsigned M) {
+    const unsigned hi = (unsigned)__double2hiint(v), lo = (unsigned)__double2loint(v);
+    const unsigned be = (hi >> 20) & 0x7ffu;
+    const unsigned long long sig = ((unsigned long long)((hi & 0xfffffu) | 0x100000u) << 32) | lo;  // 2^52 + mantissa
+    unsigned long long a;
+    // v 2^(1079 - M) = sig 2^(be - M + 4); a shift of 64 or more gives 0, the
+    // value of zero (and of subnormals, below 2^-1022)
+    asm("shr.b64 %0, %1, %2;" : "=l"(a) : "l"(sig << 4), "r"(be ? M - be : 64u));
+    const long long s = (long long)((int)hi >> 31);       // 0 or -1
+    return ((long long)a ^ s) - s;
+}
+
+// x 2^(M - 1079) rounded to the nearest FP64 value (ties to even); |x| < 2^62
+// and M within [kFxMinExp, kFxMaxExp] keep the result a normal number.
+__device__ __forceinline__ double fx_to_f64(long long x, unsigned M) {
+    if (x == 0) return 0.0;
+    const unsigned long long sgn = (unsigned long long)x & 0x8000000000000000ull;
+    unsigned long long a = sgn ? 0ull - (unsigned long long)x : (unsigned long long)x;
+    const unsigned lz = (unsigned)__clzll((long long)a);
+    a <<= lz;                                             // leading one at bit 63
+    unsigned long long m = a >> 11;                       // 53 bits, leading one at bit 52
+    const unsigned rest = (unsigned)a & 0x7ffu;
+    m += ((rest + (unsigned)(m & 1ull)) > 0x400u) ? 1ull : 0ull;   // a carry to 2^53 moves into the exponent
+    // x lies in [2^(63 - lz), 2^(64 - lz)): the value's biased exponent is
+    // M + 7 - lz, and the leading one of m adds one to the field
+    const unsigned long long field = (unsigned long long)(M + 6u - lz) << 52;
+    return __longlong_as_double((long long)(sgn | (field + m)));
+}
+
+struct I4 {
+    long long x, y, z, w;
+};
+__device__ __forceinline__ I4 fx_row(const double* p, unsigned M) {       // four cells, 16-byte aligned
+    const double2 a = ld_d2(p), b = ld_d2(p + 2);
+    return {fx_from(a.x, M), fx_from(a.y, M), fx_from(b.x, M), fx_from(b.y, M)};
+}
+__device__ __forceinline__ I4 fx_neg(const I4& c) { return {-c.x, -c.y, -c.z, -c.w}; }
+// Dirichlet ghosts 2 phi_face - c of a strip whose four face values are
+// consecutive (y and z walls); 2 phi_face on the scale of M is phi_face on
+// the scale of M - 1.
+__device__ __forceinline__ I4 fx_ghost_row(const double* face, const I4& c, unsigned M) {
+    return {fx_from(face[0], M - 1u) - c.x, fx_from(face[1], M - 1u) - c.y, fx_from(face[2], M - 1u) - c.z,
+            fx_from(face[3], M - 1u) - c.w};
+}
+
+// r = f - A phi of one cell from its integer neighbours.  Equal h: one exact
+// integer sum S, rounded to FP64 by the hardware conversion, and
+// r = f + coef S with coef = -ih2 2^(M - 1079) (a power-of-two scaling of
+// ih2, so coef S is ih2 times the rounded sum exactly); otherwise the three
+// axis sums, each rounded by fx_to_f64.
+template <bool UNIFORM>
+__device__ __forceinline__ double fx_cell(const LevelGeom& g, unsigned M, double coef, long long c, long long xm,
+                                          long long xp, long long ym, long long yp, long long zm, long long zp,
+                                          double f) {
+    if (UNIFORM) return fma(coef, __ll2double_rn(((xm + xp) + (ym + yp)) + (zm + zp) - 6 * c), f);
+    double r = fma(-g.ihx2, fx_to_f64((xm + xp) - 2 * c, M), f);
+    r = fma(-g.ihy2, fx_to_f64((ym + yp) - 2 * c, M), r);
+    return fma(-g.ihz2, fx_to_f64((zm + zp) - 2 * c, M), r);
+}
+
+// The largest biased exponent of the n FP64 values of u and, one above their
+// own, of the Dirichlet face values of g, max-combined into *out.
+__global__ void __launch_bounds__(256) k_max_exponent(const LevelGeom g, const double* __restrict__ u, long long n,
+                                                      unsigned* out) {
+    const long long tid = blockIdx.x * 256LL + threadIdx.x, stride = (long long)gridDim.x * 256LL;
+    unsigned m = 0u;
+    const uint4* v = reinterpret_cast<const uint4*>(u);   // two values per load (16-byte aligned)
+    for (long long p = tid; p < n / 2; p += stride) {
+        const uint4 w = v[p];
+        m = max(m, max(w.y & 0x7ff00000u, w.w & 0x7ff00000u));
+    }
+    if (tid == 0 && (n & 1)) m = max(m, (unsigned)__double2hiint(u[n - 1]) & 0x7ff00000u);
+    m >>= 20;
+    for (int d = 0; d < 3; ++d) {
+        if (g.per[d]) continue;
+        const long long nf = d == 0 ? (long long)g.ny * g.nz : d == 1 ? (long long)g.nx * g.nz : (long long)g.nx * g.ny;
+        for (int s = 0; s < 2; ++s) {
+            const double* fc = g.face[2 * d + s];
+            if (!fc) continue;
+            for (long long p = tid; p < nf; p += stride)
+                m = max(m, (((unsigned)__double2hiint(fc[p]) >> 20) & 0x7ffu) + 1u);
+        }
+    }
+    __shared__ unsigned s_m[8];
+    m = __reduce_max_sync(0xffffffffu, m);
+    if ((threadIdx.x & 31) == 0) s_m[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        m = threadIdx.x < 8 ? s_m[threadIdx.x] : 0u;
+        m = __reduce_max_sync(0xffffffffu, m);
+        if (threadIdx.x == 0) atomicMax(out, m);
+    }
+}
+
+// Copies into shared memory that complete asynchronously (per thread, in
+// commit groups).
+__device__ __forceinline__ void cpa_copy16(void* smem, const void* gmem) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"((unsigned)__cvta_generic_to_shared(smem)),
+                 "l"(gmem)
+                 : "memory");
+}
+__device__ __forceinline__ void cpa_copy8(void* smem, const void* gmem) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"((unsigned)__cvta_generic_to_shared(smem)),
+                 "l"(gmem)
+                 : "memory");
+}
+__device__ __forceinline__ void cpa_commit_group() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cpa_wait_but_one() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+__device__ __forceinline__ void cpa_wait_none() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// Shared memory of k_residual_fx4: raw FP64 rows of a plane (the tile's BY
+// rows and the rows j0 - 1, j0 + BY), its two x-halo cells per row and its f
+// rows, in kFxSlots slots (plane p in slot p % kFxSlots, staged two planes
+// ahead); the integer rows of two planes, with their x-halo cells.
+constexpr int kFxTW = 4 * BX;                     // cells per tile row
+constexpr int kFxSlots = 4;
+struct FxSmem {
+    double raw[kFxSlots][BY + 2][kFxTW];
+    double rawx[kFxSlots][BY][2];
+    double rawf[kFxSlots][BY][kFxTW];
+    long long irow[2][BY + 2][kFxTW + 2];         // columns kFxTW, kFxTW + 1: the x-halo cells
+};
+
+__device__ __forceinline__ I4 fx_row_smem(const double* p, unsigned M) {
+    const double2 a = *reinterpret_cast<const double2*>(p), b = *reinterpret_cast<const double2*>(p + 2);
+    return {fx_from(a.x, M), fx_from(a.y, M), fx_from(b.x, M), fx_from(b.y, M)};
+}
+__device__ __forceinline__ void fx_store_row(long long* d, const I4& v) {
+    longlong2* q = reinterpret_cast<longlong2*>(d);
+    q[0] = make_longlong2(v.x, v.y);
+    q[1] = make_longlong2(v.z, v.w);
+}
+__device__ __forceinline__ I4 fx_load_row(const long long* s) {
+    const longlong2 a = reinterpret_cast<const longlong2*>(s)[0], b = reinterpret_cast<const longlong2*>(s)[1];
+    return {a.x, a.y, b.x, b.y};
+}
+
+// The residual on strips of four x cells (nx % 4 == 0, 16-byte aligned
+// arrays): r into r64, its FP32 copy (truncated) into r32, the norms of the
+// copy into partials; *mexp is the pre-pass's M.  A block owns a tile of
+// 4 BX x BY cells and walks a z chunk.  The FP64 inputs of plane p (the
+// tile's rows, the rows above and below it, the two x-halo cells of each row,
+// the f rows) are copied into shared memory by cp.async two planes ahead; a
+// thread converts its strip of plane p + 1 (its z neighbour above, kept in
+// registers with the one below) and stores it as the integer row of that
+// plane, the first and last warps convert the rows above and below the tile,
+// and after one barrier per plane every thread reads its y neighbours from
+// the integer rows, its x neighbours from the adjacent lanes (the halo cells
+// at the tile's edges).  Cells at a wall or a periodic seam of the level take
+// their neighbours directly (ghost rule or wrapped load).
+template <bool UNIFORM, bool FACES>
+__global__ void __launch_bounds__(BX * BY, 2)
+k_residual_fx4(const LevelGeom g, const double* __restrict__ u, const double* __restrict__ rhs,
+               float* __restrict__ r32, double* __restrict__ r64, Partial* partials, int kchunk,
+               const unsigned* __restrict__ mexp) {
+    extern __shared__ __align__(16) unsigned char fx_raw_smem[];
+    FxSmem& S = *reinterpret_cast<FxSmem*>(fx_raw_smem);
+    const int lane = threadIdx.x, w = threadIdx.y, tid = w * BX + lane;
+    const int it0 = blockIdx.x * kFxTW;                 // first cell of the tile row
+    const int q = blockIdx.x * BX + lane;               // strip: cells 4q .. 4q + 3
+    const int j0 = blockIdx.y * BY, j = j0 + w;
+    const int nx = g.nx, ny = g.ny, nz = g.nz;
+    const unsigned M = *mexp;
+    const bool act = 4 * q < nx && j < ny;
+    const int i0 = 4 * q, plane = nx * ny;
+    const int k0 = blockIdx.z * kchunk;
+    const int k1 = min(k0 + kchunk, nz);
+    float sq = 0.0f, mx = 0.0f;
+    auto out = [&](int at, double ra, double rb, double rc, double rd) {
+        *reinterpret_cast<double2*>(r64 + at) = make_double2(ra, rb);
+        *reinterpret_cast<double2*>(r64 + at + 2) = make_double2(rc, rd);
+        const float4 rf = make_float4(d2f_bits(ra), d2f_bits(rb), d2f_bits(rc), d2f_bits(rd));
+        *reinterpret_cast<float4*>(r32 + at) = rf;
+        sq = fmaf(rf.x, rf.x, fmaf(rf.y, rf.y, fmaf(rf.z, rf.z, fmaf(rf.w, rf.w, sq))));
+        mx = fmaxf(mx, fmaxf(fmaxf(fabsf(rf.x), fabsf(rf.y)), fmaxf(fabsf(rf.z), fabsf(rf.w))));
+    };
+    if (M < kFxMinExp || M > kFxMaxExp) {
+        // beyond the fixed-point scale's range, or not finite: the FP64 stencil
+        if (act) {
+            int idx = k0 * plane + j * nx + i0;
+#pragma unroll 1
+            for (int k = k0; k < k1; ++k, idx += plane) {
+                double r[4];
+#pragma unroll
+                for (int t = 0; t < 4; ++t) r[t] = rhs[idx + t] - lap_at<FACES, double>(u, g, i0 + t, j, k);
+                out(idx, r[0], r[1], r[2], r[3]);
+            }
+        }
+    } else {
+        const bool px = g.per[0] != 0, py = g.per[1] != 0, pz = g.per[2] != 0;
+        const double* fxm = FACES && !px ? g.face[0] : nullptr;
+        const double* fxp = FACES && !px ? g.face[1] : nullptr;
+        const double* fym = FACES && !py ? g.face[2] : nullptr;
+        const double* fyp = FACES && !py ? g.face[3] : nullptr;
+        const double* fzm = FACES && !pz ? g.face[4] : nullptr;
+        const double* fzp = FACES && !pz ? g.face[5] : nullptr;
+        // equal h: S 2^(M - 1079) ih2 = S coef, the scale folded into one FP64 coefficient
+        const double coef = -g.ihx2 * __longlong_as_double((long long)(M - 56u) << 52);
+        // This thread's copies of a plane: two FP64 cells (16 bytes) of column
+        // cx of the rows cr, cr + 4, cr + 8 of the raw rows (row r is level
+        // row j0 - 1 + r) and of the rows cr, cr + 4 of the f rows, each only
+        // inside the level; threads of warp kFxHaloWarp copy the x-halo cells.
+        constexpr int kRowChunks = kFxTW / 2, kThreads = BX * BY;
+        static_assert(kThreads == 4 * kRowChunks && BY == 8, "the copy pattern assumes 256 threads and 8 rows");
+        constexpr int kFxHaloWarp = BY / 2;
+        const int cx = 2 * (tid % kRowChunks), cr = tid / kRowChunks;
+        const bool col_in = it0 + cx < nx;
+        const int hx_t = tid - kFxHaloWarp * BX;                                // x-halo duty: 0 .. 2 BY - 1
+        const int hx_r = hx_t >> 1, hx_side = hx_t & 1;
+        const int hx_i = hx_side ? it0 + kFxTW : it0 - 1;
+        const bool hx_in = hx_t >= 0 && hx_t < 2 * BY && j0 + hx_r < ny && hx_i >= 0 && hx_i < nx;
+        const int hx_off = (j0 + hx_r) * nx + hx_i;
+        auto stage = [&](int p) {
+            // plane 0 for p = nz on a periodic z axis; nothing beyond a z wall
+            const int ps = p < nz ? p : (pz ? 0 : -1);
+            if (ps < 0) return;
+            const int sl = p % kFxSlots;
+            const double* ub = u + (long long)ps * plane + it0 + cx;
+            const double* fb = rhs + (long long)ps * plane + it0 + cx;
+            if (col_in) {
+#pragma unroll
+                for (int t = 0; t < 3; ++t) {
+                    const int r = cr + 4 * t, jj = j0 - 1 + r;
+                    if (r < BY + 2 && jj >= 0 && jj < ny) cpa_copy16(&S.raw[sl][r][cx], ub + jj * nx);
+                }
+#pragma unroll
+                for (int t = 0; t < 2; ++t) {
+                    const int r = cr + 4 * t;
+                    if (j0 + r < ny) cpa_copy16(&S.rawf[sl][r][cx], fb + (j0 + r) * nx);
+                }
+            }
+            if (hx_in) cpa_copy8(&S.rawx[sl][hx_r][hx_side], u + (long long)ps * plane + hx_off);
+        };
+        // the integer row of plane p: own strip (the caller's value), the rows
+        // above and below the tile and the x-halo cells from the staged copies
+        auto put_rows = [&](int p, const I4& own) {
+            long long(*ir)[kFxTW + 2] = S.irow[p & 1];
+            const int sl = p % kFxSlots;
+            if (act) fx_store_row(&ir[w + 1][4 * lane], own);
+            if (w == 0 && act && j0 > 0) fx_store_row(&ir[0][4 * lane], fx_row_smem(&S.raw[sl][0][4 * lane], M));
+            if (w == BY - 1 && act && j0 + BY < ny)
+                fx_store_row(&ir[BY + 1][4 * lane], fx_row_smem(&S.raw[sl][BY + 1][4 * lane], M));
+            if (hx_in) ir[hx_r + 1][kFxTW + hx_side] = fx_from(S.rawx[sl][hx_r][hx_side], M);
+        };
+        const int idx0 = act ? j * nx + i0 : 0;
+        I4 c = {0, 0, 0, 0}, zm = {0, 0, 0, 0};
+        stage(k0);
+        cpa_commit_group();
+        if (k0 + 1 <= k1) stage(k0 + 1);
+        cpa_commit_group();
+        cpa_wait_but_one();
+        __syncthreads();
+        if (act) {
+            c = fx_row_smem(&S.raw[k0 % kFxSlots][w + 1][4 * lane], M);
+            const int at = k0 * plane + idx0;
+            zm = k0 > 0 ? fx_row(u + at - plane, M)
+                        : (pz ? fx_row(u + at + (nz - 1) * plane, M)
+                              : (fzm ? fx_ghost_row(fzm + j * nx + i0, c, M) : fx_neg(c)));
+        }
+        put_rows(k0, c);
+#pragma unroll 1
+        for (int k = k0; k < k1; ++k) {
+            if (k + 2 <= k1) stage(k + 2);
+            cpa_commit_group();
+            cpa_wait_but_one();                        // this thread's copies of plane k + 1 have landed
+            __syncthreads();                           // everyone's; the integer rows of plane k are complete
+            const int at = k * plane + idx0;
+            I4 zp = {0, 0, 0, 0};
+            if (act) {
+                zp = (k + 1 < nz || pz) ? fx_row_smem(&S.raw[(k + 1) % kFxSlots][w + 1][4 * lane], M)
+                                        : (fzp ? fx_ghost_row(fzp + j * nx + i0, c, M) : fx_neg(c));
+            }
+            long long xl = __shfl_up_sync(0xffffffffu, c.w, 1);
+            long long xr = __shfl_down_sync(0xffffffffu, c.x, 1);
+            if (act) {
+                const int sl = k % kFxSlots;
+                const long long(*ir)[kFxTW + 2] = S.irow[k & 1];
+                if (lane == 0)
+                    xl = i0 > 0 ? ir[w + 1][kFxTW]
+                                : (px ? fx_from(u[at + nx - 1], M)
+                                      : (fxm ? fx_from(fxm[k * ny + j], M - 1u) - c.x : -c.x));
+                if (i0 + 4 >= nx)
+                    xr = px ? fx_from(u[at + 4 - nx], M) : (fxp ? fx_from(fxp[k * ny + j], M - 1u) - c.w : -c.w);
+                else if (lane == BX - 1)
+                    xr = ir[w + 1][kFxTW + 1];
+                const I4 ym = j > 0 ? fx_load_row(&ir[w][4 * lane])
+                                    : (py ? fx_row(u + at + (ny - 1) * nx, M)
+                                          : (fym ? fx_ghost_row(fym + k * nx + i0, c, M) : fx_neg(c)));
+                const I4 yp = j < ny - 1 ? fx_load_row(&ir[w + 2][4 * lane])
+                                         : (py ? fx_row(u + at - (ny - 1) * nx, M)
+                                               : (fyp ? fx_ghost_row(fyp + k * nx + i0, c, M) : fx_neg(c)));
+                const double2 fa = *reinterpret_cast<const double2*>(&S.rawf[sl][w][4 * lane]);
+                const double2 fb = *reinterpret_cast<const double2*>(&S.rawf[sl][w][4 * lane + 2]);
+                out(at, fx_cell<UNIFORM>(g, M, coef, c.x, xl, c.y, ym.x, yp.x, zm.x, zp.x, fa.x),
+                    fx_cell<UNIFORM>(g, M, coef, c.y, c.x, c.z, ym.y, yp.y, zm.y, zp.y, fa.y),
+                    fx_cell<UNIFORM>(g, M, coef, c.z, c.y, c.w, ym.z, yp.z, zm.z, zp.z, fb.x),
+                    fx_cell<UNIFORM>(g, M, coef, c.w, c.z, xr, ym.w, yp.w, zm.w, zp.w, fb.y));
+            }
+            if (k + 1 < k1) put_rows(k + 1, zp);
+            zm = c;
+            c = zp;
+        }
+        cpa_wait_none();
+    }
+    const int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+    block_reduce_write<float>(sq, mx, 0.0f, partials, bid);
+}
+
+// ---------------------------------------------------------------------------
 // Small helpers.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kRedThreads) k_finalize(const Partial* __restrict__ p, int n,
@@ -1531,6 +1863,45 @@ cudaError_t launch_update_residual(const LevelGeom& g, double* phi, const float*
     if (uniform) k_update_residual<true><<<grid, block, 0, st>>>(g, phi, e, r64, r32, partials, kc);
     else k_update_residual<false><<<grid, block, 0, st>>>(g, phi, e, r64, r32, partials, kc);
     if (nblocks_out) *nblocks_out = (int)(grid.x * grid.y * grid.z);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_residual_exact(const LevelGeom& g, const double* u, const double* rhs, float* r_out,
+                                  double* r_full, Partial* partials, unsigned* scratch, int* nblocks_out,
+                                  int* nkernels, cudaStream_t st) {
+    const bool aligned = ((reinterpret_cast<uintptr_t>(u) | reinterpret_cast<uintptr_t>(rhs) |
+                           reinterpret_cast<uintptr_t>(r_out) | reinterpret_cast<uintptr_t>(r_full)) & 15) == 0;
+    if ((g.nx & 3) != 0 || !aligned || !r_out || !r_full || !scratch) {
+        if (nkernels) *nkernels = 1;
+        return launch_residual<double, float>(g, u, rhs, r_out, partials, nblocks_out, st, r_full);
+    }
+    cudaError_t e = cudaMemsetAsync(scratch, 0, sizeof(unsigned), st);
+    if (e != cudaSuccess) return e;
+    const long long n = (long long)g.nx * g.ny * g.nz;
+    k_max_exponent<<<(unsigned)std::min<long long>(kSumBlocks, (n / 2 + 255) / 256 + 1), 256, 0, st>>>(g, u, n,
+                                                                                                      scratch);
+    // as many blocks as the scalar residual launch at most (the partials buffer)
+    const long long gx = (g.nx / 4 + BX - 1) / BX, gy = (g.ny + BY - 1) / BY;
+    const long long chunks = std::min<long long>(g.nz, std::max(1LL, residual_blocks(g) / (gx * gy)));
+    const int kc = (int)((g.nz + chunks - 1) / chunks);
+    dim3 block(BX, BY, 1);
+    dim3 grid((unsigned)gx, (unsigned)gy, (unsigned)((g.nz + kc - 1) / kc));
+    const bool uniform = g.ihx2 == g.ihy2 && g.ihy2 == g.ihz2;
+    const bool faces = has_faces(g);
+    auto run = [&](auto kernel) -> cudaError_t {
+        const cudaError_t ea = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                    (int)sizeof(FxSmem));
+        if (ea != cudaSuccess) return ea;
+        kernel<<<grid, block, sizeof(FxSmem), st>>>(g, u, rhs, r_out, r_full, partials, kc, scratch);
+        return cudaSuccess;
+    };
+    if (uniform && faces) e = run(k_residual_fx4<true, true>);
+    else if (uniform) e = run(k_residual_fx4<true, false>);
+    else if (faces) e = run(k_residual_fx4<false, true>);
+    else e = run(k_residual_fx4<false, false>);
+    if (e != cudaSuccess) return e;
+    if (nblocks_out) *nblocks_out = (int)(grid.x * grid.y * grid.z);
+    if (nkernels) *nkernels = 2;
     return cudaGetLastError();
 }
 

@@ -261,6 +261,7 @@ struct sg_grid {
     int* d_sched = nullptr;
     int sched_cap = 0;
     int* d_ss = nullptr;            // coarse super-steps done (device)
+    unsigned* d_mexp = nullptr;     // the exact residual's fixed-point scale (device)
     int* host_ss = nullptr;         // pinned mirror
     sg_options opt;
     double four_pi_G = 1.0;
@@ -784,17 +785,18 @@ sg_status vcycle(sg_grid* g, int L, W* u0, const W* rhs0, bool faces, bool zero0
 
 // Residual norm of (phi, f) at level 0 into red[0]; mixed mode also writes r32.
 sg_status level0_residual(sg_grid* g, const double* phi, const double* f, bool faces) {
-    int nb = 0;
+    int nb = 0, nk = 1;
     const LevelGeom G = geom(g, 0, faces);
     {
     ProfScope ps(g, K_RES0, double(g->lv[0].n) * (g->precision == SG_MIXED ? 28.0 : 16.0));
     if (g->precision == SG_MIXED)
-        SG_CK(launch_residual<double, float>(G, phi, f, (float*)g->lv[0].rhs, g->partials, &nb, g->st, g->r64));
+        SG_CK(launch_residual_exact(G, phi, f, (float*)g->lv[0].rhs, g->r64, g->partials, g->d_mexp, &nb, &nk,
+                                    g->st));
     else
         SG_CK(launch_residual<double, double>(G, phi, f, (double*)nullptr, g->partials, &nb, g->st));
     }
     SG_CK(launch_finalize(g->partials, nb, g->red, g->st));
-    g->launches += 2;
+    g->launches += nk + 1;
     return SG_OK;
 }
 
@@ -1394,6 +1396,7 @@ void free_grid(sg_grid* g) {
     cudaFree(g->red);
     cudaFree(g->d_sched);
     cudaFree(g->d_ss);
+    cudaFree(g->d_mexp);
     cudaFree(g->dloop);
     if (g->host_loop) cudaFreeHost(g->host_loop);
     if (g->host_red) cudaFreeHost(g->host_red);
@@ -1515,6 +1518,7 @@ sg_status create_grid(int nx, int ny, int nz, const double lo[3], const double h
     ok = ok && alloc((void**)&g->partials, max_blocks * sizeof(Partial));
     ok = ok && alloc((void**)&g->red, 8 * sizeof(Reduced));
     ok = ok && alloc((void**)&g->d_ss, sizeof(int));
+    ok = ok && alloc((void**)&g->d_mexp, sizeof(unsigned));
     ok = ok && alloc((void**)&g->dloop, sizeof(DeviceLoop));
     ok = ok && cudaMallocHost((void**)&g->host_loop, sizeof(DeviceLoop)) == cudaSuccess;
     ok = ok && cudaMallocHost((void**)&g->host_red, 8 * sizeof(Reduced)) == cudaSuccess;
@@ -2061,6 +2065,26 @@ sg_status sg_op_residual_restrict(sg_grid* g, int level, int dtype, int homogene
             SG_CK(launch_residual<float, float>(G, (const float*)u, (const float*)rhs, (float*)nullptr,
                                                 g->partials, &nb, g->st));
     }
+    if (norms) {
+        SG_CK(launch_finalize(g->partials, nb, g->red + 4, g->st));
+        SG_CK(cudaMemcpyAsync(g->host_red + 4, g->red + 4, sizeof(Reduced), cudaMemcpyDeviceToHost, g->st));
+        SG_CK(cudaStreamSynchronize(g->st));
+        norms[0] = g->host_red[4].sumsq;
+        norms[1] = g->host_red[4].maxabs;
+    }
+    return SG_OK;
+}
+
+sg_status sg_op_residual_exact(sg_grid* g, int homogeneous, const double* u, const double* rhs, double* r_out,
+                               float* r32_out, double norms[2]) {
+    g_err.clear();
+    if (!g) return fail(SG_ERR_ARG, "null grid");
+    if (!u || !rhs || !r_out || !r32_out) return fail(SG_ERR_ARG, "bad pointers");
+    const bool faces = !homogeneous && g->have_faces;
+    const LevelGeom G = geom(g, 0, faces);
+    int nb = 0, nk = 1;
+    SG_CK(launch_residual_exact(G, u, rhs, r32_out, r_out, g->partials, g->d_mexp, &nb, &nk, g->st));
+    g->launches += nk;
     if (norms) {
         SG_CK(launch_finalize(g->partials, nb, g->red + 4, g->st));
         SG_CK(cudaMemcpyAsync(g->host_red + 4, g->red + 4, sizeof(Reduced), cudaMemcpyDeviceToHost, g->st));

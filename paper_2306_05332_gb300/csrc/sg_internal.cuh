@@ -106,6 +106,14 @@ cudaError_t launch_prolong_correct(const LevelGeom& fine, const T* coarse, T* fi
 
 cudaError_t launch_finalize(const Partial* partials, int n, Reduced* out, cudaStream_t st);
 
+// The FP64 residual r = rhs - A u (r into r_full, its FP32 copy into r_out,
+// the norms of the copy into partials) with the neighbour sum in exact 64-bit
+// fixed point: a pre-pass writes the scale into *scratch (one word on the
+// device), then the residual (*nkernels: the kernels launched, two; one, the
+// FP64 residual, for levels that are not strips of four cells).
+cudaError_t launch_residual_exact(const LevelGeom& g, const double* u, const double* rhs, float* r_out,
+                                  double* r_full, Partial* partials, unsigned* scratch, int* nblocks_out,
+                                  int* nkernels, cudaStream_t st);
 // phi += e (FP64) and r64 -= A_0 e (FP64 residual by recurrence, A_0 e summed
 // error-free in FP32), r32 = r64 rounded, block partials of |r32|.
 cudaError_t launch_update_residual(const LevelGeom& g, double* phi, const float* e, double* r64, float* r32,
