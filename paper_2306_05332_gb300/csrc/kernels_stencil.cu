@@ -305,6 +305,59 @@ k_gsrb(const LevelGeom g, int colour, T omega, T* u, const T* __restrict__ rhs, 
 }
 
 // ---------------------------------------------------------------------------
+// The FP64 residual r = f - A phi that confirms a mixed solve (Sec. 2.1; the
+// standard sign), its stencil sum in exact 64-bit fixed point.
+//
+// In FP64 the seven-point sum costs about seven FP64-pipe instructions per
+// cell, which GB300 issues at 1/64 of the FP32 rate.  Here every operand of
+// the sum (phi, and the Dirichlet ghost 2 phi_face - phi) becomes an integer
+// on one scale common to the level, V = trunc(v 2^(1079 - M)), where M is the
+// largest biased exponent among the phi values and, one above their own, the
+// face values (a pre-pass finds it).  The conversion works on the IEEE fields
+// with integer operations: |V| < 2^57, ghosts stay below 2^58 and the
+// neighbour sum below 9 * 2^58, so the sum is exact in 64 bits.  Truncation
+// moves an operand by less than 2^(M - 1079), 1/16 of an FP64 ulp of the
+// largest operand: the integer sum is at least as close to the exact
+// Laplacian as an FP64 evaluation of it.  The sum is rounded to FP64 once (to
+// nearest, ties to even; integer operations again) and enters r through one
+// FP64 FMA per axis, one in all when h is the same on every axis.  A level
+// whose M lies outside [kFxMinExp, kFxMaxExp] (values beyond 2^-900 .. 2^900,
+// or not finite) takes the FP64 stencil instead.
+// ---------------------------------------------------------------------------
+constexpr unsigned kFxMinExp = 1023u - 900u;
+constexpr unsigned kFxMaxExp = 1023u + 900u;
+
+// v 2^(1079 - M), truncated toward zero, for |v| < 2^(M - 1022).
+__device__ __forceinline__ long long fx_from(double v, unsigned M) {
+    const unsigned hi = (unsigned)__double2hiint(v), lo = (unsigned)__double2loint(v);
+    const unsigned be = (hi >> 20) & 0x7ffu;
+    const unsigned long long sig = ((unsigned long long)((hi & 0xfffffu) | 0x100000u) << 32) | lo;  // 2^52 + mantissa
+    unsigned long long a;
+    // v 2^(1079 - M) = sig 2^(be - M + 4); a shift of 64 or more gives 0, the
+    // value of zero (and of subnormals, below 2^-1022)
+    asm("shr.b64 %0, %1, %2;" : "=l"(a) : "l"(sig << 4), "r"(be ? M - be : 64u));
+    const long long s = (long long)((int)hi >> 31);       // 0 or -1
+    return ((long long)a ^ s) - s;
+}
+
+// x 2^(M - 1079) rounded to the nearest FP64 value (ties to even); |x| < 2^62
+// and M within [kFxMinExp, kFxMaxExp] keep the result a normal number.
+__device__ __forceinline__ double fx_to_f64(long long x, unsigned M) {
+    if (x == 0) return 0.0;
+    const unsigned long long sgn = (unsigned long long)x & 0x8000000000000000ull;
+    unsigned long long a = sgn ? 0ull - (unsigned long long)x : (unsigned long long)x;
+    const unsigned lz = (unsigned)__clzll((long long)a);
+    a <<= lz;                                             // leading one at bit 63
+    unsigned long long m = a >> 11;                       // 53 bits, leading one at bit 52
+    const unsigned rest = (unsigned)a & 0x7ffu;
+    m += ((rest + (unsigned)(m & 1ull)) > 0x400u) ? 1ull : 0ull;   // a carry to 2^53 moves into the exponent
+    // x lies in [2^(63 - lz), 2^(64 - lz)): the value's biased exponent is
+    // M + 7 - lz, and the leading one of m adds one to the field
+    const unsigned long long field = (unsigned long long)(M + 6u - lz) << 52;
+    return __longlong_as_double((long long)(sgn | (field + m)));
+}
+
+// ---------------------------------------------------------------------------
 // Acceleration g = -grad phi by the fourth-order central difference of Sec. 3
 // (Eq. 4thorder_acceleration): along each axis,
 //   g_d = -(8 (phi_{+1} - phi_{-1}) - (phi_{+2} - phi_{-2})) / (12 h_d),
@@ -321,44 +374,74 @@ k_gsrb(const LevelGeom g, int colour, T omega, T* u, const T* __restrict__ rhs, 
 constexpr int kGravHalo = 2;
 constexpr int kGravTX = BX + 2 * kGravHalo, kGravTY = BY + 2 * kGravHalo;
 
+// The value arithmetic of the kernel, FP64 or exact fixed point (the
+// confirmation residual's scale: V = trunc(phi 2^(1079 - M)), declared below):
+// from() takes a stored potential, ghost() forms 2 phi_face - mirror, and
+// comp() one component c (8 (a1 - b1) + (b2 - a2)).  In fixed point the
+// combination is exact (|V| < 2^57, ghosts below 2^58, the combination below
+// 18 * 2^58) and is rounded to FP64 once before the product with c.
+struct GravF64 {
+    using V = double;
+    __device__ __forceinline__ V from(double v) const { return v; }
+    __device__ __forceinline__ V ghost(double face, V mirror) const { return 2.0 * face - mirror; }
+    __device__ __forceinline__ double comp(double c, V a1, V b1, V a2, V b2) const {
+        return c * fma(8.0, a1 - b1, b2 - a2);
+    }
+};
+struct GravFx {
+    using V = long long;
+    unsigned M;
+    __device__ __forceinline__ V from(double v) const { return fx_from(v, M); }
+    __device__ __forceinline__ V ghost(double face, V mirror) const { return fx_from(face, M - 1u) - mirror; }
+    __device__ __forceinline__ double comp(double c, V a1, V b1, V a2, V b2) const {
+        return c * fx_to_f64(8 * (a1 - b1) + (b2 - a2), M);
+    }
+};
+
 // phi at (x, y, z) of a level with possibly out-of-range x or y (one axis at a
 // time: the halo of the star stencil has no corners): the periodic image, or
 // the reflection 2 phi_face - phi(mirror) past a Dirichlet wall (x, y >= 2 cells).
-__device__ __forceinline__ double halo_phi(const double* u, const LevelGeom& g, int x, int y, int z) {
+template <class P>
+__device__ __forceinline__ typename P::V halo_phi(const double* u, const LevelGeom& g, int x, int y, int z,
+                                                  const P& pv) {
     const int plane = g.nx * g.ny;
     if (x < 0 || x >= g.nx) {
-        if (g.per[0]) return u[z * plane + y * g.nx + (x < 0 ? x + g.nx : x - g.nx)];
+        if (g.per[0]) return pv.from(u[z * plane + y * g.nx + (x < 0 ? x + g.nx : x - g.nx)]);
         const int m = x < 0 ? -1 - x : 2 * g.nx - 1 - x;
         const double* f = x < 0 ? g.face[0] : g.face[1];
-        return 2.0 * (f ? f[z * g.ny + y] : 0.0) - u[z * plane + y * g.nx + m];
+        return pv.ghost(f ? f[z * g.ny + y] : 0.0, pv.from(u[z * plane + y * g.nx + m]));
     }
     if (y < 0 || y >= g.ny) {
-        if (g.per[1]) return u[z * plane + (y < 0 ? y + g.ny : y - g.ny) * g.nx + x];
+        if (g.per[1]) return pv.from(u[z * plane + (y < 0 ? y + g.ny : y - g.ny) * g.nx + x]);
         const int m = y < 0 ? -1 - y : 2 * g.ny - 1 - y;
         const double* f = y < 0 ? g.face[2] : g.face[3];
-        return 2.0 * (f ? f[z * g.nx + x] : 0.0) - u[z * plane + m * g.nx + x];
+        return pv.ghost(f ? f[z * g.nx + x] : 0.0, pv.from(u[z * plane + m * g.nx + x]));
     }
-    return u[z * plane + y * g.nx + x];
+    return pv.from(u[z * plane + y * g.nx + x]);
 }
 
 // phi of column (x, y) at plane q, possibly past a z wall.
-__device__ __forceinline__ double zcol_phi(const double* u, const LevelGeom& g, int col, int fz, int q) {
+template <class P>
+__device__ __forceinline__ typename P::V zcol_phi(const double* u, const LevelGeom& g, int col, int fz, int q,
+                                                  const P& pv) {
     const int plane = g.nx * g.ny;
-    if (q >= 0 && q < g.nz) return u[q * plane + col];
+    if (q >= 0 && q < g.nz) return pv.from(u[q * plane + col]);
     if (g.per[2]) {                 // nz may be 1 (a 2D grid): wrap by the remainder
         int m = q % g.nz;
         if (m < 0) m += g.nz;
-        return u[m * plane + col];
+        return pv.from(u[m * plane + col]);
     }
     const int m = q < 0 ? -1 - q : 2 * g.nz - 1 - q;
     const double* f = q < 0 ? g.face[4] : g.face[5];
-    return 2.0 * (f ? f[fz] : 0.0) - u[m * plane + col];
+    return pv.ghost(f ? f[fz] : 0.0, pv.from(u[m * plane + col]));
 }
 
-__global__ void __launch_bounds__(BX * BY)
-k_gravity_stream(const LevelGeom g, const double* __restrict__ u, double* __restrict__ out, double cx, double cy,
-                 double cz, int kchunk) {
-    __shared__ double tile[2][kGravTY][kGravTX];
+template <class P>
+__device__ __forceinline__ void gravity_body(const LevelGeom& g, const double* __restrict__ u,
+                                             double* __restrict__ out, double cx, double cy, double cz, int kchunk,
+                                             const P& pv, long long (*tile_mem)[kGravTY][kGravTX]) {
+    using V = typename P::V;
+    V(*tile)[kGravTY][kGravTX] = reinterpret_cast<V(*)[kGravTY][kGravTX]>(tile_mem);
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * BX + tx;
     const int i0 = blockIdx.x * BX, j0 = blockIdx.y * BY;
     const int i = i0 + tx, j = j0 + ty;
@@ -392,29 +475,29 @@ k_gravity_stream(const LevelGeom g, const double* __restrict__ u, double* __rest
     }
     const int col = active ? j * g.nx + i : 0;
     const int fz = col;
-    double zm2 = 0.0, zm1 = 0.0, c = 0.0, zp1 = 0.0, zp2 = 0.0;
+    V zm2 = V(0), zm1 = V(0), c = V(0), zp1 = V(0), zp2 = V(0);
     if (active) {
-        zm2 = zcol_phi(u, g, col, fz, k0 - 2);
-        zm1 = zcol_phi(u, g, col, fz, k0 - 1);
-        c = zcol_phi(u, g, col, fz, k0);
-        zp1 = zcol_phi(u, g, col, fz, k0 + 1);
+        zm2 = zcol_phi(u, g, col, fz, k0 - 2, pv);
+        zm1 = zcol_phi(u, g, col, fz, k0 - 1, pv);
+        c = zcol_phi(u, g, col, fz, k0, pv);
+        zp1 = zcol_phi(u, g, col, fz, k0 + 1, pv);
     }
     for (int k = k0; k < k1; ++k) {
-        double(*t)[kGravTX] = tile[k & 1];
+        V(*t)[kGravTX] = tile[k & 1];
         if (active) {
-            zp2 = zcol_phi(u, g, col, fz, k + 2);
+            zp2 = zcol_phi(u, g, col, fz, k + 2, pv);
             t[ty + kGravHalo][tx + kGravHalo] = c;
         } else if (i < g.nx + kGravHalo && j < g.ny + kGravHalo && (i < g.nx || j < g.ny)) {
             // a ragged tile: this position is the halo just past the level's last column or row
-            t[ty + kGravHalo][tx + kGravHalo] = halo_phi(u, g, i, j, k);
+            t[ty + kGravHalo][tx + kGravHalo] = halo_phi(u, g, i, j, k, pv);
         }
-        if (halo) t[sy][sx] = halo_phi(u, g, hx, hy, k);
+        if (halo) t[sy][sx] = halo_phi(u, g, hx, hy, k, pv);
         __syncthreads();
         if (active) {
             const int a = ty + kGravHalo, b = tx + kGravHalo;
-            const double gx = cx * fma(8.0, t[a][b + 1] - t[a][b - 1], t[a][b - 2] - t[a][b + 2]);
-            const double gy = cy * fma(8.0, t[a + 1][b] - t[a - 1][b], t[a - 2][b] - t[a + 2][b]);
-            const double gz = cz * fma(8.0, zp1 - zm1, zm2 - zp2);
+            const double gx = pv.comp(cx, t[a][b + 1], t[a][b - 1], t[a][b + 2], t[a][b - 2]);
+            const double gy = pv.comp(cy, t[a + 1][b], t[a - 1][b], t[a + 2][b], t[a - 2][b]);
+            const double gz = pv.comp(cz, zp1, zm1, zp2, zm2);
             const long long idx = (long long)k * plane + col;
             out[idx] = gx;
             out[n + idx] = gy;
@@ -425,6 +508,17 @@ k_gravity_stream(const LevelGeom g, const double* __restrict__ u, double* __rest
             zp1 = zp2;
         }
     }
+}
+
+// mexp: null for FP64 arithmetic, else the fixed-point scale's pre-pass word;
+// a scale out of range falls back to FP64 (the same for the whole launch).
+__global__ void __launch_bounds__(BX * BY)
+k_gravity_stream(const LevelGeom g, const double* __restrict__ u, double* __restrict__ out, double cx, double cy,
+                 double cz, int kchunk, const unsigned* __restrict__ mexp) {
+    __shared__ long long tile[2][kGravTY][kGravTX];
+    const unsigned M = mexp ? *mexp : 0u;
+    if (mexp && M >= kFxMinExp && M <= kFxMaxExp) gravity_body(g, u, out, cx, cy, cz, kchunk, GravFx{M}, tile);
+    else gravity_body(g, u, out, cx, cy, cz, kchunk, GravF64{}, tile);
 }
 
 // ---------------------------------------------------------------------------
@@ -1173,59 +1267,6 @@ k_update_residual4(const LevelGeom g, double* __restrict__ phi, const float* __r
     block_reduce_write<float>(sq, mx, 0.0f, partials, bid);
 }
 
-// ---------------------------------------------------------------------------
-// The FP64 residual r = f - A phi that confirms a mixed solve (Sec. 2.1; the
-// standard sign), its stencil sum in exact 64-bit fixed point.
-//
-// In FP64 the seven-point sum costs about seven FP64-pipe instructions per
-// cell, which GB300 issues at 1/64 of the FP32 rate.  Here every operand of
-// the sum (phi, and the Dirichlet ghost 2 phi_face - phi) becomes an integer
-// on one scale common to the level, V = trunc(v 2^(1079 - M)), where M is the
-// largest biased exponent among the phi values and, one above their own, the
-// face values (a pre-pass finds it).  The conversion works on the IEEE fields
-// with integer operations: |V| < 2^57, ghosts stay below 2^58 and the
-// neighbour sum below 9 * 2^58, so the sum is exact in 64 bits.  Truncation
-// moves an operand by less than 2^(M - 1079), 1/16 of an FP64 ulp of the
-// largest operand: the integer sum is at least as close to the exact
-// Laplacian as an FP64 evaluation of it.  The sum is rounded to FP64 once (to
-// nearest, ties to even; integer operations again) and enters r through one
-// FP64 FMA per axis, one in all when h is the same on every axis.  A level
-// whose M lies outside [kFxMinExp, kFxMaxExp] (values beyond 2^-900 .. 2^900,
-// or not finite) takes the FP64 stencil instead.
-// ---------------------------------------------------------------------------
-constexpr unsigned kFxMinExp = 1023u - 900u;
-constexpr unsigned kFxMaxExp = 1023u + 900u;
-
-// v 2^(1079 - M), truncated toward zero, for |v| < 2^(M - 1022).
-__device__ __forceinline__ long long fx_from(double v, unsigned M) {
-    const unsigned hi = (unsigned)__double2hiint(v), lo = (unsigned)__double2loint(v);
-    const unsigned be = (hi >> 20) & 0x7ffu;
-    const unsigned long long sig = ((unsigned long long)((hi & 0xfffffu) | 0x100000u) << 32) | lo;  // 2^52 + mantissa
-    unsigned long long a;
-    // v 2^(1079 - M) = sig 2^(be - M + 4); a shift of 64 or more gives 0, the
-    // value of zero (and of subnormals, below 2^-1022)
-    asm("shr.b64 %0, %1, %2;" : "=l"(a) : "l"(sig << 4), "r"(be ? M - be : 64u));
-    const long long s = (long long)((int)hi >> 31);       // 0 or -1
-    return ((long long)a ^ s) - s;
-}
-
-// x 2^(M - 1079) rounded to the nearest FP64 value (ties to even); |x| < 2^62
-// and M within [kFxMinExp, kFxMaxExp] keep the result a normal number.
-__device__ __forceinline__ double fx_to_f64(long long x, unsigned M) {
-    if (x == 0) return 0.0;
-    const unsigned long long sgn = (unsigned long long)x & 0x8000000000000000ull;
-    unsigned long long a = sgn ? 0ull - (unsigned long long)x : (unsigned long long)x;
-    const unsigned lz = (unsigned)__clzll((long long)a);
-    a <<= lz;                                             // leading one at bit 63
-    unsigned long long m = a >> 11;                       // 53 bits, leading one at bit 52
-    const unsigned rest = (unsigned)a & 0x7ffu;
-    m += ((rest + (unsigned)(m & 1ull)) > 0x400u) ? 1ull : 0ull;   // a carry to 2^53 moves into the exponent
-    // x lies in [2^(63 - lz), 2^(64 - lz)): the value's biased exponent is
-    // M + 7 - lz, and the leading one of m adds one to the field
-    const unsigned long long field = (unsigned long long)(M + 6u - lz) << 52;
-    return __longlong_as_double((long long)(sgn | (field + m)));
-}
-
 struct I4 {
     long long x, y, z, w;
 };
@@ -1965,11 +2006,23 @@ cudaError_t launch_gsrb(const LevelGeom& g, int colour, double omega, T* u, cons
     return cudaGetLastError();
 }
 
-cudaError_t launch_gravity(const LevelGeom& g, const double* phi, double* out, const double c[3], cudaStream_t st) {
+cudaError_t launch_gravity(const LevelGeom& g, const double* phi, double* out, const double c[3], unsigned* scratch,
+                           int* nkernels, cudaStream_t st) {
     const int kc = kchunk_for(g, BX, BY);
     dim3 block(BX, BY, 1);
     dim3 grid((g.nx + BX - 1) / BX, (g.ny + BY - 1) / BY, (g.nz + kc - 1) / kc);
-    k_gravity_stream<<<grid, block, 0, st>>>(g, phi, out, c[0], c[1], c[2], kc);
+    const unsigned* mexp = nullptr;
+    if (scratch && (reinterpret_cast<uintptr_t>(phi) & 15) == 0) {
+        // the exact fixed-point differences on the level's scale
+        cudaError_t e = cudaMemsetAsync(scratch, 0, sizeof(unsigned), st);
+        if (e != cudaSuccess) return e;
+        const long long n = (long long)g.nx * g.ny * g.nz;
+        k_max_exponent<<<(unsigned)std::min<long long>(kSumBlocks, (n / 2 + 255) / 256 + 1), 256, 0, st>>>(g, phi, n,
+                                                                                                          scratch);
+        mexp = scratch;
+    }
+    k_gravity_stream<<<grid, block, 0, st>>>(g, phi, out, c[0], c[1], c[2], kc, mexp);
+    if (nkernels) *nkernels = mexp ? 2 : 1;
     return cudaGetLastError();
 }
 

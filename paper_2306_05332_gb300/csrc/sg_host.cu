@@ -1746,11 +1746,12 @@ sg_status sg_gravity(sg_grid* g, const double* phi, double* g_out, int on_device
     }
     const Level& L0 = g->lv[0];
     const double c[3] = {-1.0 / (12.0 * L0.h[0]), -1.0 / (12.0 * L0.h[1]), -1.0 / (12.0 * L0.h[2])};
+    int nk = 1;
     {
         ProfScope ps(g, K_GRAVITY, 32.0 * n);
-        SG_CK(launch_gravity(geom(g, 0, g->have_faces), src, dst, c, g->st));
+        SG_CK(launch_gravity(geom(g, 0, g->have_faces), src, dst, c, g->d_mexp, &nk, g->st));
     }
-    ++g->launches;
+    g->launches += nk;
     if (!on_device) SG_TRY(copy_out(g_out, dst, 3 * n, 0, g->st));
     return SG_OK;
 }

@@ -5,10 +5,14 @@ host and device buffers, and at full size (256^3) on the analytic sphere
 potential.
 
 Tolerance: 1e-12 relative (max-norm of the difference over the max-norm of the
-result): both sides evaluate the same four differences in FP64, the kernel in
-the form 8 (phi_{+1} - phi_{-1}) - (phi_{+2} - phi_{-2}) times -1 / (12 h), the
-oracle in the paper's form, so they differ by rounding only.
+result).  The kernel forms 8 (phi_{+1} - phi_{-1}) - (phi_{+2} - phi_{-2})
+exactly in 64-bit fixed point on the level's scale and multiplies it by
+-1 / (12 h) in FP64, the oracle evaluates the paper's form in FP64, so they
+differ by rounding only; a second test bounds the kernel's distance from the
+exact (rational) acceleration by the fixed-point design's own error.
 """
+
+from fractions import Fraction
 
 import numpy as np
 import pytest
@@ -108,3 +112,81 @@ def test_overlapping_output_is_rejected():
     with pytest.raises(sg.SGError) as e:
         g.gravity(out=out, phi=out[1])
     assert e.value.status == 1
+
+
+def _exact_gravity(phi, h, bc, faces):
+    """g_d = -(8 (phi_{+1} - phi_{-1}) - (phi_{+2} - phi_{-2})) / (12 h_d) in rational
+    arithmetic from the FP64 inputs (ghosts: 2 phi_face - mirror past a
+    Dirichlet wall, zero faces without data; periodic images), and the
+    magnitude of the four-term combination per cell."""
+    nz, ny, nx = phi.shape
+    n = (nx, ny, nz)
+    P = {}
+
+    def val(i, j, k):
+        key = (i, j, k)
+        if key not in P:
+            P[key] = Fraction(float(phi[k, j, i]))
+        return P[key]
+
+    def at(d, idx, off):
+        p = list(idx)
+        p[d] += off
+        if 0 <= p[d] < n[d]:
+            return val(*p)
+        if bc[d] == O.PERIODIC:
+            p[d] %= n[d]
+            return val(*p)
+        side = 0 if p[d] < 0 else 1
+        m = list(idx)
+        m[d] = -1 - p[d] if side == 0 else 2 * n[d] - 1 - p[d]
+        fv = 0.0
+        if faces is not None:
+            fc = faces[2 * d + side]
+            i, j, k = idx
+            fv = fc[k, j] if d == 0 else (fc[k, i] if d == 1 else fc[j, i])
+        return 2 * Fraction(float(fv)) - val(*m)
+
+    out = np.empty((3,) + phi.shape, dtype=object)
+    mag = np.zeros((3,) + phi.shape)
+    for k in range(nz):
+        for j in range(ny):
+            for i in range(nx):
+                idx = (i, j, k)
+                for d in range(3):
+                    a1, b1, a2, b2 = at(d, idx, 1), at(d, idx, -1), at(d, idx, 2), at(d, idx, -2)
+                    comb = 8 * (a1 - b1) - (a2 - b2)
+                    out[d, k, j, i] = -comb / (12 * Fraction(h[d]))
+                    mag[d, k, j, i] = float(abs(comb))
+    return out, mag
+
+
+@pytest.mark.parametrize("shape,bc", [((10, 12, 16), (0, 0, 0)), ((8, 9, 12), (1, 0, 1))])
+def test_gravity_fixed_point_within_its_error_bound(shape, bc):
+    # the combination is exact on the level's fixed-point scale (unit
+    # 2^(M - 1079), M the largest biased exponent of phi and, one above, of the
+    # face data); a truncated operand is off by less than one unit (a ghost by
+    # two), so the combination by less than 36 units, and two FP64 roundings follow
+    g, h, fc = make_grid(shape, bc)
+    X = np.linspace(0.0, 1.0, shape[2])[None, None, :]
+    phi = 300.0 * np.cos(3.0 * X) + W.random_field(shape, 8)
+    out = torch.empty((3,) + shape, dtype=torch.float64, device="cuda")
+    g.gravity(out=out, phi=torch.tensor(phi, device="cuda"))
+    torch.cuda.synchronize()
+    got = out.cpu().numpy()
+    exact, mag = _exact_gravity(phi, h, bc, fc)
+    m = np.frexp(np.max(np.abs(phi)))[1] + 1022
+    if fc is not None:
+        for d in range(3):
+            if bc[d] != O.PERIODIC:
+                m = max(m, max(np.frexp(np.max(np.abs(fc[2 * d + s])))[1] + 1022 + 1 for s in range(2)))
+    unit = 2.0 ** (m - 1079)
+    worst = 0.0
+    for idx in np.ndindex(got.shape):
+        d = idx[0]
+        c = 1.0 / (12.0 * h[d])
+        ex = exact[idx]
+        # truncation, then the rounding of the combination and of the product
+        bound = c * 36.0 * unit + 2.0 ** -52 * (c * mag[idx] + abs(float(ex)))
+        worst = max(worst, float(abs(Fraction(float(got[idx])) - ex)) / bound)
+    assert worst <= 1.0, worst
