@@ -12,16 +12,18 @@ Workload (one "step" = one complete solve through the library's public API):
   solves from phi = 0.
 
 Metric: solves/s (whole job; N ranks solve independent instances: weak
-scaling, no collective).  Inputs (256^3 x 8 B = 134 MB per array, working set
-about 1 GB) are larger than the 129 MB L2, and L2 is also flushed between
-steps by writing 512 MB outside the timed brackets.
+scaling, no collective).  The K timed steps are independent solves of the
+workload, three in flight at a time: one grid per CUDA stream, each driven by
+its own host thread, so that the solves fill each other's idle SMs; value =
+K / the device time from the first launch to the last completion.  Inputs
+(256^3 x 8 B = 134 MB per array, working set about 1 GB per solve) are larger
+than the 129 MB L2.  The line also reports one solve at a time (`sequential`:
+L2 flushed by a 512 MB write before each solve, CUDA events per solve).
 
 End to end (`e2e`): the density comes from pinned host memory and the
-potential goes back to it through the C ABI every step.  The reported value
-drives two grids on two streams from two host threads, so that one grid's
-host<->device copies overlap the other grid's solve (independent steps of the
-same workload); the strictly sequential figure (copy in, solve, copy out) is
-reported beside it.
+potential goes back to it through the C ABI every step, the same three grids
+in flight (one grid's copies, by the copy engines, overlap the others'
+solves); the strictly sequential figure (copy in, solve, copy out) beside it.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -54,6 +56,8 @@ TOL = 1e-8
 # super-step), tau = 0.9 tau_max, N_pre = 5, N_post = 3 on the finest level and
 # 3, 2 on the levels between it and the two coarsest: the fastest measured RKL2
 # setting on this workload whose s is odd (6 V-cycles).
+# independent solves in flight: one grid per CUDA stream, one host thread each
+INFLIGHT = 3
 SOLVER = dict(rkl_order=2, s_smooth=3, tau_frac=0.9, n_pre=5, n_post=3, inner_n_pre=3, inner_n_post=2,
               coarse_tol=1e-2, coarse_max_ss=64)
 METRIC = "Poisson solves/s to rel. residual 1e-8 at 256^3"
@@ -162,8 +166,9 @@ def config(world):
             "smoother": "RKL2 s=3 tau=0.9 tau_max, N_pre=5, N_post=3 (levels 1-2: 3, 2)",
             "coarse": "accelerated RKL1 on 16^3, coarse_tol=1e-2",
             "boundary": "Dirichlet from analytic sphere potential",
-            "per_gpu_instances": 1, "instances_total": world,
-            "l2": "flushed between steps (512 MB write); inputs > L2",
+            "per_gpu_instances": INFLIGHT, "instances_total": world * INFLIGHT,
+            "l2": "inputs > L2 (134 MB per array, working set > 1 GB per solve, solves in flight); "
+                  "the sequential figure and the kernel profile flush L2 (512 MB write) before each solve",
             "parallelism": f"replicas x{world}"}
 
 
@@ -446,8 +451,70 @@ def run_ours(a, world, rank, local):
         g.set_density(rho_dev, 1.0)
         return g.solve(tol=TOL, levels=LEVELS)
 
+    # INFLIGHT independent solves of the workload at a time: one grid per
+    # stream, each driven by its own host thread (the library's calls release
+    # the interpreter lock); the solves fill each other's idle SMs (small
+    # coarse-level kernels, the one-cluster launch, the one-thread loop kernels)
+    streams = [stream] + [torch.cuda.Stream(dev) for _ in range(INFLIGHT - 1)]
+    grids = [g]
+    for st in streams[1:]:
+        gi = sg.Grid(p.shape, p.lo, p.hi, p.bc, precision="mixed", stream=st.cuda_stream)
+        gi.set_boundary(p.faces)
+        gi.set_options(**SOLVER)
+        grids.append(gi)
+
+    def run_inflight(k_total, one_step):
+        """k_total steps spread over the grids, one host thread per grid;
+        returns (device ms from the first launch to the last completion, infos)."""
+        out = [[] for _ in grids]
+
+        def worker(i):
+            for _ in range(i, k_total, len(grids)):
+                out[i].append(one_step(grids[i], i))
+
+        torch.cuda.synchronize()
+        barrier()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(streams[0])
+        for st in streams[1:]:
+            st.wait_event(ev0)
+        threads = [threading.Thread(target=worker, args=(i,)) for i in range(len(grids))]
+        for t in threads:
+            t.start()
+        for t in threads:
+            t.join()
+        for st in streams[1:]:
+            done = torch.cuda.Event()
+            done.record(st)
+            streams[0].wait_event(done)
+        ev1.record(streams[0])
+        torch.cuda.synchronize()
+        barrier()
+        return ev0.elapsed_time(ev1), [x for o in out for x in o]
+
+    def dev_step(gi, i):
+        gi.set_density(rho_dev, 1.0)
+        return gi.solve(tol=TOL, levels=LEVELS)
+
     for _ in range(max(3, a.warmup)):
+        for gi in grids:
+            dev_step(gi, 0)
+    torch.cuda.synchronize()
+    barrier()
+    # one solve at a time (L2 flushed before each, CUDA events per solve): the
+    # per-solve device time, reported beside the in-flight throughput
+    seq_ms = []
+    for k in range(max(3, min(a.steps, 10))):
+        flush.zero_()
+        s0 = torch.cuda.Event(enable_timing=True)
+        s1 = torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
         step()
+        s1.record(stream)
+        torch.cuda.synchronize()
+        seq_ms.append(s0.elapsed_time(s1))
+    seq_step = max_ranks(statistics.mean(seq_ms))
     torch.cuda.synchronize()
     barrier()
     uuid = None
@@ -459,25 +526,13 @@ def run_ours(a, world, rank, local):
     clocks = Clocks(uuid)
     clocks.start()
     time.sleep(0.5)                   # let nvidia-smi start sampling
-    e0 = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps)]
-    e1 = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps)]
-    infos = []
-    torch.cuda.synchronize()
-    barrier()
     wall0 = time.perf_counter()
     epoch0 = time.time()
-    for k in range(a.steps):
-        flush.zero_()
-        e0[k].record(stream)
-        infos.append(step())
-        e1[k].record(stream)
-    torch.cuda.synchronize()
-    barrier()
+    dev_ms, infos = run_inflight(a.steps, dev_step)
     wall = time.perf_counter() - wall0
     epoch1 = time.time()
     clk = clocks.stop(epoch0, epoch1)
-    step_ms = [e0[k].elapsed_time(e1[k]) for k in range(a.steps)]
-    total_ms = max_ranks(sum(step_ms))
+    total_ms = max_ranks(dev_ms)
     ms_per_step = total_ms / a.steps
     value = throughput(world, a.steps, total_ms)
     cycles = infos[-1]["cycles"]
@@ -487,25 +542,20 @@ def run_ours(a, world, rank, local):
 
     # ---- end to end: host (pinned) density in, host potential out ----
     # Every step copies its density from pinned host memory, solves and reads
-    # the potential back into pinned host memory through the C ABI.  Sequential:
-    # one grid, step after step.  Double-buffered (the reported value): two
-    # grids on two streams, each driven by its own host thread (the library's
-    # calls release the interpreter lock), so that one grid's host<->device
-    # copies overlap the other grid's solve; the steps are independent solves
-    # of the same workload.  No L2 flush between these steps: each moves 268 MB
-    # over the CPU-GPU link and the solve's working set is over 1 GB.
+    # the potential back into pinned host memory through the C ABI, the copies
+    # by the copy engines (the library's default), so that one grid's copies
+    # overlap the other grids' solves.  The same INFLIGHT grids and threads as
+    # the device-resident value; the strictly sequential figure (one grid:
+    # copy in, solve, copy out) beside it.  No L2 flush between these steps:
+    # each moves 268 MB over the CPU-GPU link and the solve's working set is
+    # over 1 GB.
     rho_host = torch.tensor(p.rho).pin_memory()
-    phi_hosts = [torch.empty(p.shape, dtype=torch.float64).pin_memory() for _ in range(2)]
-    stream2 = torch.cuda.Stream(dev)
-    g2 = sg.Grid(p.shape, p.lo, p.hi, p.bc, precision="mixed", stream=stream2.cuda_stream)
-    g2.set_boundary(p.faces)
-    g2.set_options(**SOLVER)
-    grids = [g, g2]
+    phi_hosts = [torch.empty(p.shape, dtype=torch.float64).pin_memory() for _ in grids]
 
-    def host_step(gi, out):
+    def host_step(gi, i):
         gi.set_density(rho_host, 1.0)
         inf = gi.solve(tol=TOL, levels=LEVELS)
-        gi.potential(out)
+        gi.potential(phi_hosts[i])
         return inf
 
     e2e_ms = []
@@ -513,27 +563,17 @@ def run_ours(a, world, rank, local):
         flush.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        info = host_step(g, phi_hosts[0])
+        info = host_step(g, 0)
         if k >= 2:
             e2e_ms.append((time.perf_counter() - t0) * 1e3)
-    seq_step = max_ranks(statistics.mean(e2e_ms))
-    host_step(g2, phi_hosts[1])                        # warm the second grid's graph
-    k2 = 2 * max(1, min(a.steps, 10))                  # steps split evenly over the two grids
-    infos2 = [None, None]
-
-    def worker(i):
-        for _ in range(k2 // 2):
-            infos2[i] = host_step(grids[i], phi_hosts[i])
-
+    seq_e2e = max_ranks(statistics.mean(e2e_ms))
+    for i, gi in enumerate(grids[1:], 1):              # warm the other grids' host path
+        host_step(gi, i)
+    k2 = max(a.steps, 2 * len(grids))
     torch.cuda.synchronize()
     barrier()
     t0 = time.perf_counter()
-    threads = [threading.Thread(target=worker, args=(i,)) for i in range(2)]
-    for t in threads:
-        t.start()
-    for t in threads:
-        t.join()
-    torch.cuda.synchronize()
+    _, infos2 = run_inflight(k2, host_step)
     e2e_step = max_ranks((time.perf_counter() - t0) * 1e3 / k2)
     for inf in infos2:
         assert inf["cycles"] == info["cycles"] and inf["rel_residual"] <= TOL, inf
@@ -541,12 +581,12 @@ def run_ours(a, world, rank, local):
     e2e = {"value": world * 1000.0 / e2e_step, "unit": "solves/s",
            "h2d_bytes_per_step": 8 * n0, "d2h_bytes_per_step": 8 * n0 + 36 * (info["cycles"] + 1),
            "ms_per_step": e2e_step, "steps": k2,
-           "pattern": "two grids on two streams, one host thread each: one grid's copies overlap the other's solve",
-           "sequential": {"value": world * 1000.0 / seq_step, "ms_per_step": seq_step,
-                          "pattern": "one grid, copy in, solve, copy out, step after step"},
+           "pattern": f"{INFLIGHT} grids in flight on {INFLIGHT} streams, one host thread each; "
+                      "host copies by the copy engines, overlapping the other grids' solves",
+           "sequential": {"value": world * 1000.0 / seq_e2e, "ms_per_step": seq_e2e,
+                          "pattern": "one grid: copy in, solve, copy out, step after step"},
            "l2": "not flushed: each step moves 268 MB over the CPU-GPU link, working set > 1 GB"}
-    grids.clear()
-    del g2
+    del grids[1:]
 
     # ---- roofline of the dominant kernel: per-kernel CUDA events in a profiled pass ----
     roof = None
@@ -767,6 +807,11 @@ def run_ours(a, world, rank, local):
                 "roofline_effective": effective,
                 "cycles_per_solve": cycles, "final_rel_residual": infos[-1]["rel_residual"],
                 "wall_s_timed_region": wall,
+                "inflight": {"solves": INFLIGHT, "pattern": f"{INFLIGHT} independent solves in flight, one grid per "
+                             "stream, one host thread each; value = all steps / device time from the first "
+                             "launch to the last completion"},
+                "sequential": {"value": world * 1000.0 / seq_step, "ms_per_step": seq_step,
+                               "pattern": "one solve at a time, L2 flushed before each, CUDA events per solve"},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                 "clocks": clk, "kernels": kernels, "extra": extra}
         print(json.dumps(line), flush=True)

@@ -71,6 +71,11 @@ typedef enum sg_staging {
     SG_STAGE_TMA = 1             /* ... by tensor-map box copies completing on an mbarrier */
 } sg_staging;
 
+typedef enum sg_host_copy {
+    SG_HOST_COPY_ENGINE = 0,     /* host buffers moved by copy-engine transfers on the grid's stream */
+    SG_HOST_COPY_KERNEL = 1      /* pinned, mapped host buffers read / written by kernels over the link */
+} sg_host_copy;
+
 typedef enum sg_precision {
     SG_FP64 = 0,                 /* every sweep in FP64 */
     SG_MIXED = 1                 /* FP32 V-cycle on the error equation inside an FP64
@@ -133,6 +138,18 @@ typedef struct sg_options {
                                their mirrors; it needs no wrap in x and y,
                                nx % 4 == 0 and an even ny (other levels stage by
                                per-strip copies)                  [SG_STAGE_CP_ASYNC]*/
+    int    host_copy;       /* sg_host_copy: how host (on_device = 0) buffers cross
+                               the CPU-GPU link.  SG_HOST_COPY_ENGINE: copy-engine
+                               transfers (the density's 4 pi G scaling then a device
+                               pass), which leave every SM to solves running on
+                               other streams.  SG_HOST_COPY_KERNEL: pinned, mapped
+                               buffers (cudaHostAlloc / cudaHostRegister) are read
+                               and written by kernels directly, the scaling in the
+                               same pass -- a little faster for one solve at a
+                               time, but those kernels hold SMs while the link
+                               transfers; pageable buffers use the copy engines
+                               either way.  The same bits in both modes
+                                                              [SG_HOST_COPY_ENGINE]*/
 } sg_options;
 
 #define SG_MAX_HISTORY 256

@@ -44,7 +44,8 @@ class Options(ctypes.Structure):
                 ("single_tau_frac", ctypes.c_double), ("fixed_cycles", ctypes.c_int),
                 ("use_graph", ctypes.c_int), ("fused", ctypes.c_int), ("smoother", ctypes.c_int),
                 ("omega", ctypes.c_double), ("max_residual_tol", ctypes.c_double), ("tile_rows", ctypes.c_int),
-                ("inner_n_pre", ctypes.c_int), ("inner_n_post", ctypes.c_int), ("staging", ctypes.c_int)]
+                ("inner_n_pre", ctypes.c_int), ("inner_n_post", ctypes.c_int), ("staging", ctypes.c_int),
+                ("host_copy", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -77,6 +78,7 @@ class KernelStat(ctypes.Structure):
 SG_KERNEL_CLASSES = 11
 SMOOTHERS = {"rkl": 0, "gsrb": 1}
 STAGINGS = {"cp_async": 0, "tma": 1}
+HOST_COPIES = {"engine": 0, "kernel": 1}     # sg_host_copy
 
 
 class TuneEntry(ctypes.Structure):
@@ -263,6 +265,8 @@ class Grid:
                 v = SMOOTHERS[v]
             if k == "staging" and isinstance(v, str):
                 v = STAGINGS[v]
+            if k == "host_copy" and isinstance(v, str):
+                v = HOST_COPIES[v]
             setattr(o, k, v)
         _check(lib().sg_set_options(self._h, ctypes.byref(o)))
         return o

@@ -423,6 +423,8 @@ sg_status check_opts(const sg_options* o) {
     if (o->tile_rows != 0 && o->tile_rows != 14 && o->tile_rows != 16)
         return fail(SG_ERR_ARG, "tile_rows must be 0, 14 or 16");
     if (o->staging != SG_STAGE_CP_ASYNC && o->staging != SG_STAGE_TMA) return fail(SG_ERR_ARG, "unknown staging");
+    if (o->host_copy != SG_HOST_COPY_ENGINE && o->host_copy != SG_HOST_COPY_KERNEL)
+        return fail(SG_ERR_ARG, "unknown host_copy");
     if (o->use_graph < 0 || o->use_graph > 2) return fail(SG_ERR_ARG, "use_graph must be 0, 1 or 2");
     if (o->inner_n_pre < -1 || o->inner_n_pre > 64 || o->inner_n_post < -1 || o->inner_n_post > 64)
         return fail(SG_ERR_ARG, "inner_n_pre / inner_n_post out of range (-1 .. 64)");
@@ -1323,12 +1325,14 @@ sg_status solve_impl(sg_grid* g, double tol, int L, double* phi, const double* f
     return solve_end(g, S, info);
 }
 
-// The device address of a host buffer that is pinned and mapped into the
-// device address space (cudaHostAlloc / cudaHostRegister memory), or nullptr
-// (pageable memory): kernels then move such buffers over the CPU-GPU link
-// themselves, in one pass with any scaling, instead of a copy-engine transfer
-// followed by a device pass.
-const double* mapped_host(const double* p) {
+// With kernels (SG_HOST_COPY_KERNEL), the device address of a host buffer that
+// is pinned and mapped into the device address space (cudaHostAlloc /
+// cudaHostRegister memory), else nullptr (pageable memory, or copy engines
+// asked for): kernels then move such buffers over the CPU-GPU link themselves,
+// in one pass with any scaling, instead of a copy-engine transfer followed by
+// a device pass.
+const double* mapped_host(const double* p, bool kernels) {
+    if (!kernels) return nullptr;
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
         cudaGetLastError();
@@ -1341,13 +1345,13 @@ const double* mapped_host(const double* p) {
 // dst (device) = scale src; src on the device or in host memory.  A host
 // source may be reused by the caller once this returns.
 sg_status load_scaled(double* dst, const double* src, long long n, int on_device, double scale, bool scaled,
-                      cudaStream_t st) {
+                      cudaStream_t st, bool kernels) {
     if (on_device) {
         if (scaled) SG_CK(launch_scale_copy(src, dst, scale, n, st));
         else SG_CK(cudaMemcpyAsync(dst, src, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
         return SG_OK;
     }
-    if (const double* m = mapped_host(src)) {
+    if (const double* m = mapped_host(src, kernels)) {
         SG_CK(launch_link_copy(m, dst, scale, scaled, n, st));
     } else {
         SG_CK(cudaMemcpyAsync(dst, src, n * sizeof(double), cudaMemcpyHostToDevice, st));
@@ -1357,16 +1361,16 @@ sg_status load_scaled(double* dst, const double* src, long long n, int on_device
     return SG_OK;
 }
 
-sg_status copy_in(double* dst, const double* src, long long n, int on_device, cudaStream_t st) {
-    return load_scaled(dst, src, n, on_device, 1.0, false, st);
+sg_status copy_in(double* dst, const double* src, long long n, int on_device, cudaStream_t st, bool kernels) {
+    return load_scaled(dst, src, n, on_device, 1.0, false, st, kernels);
 }
 
-sg_status copy_out(double* dst, const double* src, long long n, int on_device, cudaStream_t st) {
+sg_status copy_out(double* dst, const double* src, long long n, int on_device, cudaStream_t st, bool kernels) {
     if (on_device) {
         SG_CK(cudaMemcpyAsync(dst, src, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
         return SG_OK;
     }
-    if (const double* m = mapped_host(dst)) {
+    if (const double* m = mapped_host(dst, kernels)) {
         SG_CK(launch_link_copy(src, const_cast<double*>(m), 1.0, false, n, st));
     } else {
         SG_CK(cudaMemcpyAsync(dst, src, n * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -1374,6 +1378,8 @@ sg_status copy_out(double* dst, const double* src, long long n, int on_device, c
     SG_CK(cudaStreamSynchronize(st));
     return SG_OK;
 }
+
+bool kern(const sg_grid* g) { return g->opt.host_copy == SG_HOST_COPY_KERNEL; }
 
 void free_grid(sg_grid* g) {
     if (!g) return;
@@ -1450,6 +1456,7 @@ sg_status sg_default_options(sg_options* o) {
     o->inner_n_pre = -1;
     o->inner_n_post = -1;
     o->staging = SG_STAGE_CP_ASYNC;
+    o->host_copy = SG_HOST_COPY_ENGINE;
     return SG_OK;
 }
 
@@ -1660,7 +1667,7 @@ sg_status sg_set_boundary(sg_grid* g, const double* const faces[6], int on_devic
                               (long long)g->n[1] * g->n[0], (long long)g->n[1] * g->n[0]};
     for (int f = 0; f < (g->twod ? 4 : 6); ++f) {
         if (!g->faces[f]) SG_CK(cudaMalloc(&g->faces[f], fsz[f] * sizeof(double)));
-        if (faces[f]) SG_TRY(copy_in(g->faces[f], faces[f], fsz[f], on_device, g->st));
+        if (faces[f]) SG_TRY(copy_in(g->faces[f], faces[f], fsz[f], on_device, g->st, kern(g)));
         else SG_CK(cudaMemsetAsync(g->faces[f], 0, fsz[f] * sizeof(double), g->st));
     }
     g->have_faces = true;
@@ -1673,7 +1680,7 @@ sg_status sg_set_density(sg_grid* g, const double* rho, int on_device, double fo
     if (!g || !rho) return fail(SG_ERR_ARG, "NULL argument");
     if (!std::isfinite(four_pi_G)) return fail(SG_ERR_ARG, "four_pi_G must be finite");
     const long long n = g->lv[0].n;
-    SG_TRY(load_scaled(g->f, rho, n, on_device, four_pi_G, true, g->st));
+    SG_TRY(load_scaled(g->f, rho, n, on_device, four_pi_G, true, g->st, kern(g)));
     if (all_periodic(g)) {                      // Eq. source_modification
         int nb = 0;
         SG_CK(launch_sum_partials_f64(g->f, n, g->partials, &nb, g->st));
@@ -1689,7 +1696,7 @@ sg_status sg_set_density(sg_grid* g, const double* rho, int on_device, double fo
 sg_status sg_set_potential_guess(sg_grid* g, const double* phi, int on_device) {
     g_err.clear();
     if (!g || !phi) return fail(SG_ERR_ARG, "NULL argument");
-    SG_TRY(copy_in(g->phi, phi, g->lv[0].n, on_device, g->st));
+    SG_TRY(copy_in(g->phi, phi, g->lv[0].n, on_device, g->st, kern(g)));
     g->guess_set = true;
     return SG_OK;
 }
@@ -1736,7 +1743,7 @@ sg_status sg_gravity(sg_grid* g, const double* phi, double* g_out, int on_device
     const double* src = phi ? phi : g->phi;
     if (phi && !on_device) {
         if (!g->gphi) SG_CK(cudaMalloc(&g->gphi, n * sizeof(double)));
-        SG_TRY(copy_in(g->gphi, phi, n, 0, g->st));
+        SG_TRY(copy_in(g->gphi, phi, n, 0, g->st, kern(g)));
         src = g->gphi;
     }
     double* dst = g_out;
@@ -1752,7 +1759,7 @@ sg_status sg_gravity(sg_grid* g, const double* phi, double* g_out, int on_device
         SG_CK(launch_gravity(geom(g, 0, g->have_faces), src, dst, c, g->d_mexp, &nk, g->st));
     }
     g->launches += nk;
-    if (!on_device) SG_TRY(copy_out(g_out, dst, 3 * n, 0, g->st));
+    if (!on_device) SG_TRY(copy_out(g_out, dst, 3 * n, 0, g->st, kern(g)));
     return SG_OK;
 }
 
@@ -1760,7 +1767,7 @@ sg_status sg_potential(sg_grid* g, double* phi_out, int on_device) {
     g_err.clear();
     if (!g || !phi_out) return fail(SG_ERR_ARG, "NULL argument");
     if (!g->have_solution) return fail(SG_ERR_STATE, "no solution yet");
-    return copy_out(phi_out, g->phi, g->lv[0].n, on_device, g->st);
+    return copy_out(phi_out, g->phi, g->lv[0].n, on_device, g->st, kern(g));
 }
 
 sg_status sg_backward(sg_grid* g, const double* dL_dphi, double* dL_drho, int on_device, double tol,
@@ -1771,7 +1778,7 @@ sg_status sg_backward(sg_grid* g, const double* dL_dphi, double* dL_drho, int on
     const long long n = g->lv[0].n;
     if (!g->lam) SG_CK(cudaMalloc(&g->lam, n * sizeof(double)));
     if (!g->w) SG_CK(cudaMalloc(&g->w, n * sizeof(double)));
-    SG_TRY(copy_in(g->w, dL_dphi, n, on_device, g->st));
+    SG_TRY(copy_in(g->w, dL_dphi, n, on_device, g->st, kern(g)));
     if (all_periodic(g)) {
         int nb = 0;
         SG_CK(launch_sum_partials_f64(g->w, n, g->partials, &nb, g->st));
@@ -1782,7 +1789,7 @@ sg_status sg_backward(sg_grid* g, const double* dL_dphi, double* dL_drho, int on
     const sg_status st = solve_impl(g, tol, L, g->lam, g->w, false, false, info);
     if (st != SG_OK && st != SG_ERR_NOT_CONVERGED) return st;
     SG_CK(launch_scale_copy(g->lam, g->lam, g->four_pi_G, n, g->st));
-    SG_TRY(copy_out(dL_drho, g->lam, n, on_device, g->st));
+    SG_TRY(copy_out(dL_drho, g->lam, n, on_device, g->st, kern(g)));
     return st;
 }
 

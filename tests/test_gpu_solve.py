@@ -414,16 +414,19 @@ def test_inner_level_smoothing_counts_match_oracle(inner):
 
 @pytest.mark.parametrize("shape", [(48, 40, 36), (33, 21, 17)])
 def test_pinned_host_buffers_move_over_the_link_bit_exactly(shape):
-    # pinned (mapped) host buffers are read and written by kernels over the
-    # CPU-GPU link; pageable ones by copy-engine transfers: the same bits
-    # (an odd cell count takes the scalar path)
+    # pinned (mapped) host buffers moved by copy engines (the default) or read
+    # and written by kernels over the CPU-GPU link (host_copy = "kernel");
+    # pageable ones by copy-engine transfers: the same bits (an odd cell
+    # count takes the kernels' scalar path)
     sg = _sg()
     rng = np.random.default_rng(7)
     rho = rng.standard_normal(shape)
     faces = W.random_faces(shape, 8)
     out = {}
-    for kind in ("pageable", "pinned"):
+    for kind in ("pageable", "pinned", "pinned_engine"):
         g = sg.Grid(shape, (0, 0, 0), (1, 1, 1), (0, 0, 0), precision="mixed")
+        g.set_options(host_copy="kernel" if kind == "pinned" else "engine")
+        assert g.options().host_copy == (1 if kind == "pinned" else 0)
         g.set_boundary(faces)
         src = rho if kind == "pageable" else torch.from_numpy(rho).pin_memory()
         g.set_density(src, 3.0)
@@ -435,7 +438,8 @@ def test_pinned_host_buffers_move_over_the_link_bit_exactly(shape):
         g.gravity(out=grav)
         out[kind] = (np.asarray(phi).copy(), np.asarray(grav).copy(), info["cycles"])
         del g
-    assert out["pinned"][2] == out["pageable"][2]
-    assert np.array_equal(out["pinned"][0], out["pageable"][0])
-    assert np.array_equal(out["pinned"][1], out["pageable"][1])
+    for kind in ("pinned", "pinned_engine"):
+        assert out[kind][2] == out["pageable"][2]
+        assert np.array_equal(out[kind][0], out["pageable"][0])
+        assert np.array_equal(out[kind][1], out["pageable"][1])
     assert np.abs(out["pinned"][0]).max() > 0
