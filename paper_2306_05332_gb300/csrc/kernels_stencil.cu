@@ -1546,6 +1546,237 @@ k_residual_fx4(const LevelGeom g, const double* __restrict__ u, const double* __
     block_reduce_write<float>(sq, mx, 0.0f, partials, bid);
 }
 
+// Shared memory of k_gravity_fx4: the FP64 rows j0 - 2 .. j0 + BY + 1 of a
+// staged plane and its x-halo cells (it0 - 2, it0 - 1, it0 + TW, it0 + TW + 1)
+// in kGvSlots slots (plane p in slot p % kGvSlots, staged three planes
+// ahead), and the integer rows of two planes with their x-halo cells.
+constexpr int kGvSlots = 4;
+struct GvSmem {
+    double raw[kGvSlots][BY + 4][kFxTW];
+    double rawx[kGvSlots][BY][4];
+    long long irow[2][BY + 4][kFxTW + 4];
+};
+
+// The acceleration on strips of four x cells (nx % 4 == 0, 16-byte aligned phi
+// and out), every component's combination exact in fixed point on the scale of
+// *mexp (GravFx); a scale out of range falls back to FP64 per cell.  A block
+// owns a 4 BX x BY tile and walks its z chunk; the plane's rows (with two halo
+// rows on each side) and x-halo cells are copied into shared memory by
+// cp.async three planes ahead.  A thread converts its strip of plane k + 2
+// once and keeps planes k - 2 .. k + 2 of it in registers; it stores plane
+// k + 1's strip as that plane's integer row, the first two and last two warps
+// convert the halo rows, one warp the x-halo cells; after one barrier per
+// plane the y neighbours come from the integer rows, the x neighbours from
+// the adjacent lanes.  Neighbours past a Dirichlet wall are 2 phi_face - the
+// mirror cell (two ghost layers; at least two cells on such an axis), past a
+// periodic seam the wrapped cells (loaded directly).
+__global__ void __launch_bounds__(BX * BY, 2)
+k_gravity_fx4(const LevelGeom g, const double* __restrict__ u, double* __restrict__ out, double cx, double cy,
+              double cz, int kchunk, const unsigned* __restrict__ mexp) {
+    extern __shared__ __align__(16) unsigned char gv_raw_smem[];
+    GvSmem& S = *reinterpret_cast<GvSmem*>(gv_raw_smem);
+    const int lane = threadIdx.x, w = threadIdx.y, tid = w * BX + lane;
+    const int it0 = blockIdx.x * kFxTW;                 // first cell of the tile row
+    const int q = blockIdx.x * BX + lane;               // strip: cells 4q .. 4q + 3
+    const int j0 = blockIdx.y * BY, j = j0 + w;
+    const int nx = g.nx, ny = g.ny, nz = g.nz;
+    const unsigned M = *mexp;
+    const bool xin = 4 * q < nx;
+    const bool act = xin && j < ny;
+    const int i0 = 4 * q, plane = nx * ny;
+    const long long n = (long long)plane * nz;
+    const int k0 = blockIdx.z * kchunk;
+    const int k1 = min(k0 + kchunk, nz);
+    auto store = [&](long long at, const double (&r)[3][4]) {
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            *reinterpret_cast<double2*>(out + d * n + at) = make_double2(r[d][0], r[d][1]);
+            *reinterpret_cast<double2*>(out + d * n + at + 2) = make_double2(r[d][2], r[d][3]);
+        }
+    };
+    if (M < kFxMinExp || M > kFxMaxExp) {
+        // beyond the fixed-point scale's range, or not finite: FP64 per cell
+        if (act) {
+            const GravF64 pv{};
+#pragma unroll 1
+            for (int k = k0; k < k1; ++k) {
+                double r[3][4];
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    const int i = i0 + t, col = j * nx + i;
+                    r[0][t] = pv.comp(cx, halo_phi(u, g, i + 1, j, k, pv), halo_phi(u, g, i - 1, j, k, pv),
+                                      halo_phi(u, g, i + 2, j, k, pv), halo_phi(u, g, i - 2, j, k, pv));
+                    r[1][t] = pv.comp(cy, halo_phi(u, g, i, j + 1, k, pv), halo_phi(u, g, i, j - 1, k, pv),
+                                      halo_phi(u, g, i, j + 2, k, pv), halo_phi(u, g, i, j - 2, k, pv));
+                    r[2][t] = pv.comp(cz, zcol_phi(u, g, col, col, k + 1, pv), zcol_phi(u, g, col, col, k - 1, pv),
+                                      zcol_phi(u, g, col, col, k + 2, pv), zcol_phi(u, g, col, col, k - 2, pv));
+                }
+                store((long long)k * plane + j * nx + i0, r);
+            }
+        }
+        return;
+    }
+    const bool px = g.per[0] != 0, py = g.per[1] != 0, pz = g.per[2] != 0;
+    const double* fxm = !px ? g.face[0] : nullptr;
+    const double* fxp = !px ? g.face[1] : nullptr;
+    const double* fym = !py ? g.face[2] : nullptr;
+    const double* fyp = !py ? g.face[3] : nullptr;
+    const double* fzm = !pz ? g.face[4] : nullptr;
+    const double* fzp = !pz ? g.face[5] : nullptr;
+    // 2 phi_face - mirror (zero face values without data)
+    auto ghost1 = [&](const double* f, int at, long long mirror) {
+        return (f ? fx_from(f[at], M - 1u) : 0LL) - mirror;
+    };
+    auto ghost4 = [&](const double* f, int at, const I4& m) -> I4 {
+        return {ghost1(f, at, m.x), ghost1(f, at + 1, m.y), ghost1(f, at + 2, m.z), ghost1(f, at + 3, m.w)};
+    };
+    // this thread's copies of a plane: 16 bytes of column cx of the raw rows
+    // cr, cr + 4, cr + 8 (row r is level row j0 - 2 + r), inside the level;
+    // warp kGvHaloWarp copies the x-halo cells
+    constexpr int kRowChunks = kFxTW / 2;
+    static_assert(BX * BY == 4 * kRowChunks && BY == 8, "the copy pattern assumes 256 threads and 8 rows");
+    constexpr int kGvHaloWarp = BY / 2;
+    const int cx2 = 2 * (tid % kRowChunks), cr = tid / kRowChunks;
+    const bool col_in = it0 + cx2 < nx;
+    const int hx_r = lane >> 2, hx_side = lane & 3;                        // warp kGvHaloWarp: 8 rows x 4 cells
+    const int hx_i = hx_side < 2 ? it0 - 2 + hx_side : it0 + kFxTW + (hx_side - 2);
+    const bool hx_in = w == kGvHaloWarp && j0 + hx_r < ny && hx_i >= 0 && hx_i < nx;
+    const int hx_off = (j0 + hx_r) * nx + hx_i;
+    auto stage = [&](int p) {
+        const int ps = p < nz ? p : (pz ? p % nz : -1);                     // past the top: wrapped (nz may be 1), or nothing
+        if (ps < 0) return;
+        const int sl = p % kGvSlots;
+        const double* ub = u + (long long)ps * plane + it0 + cx2;
+        if (col_in) {
+#pragma unroll
+            for (int t = 0; t < 3; ++t) {
+                const int r = cr + 4 * t, jj = j0 - 2 + r;
+                if (jj >= 0 && jj < ny) cpa_copy16(&S.raw[sl][r][cx2], ub + jj * nx);
+            }
+        }
+        if (hx_in) cpa_copy8(&S.rawx[sl][hx_r][hx_side], u + (long long)ps * plane + hx_off);
+    };
+    // the integer row of plane p: own strip (the caller's value), the two halo
+    // rows on each side of the tile and the x-halo cells from the staged copies
+    auto put_rows = [&](int p, const I4& own) {
+        long long(*ir)[kFxTW + 4] = S.irow[p & 1];
+        const int sl = p % kGvSlots;
+        if (act) fx_store_row(&ir[w + 2][4 * lane], own);
+        if (xin) {
+            if (w < 2 && j0 - 2 + w >= 0)
+                fx_store_row(&ir[w][4 * lane], fx_row_smem(&S.raw[sl][w][4 * lane], M));
+            if (w >= BY - 2 && j0 + w + 2 < ny)
+                fx_store_row(&ir[w + 4][4 * lane], fx_row_smem(&S.raw[sl][w + 4][4 * lane], M));
+        }
+        if (hx_in) ir[hx_r + 2][kFxTW + hx_side] = fx_from(S.rawx[sl][hx_r][hx_side], M);
+    };
+    const int idx0 = act ? j * nx + i0 : 0;
+    // own strip at plane p straight from memory (the chunk's first planes)
+    auto own_direct = [&](int p) -> I4 {
+        if (p >= 0 && p < nz) return fx_row(u + (long long)p * plane + idx0, M);
+        if (pz) return fx_row(u + (long long)((p % nz + nz) % nz) * plane + idx0, M);
+        const int m = p < 0 ? -1 - p : 2 * nz - 1 - p;
+        return ghost4(p < 0 ? fzm : fzp, j * nx + i0, fx_row(u + (long long)m * plane + idx0, M));
+    };
+    stage(k0);
+    cpa_commit_group();
+    stage(k0 + 1);
+    cpa_commit_group();
+    if (k0 + 2 <= k1 + 1) stage(k0 + 2);
+    cpa_commit_group();
+    asm volatile("cp.async.wait_group 1;\n" ::: "memory");     // planes k0 and k0 + 1 have landed
+    __syncthreads();
+    I4 zm2 = {0, 0, 0, 0}, zm1 = zm2, c = zm2, zp1 = zm2;
+    if (act) {
+        c = fx_row_smem(&S.raw[k0 % kGvSlots][2 + w][4 * lane], M);
+        zp1 = (k0 + 1 < nz || pz) ? fx_row_smem(&S.raw[(k0 + 1) % kGvSlots][2 + w][4 * lane], M)
+                                  : ghost4(fzp, j * nx + i0, c);
+        zm1 = own_direct(k0 - 1);
+        zm2 = own_direct(k0 - 2);
+    }
+    put_rows(k0, c);
+#pragma unroll 1
+    for (int k = k0; k < k1; ++k) {
+        if (k + 3 <= k1 + 1) stage(k + 3);
+        cpa_commit_group();
+        cpa_wait_but_one();                           // this thread's copies of plane k + 2 have landed
+        __syncthreads();                              // everyone's; the integer rows of plane k are complete
+        const long long at = (long long)k * plane + idx0;
+        I4 zp2 = {0, 0, 0, 0};
+        if (act) {
+            if (k + 2 < nz || pz) zp2 = fx_row_smem(&S.raw[(k + 2) % kGvSlots][2 + w][4 * lane], M);
+            else zp2 = ghost4(fzp, j * nx + i0, k + 2 == nz ? zp1 : zm1);   // mirrors of planes nz, nz + 1
+        }
+        const long long l1 = __shfl_up_sync(0xffffffffu, c.w, 1), l2 = __shfl_up_sync(0xffffffffu, c.z, 1);
+        const long long r1 = __shfl_down_sync(0xffffffffu, c.x, 1), r2 = __shfl_down_sync(0xffffffffu, c.y, 1);
+        if (act) {
+            const long long(*ir)[kFxTW + 4] = S.irow[k & 1];
+            long long X[8] = {l2, l1, c.x, c.y, c.z, c.w, r1, r2};        // cells i0 - 2 .. i0 + 5
+            if (lane == 0) {
+                if (i0 > 0) {
+                    X[0] = ir[w + 2][kFxTW];
+                    X[1] = ir[w + 2][kFxTW + 1];
+                } else if (px) {
+                    X[0] = fx_from(u[at + nx - 2], M);
+                    X[1] = fx_from(u[at + nx - 1], M);
+                } else {
+                    X[0] = ghost1(fxm, k * ny + j, c.y);
+                    X[1] = ghost1(fxm, k * ny + j, c.x);
+                }
+            }
+            if (i0 + 4 >= nx) {
+                if (px) {
+                    X[6] = fx_from(u[at + 4 - nx], M);
+                    X[7] = fx_from(u[at + 5 - nx], M);
+                } else {
+                    X[6] = ghost1(fxp, k * ny + j, c.w);
+                    X[7] = ghost1(fxp, k * ny + j, c.z);
+                }
+            } else if (lane == BX - 1) {
+                X[6] = ir[w + 2][kFxTW + 2];
+                X[7] = ir[w + 2][kFxTW + 3];
+            }
+            // rows j - 2, j - 1, j + 1, j + 2
+            I4 Y[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int d = e < 2 ? e - 2 : e - 1, r = j + d;
+                if (r >= 0 && r < ny) {
+                    Y[e] = fx_load_row(&ir[w + 2 + d][4 * lane]);
+                } else if (py) {
+                    Y[e] = fx_row(u + (long long)k * plane + (long long)(r < 0 ? r + ny : r - ny) * nx + i0, M);
+                } else {
+                    const int m = r < 0 ? -1 - r : 2 * ny - 1 - r;             // the mirror row, staged
+                    Y[e] = ghost4(r < 0 ? fym : fyp, k * nx + i0, fx_load_row(&ir[m - j0 + 2][4 * lane]));
+                }
+            }
+            // one component at a time, stored as it is formed
+            const GravFx pv{M};
+            double* o = out + at;
+            *reinterpret_cast<double2*>(o) = make_double2(pv.comp(cx, X[3], X[1], X[4], X[0]),
+                                                          pv.comp(cx, X[4], X[2], X[5], X[1]));
+            *reinterpret_cast<double2*>(o + 2) = make_double2(pv.comp(cx, X[5], X[3], X[6], X[2]),
+                                                              pv.comp(cx, X[6], X[4], X[7], X[3]));
+            o += n;
+            *reinterpret_cast<double2*>(o) = make_double2(pv.comp(cy, Y[2].x, Y[1].x, Y[3].x, Y[0].x),
+                                                          pv.comp(cy, Y[2].y, Y[1].y, Y[3].y, Y[0].y));
+            *reinterpret_cast<double2*>(o + 2) = make_double2(pv.comp(cy, Y[2].z, Y[1].z, Y[3].z, Y[0].z),
+                                                              pv.comp(cy, Y[2].w, Y[1].w, Y[3].w, Y[0].w));
+            o += n;
+            *reinterpret_cast<double2*>(o) = make_double2(pv.comp(cz, zp1.x, zm1.x, zp2.x, zm2.x),
+                                                          pv.comp(cz, zp1.y, zm1.y, zp2.y, zm2.y));
+            *reinterpret_cast<double2*>(o + 2) = make_double2(pv.comp(cz, zp1.z, zm1.z, zp2.z, zm2.z),
+                                                              pv.comp(cz, zp1.w, zm1.w, zp2.w, zm2.w));
+        }
+        if (k + 1 < k1) put_rows(k + 1, zp1);
+        zm2 = zm1;
+        zm1 = c;
+        c = zp1;
+        zp1 = zp2;
+    }
+    cpa_wait_none();
+}
+
 // ---------------------------------------------------------------------------
 // Small helpers.
 // ---------------------------------------------------------------------------
@@ -2021,7 +2252,21 @@ cudaError_t launch_gravity(const LevelGeom& g, const double* phi, double* out, c
                                                                                                           scratch);
         mexp = scratch;
     }
-    k_gravity_stream<<<grid, block, 0, st>>>(g, phi, out, c[0], c[1], c[2], kc, mexp);
+    if (mexp && (g.nx & 3) == 0 && (reinterpret_cast<uintptr_t>(out) & 15) == 0) {
+        // 4-cell strips, planes staged in shared memory: about three waves of
+        // two CTAs per SM, whole z chunks
+        const long long gx = (g.nx / 4 + BX - 1) / BX, gy = (g.ny + BY - 1) / BY;
+        const long long want = 6 * sm_count();
+        const long long chunks = std::min<long long>(g.nz, std::max(1LL, (want + gx * gy - 1) / (gx * gy)));
+        const int kz = (int)((g.nz + chunks - 1) / chunks);
+        dim3 sgrid((unsigned)gx, (unsigned)gy, (unsigned)((g.nz + kz - 1) / kz));
+        cudaError_t e = cudaFuncSetAttribute(k_gravity_fx4, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)sizeof(GvSmem));
+        if (e != cudaSuccess) return e;
+        k_gravity_fx4<<<sgrid, block, sizeof(GvSmem), st>>>(g, phi, out, c[0], c[1], c[2], kz, mexp);
+    } else {
+        k_gravity_stream<<<grid, block, 0, st>>>(g, phi, out, c[0], c[1], c[2], kc, mexp);
+    }
     if (nkernels) *nkernels = mexp ? 2 : 1;
     return cudaGetLastError();
 }

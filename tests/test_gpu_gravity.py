@@ -26,9 +26,17 @@ pytestmark = pytest.mark.gpu
 TOL = 1e-12
 LO, HI = (0.0, -0.5, 0.25), (1.3, 0.2, 1.35)
 
+# nx % 4 == 0 takes the 4-cell strip kernel (tiles of 128 x 8 cells): ragged
+# rows (ny = 12, 10, 17, 9: a last tile of 4, 2, 1, 1 rows), two x tiles with a
+# ragged second (132 cells: one strip) or two full ones (256), one strip
+# (nx = 4, both x walls in one lane), two planes on a Dirichlet z axis, every
+# boundary kind at a tile edge and a level edge; the other shapes the one
+# cell per thread kernel
 SHAPES_BC = [((20, 12, 36), (0, 0, 0)), ((16, 24, 8), (1, 1, 1)), ((12, 20, 40), (1, 0, 1)),
              ((9, 37, 13), (0, 1, 0)), ((2, 6, 5), (0, 0, 1)), ((7, 2, 3), (1, 1, 0)),
-             ((40, 19, 70), (0, 0, 0)), ((33, 17, 66), (1, 0, 1))]
+             ((40, 19, 70), (0, 0, 0)), ((33, 17, 66), (1, 0, 1)),
+             ((6, 10, 132), (1, 1, 0)), ((5, 17, 4), (0, 1, 0)), ((3, 9, 256), (0, 0, 1)), ((2, 8, 12), (0, 0, 0)),
+             ((4, 9, 132), (0, 0, 0))]
 
 
 def _sg():
@@ -161,7 +169,8 @@ def _exact_gravity(phi, h, bc, faces):
     return out, mag
 
 
-@pytest.mark.parametrize("shape,bc", [((10, 12, 16), (0, 0, 0)), ((8, 9, 12), (1, 0, 1))])
+@pytest.mark.parametrize("shape,bc", [((10, 12, 16), (0, 0, 0)), ((8, 9, 12), (1, 0, 1)), ((5, 17, 4), (0, 1, 0)),
+                                      ((2, 9, 136), (0, 0, 1)), ((9, 6, 10), (0, 0, 0))])
 def test_gravity_fixed_point_within_its_error_bound(shape, bc):
     # the combination is exact on the level's fixed-point scale (unit
     # 2^(M - 1079), M the largest biased exponent of phi and, one above, of the
