@@ -13,7 +13,7 @@ Workload (one "step" = one complete solve through the library's public API):
 
 Metric: solves/s (whole job; N ranks solve independent instances: weak
 scaling, no collective).  The K timed steps are independent solves of the
-workload, three in flight at a time: one grid per CUDA stream, each driven by
+workload, four in flight at a time: one grid per CUDA stream, each driven by
 its own host thread, so that the solves fill each other's idle SMs; value =
 K / the device time from the first launch to the last completion.  Inputs
 (256^3 x 8 B = 134 MB per array, working set about 1 GB per solve) are larger
@@ -21,7 +21,7 @@ than the 129 MB L2.  The line also reports one solve at a time (`sequential`:
 L2 flushed by a 512 MB write before each solve, CUDA events per solve).
 
 End to end (`e2e`): the density comes from pinned host memory and the
-potential goes back to it through the C ABI every step, the same three grids
+potential goes back to it through the C ABI every step, the same four grids
 in flight (one grid's copies, by the copy engines, overlap the others'
 solves); the strictly sequential figure (copy in, solve, copy out) beside it.
 
@@ -57,7 +57,7 @@ TOL = 1e-8
 # 3, 2 on the levels between it and the two coarsest: the fastest measured RKL2
 # setting on this workload whose s is odd (6 V-cycles).
 # independent solves in flight: one grid per CUDA stream, one host thread each
-INFLIGHT = 3
+INFLIGHT = 4
 SOLVER = dict(rkl_order=2, s_smooth=3, tau_frac=0.9, n_pre=5, n_post=3, inner_n_pre=3, inner_n_post=2,
               coarse_tol=1e-2, coarse_max_ss=64)
 METRIC = "Poisson solves/s to rel. residual 1e-8 at 256^3"
