@@ -65,6 +65,16 @@ def test_default_options(sg):
     assert (o.rkl_order, o.s_smooth, o.n_pre, o.n_post) == (2, 3, 2, 1)
     assert o.tau_frac == 1.0 and o.use_graph == 1 and o.coarse_tol == 1e-2
     assert (o.smoother, o.omega, o.max_residual_tol) == (0, 1.0, 0.0)
+    assert (o.staging, o.host_copy) == (sg.STAGINGS["cp_async"], sg.HOST_COPIES["engine"])
+
+
+def test_option_enums_match_header(sg):
+    text = open(HEADER).read()
+    for names in ({"cp_async": "SG_STAGE_CP_ASYNC", "tma": "SG_STAGE_TMA"},
+                  {"engine": "SG_HOST_COPY_ENGINE", "kernel": "SG_HOST_COPY_KERNEL"}):
+        table = sg.STAGINGS if "tma" in names else sg.HOST_COPIES
+        for key, name in names.items():
+            assert re.search(rf"{name}\s*=\s*{table[key]}\b", text), name
 
 
 @pytest.mark.parametrize("shape,lo,hi,bc,prec", [
@@ -92,6 +102,7 @@ def test_null_arguments_rejected(sg):
     assert L.sg_set_density(None, None, 0, 1.0) == 1
     assert L.sg_gravity(None, None, None, 0) == 1
     assert L.sg_op_gsrb_sweep(None, 0, 0, 0, 1.0, None, None) == 1
+    assert L.sg_op_residual_exact(None, 0, None, None, None, None, None) == 1
     L.sg_destroy(None)
 
 
