@@ -32,6 +32,8 @@
 
 #include <cooperative_groups.h>
 
+#include <mutex>
+
 namespace cg = cooperative_groups;
 
 namespace sg {
@@ -479,10 +481,12 @@ constexpr int kPlanCache = 64;
 BottomPlan g_plans[kPlanCache];
 int g_nplans = 0;
 bool g_bottom_configured = false;
+std::mutex g_plans_mu;          // the cache and the one-time configuration, for callers on several threads
 
 }  // namespace
 
 cudaError_t bottom_configure() {
+    std::lock_guard<std::mutex> lock(g_plans_mu);
     if (g_bottom_configured) return cudaSuccess;
     cudaError_t e = cudaFuncSetAttribute(k_bottom_levels, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)kSmemLimit);
@@ -500,6 +504,7 @@ cudaError_t bottom_configure() {
 // memory and one cluster of that size schedulable; 0 if none.
 int bottom_plan(int nx, int ny, int nz, int s, int* threads, size_t* bytes) {
     if (s < 1 || s > kBottomMaxS || nx * ny > 1024 || nx % 2 || ny % 2 || nz % 2 || nx < 2 || ny < 2) return 0;
+    std::lock_guard<std::mutex> lock(g_plans_mu);
     for (int k = 0; k < g_nplans; ++k)
         if (g_plans[k].nx == nx && g_plans[k].ny == ny && g_plans[k].nz == nz) {
             *threads = g_plans[k].threads;

@@ -1471,9 +1471,15 @@ namespace {
 sg_status create_grid(int nx, int ny, int nz, const double lo[3], const double hi[3], const int bc[3],
                       int precision, void* cuda_stream, sg_grid** out, bool twod) {
     const int n[3] = {nx, ny, nz};
-    SG_CK(coarse_configure());
-    SG_CK(fused_configure());
-    SG_CK(bottom_configure());
+    {
+        // one-time kernel attributes and occupancy figures, set by whichever
+        // thread creates a grid first
+        static std::mutex configure_mu;
+        std::lock_guard<std::mutex> lock(configure_mu);
+        SG_CK(coarse_configure());
+        SG_CK(fused_configure());
+        SG_CK(bottom_configure());
+    }
     sg_grid* g = new sg_grid();
     static std::atomic<unsigned long long> serials{0};
     g->serial = ++serials;

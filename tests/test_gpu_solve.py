@@ -443,3 +443,37 @@ def test_pinned_host_buffers_move_over_the_link_bit_exactly(shape):
         assert np.array_equal(out[kind][0], out["pageable"][0])
         assert np.array_equal(out[kind][1], out["pageable"][1])
     assert np.abs(out["pinned"][0]).max() > 0
+
+
+def test_grids_solved_from_several_threads_match_one_at_a_time():
+    # independent grids, each created on its own stream and driven by its own
+    # host thread (the library's calls release the interpreter lock; shapes
+    # whose plans no other test made, so the threads fill the plan cache), give
+    # the same bits as the same solves one at a time
+    import threading
+    sg = _sg()
+    shapes = [(40, 48, 36), (56, 40, 44), (36, 52, 60), (44, 36, 52)]
+    rng = np.random.default_rng(31)
+    rhos = [rng.standard_normal(s) for s in shapes]
+
+    def run(i, out):
+        st = torch.cuda.Stream()
+        g = sg.Grid(shapes[i], (0.0, 0.0, 0.0), (1.0, 1.0, 1.0), (0, 0, 0), precision="mixed",
+                    stream=st.cuda_stream)
+        g.set_options(rkl_order=2, s_smooth=3, n_pre=5, n_post=3)
+        g.set_density(rhos[i], 1.0)
+        info = g.solve(tol=1e-9)
+        out[i] = (g.potential(), info["cycles"], info["rel_residual"])
+
+    together = {}
+    threads = [threading.Thread(target=run, args=(i, together)) for i in range(len(shapes))]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    alone = {}
+    for i in range(len(shapes)):
+        run(i, alone)
+    for i in range(len(shapes)):
+        assert together[i][1] == alone[i][1] and together[i][2] <= 1e-9
+        assert np.array_equal(together[i][0], alone[i][0])
