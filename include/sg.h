@@ -18,11 +18,11 @@
  *           [nz][ny], the y faces [nz][nx], the z faces [ny][nx], sampled at the
  *           centres of the boundary faces.  Unset faces are zero.
  * Memory.   `on_device = 1`: the pointer is CUDA device memory on the grid's
- *           device; `on_device = 0`: host memory (pageable or pinned).  Pinned
- *           host memory mapped into the device address space (cudaHostAlloc,
- *           cudaHostRegister) is read or written by the library's kernels over
- *           the CPU-GPU link, pageable memory by copy-engine transfers; a host
- *           buffer must hold the whole array.  Caller
+ *           device; `on_device = 0`: host memory (pageable or pinned), moved
+ *           by copy-engine transfers (with the option host_copy =
+ *           SG_HOST_COPY_KERNEL, pinned memory mapped into the device address
+ *           space is read or written by the library's kernels over the CPU-GPU
+ *           link instead); a host buffer must hold the whole array.  Caller
  *           buffers are borrowed for the duration of the call only.  All work is
  *           ordered on the CUDA stream given to sg_create_grid; calls that
  *           return data to a host pointer synchronise that stream, calls that
@@ -34,7 +34,11 @@
  *           the ABI.  On an error the output buffers are left untouched unless
  *           stated otherwise, and sg_last_error() returns a message (thread
  *           local, valid until the next call on the same thread).
- * Threads.  A grid may be used by one host thread at a time.
+ * Threads.  A grid may be used by one host thread at a time.  Different
+ *           grids may be created and used from different host threads at the
+ *           same time, each on its own stream (the library's one-time setup
+ *           and plan caches are locked); their solves then share the device
+ *           (sg_residual_restrict_noalloc excepted: see its note).
  */
 #ifndef SG_H
 #define SG_H
