@@ -228,3 +228,20 @@ def test_mixed_solve_confirmation_matches_oracle_residual():
                                                                                    p.faces))
     assert info["rel_residual"] <= 1e-9
     assert abs(info["rel_residual"] - rel) <= 1e-3 * rel
+
+
+@pytest.mark.parametrize("scale", [1e-300, 1e300])
+@pytest.mark.parametrize("shape,bc", [((8, 12, 16), (0, 0, 0)), ((6, 10, 20), (1, 0, 1))])
+def test_exact_residual_far_magnitudes_take_the_fp64_stencil(shape, bc, scale):
+    # values beyond 2^-900 .. 2^900 are outside the fixed-point scale's range:
+    # the kernel computes those levels in FP64, within FP64 evaluation error
+    g, h, faces = make_grid(shape, bc, True)
+    if faces is not None:
+        faces = [scale * fc for fc in faces]
+        g.set_boundary(faces)
+    u = scale * W.random_field(shape, 68)
+    f = scale * W.random_field(shape, 69)
+    r64, r32, _, _ = run(g, u, f)
+    ref = -O.residual(u, f, h, bc, faces)
+    assert np.all(np.isfinite(r64))
+    assert np.max(np.abs(r64 - ref)) <= 1e-12 * np.max(np.abs(ref))

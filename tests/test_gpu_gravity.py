@@ -199,3 +199,40 @@ def test_gravity_fixed_point_within_its_error_bound(shape, bc):
         bound = c * 36.0 * unit + 2.0 ** -52 * (c * mag[idx] + abs(float(ex)))
         worst = max(worst, float(abs(Fraction(float(got[idx])) - ex)) / bound)
     assert worst <= 1.0, worst
+
+
+@pytest.mark.parametrize("scale", [1e-300, 1e300])
+@pytest.mark.parametrize("shape,bc", [((8, 12, 16), (0, 0, 0)), ((6, 10, 20), (1, 0, 1)), ((7, 9, 13), (0, 1, 0))])
+def test_gravity_far_magnitudes_take_fp64_arithmetic(shape, bc, scale):
+    # potentials beyond 2^-900 .. 2^900 fall outside the fixed-point scale:
+    # both kernels (strips for nx % 4 == 0, one thread per cell otherwise)
+    # then compute in FP64
+    g, h, _ = make_grid(shape, bc, faces=False)
+    fc = None
+    if any(b == 0 for b in bc):
+        fc = [scale * f for f in W.random_faces(shape, 5)]
+        g.set_boundary(fc)
+    phi = scale * W.random_field(shape, 9)
+    out = torch.empty((3,) + shape, dtype=torch.float64, device="cuda")
+    g.gravity(out=out, phi=torch.tensor(phi, device="cuda"))
+    torch.cuda.synchronize()
+    ref = O.gravity(phi, h, bc, fc)
+    assert torch.isfinite(out).all()
+    assert relerr(out, ref) < TOL
+
+
+def test_gravity_not_finite_potential_stays_local():
+    # a non-finite value makes the scale unusable (FP64 arithmetic); cells whose
+    # stencil does not reach it keep their values
+    shape, bc = (8, 12, 16), (0, 0, 0)
+    g, h, fc = make_grid(shape, bc)
+    phi = W.random_field(shape, 10)
+    phi[4, 6, 8] = np.inf
+    out = torch.empty((3,) + shape, dtype=torch.float64, device="cuda")
+    g.gravity(out=out, phi=torch.tensor(phi, device="cuda"))
+    torch.cuda.synchronize()
+    got = out.cpu().numpy()
+    assert not np.isfinite(got[0, 4, 6, 7])
+    phi0 = np.where(np.isfinite(phi), phi, 0.0)
+    ref = O.gravity(phi0, h, bc, fc)
+    assert abs(got[0, 0, 0, 0] - ref[0, 0, 0, 0]) <= 1e-12 * np.max(np.abs(ref))
