@@ -162,7 +162,7 @@ def throughput(world, steps, max_total_ms):
 
 def config(world):
     return {"workload": f"sphere{N}", "grid": [N, N, N], "levels": LEVELS, "tol": TOL,
-            "precision": "mixed (FP32 V-cycle; FP64 residual carried by exact recurrence, confirmed in FP64 at the end; FP64 defect correction)",
+            "precision": "mixed (FP32 V-cycle; FP64 residual carried by exact recurrence, confirmed at the end by an FP64 residual whose stencil sum is exact in 64-bit fixed point; FP64 defect correction)",
             "smoother": "RKL2 s=3 tau=0.9 tau_max, N_pre=5, N_post=3 (levels 1-2: 3, 2)",
             "coarse": "accelerated RKL1 on 16^3, coarse_tol=1e-2",
             "boundary": "Dirichlet from analytic sphere potential",
